@@ -1,0 +1,303 @@
+"""Seeded synthetic inputs for the SACRA-2D hot path.
+
+This module only builds inputs: run configurations, initial data (the
+special-relativistic shock tube, TOV stars from a plain ODE solve, smooth
+random perturbations) and random states.  It holds none of the method's
+arithmetic, so both the CUDA path and the CPU oracle take their inputs from
+here without sharing any of the method's code.
+
+Units: G = c = M_sun = 1.  Level arrays are padded with 8 cells on every side:
+a plane has shape (nz + 16, nx + 16) and cell (j, k) (interior j, k in
+[1, n]) sits at [k + 7, j + 7], its centre at x = (j - 1/2) dx,
+z = (k - 1/2) dz.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+G = 8
+NMET = 25
+# metric field order: W, h_ij (xx,xy,xz,yy,yz,zz), At_ij, Khat, Gt^i, Theta, alpha, beta^i, B^i
+MET_NAMES = ["W", "hxx", "hxy", "hxz", "hyy", "hyz", "hzz", "Axx", "Axy", "Axz", "Ayy", "Ayz", "Azz",
+             "Khat", "Gx", "Gy", "Gz", "Theta", "alpha", "betax", "betay", "betaz", "Bx", "By", "Bz"]
+CONS_NAMES = ["qD", "qSx", "qSy", "qSz", "qE"]
+PRIM_NAMES = ["rho", "ux", "uy", "uz", "P", "eps"]
+
+
+@dataclasses.dataclass
+class RunConfig:
+    name: str = "custom"
+    n_levels: int = 1
+    nx: int = 64
+    nz: int = 64
+    geometry: int = 1          # 0 planar slab, 1 cylindrical (cartoon)
+    evolve_spacetime: int = 1
+    solver: int = 0            # 0 HLLC (TVDLF fallback), 1 TVDLF
+    rk: int = 0                # 0 classical RK4, 1 SSP-RK3
+    c2p_maxit: int = 100
+    dx0: float = 1.0
+    dz0: float = 1.0
+    kappa: float = 0.0
+    eta_B: float = 1.0
+    eps_ko: float = 0.5
+    r_z4: float = 1e300
+    K: float = 100.0
+    Gamma: float = 2.0
+    Gamma_th: float = 2.0
+    rho_atm: float = 1e-13
+    w_max: float = 100.0
+    c2p_tol: float = 1e-12
+    cfl: float = 0.5
+    mass: float = 1.0          # total mass M used for kappa and eta_B
+
+    @property
+    def px(self):
+        return self.nx + 2 * G
+
+    @property
+    def pz(self):
+        return self.nz + 2 * G
+
+    @property
+    def n_stages(self):
+        return 4 if self.rk == 0 else 3
+
+    def dx(self, level):
+        return self.dx0 / (1 << level)
+
+    def dz(self, level):
+        return self.dz0 / (1 << level)
+
+    @property
+    def dt(self):
+        f = self.n_levels - 1
+        return self.cfl * min(self.dx(f), self.dz(f))
+
+    @property
+    def interior_cells(self):
+        return self.n_levels * self.nx * self.nz
+
+
+def cell_centres(cfg: RunConfig, level: int):
+    j = np.arange(1 - G, cfg.nx + G + 1)
+    k = np.arange(1 - G, cfg.nz + G + 1)
+    x = (j - 0.5) * cfg.dx(level)
+    z = (k - 0.5) * cfg.dz(level)
+    return np.meshgrid(x, z)  # (pz, px)
+
+
+def flat_metric(cfg: RunConfig):
+    m = np.zeros((NMET, cfg.pz, cfg.px))
+    m[0] = 1.0     # W
+    m[18] = 1.0    # alpha
+    return m
+
+
+# ------------------------------------------------------------------ shock tube
+
+def shock_tube_config(nx=400, nz=4, solver=0, rk=0, cfl=0.4) -> RunConfig:
+    """Special-relativistic shock tube on [0, 1], Gamma-law Gamma = 5/3 (K = 0),
+    flat metric frozen, outflow boundaries (Marti & Mueller problem 1 with the
+    pressures 13.33 | 1e-6 of the benchmark configuration)."""
+    dx = 1.0 / nx
+    return RunConfig(name="shock_tube_%dx%d" % (nx, nz), n_levels=1, nx=nx, nz=nz, geometry=0, evolve_spacetime=0,
+                     solver=solver, rk=rk, dx0=dx, dz0=dx, K=0.0, Gamma=5.0 / 3.0, Gamma_th=5.0 / 3.0,
+                     rho_atm=1e-10, cfl=cfl)
+
+
+def shock_tube_data(cfg: RunConfig, left=(10.0, 13.33, 0.0), right=(1.0, 1e-6, 0.0), x0=0.5):
+    """Kind-0 level data: 25 metric planes + (rho, u_x, u_y, u_z, P)."""
+    X, Z = cell_centres(cfg, 0)
+    d = np.zeros((30, cfg.pz, cfg.px))
+    d[:NMET] = flat_metric(cfg)
+    L = X < x0
+    rho = np.where(L, left[0], right[0])
+    P = np.where(L, left[1], right[1])
+    v = np.where(L, left[2], right[2])
+    d[25] = rho
+    d[26] = v / np.sqrt(1.0 - v * v)   # u_x = w v on the flat metric
+    d[29] = P
+    return d
+
+
+# ------------------------------------------------------------------ TOV stars
+
+@dataclasses.dataclass
+class TOVSolution:
+    K: float
+    Gamma: float
+    rho_c: float
+    M: float            # gravitational mass
+    Mb: float           # baryon mass
+    R_areal: float
+    r_iso: float        # isotropic surface radius
+    r: np.ndarray       # isotropic radius table (inside)
+    rho: np.ndarray
+    P: np.ndarray
+    psi: np.ndarray
+
+
+def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
+    """Tolman-Oppenheimer-Volkoff equilibrium of P = K rho^Gamma by classical
+    RK4 in the areal radius R, with the isotropic radius r(R) integrated
+    alongside and matched to exterior Schwarzschild at the surface."""
+    def eos_e(P):
+        if P <= 0.0:
+            return 0.0, 0.0
+        rho = (P / K) ** (1.0 / Gamma)
+        return rho, rho + P / (Gamma - 1.0)
+
+    def rhs(R, y):
+        m, P, lnr, mb = y
+        rho, e = eos_e(P)
+        if P <= 0.0:
+            return np.array([0.0, 0.0, 1.0 / (R * math.sqrt(1.0 - 2.0 * m / R)), 0.0])
+        dm = 4.0 * math.pi * R * R * e
+        dP = -(e + P) * (m + 4.0 * math.pi * R ** 3 * P) / (R * (R - 2.0 * m))
+        dlnr = 1.0 / (R * math.sqrt(1.0 - 2.0 * m / R))
+        dmb = 4.0 * math.pi * R * R * rho / math.sqrt(1.0 - 2.0 * m / R)
+        return np.array([dm, dP, dlnr, dmb])
+
+    Pc = K * rho_c ** Gamma
+    ec = rho_c + Pc / (Gamma - 1.0)
+    R = dR * 1e-3
+    y = np.array([4.0 / 3.0 * math.pi * R ** 3 * ec, Pc, math.log(R), 4.0 / 3.0 * math.pi * R ** 3 * rho_c])
+    Rs, Ys = [R], [y.copy()]
+    h = dR
+    while True:
+        k1 = rhs(R, y)
+        k2 = rhs(R + h / 2, y + h / 2 * k1)
+        k3 = rhs(R + h / 2, y + h / 2 * k2)
+        k4 = rhs(R + h, y + h * k3)
+        yn = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        if yn[1] <= 0.0:
+            if h < 1e-10:
+                break
+            h *= 0.5
+            continue
+        R += h
+        y = yn
+        Rs.append(R)
+        Ys.append(y.copy())
+        if y[1] < 1e-14 * Pc:
+            break
+    Rs = np.array(Rs)
+    Ys = np.array(Ys)
+    M = Ys[-1, 0]
+    Rsurf = Rs[-1]
+    rsurf = 0.5 * (Rsurf - M + math.sqrt(Rsurf * Rsurf - 2.0 * M * Rsurf))
+    lnr = Ys[:, 2] - Ys[-1, 2] + math.log(rsurf)
+    r = np.exp(lnr)
+    P = np.maximum(Ys[:, 1], 0.0)
+    rho = (P / K) ** (1.0 / Gamma)
+    psi = np.sqrt(Rs / r)
+    return TOVSolution(K=K, Gamma=Gamma, rho_c=rho_c, M=M, Mb=Ys[-1, 3], R_areal=Rsurf, r_iso=rsurf,
+                       r=r, rho=rho, P=P, psi=psi)
+
+
+def tov_config(name, rho_c=1.28e-3, n_levels=3, N=256, dx_fine=0.25, rk=1, solver=0, f_atm=1e-10,
+               K=100.0, Gamma=2.0, Gamma_th=2.0, tov: TOVSolution | None = None) -> tuple[RunConfig, TOVSolution]:
+    if tov is None:
+        tov = tov_solve(K, Gamma, rho_c)
+    dx0 = dx_fine * (1 << (n_levels - 1))
+    xmax = dx0 * N
+    cfg = RunConfig(name=name, n_levels=n_levels, nx=N, nz=N, geometry=1, evolve_spacetime=1, solver=solver,
+                    rk=rk, dx0=dx0, dz0=dx0, kappa=5e-3 / tov.M, eta_B=1.0 / tov.M, eps_ko=0.5, r_z4=xmax / 6.0,
+                    K=K, Gamma=Gamma, Gamma_th=Gamma_th, rho_atm=f_atm * rho_c, cfl=0.5, mass=tov.M)
+    return cfg, tov
+
+
+def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0):
+    """Kind-0 level data of a TOV star: W = psi^-2, alpha = psi^-2, h = At =
+    Khat = Theta = Gt = beta = B = 0, fluid at rest; atmosphere outside.  A
+    pressure depletion factor lowers P on the cold curve (rho scaled so that
+    P = K rho^Gamma still holds)."""
+    X, Z = cell_centres(cfg, level)
+    r = np.sqrt(X * X + Z * Z)
+    inside = r < tov.r_iso
+    rho = np.where(inside, np.interp(r, tov.r, tov.rho), 0.0)
+    psi = np.where(inside, np.interp(r, tov.r, tov.psi), 1.0 + tov.M / (2.0 * np.maximum(r, 1e-300)))
+    rho_atm = cfg.rho_atm
+    if p_deplete != 1.0:
+        rho = rho * p_deplete ** (1.0 / cfg.Gamma)
+    rho = np.maximum(rho, rho_atm)
+    P = cfg.K * rho ** cfg.Gamma
+    d = np.zeros((30, cfg.pz, cfg.px))
+    d[0] = psi ** -2
+    d[18] = psi ** -2
+    d[25] = rho
+    d[29] = P
+    return d
+
+
+# ------------------------------------------------------------------ configurations
+
+def config_shock_tube():
+    """Special-relativistic shock tube, 400 x 4 cells, HLLC, CFL 0.4."""
+    return shock_tube_config(400, 4, solver=0, rk=0, cfl=0.4)
+
+
+def config_tov_stable():
+    """Stable TOV star K=100, Gamma=2, rho_c=1.28e-3, 3 levels of 256^2, finest dx 0.25, SSP-RK3."""
+    return tov_config("tov_stable_3x256", rho_c=1.28e-3, n_levels=3, N=256, dx_fine=0.25, rk=1)
+
+
+def config_migration(N=512, n_levels=5, dx_fine=0.1):
+    """Unstable TOV (rho_c = 7.993e-3) with a 1% pressure depletion, 5 levels of 512^2, finest dx 0.1, RK4."""
+    return tov_config("migration_5x512", rho_c=7.993e-3, n_levels=n_levels, N=N, dx_fine=dx_fine, rk=0)
+
+
+# ------------------------------------------------------------------ random inputs
+
+def random_metric_perturbation(cfg: RunConfig, level: int, rng: np.random.Generator, amp=1e-2, nbump=3):
+    """Smooth axisymmetric-consistent perturbation of every metric field: a sum
+    of Gaussian bumps in (x, z), each field with the parity (odd/even in x and
+    z) it has on the cartoon plane, so that ghost fills reproduce it."""
+    X, Z = cell_centres(cfg, level)
+    L = max(cfg.nx * cfg.dx(level), cfg.nz * cfg.dz(level))
+    odd_x = {3, 5, 9, 11, 14, 15, 19, 20, 22, 23}   # hxz hyz Axz Ayz Gx Gy betax betay Bx By
+    odd_z = {3, 5, 9, 11, 16, 21, 24}               # hxz hyz Axz Ayz Gz betaz Bz
+    out = np.zeros((NMET, cfg.pz, cfg.px))
+    for f in range(NMET):
+        acc = np.zeros_like(X)
+        for _ in range(nbump):
+            x0, z0 = rng.uniform(0.1, 0.6, 2) * L
+            s = rng.uniform(0.15, 0.3) * L
+            a = rng.uniform(-1, 1)
+            base = np.zeros_like(X)
+            for sx in (1, -1):
+                for sz in (1, -1):
+                    px_ = sx if f in odd_x else 1
+                    pz_ = sz if f in odd_z else 1
+                    base += px_ * pz_ * np.exp(-((X - sx * x0) ** 2 + (Z - sz * z0) ** 2) / (s * s))
+            acc += a * base
+        out[f] = amp * acc
+    return out
+
+
+def random_prims(rng: np.random.Generator, n, w_max=50.0, log_rho=(-10.0, -2.0)):
+    """n random primitive states (rho, u_x, u_y, u_z, P-factor) with Lorentz
+    factors up to w_max and densities over the given decades."""
+    rho = 10.0 ** rng.uniform(*log_rho, n)
+    w = 1.0 + (w_max - 1.0) * rng.uniform(0, 1, n) ** 3
+    dirs = rng.normal(size=(n, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    u = dirs * np.sqrt(w * w - 1.0)[:, None]
+    pfac = 10.0 ** rng.uniform(-3, 1, n)
+    return rho, u, pfac
+
+
+def random_conformal_metric(rng: np.random.Generator, amp=0.1):
+    """A random symmetric positive-definite gt_ij with det gt = 1 (the algebraic
+    constraint the evolution keeps), returned as h_ij = gt_ij - delta_ij in the
+    order (xx,xy,xz,yy,yz,zz), and a conformal factor W."""
+    a = rng.uniform(-amp, amp, 6)
+    a[0] = abs(a[0]); a[3] = abs(a[3]); a[5] = abs(a[5])
+    g = np.array([[1 + a[0], a[1], a[2]], [a[1], 1 + a[3], a[4]], [a[2], a[4], 1 + a[5]]])
+    g = g * np.linalg.det(g) ** (-1.0 / 3.0)
+    h = np.array([g[0, 0] - 1, g[0, 1], g[0, 2], g[1, 1] - 1, g[1, 2], g[2, 2] - 1])
+    W = rng.uniform(0.6, 1.0)
+    return W, h
