@@ -100,6 +100,8 @@ def lib():
             L.orc_read.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, _dp]
             L.orc_diag.argtypes = [C.c_void_p, _dp]
             L.orc_fallbacks.argtypes = [C.c_void_p]
+            L.orc_derivs_batch.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           _dp, _dp, _dp]
             L.orc_stencil_init.argtypes = []
             L.orc_fd_weights.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp]
             L.orc_lagrange.argtypes = [C.c_int, _dp, C.c_double, _dp]
@@ -297,6 +299,18 @@ class Oracle:
         out = np.zeros(8)
         self._L.orc_diag(self._c, _ptr(out))
         return out
+
+    def derivs(self, level, js, ks):
+        """Derivatives of all metric fields of the step-start state at cells
+        (js[i], ks[i]): (dQ[n,25,3], ddQ[n,25,6] in xx,xy,xz,yy,yz,zz, adv[n,25])."""
+        js = np.ascontiguousarray(js, dtype=np.int32)
+        ks = np.ascontiguousarray(ks, dtype=np.int32)
+        n = len(js)
+        dQ = np.zeros((n, NMET, 3)); ddQ = np.zeros((n, NMET, 6)); adv = np.zeros((n, NMET))
+        ip = C.POINTER(C.c_int)
+        self._L.orc_derivs_batch(self._c, level, n, js.ctypes.data_as(ip), ks.ctypes.data_as(ip),
+                                 _ptr(dQ), _ptr(ddQ), _ptr(adv))
+        return dQ, ddQ, adv
 
     def fallbacks(self):
         return self._L.orc_fallbacks(self._c)

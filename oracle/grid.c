@@ -304,6 +304,10 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
       face_prims(L, j, k, 1, pl, prr);
       face_metric(L, U, j, k, 1, &al, be, &W, h);
       c->n_fallback += orc_riemann_flux(p, 1, pl, prr, al, be, W, h, f);
+      /* equatorial mirror face: D, S_x, S_phi and E are even in z, so their
+         z-fluxes vanish on the symmetry plane (only the pressure term of the
+         S_z flux remains); the solver reproduces this only up to rounding */
+      if (cyl && k == 0) f[O_QD] = f[O_QSX] = f[O_QSY] = f[O_QE] = 0.0;
       double x = xc(L, j);
       double area = cyl ? x * L->dx : L->dx;
       int id = oidx(L, j, k);
@@ -722,3 +726,25 @@ void orc_step(orc_ctx *c, double dt, int nsteps) {
 }
 
 int orc_fallbacks(const orc_ctx *c) { return c->n_fallback; }
+
+/* Derivatives (central first, second, advection) of every metric field of the
+   step-start state at n cells, with the cartoon y-derivatives; for tests. */
+void orc_derivs_batch(orc_ctx *c, int l, int n, const int *js, const int *ks, double *dQo, double *ddQo, double *advo) {
+  orc_level *L = &c->lv[l];
+  size_t np = (size_t)L->px * L->pz;
+  int cyl = c->p.geometry == 1;
+  double *dy[O_NMET], *dyy[O_NMET];
+  if (cyl) {
+    for (int f = 0; f < O_NMET; ++f) { dy[f] = alloc_arr(np); dyy[f] = alloc_arr(np); }
+    orc_cartoon_dy(c, l, L->un, dy, dyy);
+  }
+  for (int i = 0; i < n; ++i) {
+    double Q[O_NMET], dQ[O_NMET][3], ddQ[O_NMET][6], adv[O_NMET];
+    orc_derivs_cell(c, l, L->un, cyl ? dy : NULL, cyl ? dyy : NULL, js[i], ks[i], Q, dQ, ddQ, adv);
+    memcpy(dQo + (size_t)i * O_NMET * 3, dQ, sizeof(dQ));
+    memcpy(ddQo + (size_t)i * O_NMET * 6, ddQ, sizeof(ddQ));
+    memcpy(advo + (size_t)i * O_NMET, adv, sizeof(adv));
+  }
+  if (cyl)
+    for (int f = 0; f < O_NMET; ++f) { free(dy[f]); free(dyy[f]); }
+}

@@ -138,6 +138,7 @@ class TOVSolution:
     rho: np.ndarray
     P: np.ndarray
     psi: np.ndarray
+    alpha: np.ndarray   # equilibrium lapse on the table (exterior: isotropic Schwarzschild)
 
 
 def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
@@ -151,20 +152,21 @@ def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
         return rho, rho + P / (Gamma - 1.0)
 
     def rhs(R, y):
-        m, P, lnr, mb = y
+        m, P, lnr, mb, nu = y
         rho, e = eos_e(P)
         if P <= 0.0:
-            return np.array([0.0, 0.0, 1.0 / (R * math.sqrt(1.0 - 2.0 * m / R)), 0.0])
+            return np.array([0.0, 0.0, 1.0 / (R * math.sqrt(1.0 - 2.0 * m / R)), 0.0, m / (R * (R - 2.0 * m))])
         dm = 4.0 * math.pi * R * R * e
-        dP = -(e + P) * (m + 4.0 * math.pi * R ** 3 * P) / (R * (R - 2.0 * m))
+        dnu = (m + 4.0 * math.pi * R ** 3 * P) / (R * (R - 2.0 * m))
+        dP = -(e + P) * dnu
         dlnr = 1.0 / (R * math.sqrt(1.0 - 2.0 * m / R))
         dmb = 4.0 * math.pi * R * R * rho / math.sqrt(1.0 - 2.0 * m / R)
-        return np.array([dm, dP, dlnr, dmb])
+        return np.array([dm, dP, dlnr, dmb, dnu])
 
     Pc = K * rho_c ** Gamma
     ec = rho_c + Pc / (Gamma - 1.0)
     R = dR * 1e-3
-    y = np.array([4.0 / 3.0 * math.pi * R ** 3 * ec, Pc, math.log(R), 4.0 / 3.0 * math.pi * R ** 3 * rho_c])
+    y = np.array([4.0 / 3.0 * math.pi * R ** 3 * ec, Pc, math.log(R), 4.0 / 3.0 * math.pi * R ** 3 * rho_c, 0.0])
     Rs, Ys = [R], [y.copy()]
     h = dR
     while True:
@@ -194,8 +196,10 @@ def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
     P = np.maximum(Ys[:, 1], 0.0)
     rho = (P / K) ** (1.0 / Gamma)
     psi = np.sqrt(Rs / r)
+    # lapse e^nu matched to sqrt(1 - 2M/R) at the surface
+    alpha = np.exp(Ys[:, 4] - Ys[-1, 4]) * math.sqrt(1.0 - 2.0 * M / Rsurf)
     return TOVSolution(K=K, Gamma=Gamma, rho_c=rho_c, M=M, Mb=Ys[-1, 3], R_areal=Rsurf, r_iso=rsurf,
-                       r=r, rho=rho, P=P, psi=psi)
+                       r=r, rho=rho, P=P, psi=psi, alpha=alpha)
 
 
 def tov_config(name, rho_c=1.28e-3, n_levels=3, N=256, dx_fine=0.25, rk=1, solver=0, f_atm=1e-10,
@@ -210,7 +214,7 @@ def tov_config(name, rho_c=1.28e-3, n_levels=3, N=256, dx_fine=0.25, rk=1, solve
     return cfg, tov
 
 
-def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0):
+def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0, equilibrium_lapse=False):
     """Kind-0 level data of a TOV star: W = psi^-2, alpha = psi^-2, h = At =
     Khat = Theta = Gt = beta = B = 0, fluid at rest; atmosphere outside.  A
     pressure depletion factor lowers P on the cold curve (rho scaled so that
@@ -228,6 +232,10 @@ def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0):
     d = np.zeros((30, cfg.pz, cfg.px))
     d[0] = psi ** -2
     d[18] = psi ** -2
+    if equilibrium_lapse:
+        rr = np.maximum(r, 1e-300)
+        d[18] = np.where(inside, np.interp(r, tov.r, tov.alpha),
+                         (1.0 - tov.M / (2.0 * rr)) / (1.0 + tov.M / (2.0 * rr)))
     d[25] = rho
     d[29] = P
     return d
