@@ -1,0 +1,158 @@
+/*
+ * sacra2d.h - C ABI of the GB300 (sm_103a) implementation of the SACRA-2D hot
+ * path: one Runge-Kutta stage of BSSN-Z4c + HLLC general-relativistic
+ * hydrodynamics on an axisymmetric (cartoon) fixed-mesh-refinement grid
+ * (Lam & Shibata, "SACRA-2D", arXiv:2502.03223).
+ *
+ * Every entry point returns a sacra_status and never aborts; on failure
+ * sacra_last_error() describes the cause.  Physics failures inside cells
+ * (non-converged primitive recovery, atmosphere resets, HLLC -> TVDLF
+ * fallbacks) are counted, not fatal (see sacra_diag).
+ *
+ * Memory and streams.  The library does all arithmetic in its own CUDA
+ * kernels.  Device memory is one arena owned by the context: the caller may
+ * pass a device buffer of at least sacra_arena_bytes() bytes (for instance a
+ * torch uint8 tensor) or NULL, in which case the library allocates it with
+ * cudaMalloc and frees it in sacra_destroy.  All work is issued on the CUDA
+ * stream given to sacra_init_grid (NULL = legacy default stream).  Host
+ * buffers passed to the library stay owned by the caller; copies to and from
+ * them are complete when the call returns.
+ *
+ * Grid layout (Sec. II.A, Eqs. for Delta x^(l) and x_j^(l)).  L levels of
+ * nx x nz cells; level l has spacing dx0 / 2^l; cell (j, k), j in [1, nx],
+ * k in [1, nz], has centre x_j = (j - 1/2) dx, z_k = (k - 1/2) dz.  Each level
+ * is stored padded with 8 cells on every side (the (4+4) buffer zone of
+ * Sec. II.A): a field plane has pz = nz + 16 rows of px = nx + 16 doubles,
+ * cell (j, k) at index (k + 7) * px + (j + 7), row-major with x fastest.
+ * Level l (l >= 1) covers the parent cells [1, N/2]^2 (box-in-box, anchored
+ * at the axis and the equator, Sec. II.D).
+ *
+ * Field numbering (state planes):
+ *   0 W, 1-6 h_ij (xx,xy,xz,yy,yz,zz; gt_ij = delta_ij + h_ij), 7-12 At_ij,
+ *   13 Khat, 14-16 Gt^i, 17 Theta, 18 alpha, 19-21 beta^i, 22-24 B^i
+ *   (Sec. II.B.1, Eq. bssn and Eq. moving_puncture);
+ *   25 q_D, 26 q_Sx, 27 q_Sy (cylindrical: q_Sphi = x q_Sy), 28 q_Sz, 29 q_E
+ *   (Eq. cons_var, q = psi^6 (D, S_i, E), psi^6 = W^-3).
+ * Primitive planes: 0 rho, 1 u_x, 2 u_y, 3 u_z (covariant), 4 P, 5 eps.
+ */
+#ifndef SACRA2D_H
+#define SACRA2D_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sacra_ctx sacra_ctx;
+
+typedef enum {
+  SACRA_OK = 0,
+  SACRA_ERR_ARG = -1,      /* invalid argument or configuration */
+  SACRA_ERR_CUDA = -2,     /* a CUDA call failed; the message names it */
+  SACRA_ERR_OOM = -3,      /* arena too small or allocation failed */
+  SACRA_ERR_STATE = -4     /* call out of sequence (e.g. no initial data) */
+} sacra_status;
+
+enum { SACRA_PLANAR = 0, SACRA_CYLINDRICAL = 1 };
+enum { SACRA_HLLC = 0, SACRA_TVDLF = 1 };
+enum { SACRA_RK4 = 0, SACRA_SSPRK3 = 1 };
+enum { SACRA_PRIM_METRIC = 0, SACRA_RAW = 1 };
+enum { SACRA_FILL = 0, SACRA_RESTRICT_REFLUX = 1 };
+enum { SACRA_STATE_STEP = 0, SACRA_STATE_STAGE = 1, SACRA_PRIMS = 2, SACRA_RHS = 3, SACRA_STATUS = 4 };
+
+/* Run configuration.  Parameters the paper fixes: kappa = 5e-3/M (Sec. II.B.1),
+   eps_ko = 0.5, eta_B ~ 1/M, r_z4 <= L_max/6 (Sec. II.B.3), w_max = 100 and
+   rho_atm = f_atm rho_max(t=0) (Sec. II.C.4). */
+typedef struct {
+  int n_levels;          /* L >= 1; L > 1 needs nx == nz, even, >= 16, cylindrical */
+  int nx, nz;            /* cells per level */
+  int geometry;          /* SACRA_PLANAR (Cartesian slab, outflow boundaries) or SACRA_CYLINDRICAL
+                            (x = varpi, axis and equatorial symmetry, outgoing outer boundary) */
+  int evolve_spacetime;  /* 0: metric frozen */
+  int solver;            /* SACRA_HLLC (with TVDLF fallback) or SACRA_TVDLF */
+  int rk;                /* SACRA_RK4 (the paper's integrator) or SACRA_SSPRK3 */
+  int c2p_maxit;         /* iteration cap of the primitive recovery */
+  int reserved;
+  double dx0, dz0;       /* spacing of level 0 */
+  double kappa, eta_B, eps_ko, r_z4;
+  double K, Gamma, Gamma_th;   /* cold polytrope P = K rho^Gamma plus thermal Gamma_th law (Sec. II.C.3) */
+  double rho_atm, w_max, c2p_tol;
+} sacra_params;
+
+/* Global diagnostics (Sec. II.F.1) over the cells not covered by a finer
+   level, volume element 2 pi x dx dz (cylindrical) or dx dz (planar),
+   integrated over the computational domain. */
+typedef struct {
+  double H_L2;           /* sqrt(sum H^2 dV / sum dV) */
+  double M_L2[3];        /* same for M_x, M_y (= M_phi / x), M_z */
+  double Mb;             /* rest mass  sum q_D dV */
+  double J;              /* angular momentum sum q_Sphi dV (cylindrical) */
+  double rho_max;
+  double n_c2p_fail;     /* cells whose last recovery did not converge or was invalid */
+  double n_fallback;     /* HLLC -> TVDLF fallbacks since creation */
+} sacra_diag;
+
+/* Bytes of device memory the configuration needs (one arena). */
+sacra_status sacra_arena_bytes(const sacra_params *p, size_t *bytes);
+
+/* Create a context.  stream: a cudaStream_t (NULL = default stream);
+   arena: device buffer of at least sacra_arena_bytes() bytes, 256-byte
+   aligned, or NULL to let the library allocate one.  The arena must outlive
+   the context.  *out receives the context (NULL on failure). */
+sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *arena, size_t arena_bytes,
+                             sacra_ctx **out);
+
+/* Initial data of one level from HOST memory (copied before returning).
+   kind SACRA_PRIM_METRIC: n_fields = 30 padded planes, 25 metric fields then
+   (rho, u_x, u_y, u_z, P); eps follows from the EOS and the conserved
+   variables from Eq. cons_var, on every cell including the padding.
+   kind SACRA_RAW: n_fields = 30 padded state planes (metric + conserved);
+   the primitives are recovered.  host_planes: n_fields * pz * px doubles. */
+sacra_status sacra_set_initial_data(sacra_ctx *c, int level, int kind, const double *host_planes, int n_fields);
+
+/* Ghost and buffer fill (what = SACRA_FILL) for RK stage `stage` of a step of
+   size dt: axis/equator parity, the outgoing condition of Sec. II.B.3 on the
+   coarsest level's outer cells (tau = c_stage dt), and prolongation into the
+   buffer zone of each finer level (Sec. II.D: [N+1, N+8] at stage 0,
+   [N+5, N+8] afterwards).  what = SACRA_RESTRICT_REFLUX ends a step:
+   conservative restriction of q and 8th-order restriction of the metric onto
+   the parent, reflux of the coarse cells next to each refinement boundary,
+   primitive recovery there (stage and dt are ignored). */
+sacra_status sacra_regrid_ghosts(sacra_ctx *c, int what, int stage, double dt);
+
+/* RK stage `stage` (0-based) on all levels: hydro RHS (PPM, tetrad HLLC/TVDLF,
+   cylindrical finite-volume update with sources), Z4c RHS with cartoon terms
+   and KO dissipation, RK combination, algebraic constraints, primitive
+   recovery with atmosphere.  Requires the ghosts filled for this stage. */
+sacra_status sacra_rk_stage(sacra_ctx *c, int stage, double dt);
+
+/* n_steps full steps (fill + stage for every stage, then restrict/reflux).
+   use_graph != 0 captures one step in a CUDA graph on first use and replays it. */
+sacra_status sacra_step(sacra_ctx *c, double dt, int n_steps, int use_graph);
+
+/* Copy one plane to HOST memory.  which: SACRA_STATE_STEP (state at the start
+   of the step, i.e. the current state between steps), SACRA_STATE_STAGE,
+   SACRA_PRIMS, SACRA_RHS or SACRA_STATUS (per-cell recovery flags as
+   doubles).  n = nx*nz copies the interior (row-major, x fastest), n = px*pz
+   the padded plane. */
+sacra_status sacra_read_state(sacra_ctx *c, int level, int which, int field, double *host_out, size_t n);
+
+/* Diagnostics of the current state (a stage-0 ghost fill is done first). */
+sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out);
+
+/* Wait for all work of the context. */
+sacra_status sacra_sync(sacra_ctx *c);
+
+/* Number of kernels the library has launched since creation (graph replays
+   count their kernels). */
+long long sacra_launch_count(const sacra_ctx *c);
+
+void sacra_destroy(sacra_ctx *c);
+const char *sacra_last_error(const sacra_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,492 @@
+// FMR grid kernels on sm_103a (Lam & Shibata, arXiv:2502.03223, Sec. II.A,
+// II.B.3, II.D, II.F.1): symmetry and outer-boundary ghost fill, buffer-zone
+// prolongation, the RK stage update with the algebraic constraints and the
+// primitive recovery, restriction, reflux and deterministic diagnostics.
+#include "kernels.h"
+#include "z4c.cuh"
+
+namespace sacra {
+
+__constant__ GridWeights cW;
+
+void set_grid_weights(const GridWeights &w) { cudaMemcpyToSymbol(cW, &w, sizeof(GridWeights)); }
+
+// x -> -x parity (rotation by pi about z) and z -> -z parity of every field
+__device__ __forceinline__ double sgn_x(int f) {
+  switch (f) {
+    case fGX: case fGY: case fBX: case fBY: case fBBX: case fBBY:
+    case fHXZ: case fHYZ: case fAXZ: case fAYZ:
+      return -1.0;
+    default:
+      return 1.0;
+  }
+}
+__device__ __forceinline__ double sgn_z(int f) {
+  switch (f) {
+    case fGZ: case fBZ: case fBBZ: case fHXZ: case fHYZ: case fAXZ: case fAYZ:
+      return -1.0;
+    default:
+      return 1.0;
+  }
+}
+
+// axis ghosts j in [-7, 0] for rows [1, nz+8] (metric + primitives)
+__global__ void k_parity_x(Lev L, double *__restrict__ U) {
+  const int j = -7 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (j > 0 || k > L.nz + GH) return;
+  const size_t P = L.P;
+  const int d = cid(L, j, k), s = cid(L, 1 - j, k);
+  for (int f = 0; f < NMET; ++f) U[(size_t)f * P + d] = sgn_x(f) * U[(size_t)f * P + s];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f)
+    L.prim[(size_t)f * P + d] = ((f == pUX || f == pUY) ? -1.0 : 1.0) * L.prim[(size_t)f * P + s];
+}
+
+// equator ghosts k in [-7, 0] for all columns
+__global__ void k_parity_z(Lev L, double *__restrict__ U) {
+  const int j = -7 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = -7 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (j > L.nx + GH || k > 0) return;
+  const size_t P = L.P;
+  const int d = cid(L, j, k), s = cid(L, j, 1 - k);
+  for (int f = 0; f < NMET; ++f) U[(size_t)f * P + d] = sgn_z(f) * U[(size_t)f * P + s];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = (f == pUZ ? -1.0 : 1.0) * L.prim[(size_t)f * P + s];
+}
+
+// planar slab: zero-gradient copy into every ghost cell
+__global__ void k_outflow(Lev L, double *__restrict__ U) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.px * L.pz) return;
+  const int j = i % L.px - GH + 1, k = i / L.px - GH + 1;
+  if (j >= 1 && j <= L.nx && k >= 1 && k <= L.nz) return;
+  const int jj = min(max(j, 1), L.nx), kk = min(max(k, 1), L.nz);
+  const int s = cid(L, jj, kk);
+  const size_t P = L.P;
+  for (int f = 0; f < NST; ++f) U[(size_t)f * P + i] = U[(size_t)f * P + s];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + i] = L.prim[(size_t)f * P + s];
+}
+
+// Outer boundary of the coarsest level (Sec. II.B.3): Q = Q_inf + (1 - tau/r)
+// (Q^n - Q_inf)(r - tau), quadratic (3x3) Lagrange interpolation of the step-
+// start state Un; hydro primitives copied from the nearest interior cell.
+__global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict__ U, double tau) {
+  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (j > L.nx + GH || k > L.nz + GH || (j <= L.nx && k <= L.nz)) return;
+  const size_t P = L.P;
+  const double x = (j - 0.5) * L.dx, z = (k - 0.5) * L.dz;
+  const double r = sqrt(x * x + z * z);
+  const double fac = 1.0 - tau / r;
+  const double xi = x * fac / L.dx + 0.5, ze = z * fac / L.dz + 0.5;
+  const int i0 = min((int)floor(xi + 0.5), L.nx + GH - 1), k0 = min((int)floor(ze + 0.5), L.nz + GH - 1);
+  const double tx = xi - i0, tz = ze - k0;
+  const double wx[3] = {0.5 * tx * (tx - 1.0), (1.0 - tx) * (1.0 + tx), 0.5 * tx * (tx + 1.0)};
+  const double wz[3] = {0.5 * tz * (tz - 1.0), (1.0 - tz) * (1.0 + tz), 0.5 * tz * (tz + 1.0)};
+  const int d = cid(L, j, k), c0 = cid(L, i0, k0);
+  for (int f = 0; f < NMET; ++f) {
+    const double qinf = (f == fW || f == fAL) ? 1.0 : 0.0;
+    const double *u = Un + (size_t)f * P + c0;
+    const double u0 = u[0] - qinf;
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) s += wx[a] * wz[b] * (u[(b - 1) * L.px + (a - 1)] - qinf - u0);
+    U[(size_t)f * P + d] = qinf + fac * (u0 + s);
+  }
+  const int sc = cid(L, min(j, L.nx), min(k, L.nz));
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = L.prim[(size_t)f * P + sc];
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+  return a * b <= 0.0 ? 0.0 : (fabs(a) < fabs(b) ? a : b);
+}
+
+// Buffer-zone prolongation (Sec. II.D): 8th-order Lagrange (tensor product)
+// for the metric, minmod-limited linear for the primitives, then conserved
+// variables from the primitives.  full: [N+1, N+8], else [N+5, N+8].
+__global__ void k_prolong(Lev L, Lev Pa, DevParams p, double *__restrict__ U, const double *__restrict__ Up, int full) {
+  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  const int lo = full ? L.nx + 1 : L.nx + 5;
+  if (j > L.nx + GH || k > L.nz + GH || (j < lo && k < lo)) return;
+  const size_t P = L.P, PP = Pa.P;
+  // parent cell m holding the child centre, and the side of the quarter offset
+  const bool ex = (j & 1) == 0, ez = (k & 1) == 0;
+  const int mx = ex ? j / 2 : (j + 1) / 2, mz = ez ? k / 2 : (k + 1) / 2;
+  double wx[8], wz[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) {
+    wx[n] = ex ? cW.prol[n] : cW.prol[7 - n];
+    wz[n] = ez ? cW.prol[n] : cW.prol[7 - n];
+  }
+  const int bx = ex ? mx - 3 : mx - 4, bz = ez ? mz - 3 : mz - 4;
+  const int pc = cid(Pa, mx, mz), pb = cid(Pa, bx, bz);
+  const int d = cid(L, j, k);
+  for (int f = 0; f < NMET; ++f) {
+    const double *u = Up + (size_t)f * PP;
+    const double u0 = u[pc];
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      double r = 0.0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) r += wx[a] * (u[pb + b * Pa.px + a] - u0);
+      s += wz[b] * r;
+    }
+    U[(size_t)f * P + d] = u0 + s;
+  }
+  const double ox = ex ? 0.25 : -0.25, oz = ez ? 0.25 : -0.25;
+  double pr[NPRIM];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) {
+    const double *a = Pa.prim + (size_t)f * PP + pc;
+    const double a0 = a[0];
+    pr[f] = a0 + ox * minmod(a[1] - a0, a0 - a[-1]) + oz * minmod(a[Pa.px] - a0, a0 - a[-Pa.px]);
+  }
+  const double pc0 = eos_pc(p, pr[pRHO]);
+  if (pr[pP] < pc0) pr[pP] = pc0;
+  pr[pEPS] = eos_eps(p, pr[pRHO], pr[pP]);
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = pr[f];
+  const Sym3 g = conf_metric(U, P, d);
+  double q[NCONS];
+  prim_to_cons(p, pr, U[(size_t)fW * P + d], g, (j - 0.5) * L.dx, q);
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + d] = q[v];
+}
+
+// det gt = 1 and tr At = 0 after every stage (Sec. II.B.1):
+// gt <- d^(-1/3) gt, W <- d^(-1/6) W, At <- d^(-1/3)(At - gt tr/3), Khat += tr
+__device__ inline void enforce_algebraic(double m[NST]) {
+  Sym3 g;
+  g.xx = 1.0 + m[fHXX]; g.xy = m[fHXY]; g.xz = m[fHXZ]; g.yy = 1.0 + m[fHYY]; g.yz = m[fHYZ]; g.zz = 1.0 + m[fHZZ];
+  double det;
+  const Sym3 gi = s3inv(g, &det);
+  const double tr = gi.xx * m[fAXX] + gi.yy * m[fAYY] + gi.zz * m[fAZZ]
+                  + 2.0 * (gi.xy * m[fAXY] + gi.xz * m[fAXZ] + gi.yz * m[fAYZ]);
+  const double c13 = rcbrt(det), c16 = sqrt(c13);
+  const double gv[6] = {g.xx, g.xy, g.xz, g.yy, g.yz, g.zz};
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    m[fAXX + a] = c13 * (m[fAXX + a] - gv[a] * tr / 3.0);
+    const double gn = c13 * gv[a];
+    m[fHXX + a] = (a == 0 || a == 3 || a == 5) ? gn - 1.0 : gn;
+  }
+  m[fW] *= c16;
+  m[fKH] += tr;
+}
+
+// RK stage combination on [1, jmax] x [1, kmax], then algebraic constraints
+// and primitive recovery.  Ust = stage state read (Un at stage 0, Us after);
+// the result is written to Us.
+__global__ void __launch_bounds__(128) k_rk_update(Lev L, DevParams p, const double *__restrict__ Ust, int stage, double dt,
+                                                   int jmax, int kmax) {
+  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (j > jmax || k > kmax) return;
+  const size_t P = L.P;
+  const int id = cid(L, j, k);
+  double m[NST];
+  const int f0 = p.evolve ? 0 : NMET;
+  for (int f = 0; f < NST; ++f) {
+    const size_t o = (size_t)f * P + id;
+    if (f < f0) { m[f] = L.us[o]; continue; }
+    const double un = L.un[o], kk = L.rhs[o];
+    double out;
+    if (p.rk == SACRA_RK4) {
+      if (stage < 3) {
+        const double bw = stage == 0 ? 1.0 / 6.0 : 1.0 / 3.0;
+        L.ka[o] = (stage == 0 ? 0.0 : L.ka[o]) + bw * kk;
+        out = un + (stage == 2 ? 1.0 : 0.5) * dt * kk;
+      } else {
+        out = un + dt * (L.ka[o] + kk / 6.0);
+      }
+    } else {
+      if (stage == 0) out = un + dt * kk;
+      else if (stage == 1) out = 0.75 * un + 0.25 * Ust[o] + 0.25 * dt * kk;
+      else out = un / 3.0 + (2.0 / 3.0) * Ust[o] + (2.0 / 3.0) * dt * kk;
+    }
+    m[f] = out;
+  }
+  if (p.evolve) enforce_algebraic(m);
+  Sym3 g;
+  g.xx = 1.0 + m[fHXX]; g.xy = m[fHXY]; g.xz = m[fHXZ]; g.yy = 1.0 + m[fHYY]; g.yz = m[fHYZ]; g.zz = 1.0 + m[fHZZ];
+  double pr[NPRIM];
+  const int st = cons_to_prim(p, m + fQD, m[fW], g, (j - 0.5) * L.dx, pr);
+  for (int f = f0; f < NST; ++f) L.us[(size_t)f * P + id] = m[f];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + id] = pr[f];
+  L.status[id] = st;
+}
+
+// Restriction of child level C onto parent cells [1, N/2]^2 (Sec. II.D):
+// q as the volume-weighted average of the 2x2 children, the metric by 8th-
+// order Lagrange (nodes shifted inward so that none passes the child edge N).
+__global__ void k_restrict(Lev C, Lev Pa) {
+  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  const int nh = Pa.nx / 2;
+  if (j > nh || k > nh) return;
+  const size_t P = C.P, PP = Pa.P;
+  const int d = cid(Pa, j, k);
+  const double xp = (j - 0.5) * Pa.dx;
+  const double xa = (2 * j - 1.5) * C.dx, xb = (2 * j - 0.5) * C.dx;
+  const int c00 = cid(C, 2 * j - 1, 2 * k - 1);
+  for (int v = 0; v < NCONS; ++v) {
+    const double *q = C.un + (size_t)(fQD + v) * P + c00;
+    // (x-weighted sum of 4 children) * dxc dzc / (x_p dxp dzp); dxp dzp = 4 dxc dzc
+    const double s = xa * (q[0] + q[C.px]) + xb * (q[1] + q[C.px + 1]);
+    Pa.un[(size_t)(fQD + v) * PP + d] = s / (4.0 * xp);
+  }
+  const double *wx, *wz;
+  int bx, bz;
+  const int N = C.nx;
+  if (j <= nh - 2) { wx = cW.rest_c; bx = 2 * j - 4; } else { wx = (j == nh) ? cW.rest_s0 : cW.rest_s1; bx = N - 7; }
+  if (k <= nh - 2) { wz = cW.rest_c; bz = 2 * k - 4; } else { wz = (k == nh) ? cW.rest_s0 : cW.rest_s1; bz = N - 7; }
+  const int cb = cid(C, bx, bz);
+  for (int f = 0; f < NMET; ++f) {
+    const double *u = C.un + (size_t)f * P;
+    const double u0 = u[c00];
+    double s = 0.0;
+    for (int b = 0; b < 8; ++b) {
+      double r = 0.0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) r += wx[a] * (u[cb + b * C.px + a] - u0);
+      s += wz[b] * r;
+    }
+    Pa.un[(size_t)f * PP + d] = u0 + s;
+  }
+}
+
+// Reflux (Sec. II.D): parent cells next to the child's outer faces get the
+// sum of the fine fluxes (RK-weighted) instead of the coarse flux.
+__global__ void k_reflux(Lev C, Lev Pa, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nh = Pa.nx / 2;
+  if (i >= 2 * nh) return;
+  const bool xface = i < nh;
+  const int t = (xface ? i : i - nh) + 1;            // k (x-face) or j (z-face) in [1, N/2]
+  const int j = xface ? nh + 1 : t, k = xface ? t : nh + 1;
+  const int d = cid(Pa, j, k);
+  const double vol = (j - 0.5) * Pa.dx * Pa.dx * Pa.dz;
+  const int rc = xface ? 0 : 2, rf = xface ? 1 : 3;
+  for (int v = 0; v < NCONS; ++v) {
+    const double fine = C.freg[(size_t)(rf * NCONS + v) * C.rw + 2 * t - 1] + C.freg[(size_t)(rf * NCONS + v) * C.rw + 2 * t];
+    const double coarse = Pa.freg[(size_t)(rc * NCONS + v) * Pa.rw + t];
+    Pa.un[(size_t)(fQD + v) * Pa.P + d] += dt * (fine - coarse) / vol;
+  }
+}
+
+// ---------------------------------------------------------------- diagnostics
+
+constexpr int DIAG_Q = 9;   // H^2 dV, Mx^2 dV, My^2 dV, Mz^2 dV, dV, qD dV, qSphi dV, rho_max, n_fail
+constexpr int DIAG_T = 128;
+
+__global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const double *__restrict__ DS, int covered,
+                                                 int evolve, double *__restrict__ partials) {
+  __shared__ double sh[DIAG_Q][DIAG_T];
+  const int t = threadIdx.x;
+  const int n = L.nx * L.nz;
+  const int i = blockIdx.x * DIAG_T + t;
+  double acc[DIAG_Q];
+#pragma unroll
+  for (int q = 0; q < DIAG_Q; ++q) acc[q] = 0.0;
+  if (i < n) {
+    const int j = 1 + i % L.nx, k = 1 + i / L.nx;
+    const bool skip = covered && j <= L.nx / 2 && k <= L.nz / 2;
+    if (!skip) {
+      constexpr double PI = 3.14159265358979323846;
+      const size_t P = L.P;
+      const int id = cid(L, j, k);
+      const bool cyl = p.geometry == SACRA_CYLINDRICAL;
+      const double x = (j - 0.5) * L.dx;
+      const double vol = cyl ? 2.0 * PI * x * L.dx * L.dz : L.dx * L.dz;
+      const double *U = L.un;
+      acc[4] = vol;
+      acc[5] = U[(size_t)fQD * P + id] * vol;
+      acc[6] = U[(size_t)fQSY * P + id] * vol;
+      acc[7] = L.prim[(size_t)pRHO * P + id];
+      acc[8] = (L.status[id] & (ST_NOCONV | ST_BAD)) ? 1.0 : 0.0;
+      if (evolve) {
+        // DS holds the derivative scratch of the Z4c pass for this level
+        constexpr int D1 = 0, D2 = 48;
+        Z4cIn z;
+        z.W = U[(size_t)fW * P + id]; z.al = U[(size_t)fAL * P + id];
+        z.Kh = U[(size_t)fKH * P + id]; z.Th = U[(size_t)fTH * P + id];
+        for (int a = 0; a < 6; ++a) { z.h[a] = U[(size_t)(fHXX + a) * P + id]; z.A[a] = U[(size_t)(fAXX + a) * P + id]; }
+        for (int c = 0; c < 3; ++c) {
+          z.Gt[c] = U[(size_t)(fGX + c) * P + id]; z.beta[c] = U[(size_t)(fBX + c) * P + id];
+          z.B[c] = U[(size_t)(fBBX + c) * P + id];
+        }
+        for (int c = 0; c < 3; ++c) {
+          z.dW[c] = DS[(size_t)(D1 + c) * P + id];
+          for (int a = 0; a < 6; ++a) z.dh[a][c] = DS[(size_t)(D1 + 3 * (1 + a) + c) * P + id];
+          z.dKh[c] = DS[(size_t)(D1 + 21 + c) * P + id];
+          for (int a = 0; a < 3; ++a) z.dGt[a][c] = DS[(size_t)(D1 + 3 * (8 + a) + c) * P + id];
+          z.dTh[c] = DS[(size_t)(D1 + 33 + c) * P + id];
+          z.dal[c] = DS[(size_t)(D1 + 36 + c) * P + id];
+          for (int a = 0; a < 3; ++a) z.db[a][c] = DS[(size_t)(D1 + 3 * (13 + a) + c) * P + id];
+        }
+        for (int q = 0; q < 6; ++q) {
+          z.ddW[q] = DS[(size_t)(D2 + q) * P + id];
+          for (int a = 0; a < 6; ++a) z.ddh[a][q] = DS[(size_t)(D2 + 6 * (1 + a) + q) * P + id];
+          z.ddal[q] = DS[(size_t)(D2 + 42 + q) * P + id];
+          for (int a = 0; a < 3; ++a) z.ddb[a][q] = DS[(size_t)(D2 + 6 * (8 + a) + q) * P + id];
+        }
+        Geo G;
+        geo_fill(z, G);
+        geo_ricci(z, G);
+        double pr[NPRIM];
+        for (int f = 0; f < NPRIM; ++f) pr[f] = L.prim[(size_t)f * P + id];
+        double E, Si[3], Sij[6];
+        matter(pr, z.W, G.g, G.gi, E, Si, Sij);
+        const double K = z.Kh + 2.0 * z.Th;
+        const Sym3 &gi = G.gi;
+        const double gim[3][3] = {{gi.xx, gi.xy, gi.xz}, {gi.xy, gi.yy, gi.yz}, {gi.xz, gi.yz, gi.zz}};
+        double Am[3][3];   // At^j_i -> Am[j][i]
+        for (int jj = 0; jj < 3; ++jj)
+          for (int ii = 0; ii < 3; ++ii)
+            Am[jj][ii] = gim[jj][0] * z.A[sp(0, ii)] + gim[jj][1] * z.A[sp(1, ii)] + gim[jj][2] * z.A[sp(2, ii)];
+        double AA = 0.0, trA = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          trA += Am[a][a];
+          for (int b = 0; b < 3; ++b) AA += Am[a][b] * Am[b][a];
+        }
+        const double H = G.Rs + K * K - (AA + (2.0 / 3.0) * K * trA + K * K / 3.0) - 16.0 * PI * E;
+        // d_k At_ij: x, z by central differences, y from the cartoon planes
+        double dA[6][3];
+        const double i60x = 1.0 / (60.0 * L.dx), i60z = 1.0 / (60.0 * L.dz);
+        for (int a = 0; a < 6; ++a) {
+          const double *u = U + (size_t)(fAXX + a) * P + id;
+          dA[a][0] = (45.0 * (u[1] - u[-1]) - 9.0 * (u[2] - u[-2]) + (u[3] - u[-3])) * i60x;
+          dA[a][2] = (45.0 * (u[L.px] - u[-L.px]) - 9.0 * (u[2 * L.px] - u[-2 * L.px]) + (u[3 * L.px] - u[-3 * L.px])) * i60z;
+          dA[a][1] = (cyl && a != 5) ? L.dy[(size_t)(fAXX + a) * P + id] : 0.0;
+        }
+        double M[3];
+        for (int ii = 0; ii < 3; ++ii) {
+          double s = 0.0;
+          for (int jj = 0; jj < 3; ++jj)
+            for (int kk = 0; kk < 3; ++kk) {
+              // d_j gt^jk = -gt^ja gt^kb d_j gt_ab
+              double dgi = 0.0;
+              for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) dgi -= gim[jj][a] * gim[kk][b] * z.dh[sp(a, b)][jj];
+              s += dgi * z.A[sp(kk, ii)] + gim[jj][kk] * dA[sp(kk, ii)][jj];
+            }
+          for (int jj = 0; jj < 3; ++jj)
+            for (int l = 0; l < 3; ++l) s -= G.G2[l][sp(jj, ii)] * Am[jj][l];
+          for (int l = 0; l < 3; ++l) s -= 3.0 / z.W * Am[l][ii] * z.dW[l];
+          s -= (2.0 / 3.0) * (z.dKh[ii] + 2.0 * z.dTh[ii]) + 8.0 * PI * Si[ii];
+          M[ii] = s;
+        }
+        acc[0] = H * H * vol;
+        acc[1] = M[0] * M[0] * vol; acc[2] = M[1] * M[1] * vol; acc[3] = M[2] * M[2] * vol;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = acc[q];
+  __syncthreads();
+  for (int w = DIAG_T / 2; w > 0; w >>= 1) {
+    if (t < w)
+#pragma unroll
+      for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = (q == 7) ? fmax(sh[q][t], sh[q][t + w]) : sh[q][t] + sh[q][t + w];
+    __syncthreads();
+  }
+  if (t == 0)
+#pragma unroll
+    for (int q = 0; q < DIAG_Q; ++q) partials[(size_t)blockIdx.x * DIAG_Q + q] = sh[q][0];
+}
+
+// fixed-order sum of the block partials (deterministic)
+__global__ void k_diag_final(const double *__restrict__ partials, int n, double *__restrict__ out) {
+  __shared__ double sh[DIAG_Q][DIAG_T];
+  const int t = threadIdx.x;
+  double acc[DIAG_Q];
+#pragma unroll
+  for (int q = 0; q < DIAG_Q; ++q) acc[q] = 0.0;
+  for (int b = t; b < n; b += DIAG_T)
+#pragma unroll
+    for (int q = 0; q < DIAG_Q; ++q)
+      acc[q] = (q == 7) ? fmax(acc[q], partials[(size_t)b * DIAG_Q + q]) : acc[q] + partials[(size_t)b * DIAG_Q + q];
+#pragma unroll
+  for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = acc[q];
+  __syncthreads();
+  for (int w = DIAG_T / 2; w > 0; w >>= 1) {
+    if (t < w)
+#pragma unroll
+      for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = (q == 7) ? fmax(sh[q][t], sh[q][t + w]) : sh[q][t] + sh[q][t + w];
+    __syncthreads();
+  }
+  if (t == 0)
+#pragma unroll
+    for (int q = 0; q < DIAG_Q; ++q) out[q] = sh[q][0];
+}
+
+// ---------------------------------------------------------------- host launchers
+
+void launch_parity(const Lev &L, double *U, cudaStream_t s, long long *nl) {
+  dim3 b(8, 32);
+  k_parity_x<<<dim3(1, (L.nz + GH + 31) / 32), b, 0, s>>>(L, U);
+  dim3 b2(32, 8);
+  k_parity_z<<<dim3((L.nx + 2 * GH + 31) / 32, 1), b2, 0, s>>>(L, U);
+  *nl += 2;
+}
+
+void launch_outflow(const Lev &L, double *U, cudaStream_t s, long long *nl) {
+  k_outflow<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(L, U);
+  ++*nl;
+}
+
+void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s, long long *nl) {
+  dim3 b(32, 4), g((L.nx + GH + 31) / 32, (L.nz + GH + 3) / 4);
+  k_outer<<<g, b, 0, s>>>(L, Un, U, tau);
+  ++*nl;
+}
+
+void launch_prolong(const Lev &L, const Lev &Pa, const DevParams &p, double *U, const double *Up, int full,
+                    cudaStream_t s, long long *nl) {
+  dim3 b(32, 4), g((L.nx + GH + 31) / 32, (L.nz + GH + 3) / 4);
+  k_prolong<<<g, b, 0, s>>>(L, Pa, p, U, Up, full);
+  ++*nl;
+}
+
+void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, double dt, int jmax, int kmax,
+                      cudaStream_t s, long long *nl) {
+  dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
+  k_rk_update<<<g, b, 0, s>>>(L, p, Ust, stage, dt, jmax, kmax);
+  ++*nl;
+}
+
+void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s, long long *nl) {
+  const int nh = Pa.nx / 2;
+  dim3 b(32, 4), g((nh + 31) / 32, (nh + 3) / 4);
+  k_restrict<<<g, b, 0, s>>>(C, Pa);
+  ++*nl;
+}
+
+void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s, long long *nl) {
+  const int n = Pa.nx;  // 2 * N/2 cells
+  k_reflux<<<(n + 127) / 128, 128, 0, s>>>(C, Pa, dt);
+  ++*nl;
+}
+
+int diag_blocks(const Lev &L) { return (L.nx * L.nz + DIAG_T - 1) / DIAG_T; }
+
+void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials, int slot,
+                 cudaStream_t s, long long *nl) {
+  k_diag<<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, covered, evolve, partials + (size_t)slot * DIAG_Q);
+  ++*nl;
+}
+
+void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s, long long *nl) {
+  k_diag_final<<<1, DIAG_T, 0, s>>>(partials, n, out);
+  ++*nl;
+}
+
+}  // namespace sacra

@@ -1,0 +1,263 @@
+// GRHD kernels on sm_103a (Lam & Shibata, arXiv:2502.03223, Sec. II.C):
+// per-face PPM reconstruction + metric interpolation + tetrad HLLC/TVDLF flux,
+// per-cell flux divergence with cylindrical areas/volumes and the geometric and
+// gravitational sources, primitive recovery, initial conserved variables.
+#include "kernels.h"
+
+namespace sacra {
+
+// 6-point (6th-order) interpolation of a metric field to the face between
+// u[0] and u[s], in difference form about u[0]: (3,-25,150,150,-25,3)/256.
+__device__ __forceinline__ double face6(const double *u, int s) {
+  const double u0 = u[0];
+  return u0 + (3.0 * (u[-2 * s] - u0) - 25.0 * (u[-s] - u0) + 150.0 * (u[s] - u0) - 25.0 * (u[2 * s] - u0)
+               + 3.0 * (u[3 * s] - u0)) * (1.0 / 256.0);
+}
+
+// Face j+1/2 (dir 0, stride 1) or k+1/2 (dir 1, stride px) of cell (j, k).
+template <int DIR>
+__device__ inline void flux_at(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                               double out[NCONS], int *fb) {
+  const size_t P = L.P;
+  const int s = DIR == 0 ? 1 : L.px;
+  const int id = cid(L, j, k);
+  const int pf[5] = {pRHO, pUX, pUY, pUZ, pP};
+  double pl[5], pr[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double *a = L.prim + (size_t)pf[v] * P + id;
+    const double c[6] = {a[-2 * s], a[-s], a[0], a[s], a[2 * s], a[3 * s]};
+    ppm_pair(c, pl[v], pr[v]);
+  }
+  if (!(pl[0] > 0.0) || !(pl[4] > 0.0))
+#pragma unroll
+    for (int v = 0; v < 5; ++v) pl[v] = L.prim[(size_t)pf[v] * P + id];
+  if (!(pr[0] > 0.0) || !(pr[4] > 0.0))
+#pragma unroll
+    for (int v = 0; v < 5; ++v) pr[v] = L.prim[(size_t)pf[v] * P + id + s];
+  const double alpha = face6(U + (size_t)fAL * P + id, s);
+  const double W = face6(U + (size_t)fW * P + id, s);
+  double beta[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) beta[i] = face6(U + (size_t)(fBX + i) * P + id, s);
+  Sym3 g;
+  g.xx = 1.0 + face6(U + (size_t)fHXX * P + id, s);
+  g.xy = face6(U + (size_t)fHXY * P + id, s);
+  g.xz = face6(U + (size_t)fHXZ * P + id, s);
+  g.yy = 1.0 + face6(U + (size_t)fHYY * P + id, s);
+  g.yz = face6(U + (size_t)fHYZ * P + id, s);
+  g.zz = 1.0 + face6(U + (size_t)fHZZ * P + id, s);
+  *fb = face_flux(p, DIR, pl, pr, alpha, beta, W, g, out);
+}
+
+// x-faces j+1/2 for j in [0, jmax], rows [1, kmax].  Stores area-weighted
+// fluxes (cylindrical: area x_{j+1/2} dz, and one more factor x for S_phi)
+// and accumulates the flux registers of the refinement boundaries.
+__global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
+                                                 double wb, int has_child, int has_parent) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (j > jmax || k > kmax) return;
+  double f[NCONS];
+  int fb;
+  flux_at<0>(L, p, U, j, k, f, &fb);
+  const bool cyl = p.geometry == SACRA_CYLINDRICAL;
+  const double xf = j * L.dx;
+  const double area = cyl ? xf * L.dz : L.dz;
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) f[v] *= area;
+  if (cyl) f[2] *= xf;
+  const int id = cid(L, j, k);
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) L.fx[(size_t)v * L.P + id] = f[v];
+  if (has_child && j == L.nx / 2 && k <= L.nz / 2)
+#pragma unroll
+    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(0 * NCONS + v) * L.rw + k] += wb * f[v];
+  if (has_parent && j == L.nx && k <= L.nz)
+#pragma unroll
+    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(1 * NCONS + v) * L.rw + k] += wb * f[v];
+  if (fb) atomicAdd(L.nfb, 1ull);
+}
+
+__global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
+                                                 double wb, int has_child, int has_parent) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  if (j > jmax || k > kmax) return;
+  double f[NCONS];
+  int fb;
+  flux_at<1>(L, p, U, j, k, f, &fb);
+  const bool cyl = p.geometry == SACRA_CYLINDRICAL;
+  // equatorial mirror plane: D, S_x, S_phi, E are even in z, their z-fluxes vanish there
+  if (cyl && k == 0) f[0] = f[1] = f[2] = f[4] = 0.0;
+  const double x = (j - 0.5) * L.dx;
+  const double area = cyl ? x * L.dx : L.dx;
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) f[v] *= area;
+  if (cyl) f[2] *= x;
+  const int id = cid(L, j, k);
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) L.fz[(size_t)v * L.P + id] = f[v];
+  if (has_child && k == L.nz / 2 && j <= L.nx / 2)
+#pragma unroll
+    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(2 * NCONS + v) * L.rw + j] += wb * f[v];
+  if (has_parent && k == L.nz && j <= L.nx)
+#pragma unroll
+    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(3 * NCONS + v) * L.rw + j] += wb * f[v];
+  if (fb) atomicAdd(L.nfb, 1ull);
+}
+
+__device__ __forceinline__ double cd1(const double *u, int s, double idx) {
+  return (45.0 * (u[s] - u[-s]) - 9.0 * (u[2 * s] - u[-2 * s]) + (u[3 * s] - u[-3 * s])) * idx;
+}
+
+// d_t q = <s> - (1/dV) sum (area-weighted fluxes), Sec. II.C.1.  Sources:
+//   s_Sk = P d_k(alpha W^-3) - W^-3 rho h w^2 [d_k alpha - v_i d_k beta^i
+//          + (W^2/2) alpha v_a v_b d_k gt^ab + (alpha/W) v_i v^i d_k W]
+//        (+ alpha W^-3 (S_y vbar^y + P)/x for k = x, cylindrical),
+//   s_E  = W^-3 (alpha K^ij S_ij - rho h w^2 v^i d_i alpha), s_D = s_Sphi = 0.
+__global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
+  if (j > jmax || k > kmax) return;
+  const size_t P = L.P;
+  const int id = cid(L, j, k);
+  const int sz = L.px;
+  const bool cyl = p.geometry == SACRA_CYLINDRICAL;
+  const double x = (j - 0.5) * L.dx;
+  const double ivol = 1.0 / (cyl ? x * L.dx * L.dz : L.dx * L.dz);
+  double div[NCONS];
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) {
+    const double *fx = L.fx + (size_t)v * P + id;
+    const double *fz = L.fz + (size_t)v * P + id;
+    div[v] = (fx[0] - fx[-1] + fz[0] - fz[-sz]) * ivol;
+  }
+  const double W = U[(size_t)fW * P + id], al = U[(size_t)fAL * P + id];
+  const Sym3 g = conf_metric(U, P, id);
+  const Sym3 gi = s3inv(g, nullptr);
+  const double i60[2] = {1.0 / (60.0 * L.dx), 1.0 / (60.0 * L.dz)};
+  const int st[2] = {1, sz};
+  double pr[NPRIM];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) pr[f] = L.prim[(size_t)f * P + id];
+  const double rho = pr[pRHO], Pp = pr[pP];
+  const double u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
+  const double w = sqrt(1.0 + W * W * s3quad(gi, u, u));
+  const double rhw2 = rho * (1.0 + pr[pEPS] + Pp / rho) * w * w;
+  const double vd[3] = {u[0] / w, u[1] / w, u[2] / w};
+  double vu[3];
+  s3vec(gi, vd, vu);
+  vu[0] *= W * W; vu[1] *= W * W; vu[2] *= W * W;
+  const double vv = vd[0] * vu[0] + vd[1] * vu[1] + vd[2] * vu[2];
+  const double iW = 1.0 / W, iW3 = iW * iW * iW;
+  // gt^ac v_c, used in v_a v_b d gt^ab = -(gt^ac v_c)(gt^bd v_d) d gt_cd
+  double gv[3];
+  s3vec(gi, vd, gv);
+  double src[2], dal[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int s = st[e];
+    dal[e] = cd1(U + (size_t)fAL * P + id, s, i60[e]);
+    const double dW = cd1(U + (size_t)fW * P + id, s, i60[e]);
+    double vdb = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vdb += vd[i] * cd1(U + (size_t)(fBX + i) * P + id, s, i60[e]);
+    Sym3 dg;
+    dg.xx = cd1(U + (size_t)fHXX * P + id, s, i60[e]);
+    dg.xy = cd1(U + (size_t)fHXY * P + id, s, i60[e]);
+    dg.xz = cd1(U + (size_t)fHXZ * P + id, s, i60[e]);
+    dg.yy = cd1(U + (size_t)fHYY * P + id, s, i60[e]);
+    dg.yz = cd1(U + (size_t)fHYZ * P + id, s, i60[e]);
+    dg.zz = cd1(U + (size_t)fHZZ * P + id, s, i60[e]);
+    const double vvdgi = -s3quad(dg, gv, gv);
+    const double dalW3 = iW3 * dal[e] - 3.0 * al * iW3 * iW * dW;
+    src[e] = Pp * dalW3 - iW3 * rhw2 * (dal[e] - vdb + 0.5 * W * W * al * vvdgi + al * iW * vv * dW);
+  }
+  double geo = 0.0;
+  if (cyl) {
+    const double vbary = vu[1] - U[(size_t)fBY * P + id] / al;
+    geo = al * iW3 * (rhw2 * vd[1] * vbary + Pp) / x;
+  }
+  // K^ij S_ij = rho h w^2 K_ij v^i v^j + P K, K_ij = (At_ij + gt_ij K/3) / W^2
+  const double K = U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id];
+  Sym3 Kd;
+  Kd.xx = (U[(size_t)fAXX * P + id] + g.xx * K / 3.0) * iW * iW;
+  Kd.xy = (U[(size_t)fAXY * P + id] + g.xy * K / 3.0) * iW * iW;
+  Kd.xz = (U[(size_t)fAXZ * P + id] + g.xz * K / 3.0) * iW * iW;
+  Kd.yy = (U[(size_t)fAYY * P + id] + g.yy * K / 3.0) * iW * iW;
+  Kd.yz = (U[(size_t)fAYZ * P + id] + g.yz * K / 3.0) * iW * iW;
+  Kd.zz = (U[(size_t)fAZZ * P + id] + g.zz * K / 3.0) * iW * iW;
+  const double KS = rhw2 * s3quad(Kd, vu, vu) + Pp * K;
+  const double sE = iW3 * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
+  L.rhs[(size_t)fQD * P + id] = -div[0];
+  L.rhs[(size_t)fQSX * P + id] = src[0] + geo - div[1];
+  L.rhs[(size_t)fQSY * P + id] = -div[2];
+  L.rhs[(size_t)fQSZ * P + id] = src[1] - div[3];
+  L.rhs[(size_t)fQE * P + id] = sE - div[4];
+}
+
+// eps from the EOS and conserved variables on every padded cell (initial data)
+__global__ void k_prim2cons_all(Lev L, DevParams p, double *__restrict__ U) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.px * L.pz) return;
+  const size_t P = L.P;
+  double pr[NPRIM];
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) pr[f] = L.prim[(size_t)f * P + i];
+  pr[pEPS] = eos_eps(p, pr[pRHO], pr[pP]);
+  L.prim[(size_t)pEPS * P + i] = pr[pEPS];
+  const int j = i % L.px - GH + 1;
+  const double x = (j - 0.5) * L.dx;
+  const Sym3 g = conf_metric(U, P, i);
+  double q[NCONS];
+  prim_to_cons(p, pr, U[(size_t)fW * P + i], g, x, q);
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + i] = q[v];
+}
+
+// primitive recovery on [j0, j1] x [k0, k1] of state U
+__global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0, int j1, int k0, int k1) {
+  const int j = j0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int k = k0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  if (j > j1 || k > k1) return;
+  const size_t P = L.P;
+  const int id = cid(L, j, k);
+  double q[NCONS], pr[NPRIM];
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) q[v] = U[(size_t)(fQD + v) * P + id];
+  const Sym3 g = conf_metric(U, P, id);
+  const int st = cons_to_prim(p, q, U[(size_t)fW * P + id], g, (j - 0.5) * L.dx, pr);
+#pragma unroll
+  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + id] = pr[f];
+  if (st & (ST_ATM | ST_COLD | ST_KRESCALE))
+#pragma unroll
+    for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + id] = q[v];
+  L.status[id] = st;
+}
+
+// ---------------------------------------------------------------- host launchers
+
+void launch_hydro_rhs(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
+                      int has_parent, cudaStream_t s, long long *nlaunch) {
+  dim3 b(32, 4);
+  k_flux_x<<<dim3((jmax + 1 + 31) / 32, (kmax + 3) / 4), b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+  k_flux_z<<<dim3((jmax + 31) / 32, (kmax + 1 + 3) / 4), b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+  k_hydro_rhs<<<dim3((jmax + 31) / 32, (kmax + 3) / 4), b, 0, s>>>(L, p, U, jmax, kmax);
+  *nlaunch += 3;
+}
+
+void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s, long long *nlaunch) {
+  k_prim2cons_all<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(L, p, U);
+  ++*nlaunch;
+}
+
+void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s,
+                       long long *nlaunch) {
+  if (j1 < j0 || k1 < k0) return;
+  dim3 b(32, 4), g((j1 - j0 + 1 + 31) / 32, (k1 - k0 + 1 + 3) / 4);
+  k_c2p_region<<<g, b, 0, s>>>(L, p, U, j0, j1, k0, k1);
+  ++*nlaunch;
+}
+
+}  // namespace sacra

@@ -1,0 +1,180 @@
+"""ctypes binding of the C ABI in include/sacra2d.h (argument marshalling only).
+
+The compiled library (paper_2502_03223_gb300/_build/libsacra2d.so, built by
+``paper_2502_03223_gb300.build.build()``) does all the arithmetic on the GPU.
+There is no CPU fallback: if the library is missing, importing it fails.
+PyTorch, when present, provides the device arena and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsacra2d.so")
+
+SACRA_OK = 0
+PLANAR, CYLINDRICAL = 0, 1
+HLLC, TVDLF = 0, 1
+RK4, SSPRK3 = 0, 1
+PRIM_METRIC, RAW = 0, 1
+FILL, RESTRICT_REFLUX = 0, 1
+STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
+
+EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
+           "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync",
+           "sacra_launch_count", "sacra_destroy", "sacra_last_error"]
+
+
+class SacraParams(C.Structure):
+    _fields_ = [
+        ("n_levels", C.c_int), ("nx", C.c_int), ("nz", C.c_int), ("geometry", C.c_int),
+        ("evolve_spacetime", C.c_int), ("solver", C.c_int), ("rk", C.c_int), ("c2p_maxit", C.c_int),
+        ("reserved", C.c_int),
+        ("dx0", C.c_double), ("dz0", C.c_double),
+        ("kappa", C.c_double), ("eta_B", C.c_double), ("eps_ko", C.c_double), ("r_z4", C.c_double),
+        ("K", C.c_double), ("Gamma", C.c_double), ("Gamma_th", C.c_double),
+        ("rho_atm", C.c_double), ("w_max", C.c_double), ("c2p_tol", C.c_double),
+    ]
+
+
+class SacraDiag(C.Structure):
+    _fields_ = [("H_L2", C.c_double), ("M_L2", C.c_double * 3), ("Mb", C.c_double), ("J", C.c_double),
+                ("rho_max", C.c_double), ("n_c2p_fail", C.c_double), ("n_fallback", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libsacra2d.so not built (run paper_2502_03223_gb300.build.build()): " + path)
+    L = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.sacra_arena_bytes.argtypes = [C.POINTER(SacraParams), C.POINTER(C.c_size_t)]
+    L.sacra_init_grid.argtypes = [C.POINTER(SacraParams), vp, vp, C.c_size_t, C.POINTER(vp)]
+    L.sacra_set_initial_data.argtypes = [vp, C.c_int, C.c_int, dp, C.c_int]
+    L.sacra_regrid_ghosts.argtypes = [vp, C.c_int, C.c_int, C.c_double]
+    L.sacra_rk_stage.argtypes = [vp, C.c_int, C.c_double]
+    L.sacra_step.argtypes = [vp, C.c_double, C.c_int, C.c_int]
+    L.sacra_read_state.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, C.c_size_t]
+    L.sacra_constraints.argtypes = [vp, C.POINTER(SacraDiag)]
+    L.sacra_sync.argtypes = [vp]
+    L.sacra_launch_count.argtypes = [vp]
+    L.sacra_launch_count.restype = C.c_longlong
+    L.sacra_destroy.argtypes = [vp]
+    L.sacra_last_error.argtypes = [vp]
+    L.sacra_last_error.restype = C.c_char_p
+    for name in ("sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
+                 "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def make_params(cfg) -> SacraParams:
+    p = SacraParams()
+    p.n_levels = int(cfg.n_levels); p.nx = int(cfg.nx); p.nz = int(cfg.nz)
+    p.geometry = int(cfg.geometry); p.evolve_spacetime = int(cfg.evolve_spacetime)
+    p.solver = int(cfg.solver); p.rk = int(cfg.rk); p.c2p_maxit = int(cfg.c2p_maxit)
+    p.dx0 = float(cfg.dx0); p.dz0 = float(cfg.dz0)
+    p.kappa = float(cfg.kappa); p.eta_B = float(cfg.eta_B); p.eps_ko = float(cfg.eps_ko); p.r_z4 = float(cfg.r_z4)
+    p.K = float(cfg.K); p.Gamma = float(cfg.Gamma); p.Gamma_th = float(cfg.Gamma_th)
+    p.rho_atm = float(cfg.rho_atm); p.w_max = float(cfg.w_max); p.c2p_tol = float(cfg.c2p_tol)
+    return p
+
+
+class SacraError(RuntimeError):
+    pass
+
+
+class Sacra:
+    """One level hierarchy on the GPU.  The arena is a torch uint8 tensor on
+    the current CUDA device and the work runs on ``stream`` (a
+    torch.cuda.Stream; default: a new non-default stream, so that whole steps
+    can be captured in CUDA graphs)."""
+
+    def __init__(self, cfg, stream=None):
+        import torch
+        self.cfg = cfg
+        self._L = load()
+        self._p = make_params(cfg)
+        nbytes = C.c_size_t(0)
+        if self._L.sacra_arena_bytes(C.byref(self._p), C.byref(nbytes)) != SACRA_OK:
+            raise SacraError("configuration rejected by sacra_arena_bytes")
+        self.arena_bytes = nbytes.value
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._arena = torch.empty(self.arena_bytes, dtype=torch.uint8, device="cuda")
+        ctx = C.c_void_p()
+        rc = self._L.sacra_init_grid(C.byref(self._p), C.c_void_p(self.stream.cuda_stream),
+                                     C.c_void_p(self._arena.data_ptr()), nbytes, C.byref(ctx))
+        if rc != SACRA_OK:
+            raise SacraError("sacra_init_grid failed with status %d" % rc)
+        self._c = ctx
+        self.px, self.pz = cfg.nx + 16, cfg.nz + 16
+
+    def _chk(self, rc, what):
+        if rc != SACRA_OK:
+            msg = self._L.sacra_last_error(self._c).decode()
+            raise SacraError("%s failed (%d): %s" % (what, rc, msg))
+
+    def close(self):
+        if getattr(self, "_c", None):
+            self._L.sacra_destroy(self._c)
+            self._c = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_initial_data(self, level, kind, planes):
+        a = np.ascontiguousarray(planes, dtype=np.float64)
+        assert a.size == 30 * self.px * self.pz
+        self._chk(self._L.sacra_set_initial_data(self._c, level, kind, a.ctypes.data_as(C.POINTER(C.c_double)), 30),
+                  "set_initial_data")
+
+    def regrid_ghosts(self, what, stage=0, dt=0.0):
+        self._chk(self._L.sacra_regrid_ghosts(self._c, what, stage, dt), "regrid_ghosts")
+
+    def fill(self, stage, dt):
+        self.regrid_ghosts(FILL, stage, dt)
+
+    def restrict_reflux(self):
+        self.regrid_ghosts(RESTRICT_REFLUX)
+
+    def rk_stage(self, stage, dt):
+        self._chk(self._L.sacra_rk_stage(self._c, stage, dt), "rk_stage")
+
+    def step(self, dt, n=1, use_graph=False):
+        self._chk(self._L.sacra_step(self._c, dt, n, 1 if use_graph else 0), "step")
+
+    def sync(self):
+        self._chk(self._L.sacra_sync(self._c), "sync")
+
+    def read(self, level, which, field, padded=True):
+        n = self.px * self.pz if padded else self.cfg.nx * self.cfg.nz
+        out = np.zeros(n)
+        self._chk(self._L.sacra_read_state(self._c, level, which, field, out.ctypes.data_as(C.POINTER(C.c_double)), n),
+                  "read_state")
+        return out.reshape((self.pz, self.px) if padded else (self.cfg.nz, self.cfg.nx))
+
+    def constraints(self):
+        d = SacraDiag()
+        self._chk(self._L.sacra_constraints(self._c, C.byref(d)), "constraints")
+        return np.array([d.H_L2, d.M_L2[0], d.M_L2[1], d.M_L2[2], d.Mb, d.J, d.rho_max, d.n_c2p_fail, d.n_fallback])
+
+    @property
+    def launch_count(self):
+        return self._L.sacra_launch_count(self._c)
+
+    @property
+    def n_stages(self):
+        return 4 if self.cfg.rk == 0 else 3

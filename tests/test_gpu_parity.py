@@ -1,0 +1,146 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle on the
+same seeded inputs: per cell and per RK stage within 1e-11 relative (with a
+field-scaled floor near zero), and the rest-mass density L1 norm within 1e-9
+after 100 steps."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_03223_gb300 import sacra2d as S
+from paper_2502_03223_gb300 import workloads as W
+
+from gpu_common import G, both, compare_level
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2502_03223_gb300 import build as B
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def _stagewise(cfg, datas, steps=1, tol=1e-11):
+    gpu, orc = both(cfg, datas)
+    worst = 0.0
+    for it in range(steps):
+        for s in range(cfg.n_stages):
+            gpu.fill(s, cfg.dt); orc.fill(s, cfg.dt)
+            gpu.rk_stage(s, cfg.dt); orc.stage(s, cfg.dt)
+            for l in range(cfg.n_levels):
+                worst = max(worst, compare_level(gpu, orc, l, tol, which=(S.STATE_STAGE, S.PRIMS, S.RHS)
+                                                 if s < cfg.n_stages - 1 else (S.STATE_STEP, S.PRIMS, S.RHS)))
+        gpu.restrict_reflux(); orc.restrict_reflux()
+        for l in range(cfg.n_levels):
+            worst = max(worst, compare_level(gpu, orc, l, tol, which=(S.STATE_STEP, S.PRIMS)))
+    return gpu, orc, worst
+
+
+@pytest.mark.parametrize("solver,nx", [(0, 64), (1, 64), (0, 37)])
+def test_shock_tube_stagewise(solver, nx):
+    cfg = W.shock_tube_config(nx, 5, solver=solver)
+    _, _, worst = _stagewise(cfg, [W.shock_tube_data(cfg)], steps=3)
+    assert worst < 1e-11
+
+
+def test_shock_tube_rho_l1_after_100_steps():
+    cfg = W.config_shock_tube()
+    gpu, orc = both(cfg, [W.shock_tube_data(cfg)])
+    gpu.step(cfg.dt, 100)
+    orc.step(cfg.dt, 100)
+    a = gpu.read(0, S.PRIMS, 0)[G:G + cfg.nz, G:G + cfg.nx]
+    b = orc.read(0, 2, 0)[G:G + cfg.nz, G:G + cfg.nx]
+    assert np.abs(a - b).sum() / np.abs(b).sum() < 1e-9
+    m = gpu.read(0, S.STATE_STEP, 25)[G:G + cfg.nz, G:G + cfg.nx].sum()
+    m0 = W.shock_tube_data(cfg)  # rest mass at t = 0 from the initial primitives (w = 1)
+    assert abs(m - m0[25][G:G + cfg.nz, G:G + cfg.nx].sum()) / m < 1e-13
+
+
+def _tov_small(rk=0, N=32, L=2, dx_fine=0.5, perturb=True, seed=0, solver=0):
+    cfg, tov = W.tov_config("tov_small", rho_c=1.28e-3, n_levels=L, N=N, dx_fine=dx_fine, rk=rk, solver=solver)
+    rng = np.random.default_rng(seed)
+    datas = []
+    for l in range(L):
+        d = W.tov_level_data(cfg, tov, l)
+        if perturb:
+            d[:25] += W.random_metric_perturbation(cfg, l, np.random.default_rng(seed + 100), amp=1e-3)
+            X, Z = W.cell_centres(cfg, l)
+            bump = np.exp(-((X - 3.0) ** 2 + (Z - 2.0) ** 2) / 4.0)
+            d[26] = 0.05 * bump * X / (np.abs(X) + 1.0)
+            d[27] = 0.03 * bump * X / (np.abs(X) + 1.0)
+        datas.append(d)
+    return cfg, datas
+
+
+@pytest.mark.parametrize("rk", [0, 1])
+def test_tov_fmr_stagewise(rk):
+    cfg, datas = _tov_small(rk=rk)
+    _, _, worst = _stagewise(cfg, datas, steps=2)
+    assert worst < 1e-11
+
+
+def test_tov_fmr_tvdlf_and_ragged():
+    cfg, datas = _tov_small(rk=0, N=18, dx_fine=0.9, solver=1)
+    _stagewise(cfg, datas, steps=1)
+
+
+def test_tov_many_steps_and_diagnostics():
+    cfg, datas = _tov_small(rk=0, L=3, N=32, dx_fine=0.5)
+    gpu, orc = both(cfg, datas)
+    gpu.step(cfg.dt, 10)
+    orc.step(cfg.dt, 10)
+    for l in range(cfg.n_levels):
+        a = gpu.read(l, S.PRIMS, 0)[G:G + 32, G:G + 32]
+        b = orc.read(l, 2, 0)[G:G + 32, G:G + 32]
+        assert np.abs(a - b).sum() / np.abs(b).sum() < 1e-10
+    dg, do = gpu.constraints(), orc.diag()
+    assert abs(dg[4] - do[4]) < 1e-12 * do[4]            # rest mass
+    assert abs(dg[0] - do[0]) < 1e-8 * do[0]             # ||H||
+    assert np.allclose(dg[1:4], do[1:4], rtol=1e-7, atol=1e-14)
+    assert dg[6] == pytest.approx(do[6], rel=1e-12)
+
+
+def test_graph_replay_matches_eager_and_is_deterministic():
+    cfg, datas = _tov_small(rk=1)
+    a = S.Sacra(cfg)
+    b = S.Sacra(cfg)
+    for l, d in enumerate(datas):
+        a.set_initial_data(l, S.PRIM_METRIC, d)
+        b.set_initial_data(l, S.PRIM_METRIC, d)
+    a.step(cfg.dt, 5, use_graph=False)
+    b.step(cfg.dt, 5, use_graph=True)
+    for l in range(cfg.n_levels):
+        for f in range(30):
+            assert np.array_equal(a.read(l, S.STATE_STEP, f), b.read(l, S.STATE_STEP, f)), (l, f)
+
+
+def test_recovery_edge_cases_cold_atmosphere_fast():
+    """Cells driven into the cold branch (P below the cold curve), the
+    atmosphere and a fast (w ~ 20) stream: same flags and primitives."""
+    cfg, tov = W.tov_config("edge", rho_c=1.28e-3, n_levels=1, N=48, dx_fine=0.5, rk=0)
+    d = W.tov_level_data(cfg, tov, 0)
+    d[29][G + 3:G + 6, G + 3:G + 6] *= 0.97                 # below the cold curve -> cold recovery
+    d[26][G + 20:G + 24, G + 10:G + 14] = 20.0              # fast stream inside the star
+    gpu, orc = both(cfg, [d])
+    for s in range(cfg.n_stages):
+        gpu.fill(s, cfg.dt); orc.fill(s, cfg.dt)
+        gpu.rk_stage(s, cfg.dt); orc.stage(s, cfg.dt)
+    st_g = gpu.read(0, S.STATUS, 0)
+    st_o = orc.read(0, 4, 0)
+    assert (st_o != 0).any()
+    assert np.mean(st_g != st_o) < 1e-3
+    compare_level(gpu, orc, 0, 1e-11, which=(S.STATE_STEP, S.PRIMS))
+
+
+def test_full_size_tov_stable_one_step():
+    """The benchmark workload (3 levels of 256^2, SSP-RK3) in the launch
+    configuration the benchmark times: one full step, every cell compared."""
+    cfg, tov = W.config_tov_stable()
+    datas = [W.tov_level_data(cfg, tov, l) for l in range(cfg.n_levels)]
+    gpu, orc = both(cfg, datas)
+    gpu.step(cfg.dt, 1, use_graph=True)
+    orc.step(cfg.dt, 1)
+    for l in range(cfg.n_levels):
+        compare_level(gpu, orc, l, 1e-11, which=(S.STATE_STEP, S.PRIMS))
