@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput of the SACRA-2D hot path on GB300: cell-updates per second per
+RK stage of Z4c + HLLC GRHD on the fixed-mesh-refinement cartoon grid.
+
+Workload (default): the stable TOV star (K=100, Gamma=2, rho_c=1.28e-3,
+Gamma_th=2, atmosphere 1e-10 of rho_c), equatorial symmetry, 3 FMR levels of
+256^2 cells, finest dx = 0.25, SSP-RK3, FP64.  One step = the whole hot path:
+ghost fill / prolongation, hydro and Z4c right-hand sides, RK combination with
+algebraic constraints and primitive recovery for every stage, then
+restriction + reflux and the constraint diagnostics.  The working set (about
+0.7 GB of FP64 state per step) exceeds the 129 MB L2, so no flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun every rank advances its own replica (the path has no exchange
+step on one level set; weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s per RK stage (Z4c+HLLC), FP64 vs mixed/batched, % of roofline"
+UNIT = "cell-updates/s"
+
+# Algorithmic FLOPs per unit of work, counted on the oracle's plain
+# restatement with its op-counting build (oracle/opcount.cpp), benchmark
+# workload, one RK stage.  Unit: a cell of the update region, a face for the
+# flux kernels, a cell of the plane patch for the cartoon kernel.
+ALG_FLOPS = {
+    "k_flux_x": 1069.2, "k_flux_z": 1069.2, "k_hydro_rhs": 1313.2, "k_cartoon": 7621.7,
+    "k_z4c_derivs": 9882.0, "k_z4c_point": 4197.0, "k_rk_update": 598.0,
+}
+NOMINAL_FP64_TFLOPS = 1.25
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if ws > 1:
+        import torch
+        import torch.distributed as td
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        td.init_process_group(backend=backend)
+        dist = td
+    return dist, rank, ws, local
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock, max clock and throttle
+    reasons of one GPU while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workloads
+
+def workload(name):
+    from paper_2502_03223_gb300 import workloads as W
+    if name == "tov_stable_3x256":
+        cfg, tov = W.config_tov_stable()
+        return cfg, [W.tov_level_data(cfg, tov, l) for l in range(cfg.n_levels)]
+    if name == "migration_5x512":
+        cfg, tov = W.config_migration()
+        return cfg, [W.tov_level_data(cfg, tov, l, p_deplete=0.99) for l in range(cfg.n_levels)]
+    if name == "shock_tube_400x4":
+        cfg = W.config_shock_tube()
+        return cfg, [W.shock_tube_data(cfg)]
+    raise SystemExit("unknown workload " + name)
+
+
+def fp64_peak():
+    """Measured FP64 FMA throughput (TFLOP/s) of this GPU by the probe kernel."""
+    from paper_2502_03223_gb300 import build as B
+    lib = ctypes.CDLL(B.PROBE)
+    lib.sacra_probe_fp64.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    tf, ms = ctypes.c_double(0), ctypes.c_double(0)
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    rc = lib.sacra_probe_fp64(sms * 8, 256, 2048, 5, ctypes.byref(tf), ctypes.byref(ms))
+    return tf.value if rc == 0 else None
+
+
+def read_traffic():
+    """dram bytes per launch of a kernel from the committed ncu summary
+    (profiles/traffic_tov_stable_3x256.txt) if it was taken on the current
+    kernel sources; None otherwise."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_tov_stable_3x256.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2502_03223_gb300", "csrc"))):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(ROOT, "paper_2502_03223_gb300", "csrc", fn), "rb").read())
+    digest = h.hexdigest()[:16]
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) == 4 and not ln.startswith("#"):
+            name, bytes_per_launch, cells_per_launch, src = parts
+            if src == digest:
+                out[name] = (float(bytes_per_launch), float(cells_per_launch))
+    return out
+
+
+# ---------------------------------------------------------------- arms
+
+def oracle_sample(cfg, datas, stages=1):
+    """Time `stages` RK stages (ghost fill + stage) of the whole hierarchy on
+    the CPU oracle (single thread).  Returns (cell-updates, seconds)."""
+    import oracle as O
+    o = O.Oracle(cfg)
+    for l, d in enumerate(datas):
+        o.set_level(l, 0, d)
+    t0 = time.perf_counter()
+    for s in range(stages):
+        o.fill(s % cfg.n_stages, cfg.dt)
+        o.stage(s % cfg.n_stages, cfg.dt)
+    el = time.perf_counter() - t0
+    o.close()
+    return cfg.interior_cells * stages, el
+
+
+def run_reference(args, dist, rank, ws):
+    """The reference arm: the CPU oracle on the host cores, each step one RK
+    stage of the workload (a bounded sample), rank 0 only."""
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    cfg, datas = workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample(cfg, datas, 1)
+    cells = 0
+    el = 0.0
+    for _ in range(args.steps):
+        c, t = oracle_sample(cfg, datas, 1)
+        cells += c
+        el += t
+    value = cells / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "levels": cfg.n_levels, "cells_per_level": [cfg.nx, cfg.nz],
+                       "integrator": "SSP-RK3" if cfg.rk else "RK4", "reference": "CPU oracle (plain FP64 C)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: one RK stage (ghost fill + stage) of the whole %s hierarchy" % cfg.name},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, dist, rank, ws, local):
+    import torch
+    from paper_2502_03223_gb300 import build as B
+    B.build()
+    from paper_2502_03223_gb300 import sacra2d as S
+    torch.cuda.set_device(local)
+    cfg, datas = workload(args.workload)
+    sim = S.Sacra(cfg)
+    for l, d in enumerate(datas):
+        sim.set_initial_data(l, S.PRIM_METRIC, d)
+    dt = cfg.dt
+    cells_per_step = cfg.interior_cells * cfg.n_stages
+
+    def one_step(graph=True):
+        sim.step(dt, 1, use_graph=graph)
+        return sim.constraints()
+
+    for _ in range(args.warmup):
+        one_step()
+    sim.sync()
+    diag0 = sim.constraints()
+
+    # ---- timed region (device time, CUDA events on the library's stream)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    n0 = sim.launch_count
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    for _ in range(args.steps):
+        diag = one_step()
+    ev1.record(sim.stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    launches = sim.launch_count - n0
+    ms_max = max_over_ranks(dist, ms)
+    value = ws * cells_per_step * args.steps / (ms_max * 1e-3)
+
+    # ---- end to end through the C ABI with host buffers: every step the state
+    # of all levels goes host -> device from pinned memory (set_initial_data, RAW),
+    # one step runs, and the diagnostics come back to the host
+    host = []
+    for l in range(cfg.n_levels):
+        buf = torch.empty(30 * sim.px * sim.pz, dtype=torch.float64, pin_memory=True)
+        a = buf.numpy()
+        for f in range(30):
+            a[f * sim.px * sim.pz:(f + 1) * sim.px * sim.pz] = sim.read(l, S.STATE_STEP, f).ravel()
+        host.append(a)
+    e2e_steps = max(3, min(args.steps, 20))
+    h2d = sum(a.nbytes for a in host)
+    d2h = ctypes.sizeof(S.SacraDiag)
+    sim.sync()
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for l in range(cfg.n_levels):
+            sim.set_initial_data(l, S.RAW, host[l])
+        one_step()
+    el = time.perf_counter() - t0
+    el = max_over_ranks(dist, el)
+    e2e = ws * cells_per_step * e2e_steps / el
+
+    # ---- per-kernel device time (eager launches bracketed by CUDA events)
+    sim.profile(True)
+    prof_steps = max(2, min(args.steps, 10))
+    for _ in range(prof_steps):
+        one_step(graph=False)
+    rep = sim.profile_report()
+    sim.profile(False)
+    kern = {k: v for k, v in rep.items()}
+    dom = max((k for k in kern if k in ALG_FLOPS), key=lambda k: kern[k][0])
+    tot_ms, n_launch, n_cells = kern[dom]
+    avg_s = tot_ms * 1e-3 / n_launch
+    units_per_launch = n_cells / n_launch
+    if dom == "k_flux_x":
+        units_per_launch = n_cells / n_launch * 1.0   # faces ~ cells of the region
+    achieved = ALG_FLOPS[dom] * units_per_launch / avg_s / 1e12
+    peak = fp64_peak()
+    traffic = read_traffic().get(dom)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None,
+                "traffic": (traffic[0] / traffic[1] * units_per_launch) if traffic else None,
+                "peak_source": "FP64 FMA probe measured in this run (nominal %.2f TFLOP/s)" % NOMINAL_FP64_TFLOPS,
+                "alg_flops_per_unit": ALG_FLOPS[dom], "avg_launch_ms": avg_s * 1e3,
+                "units_per_launch": units_per_launch,
+                "kernel_share": {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in
+                                 sorted(kern.items(), key=lambda kv: -kv[1][0])[:8]}}
+
+    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        O.build()
+        c, t = oracle_sample(cfg, datas, 1)
+        cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one RK stage (ghost fill + stage) of the whole %s hierarchy, single thread" % cfg.name}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": cfg.name, "levels": cfg.n_levels, "cells_per_level": [cfg.nx, cfg.nz],
+                           "finest_dx": cfg.dx(cfg.n_levels - 1), "integrator": "SSP-RK3" if cfg.rk else "RK4",
+                           "stages_per_step": cfg.n_stages, "cell_updates_per_step": cells_per_step,
+                           "parallelism": "replicas" if ws > 1 else "single",
+                           "l2": "working set > L2 (no flush)", "cuda_graph": True},
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "diag": {"H_L2": diag[0], "Mb": diag[4], "rho_max": diag[6], "Mb_drift": (diag[4] - diag0[4]) / diag0[4]}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="tov_stable_3x256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    dist, rank, ws, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist, rank, ws)
+        else:
+            run_native(args, dist, rank, ws, local)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

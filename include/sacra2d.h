@@ -148,6 +148,17 @@ sacra_status sacra_sync(sacra_ctx *c);
    count their kernels). */
 long long sacra_launch_count(const sacra_ctx *c);
 
+/* Optional per-kernel device timing for measurement.  enable != 0 starts (and
+   resets) recording: every kernel launched outside a CUDA graph is bracketed
+   by CUDA events on the context's stream.  sacra_profile_get reports kernel
+   kind idx (0-based; SACRA_ERR_ARG past the last kind): its name (written to
+   name, at most name_len bytes), the summed device time in ms, the number of
+   launches and the cells (threads' units of work) they processed.  Waits for
+   the stream. */
+sacra_status sacra_profile(sacra_ctx *c, int enable);
+sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_len, double *total_ms,
+                               long long *launches, long long *cells);
+
 void sacra_destroy(sacra_ctx *c);
 const char *sacra_last_error(const sacra_ctx *c);
 

@@ -48,6 +48,37 @@ def build(force: bool = False) -> str:
     return out
 
 
+def build_opcount(force: bool = False) -> str:
+    """Compile the op-counting build of the oracle (oracle/opcount.cpp)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    out = os.path.join(_BUILD, "opcount")
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES + ["orc.h", "opcount.cpp"]]
+    if force or not os.path.exists(out) or any(os.path.getmtime(s) > os.path.getmtime(out) for s in srcs):
+        tmp = out + ".tmp%d" % os.getpid()
+        subprocess.check_call(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-w", "-o", tmp,
+                               os.path.join(_HERE, "opcount.cpp")], cwd=_HERE)
+        os.replace(tmp, out)
+    return out
+
+
+def opcount(cfg, level_data) -> dict:
+    """Algorithmic FLOPs of one RK stage, per face or cell and per phase,
+    counted on the oracle's plain restatement (see opcount.cpp)."""
+    import json
+    import tempfile
+    exe = build_opcount()
+    with tempfile.TemporaryDirectory() as td:
+        files = []
+        for l, d in enumerate(level_data):
+            fn = os.path.join(td, "l%d.bin" % l)
+            np.ascontiguousarray(d, dtype=np.float64).tofile(fn)
+            files.append(fn)
+        args = [exe, str(cfg.n_levels), str(cfg.nx), repr(cfg.dx0), repr(cfg.K), repr(cfg.Gamma), repr(cfg.Gamma_th),
+                repr(cfg.rho_atm), repr(cfg.kappa), repr(cfg.eta_B), repr(cfg.r_z4)] + files
+        out = subprocess.check_output(args, text=True)
+    return json.loads(out)
+
+
 class Params(C.Structure):
     _fields_ = [
         ("n_levels", C.c_int), ("nx", C.c_int), ("nz", C.c_int), ("geometry", C.c_int),

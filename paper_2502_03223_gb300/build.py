@@ -18,6 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["hydro.cu", "z4c.cu", "grid.cu", "capi.cu"]
 HEADERS = ["common.cuh", "z4c.cuh", "kernels.h"]
 LIB = os.path.join(BUILD, "libsacra2d.so")
+PROBE = os.path.join(BUILD, "libsacra_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -65,6 +66,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         tmp = LIB + ".tmp%d" % os.getpid()
         subprocess.check_call([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"])
         os.replace(tmp, LIB)
+    probe_src = os.path.join(CSRC, "probe.cu")
+    if force or _stale(PROBE, [probe_src]):
+        tmp = PROBE + ".tmp%d" % os.getpid()
+        subprocess.check_call([nvcc(), *_flags(), "-shared", "-o", tmp, probe_src, "-lcudart"])
+        os.replace(tmp, PROBE)
     return LIB
 
 

@@ -82,6 +82,22 @@ Layout layout(const sacra_params *p) {
 
 }  // namespace
 
+// kernel kinds for launch counting and the optional per-kernel profile
+enum Kid {
+  K_OUTFLOW, K_OUTER, K_PROLONG, K_PARITY_X, K_PARITY_Z, K_FLUX_X, K_FLUX_Z, K_HYDRO_DIV, K_CARTOON, K_Z4C_DERIVS,
+  K_Z4C_POINT, K_RK_UPDATE, K_RESTRICT, K_REFLUX, K_C2P, K_PRIM2CONS, K_DIAG, K_DIAG_FINAL, K_COUNT
+};
+static const char *kKidName[K_COUNT] = {"k_outflow", "k_outer", "k_prolong", "k_parity_x", "k_parity_z", "k_flux_x",
+                                        "k_flux_z", "k_hydro_rhs", "k_cartoon", "k_z4c_derivs", "k_z4c_point",
+                                        "k_rk_update", "k_restrict", "k_reflux", "k_c2p_region", "k_prim2cons_all",
+                                        "k_diag", "k_diag_final"};
+
+struct ProfRec {
+  int kid;
+  cudaEvent_t a, b;
+  long long cells;
+};
+
 struct sacra_ctx {
   sacra_params prm;
   DevParams dp;
@@ -101,6 +117,12 @@ struct sacra_ctx {
   double gdt[2] = {0.0, 0.0};
   long long glaunch[2] = {0, 0};
   int parity = 0;    // number of register swaps mod 2
+  bool capturing = false;
+  // per-kernel profile (eager launches only)
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
 };
 
 namespace {
@@ -114,6 +136,31 @@ sacra_status cuda_check(sacra_ctx *c, const char *where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, SACRA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
   return SACRA_OK;
+}
+
+cudaEvent_t pool_event(sacra_ctx *c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+// every kernel launch goes through here: count it, and bracket it with
+// events when profiling (not while a graph is being captured)
+template <class F>
+void run(sacra_ctx *c, Kid k, long long cells, F &&launch) {
+  if (c->prof && !c->capturing) {
+    ProfRec r{(int)k, pool_event(c), pool_event(c), cells};
+    cudaEventRecord(r.a, c->stream);
+    launch();
+    cudaEventRecord(r.b, c->stream);
+    c->recs.push_back(r);
+  } else {
+    launch();
+  }
+  ++c->launches;
 }
 
 int n_stages(const sacra_ctx *c) { return c->prm.rk == SACRA_RK4 ? 4 : 3; }
@@ -133,16 +180,28 @@ void region(const sacra_ctx *c, int l, int s, int *jmax, int *kmax) {
   *kmax = c->prm.nz + ext;
 }
 
+void enqueue_parity(sacra_ctx *c, int l, double *U) {
+  const Lev &L = c->lv[l];
+  run(c, K_PARITY_X, 8LL * (L.nz + GH), [&] { launch_parity_x(L, U, c->stream); });
+  run(c, K_PARITY_Z, 8LL * (L.nx + 2 * GH), [&] { launch_parity_z(L, U, c->stream); });
+}
+
 void enqueue_fill(sacra_ctx *c, int s, double dt) {
   for (int l = 0; l < c->prm.n_levels; ++l) {
     double *U = stage_state(c, l, s);
+    const Lev &L = c->lv[l];
     if (c->prm.geometry == SACRA_PLANAR) {
-      launch_outflow(c->lv[l], U, c->stream, &c->launches);
+      run(c, K_OUTFLOW, (long long)L.px * L.pz, [&] { launch_outflow(L, U, c->stream); });
       continue;
     }
-    if (l == 0) launch_outer(c->lv[0], c->lv[0].un, U, stage_c(c, s) * dt, c->stream, &c->launches);
-    else launch_prolong(c->lv[l], c->lv[l - 1], c->dp, U, stage_state(c, l - 1, s), s == 0, c->stream, &c->launches);
-    launch_parity(c->lv[l], U, c->stream, &c->launches);
+    if (l == 0) {
+      run(c, K_OUTER, (long long)(L.nx + GH) * (L.nz + GH) - (long long)L.nx * L.nz,
+          [&] { launch_outer(L, L.un, U, stage_c(c, s) * dt, c->stream); });
+    } else {
+      double *Up = stage_state(c, l - 1, s);
+      run(c, K_PROLONG, 0, [&] { launch_prolong(L, c->lv[l - 1], c->dp, U, Up, s == 0, c->stream); });
+    }
+    enqueue_parity(c, l, U);
   }
 }
 
@@ -168,14 +227,26 @@ void enqueue_stage(sacra_ctx *c, int s, double dt) {
     double *U = stage_state(c, l, s);
     int jmax, kmax;
     region(c, l, s, &jmax, &kmax);
-    launch_hydro_rhs(lv, c->dp, U, jmax, kmax, stage_b(c, s), l < L - 1, l > 0, c->stream, &c->launches);
-    if (c->prm.evolve_spacetime)
-      launch_z4c_rhs(lv, c->dp, U, c->ds, c->tab, kTabStride, jmax, kmax, c->stream, &c->launches);
-    launch_rk_update(lv, c->dp, U, s, dt, jmax, kmax, c->stream, &c->launches);
+    const long long cells = (long long)jmax * kmax;
+    const double wb = stage_b(c, s);
+    const int hc = l < L - 1, hp = l > 0;
+    run(c, K_FLUX_X, cells, [&] { launch_flux_x(lv, c->dp, U, jmax, kmax, wb, hc, hp, c->stream); });
+    run(c, K_FLUX_Z, cells, [&] { launch_flux_z(lv, c->dp, U, jmax, kmax, wb, hc, hp, c->stream); });
+    run(c, K_HYDRO_DIV, cells, [&] { launch_hydro_div(lv, c->dp, U, jmax, kmax, c->stream); });
+    if (c->prm.evolve_spacetime) {
+      if (c->prm.geometry == SACRA_CYLINDRICAL)
+        run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, U, c->tab, kTabStride, c->stream); });
+      run(c, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, c->dp, U, c->ds, jmax, kmax, c->stream); });
+      run(c, K_Z4C_POINT, cells, [&] { launch_z4c_point(lv, c->dp, U, c->ds, jmax, kmax, c->stream); });
+    }
+    run(c, K_RK_UPDATE, cells, [&] { launch_rk_update(lv, c->dp, U, s, dt, jmax, kmax, c->stream); });
   }
   if (s == S - 1) {
-    if (c->prm.geometry == SACRA_CYLINDRICAL)
-      launch_outer(c->lv[0], c->lv[0].un, c->lv[0].us, dt, c->stream, &c->launches);
+    if (c->prm.geometry == SACRA_CYLINDRICAL) {
+      const Lev &L0 = c->lv[0];
+      run(c, K_OUTER, (long long)(L0.nx + GH) * (L0.nz + GH) - (long long)L0.nx * L0.nz,
+          [&] { launch_outer(L0, L0.un, L0.us, dt, c->stream); });
+    }
     swap_registers(c);
   }
 }
@@ -185,13 +256,13 @@ void enqueue_restrict(sacra_ctx *c) {
   if (L < 2) return;
   for (int l = L - 1; l >= 1; --l) {
     Lev &C = c->lv[l], &Pa = c->lv[l - 1];
-    launch_parity(C, C.un, c->stream, &c->launches);
-    launch_restrict(C, Pa, c->stream, &c->launches);
-    launch_reflux(C, Pa, c->dt_step, c->stream, &c->launches);
+    enqueue_parity(c, l, C.un);
     const int nh = Pa.nx / 2;
-    launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, 1, nh, c->stream, &c->launches);
-    launch_c2p_region(Pa, c->dp, Pa.un, nh + 1, nh + 1, 1, nh, c->stream, &c->launches);
-    launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, nh + 1, nh + 1, c->stream, &c->launches);
+    run(c, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, c->stream); });
+    run(c, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, c->dt_step, c->stream); });
+    run(c, K_C2P, (long long)nh * nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, 1, nh, c->stream); });
+    run(c, K_C2P, nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, nh + 1, nh + 1, 1, nh, c->stream); });
+    run(c, K_C2P, nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, nh + 1, nh + 1, c->stream); });
   }
 }
 
@@ -332,11 +403,11 @@ sacra_status sacra_set_initial_data(sacra_ctx *c, int level, int kind, const dou
     for (int v = 0; v < 5; ++v)
       cudaMemcpyAsync(L.prim + (size_t)v * L.P, host + (size_t)(NMET + v) * np, np * 8, cudaMemcpyHostToDevice,
                       c->stream);
-    launch_prim2cons_all(L, c->dp, L.un, c->stream, &c->launches);
+    run(c, K_PRIM2CONS, (long long)np, [&] { launch_prim2cons_all(L, c->dp, L.un, c->stream); });
   } else if (kind == SACRA_RAW) {
     for (int f = 0; f < NST; ++f)
       cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, c->stream);
-    launch_c2p_region(L, c->dp, L.un, 1 - GH, L.nx + GH, 1 - GH, L.nz + GH, c->stream, &c->launches);
+    run(c, K_C2P, (long long)np, [&] { launch_c2p_region(L, c->dp, L.un, 1 - GH, L.nx + GH, 1 - GH, L.nz + GH, c->stream); });
   } else {
     return fail(c, SACRA_ERR_ARG, "unknown kind");
   }
@@ -390,7 +461,9 @@ sacra_status sacra_step(sacra_ctx *c, double dt, int n_steps, int use_graph) {
       const long long before = c->launches;
       if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return cuda_check(c, "graph capture (the stream must be a non-default stream)");
+      c->capturing = true;
       enqueue_step(c, dt);       // swaps the registers on the host side
+      c->capturing = false;
       if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess) return cuda_check(c, "graph capture");
       c->glaunch[par] = c->launches - before;
       c->launches = before;
@@ -455,14 +528,16 @@ sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out) {
   int slot = 0;
   for (int l = 0; l < L; ++l) {
     Lev &lv = c->lv[l];
+    const long long cells = (long long)lv.nx * lv.nz;
     if (c->prm.evolve_spacetime) {
-      launch_cartoon(lv, lv.un, c->tab, kTabStride, c->stream, &c->launches);
-      launch_z4c_derivs(lv, c->dp, lv.un, c->ds, lv.nx, lv.nz, c->stream, &c->launches);
+      run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, lv.un, c->tab, kTabStride, c->stream); });
+      run(c, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, c->dp, lv.un, c->ds, lv.nx, lv.nz, c->stream); });
     }
-    launch_diag(lv, c->dp, c->ds, l < L - 1, c->prm.evolve_spacetime, c->part, slot, c->stream, &c->launches);
+    const int sl = slot;
+    run(c, K_DIAG, cells, [&] { launch_diag(lv, c->dp, c->ds, l < L - 1, c->prm.evolve_spacetime, c->part, sl, c->stream); });
     slot += diag_blocks(lv);
   }
-  launch_diag_final(c->part, slot, c->dout, c->stream, &c->launches);
+  run(c, K_DIAG_FINAL, slot, [&] { launch_diag_final(c->part, slot, c->dout, c->stream); });
   double h[9];
   unsigned long long nfb = 0;
   cudaMemcpyAsync(h, c->dout, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
@@ -486,11 +561,41 @@ sacra_status sacra_sync(sacra_ctx *c) {
 
 long long sacra_launch_count(const sacra_ctx *c) { return c ? c->launches : -1; }
 
+sacra_status sacra_profile(sacra_ctx *c, int enable) {
+  if (!c) return SACRA_ERR_ARG;
+  c->prof = enable != 0;
+  c->recs.clear();
+  c->pool_used = 0;
+  return SACRA_OK;
+}
+
+sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_len, double *total_ms,
+                               long long *launches, long long *cells) {
+  if (!c || idx < 0 || idx >= K_COUNT || !name || name_len == 0) return SACRA_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "profile_get");
+  double ms = 0.0;
+  long long n = 0, cl = 0;
+  for (const ProfRec &r : c->recs) {
+    if (r.kid != idx) continue;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    ms += t;
+    ++n;
+    cl += r.cells;
+  }
+  snprintf(name, name_len, "%s", kKidName[idx]);
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = n;
+  if (cells) *cells = cl;
+  return cuda_check(c, "profile_get");
+}
+
 void sacra_destroy(sacra_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (int i = 0; i < 2; ++i)
     if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   if (c->own_arena) cudaFree(c->arena);
   delete c;
 }

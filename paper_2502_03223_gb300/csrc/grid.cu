@@ -430,63 +430,55 @@ __global__ void k_diag_final(const double *__restrict__ partials, int n, double 
 
 // ---------------------------------------------------------------- host launchers
 
-void launch_parity(const Lev &L, double *U, cudaStream_t s, long long *nl) {
-  dim3 b(8, 32);
-  k_parity_x<<<dim3(1, (L.nz + GH + 31) / 32), b, 0, s>>>(L, U);
-  dim3 b2(32, 8);
-  k_parity_z<<<dim3((L.nx + 2 * GH + 31) / 32, 1), b2, 0, s>>>(L, U);
-  *nl += 2;
+void launch_parity_x(const Lev &L, double *U, cudaStream_t s) {
+  k_parity_x<<<dim3(1, (L.nz + GH + 31) / 32), dim3(8, 32), 0, s>>>(L, U);
 }
 
-void launch_outflow(const Lev &L, double *U, cudaStream_t s, long long *nl) {
+void launch_parity_z(const Lev &L, double *U, cudaStream_t s) {
+  k_parity_z<<<dim3((L.nx + 2 * GH + 31) / 32, 1), dim3(32, 8), 0, s>>>(L, U);
+}
+
+void launch_outflow(const Lev &L, double *U, cudaStream_t s) {
   k_outflow<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(L, U);
-  ++*nl;
 }
 
-void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s, long long *nl) {
+void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s) {
   dim3 b(32, 4), g((L.nx + GH + 31) / 32, (L.nz + GH + 3) / 4);
   k_outer<<<g, b, 0, s>>>(L, Un, U, tau);
-  ++*nl;
 }
 
 void launch_prolong(const Lev &L, const Lev &Pa, const DevParams &p, double *U, const double *Up, int full,
-                    cudaStream_t s, long long *nl) {
+                    cudaStream_t s) {
   dim3 b(32, 4), g((L.nx + GH + 31) / 32, (L.nz + GH + 3) / 4);
   k_prolong<<<g, b, 0, s>>>(L, Pa, p, U, Up, full);
-  ++*nl;
 }
 
 void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, double dt, int jmax, int kmax,
-                      cudaStream_t s, long long *nl) {
+                      cudaStream_t s) {
   dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
   k_rk_update<<<g, b, 0, s>>>(L, p, Ust, stage, dt, jmax, kmax);
-  ++*nl;
 }
 
-void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s, long long *nl) {
+void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s) {
   const int nh = Pa.nx / 2;
   dim3 b(32, 4), g((nh + 31) / 32, (nh + 3) / 4);
   k_restrict<<<g, b, 0, s>>>(C, Pa);
-  ++*nl;
 }
 
-void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s, long long *nl) {
+void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s) {
   const int n = Pa.nx;  // 2 * N/2 cells
   k_reflux<<<(n + 127) / 128, 128, 0, s>>>(C, Pa, dt);
-  ++*nl;
 }
 
 int diag_blocks(const Lev &L) { return (L.nx * L.nz + DIAG_T - 1) / DIAG_T; }
 
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials, int slot,
-                 cudaStream_t s, long long *nl) {
+                 cudaStream_t s) {
   k_diag<<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, covered, evolve, partials + (size_t)slot * DIAG_Q);
-  ++*nl;
 }
 
-void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s, long long *nl) {
+void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s) {
   k_diag_final<<<1, DIAG_T, 0, s>>>(partials, n, out);
-  ++*nl;
 }
 
 }  // namespace sacra

@@ -238,26 +238,27 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
 
 // ---------------------------------------------------------------- host launchers
 
-void launch_hydro_rhs(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
-                      int has_parent, cudaStream_t s, long long *nlaunch) {
-  dim3 b(32, 4);
-  k_flux_x<<<dim3((jmax + 1 + 31) / 32, (kmax + 3) / 4), b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
-  k_flux_z<<<dim3((jmax + 31) / 32, (kmax + 1 + 3) / 4), b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
-  k_hydro_rhs<<<dim3((jmax + 31) / 32, (kmax + 3) / 4), b, 0, s>>>(L, p, U, jmax, kmax);
-  *nlaunch += 3;
+void launch_flux_x(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
+                   int has_parent, cudaStream_t s) {
+  k_flux_x<<<dim3((jmax + 1 + 31) / 32, (kmax + 3) / 4), dim3(32, 4), 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
 }
 
-void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s, long long *nlaunch) {
+void launch_flux_z(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
+                   int has_parent, cudaStream_t s) {
+  k_flux_z<<<dim3((jmax + 31) / 32, (kmax + 1 + 3) / 4), dim3(32, 4), 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+}
+
+void launch_hydro_div(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, cudaStream_t s) {
+  k_hydro_rhs<<<dim3((jmax + 31) / 32, (kmax + 3) / 4), dim3(32, 4), 0, s>>>(L, p, U, jmax, kmax);
+}
+
+void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s) {
   k_prim2cons_all<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(L, p, U);
-  ++*nlaunch;
 }
 
-void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s,
-                       long long *nlaunch) {
-  if (j1 < j0 || k1 < k0) return;
+void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s) {
   dim3 b(32, 4), g((j1 - j0 + 1 + 31) / 32, (k1 - k0 + 1 + 3) / 4);
   k_c2p_region<<<g, b, 0, s>>>(L, p, U, j0, j1, k0, k1);
-  ++*nlaunch;
 }
 
 }  // namespace sacra

@@ -14,31 +14,33 @@ struct GridWeights {
 };
 void set_grid_weights(const GridWeights &w);
 
-void launch_hydro_rhs(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
-                      int has_parent, cudaStream_t s, long long *nlaunch);
-void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s, long long *nlaunch);
-void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s,
-                       long long *nlaunch);
+void launch_flux_x(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
+                   int has_parent, cudaStream_t s);
+void launch_flux_z(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
+                   int has_parent, cudaStream_t s);
+void launch_hydro_div(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, cudaStream_t s);
+void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s);
+void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s);
 
-void launch_z4c_rhs(const Lev &L, const DevParams &p, const double *U, double *DS, const double *tab, int tab_stride,
-                    int jmax, int kmax, cudaStream_t s, long long *nlaunch);
-void launch_cartoon(const Lev &L, const double *U, const double *tab, int tab_stride, cudaStream_t s, long long *nlaunch);
-void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax,
-                       cudaStream_t s, long long *nlaunch);
+void launch_cartoon(const Lev &L, const double *U, const double *tab, int tab_stride, cudaStream_t s);
+void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s);
+void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const double *DS, int jmax, int kmax,
+                      cudaStream_t s);
 int z4c_scratch_planes();
 
-void launch_parity(const Lev &L, double *U, cudaStream_t s, long long *nlaunch);
-void launch_outflow(const Lev &L, double *U, cudaStream_t s, long long *nlaunch);
-void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s, long long *nlaunch);
+void launch_parity_x(const Lev &L, double *U, cudaStream_t s);
+void launch_parity_z(const Lev &L, double *U, cudaStream_t s);
+void launch_outflow(const Lev &L, double *U, cudaStream_t s);
+void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s);
 void launch_prolong(const Lev &L, const Lev &Pa, const DevParams &p, double *U, const double *Up, int full,
-                    cudaStream_t s, long long *nlaunch);
+                    cudaStream_t s);
 void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, double dt, int jmax, int kmax,
-                      cudaStream_t s, long long *nlaunch);
-void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s, long long *nlaunch);
-void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s, long long *nlaunch);
+                      cudaStream_t s);
+void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s);
+void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s);
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials,
-                 int slot, cudaStream_t s, long long *nlaunch);
+                 int slot, cudaStream_t s);
 int diag_blocks(const Lev &L);
-void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s, long long *nlaunch);
+void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s);
 
 }  // namespace sacra

@@ -300,31 +300,20 @@ __global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const dou
 
 // ---------------------------------------------------------------- host launchers
 
-void launch_z4c_rhs(const Lev &L, const DevParams &p, const double *U, double *DS, const double *tab, int tab_stride,
-                    int jmax, int kmax, cudaStream_t s, long long *nlaunch) {
-  const int cyl = p.geometry == SACRA_CYLINDRICAL;
-  if (cyl) {
-    dim3 b(32, 4), g((L.nx + 7 + 31) / 32, (L.nz + 10 + 3) / 4);
-    k_cartoon<<<g, b, 0, s>>>(L, U, tab, tab_stride);
-    ++*nlaunch;
-  }
-  dim3 b2(32, 4), g2((jmax + 31) / 32, (kmax + 3) / 4);
-  k_z4c_derivs<<<g2, b2, 0, s>>>(L, p, U, DS, jmax, kmax, cyl);
-  k_z4c_point<<<g2, b2, 0, s>>>(L, p, U, DS, jmax, kmax);
-  *nlaunch += 2;
+void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const double *DS, int jmax, int kmax,
+                      cudaStream_t s) {
+  dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
+  k_z4c_point<<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax);
 }
 
-void launch_cartoon(const Lev &L, const double *U, const double *tab, int tab_stride, cudaStream_t s, long long *nlaunch) {
+void launch_cartoon(const Lev &L, const double *U, const double *tab, int tab_stride, cudaStream_t s) {
   dim3 b(32, 4), g((L.nx + 7 + 31) / 32, (L.nz + 10 + 3) / 4);
   k_cartoon<<<g, b, 0, s>>>(L, U, tab, tab_stride);
-  ++*nlaunch;
 }
 
-void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s,
-                       long long *nlaunch) {
+void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s) {
   dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
   k_z4c_derivs<<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax, p.geometry == SACRA_CYLINDRICAL);
-  ++*nlaunch;
 }
 
 int z4c_scratch_planes() { return DS_N; }

@@ -25,7 +25,7 @@ STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
 
 EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
            "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync",
-           "sacra_launch_count", "sacra_destroy", "sacra_last_error"]
+           "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_destroy", "sacra_last_error"]
 
 
 class SacraParams(C.Structure):
@@ -68,6 +68,11 @@ def load(path: str = LIB_PATH):
     L.sacra_sync.argtypes = [vp]
     L.sacra_launch_count.argtypes = [vp]
     L.sacra_launch_count.restype = C.c_longlong
+    L.sacra_profile.argtypes = [vp, C.c_int]
+    L.sacra_profile.restype = C.c_int
+    L.sacra_profile_get.argtypes = [vp, C.c_int, C.c_char_p, C.c_size_t, dp, C.POINTER(C.c_longlong),
+                                    C.POINTER(C.c_longlong)]
+    L.sacra_profile_get.restype = C.c_int
     L.sacra_destroy.argtypes = [vp]
     L.sacra_last_error.argtypes = [vp]
     L.sacra_last_error.restype = C.c_char_p
@@ -170,6 +175,24 @@ class Sacra:
         d = SacraDiag()
         self._chk(self._L.sacra_constraints(self._c, C.byref(d)), "constraints")
         return np.array([d.H_L2, d.M_L2[0], d.M_L2[1], d.M_L2[2], d.Mb, d.J, d.rho_max, d.n_c2p_fail, d.n_fallback])
+
+    def profile(self, enable=True):
+        self._chk(self._L.sacra_profile(self._c, 1 if enable else 0), "profile")
+
+    def profile_report(self):
+        """{kernel name: (total ms, launches, cells)} of the launches recorded since profile(True)."""
+        out = {}
+        idx = 0
+        buf = C.create_string_buffer(64)
+        while True:
+            ms = C.c_double(0.0); n = C.c_longlong(0); cells = C.c_longlong(0)
+            rc = self._L.sacra_profile_get(self._c, idx, buf, 64, C.byref(ms), C.byref(n), C.byref(cells))
+            if rc != SACRA_OK:
+                break
+            if n.value:
+                out[buf.value.decode()] = (ms.value, n.value, cells.value)
+            idx += 1
+        return out
 
     @property
     def launch_count(self):

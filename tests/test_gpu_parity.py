@@ -1,7 +1,8 @@
 """Parity of the CUDA library (through the C ABI) with the CPU oracle on the
-same seeded inputs: per cell and per RK stage within 1e-11 relative (with a
-field-scaled floor near zero), and the rest-mass density L1 norm within 1e-9
-after 100 steps."""
+same seeded inputs: per cell and per RK stage within 1e-11 relative, with the
+floor S_group of gpu_common.compare_level for values formed by cancellation,
+and the rest-mass density L1 norm within 1e-9 after 100 steps.  Status flags of
+the primitive recovery agree except where a branch flipped (< 0.1% of cells)."""
 import numpy as np
 import pytest
 
@@ -9,7 +10,7 @@ import oracle as O
 from paper_2502_03223_gb300 import sacra2d as S
 from paper_2502_03223_gb300 import workloads as W
 
-from gpu_common import G, both, compare_level
+from gpu_common import G, both, compare_level, compare_status
 
 pytestmark = pytest.mark.gpu
 
@@ -32,6 +33,7 @@ def _stagewise(cfg, datas, steps=1, tol=1e-11):
             for l in range(cfg.n_levels):
                 worst = max(worst, compare_level(gpu, orc, l, tol, which=(S.STATE_STAGE, S.PRIMS, S.RHS)
                                                  if s < cfg.n_stages - 1 else (S.STATE_STEP, S.PRIMS, S.RHS)))
+                compare_status(gpu, orc, l)
         gpu.restrict_reflux(); orc.restrict_reflux()
         for l in range(cfg.n_levels):
             worst = max(worst, compare_level(gpu, orc, l, tol, which=(S.STATE_STEP, S.PRIMS)))
@@ -130,7 +132,7 @@ def test_recovery_edge_cases_cold_atmosphere_fast():
     st_g = gpu.read(0, S.STATUS, 0)
     st_o = orc.read(0, 4, 0)
     assert (st_o != 0).any()
-    assert np.mean(st_g != st_o) < 1e-3
+    compare_status(gpu, orc, 0)
     compare_level(gpu, orc, 0, 1e-11, which=(S.STATE_STEP, S.PRIMS))
 
 
