@@ -557,10 +557,11 @@ static void rest_weights(int j, int N, int *base, double w[8]) {
 void orc_restrict_reflux(orc_ctx *c) {
   const orc_params *p = &c->p;
   if (p->n_levels < 2) return;
-  for (int l = 0; l < p->n_levels; ++l) parity_fill(c, l, c->lv[l].un);
   for (int l = p->n_levels - 1; l >= 1; --l) {
     orc_level *C = &c->lv[l], *P = &c->lv[l - 1];
     double **Uc = C->un, **Up = P->un;
+    /* the child's axis/equator ghosts mirror its final (already restricted) interior */
+    parity_fill(c, l, Uc);
     int Nh = P->nx / 2;
     for (int k = 1; k <= Nh; ++k)
       for (int j = 1; j <= Nh; ++j) {
@@ -611,6 +612,8 @@ void orc_restrict_reflux(orc_ctx *c) {
     c2p_region(c, l - 1, Up, Nh + 1, Nh + 1, 1, Nh);
     c2p_region(c, l - 1, Up, 1, Nh, Nh + 1, Nh + 1);
   }
+  /* ghosts of the parents mirror their restricted interiors */
+  for (int l = 0; l < p->n_levels - 1; ++l) parity_fill(c, l, c->lv[l].un);
 }
 
 /* ---------------- diagnostics, Sec. II.F.1 ---------------- */

@@ -199,7 +199,8 @@ void enqueue_fill(sacra_ctx *c, int s, double dt) {
           [&] { launch_outer(L, L.un, U, stage_c(c, s) * dt, c->stream); });
     } else {
       double *Up = stage_state(c, l - 1, s);
-      run(c, K_PROLONG, 0, [&] { launch_prolong(L, c->lv[l - 1], c->dp, U, Up, s == 0, c->stream); });
+      run(c, K_PROLONG, prolong_cells(L, s == 0), [&] { launch_prolong(L, c->lv[l - 1], c->dp, U, Up, s == 0, c->stream); });
+      ++c->launches;   // the prolongation is two kernels
     }
     enqueue_parity(c, l, U);
   }
@@ -264,6 +265,8 @@ void enqueue_restrict(sacra_ctx *c) {
     run(c, K_C2P, nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, nh + 1, nh + 1, 1, nh, c->stream); });
     run(c, K_C2P, nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, nh + 1, nh + 1, c->stream); });
   }
+  // the parents' axis/equator ghosts mirror their restricted interiors
+  for (int l = 0; l < L - 1; ++l) enqueue_parity(c, l, c->lv[l].un);
 }
 
 void enqueue_step(sacra_ctx *c, double dt) {

@@ -108,9 +108,16 @@ __device__ inline Sym3 conf_metric(const double *U, size_t P, int id) {
 
 // ------------------------------------------------------------------ EOS (Sec. II.C.3)
 
-__device__ inline double eos_pc(const DevParams &p, double rho) { return p.K == 0.0 ? 0.0 : p.K * pow(rho, p.Gamma); }
+// The FP64 pow is a long instruction sequence on this part; Gamma = 2 (all
+// the neutron-star workloads) takes the exact product instead, rounded the
+// same way as K * pow(rho, 2).
+__device__ inline double eos_pc(const DevParams &p, double rho) {
+  if (p.K == 0.0) return 0.0;
+  return p.Gamma == 2.0 ? p.K * (rho * rho) : p.K * pow(rho, p.Gamma);
+}
 __device__ inline double eos_ec(const DevParams &p, double rho) {
-  return p.K == 0.0 ? 0.0 : p.K * pow(rho, p.Gamma - 1.0) / (p.Gamma - 1.0);
+  if (p.K == 0.0) return 0.0;
+  return p.Gamma == 2.0 ? p.K * rho : p.K * pow(rho, p.Gamma - 1.0) / (p.Gamma - 1.0);
 }
 __device__ inline double eos_p(const DevParams &p, double rho, double eps) {
   return eos_pc(p, rho) + (p.Gamma_th - 1.0) * rho * (eps - eos_ec(p, rho));

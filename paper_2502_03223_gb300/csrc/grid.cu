@@ -106,40 +106,59 @@ __device__ __forceinline__ double minmod(double a, double b) {
   return a * b <= 0.0 ? 0.0 : (fabs(a) < fabs(b) ? a : b);
 }
 
-// Buffer-zone prolongation (Sec. II.D): 8th-order Lagrange (tensor product)
-// for the metric, minmod-limited linear for the primitives, then conserved
-// variables from the primitives.  full: [N+1, N+8], else [N+5, N+8].
-__global__ void k_prolong(Lev L, Lev Pa, DevParams p, double *__restrict__ U, const double *__restrict__ Up, int full) {
-  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
-  const int lo = full ? L.nx + 1 : L.nx + 5;
-  if (j > L.nx + GH || k > L.nz + GH || (j < lo && k < lo)) return;
-  const size_t P = L.P, PP = Pa.P;
-  // parent cell m holding the child centre, and the side of the quarter offset
+// Buffer cells of a level: the L-shaped strip {j >= lo or k >= lo} of
+// [1, N+8]^2 (lo = N+1 at the start of a step, N+5 afterwards), indexed
+// compactly: first the rows k >= lo, then the columns j >= lo below them.
+__device__ __forceinline__ bool buffer_cell(const Lev &L, int lo, int i, int &j, int &k) {
+  const int w = L.nx + GH;                 // cells 1..N+8 in x
+  const int rows = (L.nz + GH) - lo + 1;   // rows lo..N+8
+  const int top = rows * w;
+  if (i < top) {
+    j = 1 + i % w;
+    k = lo + i / w;
+    return true;
+  }
+  i -= top;
+  const int cols = w - lo + 1;             // columns lo..N+8
+  if (i >= cols * (lo - 1)) return false;
+  j = lo + i % cols;
+  k = 1 + i / cols;
+  return true;
+}
+
+// Buffer-zone prolongation of the metric (Sec. II.D): 8th-order Lagrange,
+// tensor product over 8x8 parent cells, one thread per (buffer cell, field).
+__global__ void k_prolong_metric(Lev L, Lev Pa, double *__restrict__ U, const double *__restrict__ Up, int lo) {
+  int j, k;
+  if (!buffer_cell(L, lo, blockIdx.x * blockDim.x + threadIdx.x, j, k)) return;
+  const int f = blockIdx.y;
   const bool ex = (j & 1) == 0, ez = (k & 1) == 0;
   const int mx = ex ? j / 2 : (j + 1) / 2, mz = ez ? k / 2 : (k + 1) / 2;
-  double wx[8], wz[8];
-#pragma unroll
-  for (int n = 0; n < 8; ++n) {
-    wx[n] = ex ? cW.prol[n] : cW.prol[7 - n];
-    wz[n] = ez ? cW.prol[n] : cW.prol[7 - n];
-  }
   const int bx = ex ? mx - 3 : mx - 4, bz = ez ? mz - 3 : mz - 4;
-  const int pc = cid(Pa, mx, mz), pb = cid(Pa, bx, bz);
-  const int d = cid(L, j, k);
-  for (int f = 0; f < NMET; ++f) {
-    const double *u = Up + (size_t)f * PP;
-    const double u0 = u[pc];
-    double s = 0.0;
+  const double *u = Up + (size_t)f * Pa.P;
+  const double u0 = u[cid(Pa, mx, mz)];
+  const int pb = cid(Pa, bx, bz);
+  double s = 0.0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      double r = 0.0;
+  for (int b = 0; b < 8; ++b) {
+    double r = 0.0;
 #pragma unroll
-      for (int a = 0; a < 8; ++a) r += wx[a] * (u[pb + b * Pa.px + a] - u0);
-      s += wz[b] * r;
-    }
-    U[(size_t)f * P + d] = u0 + s;
+    for (int a = 0; a < 8; ++a) r += (ex ? cW.prol[a] : cW.prol[7 - a]) * (u[pb + b * Pa.px + a] - u0);
+    s += (ez ? cW.prol[b] : cW.prol[7 - b]) * r;
   }
+  U[(size_t)f * L.P + cid(L, j, k)] = u0 + s;
+}
+
+// Buffer-zone primitives by minmod-limited linear prolongation, then the
+// conserved variables from them with the prolongated metric.
+__global__ void k_prolong_hydro(Lev L, Lev Pa, DevParams p, double *__restrict__ U, int lo) {
+  int j, k;
+  if (!buffer_cell(L, lo, blockIdx.x * blockDim.x + threadIdx.x, j, k)) return;
+  const size_t P = L.P, PP = Pa.P;
+  const bool ex = (j & 1) == 0, ez = (k & 1) == 0;
+  const int mx = ex ? j / 2 : (j + 1) / 2, mz = ez ? k / 2 : (k + 1) / 2;
+  const int pc = cid(Pa, mx, mz);
+  const int d = cid(L, j, k);
   const double ox = ex ? 0.25 : -0.25, oz = ez ? 0.25 : -0.25;
   double pr[NPRIM];
 #pragma unroll
@@ -447,10 +466,18 @@ void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStr
   k_outer<<<g, b, 0, s>>>(L, Un, U, tau);
 }
 
+int prolong_cells(const Lev &L, int full) {
+  const int lo = full ? L.nx + 1 : L.nx + 5;
+  const int w = L.nx + GH;
+  return ((L.nz + GH) - lo + 1) * w + (w - lo + 1) * (lo - 1);
+}
+
 void launch_prolong(const Lev &L, const Lev &Pa, const DevParams &p, double *U, const double *Up, int full,
                     cudaStream_t s) {
-  dim3 b(32, 4), g((L.nx + GH + 31) / 32, (L.nz + GH + 3) / 4);
-  k_prolong<<<g, b, 0, s>>>(L, Pa, p, U, Up, full);
+  const int lo = full ? L.nx + 1 : L.nx + 5;
+  const int n = prolong_cells(L, full);
+  k_prolong_metric<<<dim3((n + 127) / 128, NMET), 128, 0, s>>>(L, Pa, U, Up, lo);
+  k_prolong_hydro<<<(n + 127) / 128, 128, 0, s>>>(L, Pa, p, U, lo);
 }
 
 void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, double dt, int jmax, int kmax,

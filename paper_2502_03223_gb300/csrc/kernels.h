@@ -32,8 +32,10 @@ void launch_parity_x(const Lev &L, double *U, cudaStream_t s);
 void launch_parity_z(const Lev &L, double *U, cudaStream_t s);
 void launch_outflow(const Lev &L, double *U, cudaStream_t s);
 void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s);
+// two launches: the metric (one thread per buffer cell and field), then the hydro
 void launch_prolong(const Lev &L, const Lev &Pa, const DevParams &p, double *U, const double *Up, int full,
                     cudaStream_t s);
+int prolong_cells(const Lev &L, int full);
 void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, double dt, int jmax, int kmax,
                       cudaStream_t s);
 void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s);
