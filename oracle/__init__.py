@@ -152,6 +152,8 @@ def lib():
             L.orc_ricci_point.argtypes = [_dp, _dp, _dp, _dp]
             L.orc_constraints_point.argtypes = [_dp, _dp, _dp, C.c_double, _dp, _dp, _dp]
             L.orc_matter_point.argtypes = [P, _dp, C.c_double, _dp, _dp, _dp, _dp]
+            L.orc_hydro_source.argtypes = [P, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp, C.c_double, _dp,
+                                           _dp, _dp, _dp, C.c_double, _dp]
             L.orc_stencil_init()
             _lib = L
     return _lib
@@ -245,6 +247,17 @@ def z4c_point(cfg, Q, dQ, ddQ, adv, E, Si, Sij, fz=1.0):
     lib().orc_z4c_point(C.byref(make_params(cfg)), _ptr(Q), _ptr(dQ), _ptr(ddQ), _ptr(adv), float(E), _ptr(Si),
                         _ptr(Sij), float(fz), _ptr(r))
     return r
+
+
+def hydro_source(cfg, prim, alpha, betay, W, h, A, K, dal, db, dW, dh, x=0.0):
+    """Pointwise hydro sources (x > 0 adds the cylindrical geometric term).
+    dal, dW: [2] (x, z); db: [2, 3]; dh: [2, 6]."""
+    arr = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    out = np.zeros(5)
+    pr, hh, AA, da, dbb, dw, dhh = map(arr, (prim, h, A, dal, db, dW, dh))
+    lib().orc_hydro_source(C.byref(make_params(cfg)), _ptr(pr), float(alpha), float(betay), float(W), _ptr(hh),
+                           _ptr(AA), float(K), _ptr(da), _ptr(dbb), _ptr(dw), _ptr(dhh), float(x), _ptr(out))
+    return out
 
 
 def ricci_point(Q, dQ, ddQ):

@@ -10,10 +10,6 @@
 #include <string.h>
 #include "orc.h"
 
-void orc_cartoon_dy(const orc_ctx *c, int l, double **U, double **dy, double **dyy);
-void orc_derivs_cell(const orc_ctx *c, int l, double **U, double **dy, double **dyy, int j, int k,
-                     double Q[O_NMET], double dQ[O_NMET][3], double ddQ[O_NMET][6], double adv[O_NMET]);
-void orc_ko_cell(const orc_ctx *c, int l, double **U, int j, int k, double ko[O_NMET]);
 
 static const double PI = 3.14159265358979323846;
 
@@ -274,6 +270,73 @@ static void face_prims(const orc_level *L, int j, int k, int dir, double pl[5], 
     for (int v = 0; v < 5; ++v) prr[v] = L->prim[pf[v]][cr];
 }
 
+/* Hydro sources at a cell centre (Sec. II.C.1), in the conformal variables:
+   s_S_k = P d_k(alpha W^-3) - W^-3 rho h w^2 [d_k alpha - v_i d_k beta^i
+           + (W^2/2) alpha v_a v_b d_k gt^ab + (alpha/W) v_i v^i d_k W]   (k = x, z)
+   plus alpha W^-3 (S_y vbar^y + P)/x on s_Sx when x > 0 (cylindrical),
+   s_E = W^-3 (alpha K^ij S_ij - rho h w^2 v^i d_i alpha), s_D = s_Sphi = 0.
+   d*[e]: derivatives in e = 0 (x), 1 (z); dh[e][ij]; db[e][i] = d_e beta^i. */
+void orc_hydro_source(const orc_params *p, const double pr[O_NPRIM], double al, double betay, double W,
+                      const double h[6], const double A[6], double K, const double dal[2], const double db[2][3],
+                      const double dW[2], const double dh[2][6], double x, double src[O_NCONS]) {
+  (void)p;
+  static const int S6[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  double g[6] = {1.0 + h[0], h[1], h[2], 1.0 + h[3], h[4], 1.0 + h[5]}, gi[6];
+  orc_inv3(g, gi, 0);
+  double rho = pr[O_RHO], P = pr[O_P];
+  double u[3] = {pr[O_UX], pr[O_UY], pr[O_UZ]};
+  double uu = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) uu += gi[S6[a][b]] * u[a] * u[b];
+  double w = sqrt(1.0 + W * W * uu);
+  double rhw2 = rho * (1.0 + pr[O_EPS] + P / rho) * w * w;
+  double vd[3] = {u[0] / w, u[1] / w, u[2] / w};    /* v_i */
+  double vu[3];                                      /* v^i = W^2 gt^ij v_j */
+  for (int a = 0; a < 3; ++a) {
+    double sum = 0.0;
+    for (int b = 0; b < 3; ++b) sum += gi[S6[a][b]] * vd[b];
+    vu[a] = W * W * sum;
+  }
+  double vv = vd[0] * vu[0] + vd[1] * vu[1] + vd[2] * vu[2];
+  double W3i = 1.0 / (W * W * W);
+  double sk[2];
+  for (int e = 0; e < 2; ++e) {
+    /* d_e gt^ab = -gt^ac gt^bd d_e gt_cd */
+    double vvdg = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double dgi = 0.0;
+        for (int cc = 0; cc < 3; ++cc)
+          for (int d2 = 0; d2 < 3; ++d2) dgi -= gi[S6[a][cc]] * gi[S6[b][d2]] * dh[e][S6[cc][d2]];
+        vvdg += vd[a] * vd[b] * dgi;
+      }
+    double vdb = vd[0] * db[e][0] + vd[1] * db[e][1] + vd[2] * db[e][2];
+    double dalW3 = W3i * dal[e] - 3.0 * al * W3i / W * dW[e];  /* d(alpha W^-3) */
+    sk[e] = P * dalW3 - W3i * rhw2 * (dal[e] - vdb + 0.5 * W * W * al * vvdg + al / W * vv * dW[e]);
+  }
+  /* geometric source (f_Sphi)^phi / varpi = alpha psi^6 (S_y vbar^y + P) / x */
+  double geo = 0.0;
+  if (x > 0.0) {
+    double vbary = vu[1] - betay / al;
+    geo = al * W3i * (rhw2 * vd[1] * vbary + P) / x;
+  }
+  /* K^ij S_ij = rho h w^2 K_ij v^i v^j + P gamma^ij K_ij, K_ij = (At_ij + gt_ij K/3) / W^2 */
+  double Kd[3][3], vKv = 0.0, trK = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Kd[a][b] = (A[S6[a][b]] + g[S6[a][b]] * K / 3.0) / (W * W);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      vKv += vu[a] * vu[b] * Kd[a][b];
+      trK += W * W * gi[S6[a][b]] * Kd[a][b];
+    }
+  double KS = rhw2 * vKv + P * trK;
+  src[O_QD] = 0.0;
+  src[O_QSX] = sk[0] + geo;
+  src[O_QSY] = 0.0;
+  src[O_QSZ] = sk[1];
+  src[O_QE] = W3i * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
+}
+
 static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) {
   orc_level *L = &c->lv[l];
   const orc_params *p = &c->p;
@@ -358,63 +421,12 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
       }
       double pr[O_NPRIM];
       for (int f = 0; f < O_NPRIM; ++f) pr[f] = L->prim[f][id];
-      double rho = pr[O_RHO], P = pr[O_P];
-      double u[3] = {pr[O_UX], pr[O_UY], pr[O_UZ]};
-      double uu = 0.0;
-      for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) uu += gi[S6[a][b]] * u[a] * u[b];
-      double w = sqrt(1.0 + W * W * uu);
-      double rhw2 = rho * (1.0 + pr[O_EPS] + P / rho) * w * w;
-      double vd[3] = {u[0] / w, u[1] / w, u[2] / w};    /* v_i */
-      double vu[3];                                      /* v^i = W^2 gt^ij v_j */
-      for (int a = 0; a < 3; ++a) {
-        double sum = 0.0;
-        for (int b = 0; b < 3; ++b) sum += gi[S6[a][b]] * vd[b];
-        vu[a] = W * W * sum;
-      }
-      double vv = vd[0] * vu[0] + vd[1] * vu[1] + vd[2] * vu[2];
-      double W3i = 1.0 / (W * W * W);
-      double src[2];
-      for (int e = 0; e < 2; ++e) {
-        /* d_e gt^ab = -gt^ac gt^bd d_e gt_cd */
-        double vvdg = 0.0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) {
-            double dgi = 0.0;
-            for (int cc = 0; cc < 3; ++cc)
-              for (int d2 = 0; d2 < 3; ++d2) dgi -= gi[S6[a][cc]] * gi[S6[b][d2]] * dh[e][S6[cc][d2]];
-            vvdg += vd[a] * vd[b] * dgi;
-          }
-        double vdb = vd[0] * db[e][0] + vd[1] * db[e][1] + vd[2] * db[e][2];
-        double dalW3 = W3i * dal[e] - 3.0 * al * W3i / W * dW[e];  /* d(alpha W^-3) */
-        src[e] = P * dalW3 - W3i * rhw2 * (dal[e] - vdb + 0.5 * W * W * al * vvdg + al / W * vv * dW[e]);
-      }
-      /* geometric source (f_Sphi)^phi / varpi = alpha psi^6 (S_y vbar^y + P) / x */
-      double geo = 0.0;
-      if (cyl) {
-        double vbary = vu[1] - U[O_BY][id] / al;
-        geo = al * W3i * (rhw2 * vd[1] * vbary + P) / x;
-      }
-      /* energy source W^-3 (alpha K^ij S_ij - rho h w^2 v^i d_i alpha) */
-      double K = U[O_KH][id] + 2.0 * U[O_TH][id];
       double A[6];
       for (int a = 0; a < 6; ++a) A[a] = U[O_AXX + a][id];
-      double KS = 0.0;  /* K^ij S_ij = rho h w^2 K^ij v_i v_j + P K */
-      {
-        double Kd[3][3], vKv = 0.0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) Kd[a][b] = (A[S6[a][b]] + g[S6[a][b]] * K / 3.0) / (W * W);
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) vKv += vu[a] * vu[b] * Kd[a][b];
-        KS = rhw2 * vKv + P * K;
-      }
-      double sE = W3i * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
-
-      L->rhs[O_NMET + O_QD][id] = -div[O_QD];
-      L->rhs[O_NMET + O_QSX][id] = src[0] + geo - div[O_QSX];
-      L->rhs[O_NMET + O_QSY][id] = -div[O_QSY];
-      L->rhs[O_NMET + O_QSZ][id] = src[1] - div[O_QSZ];
-      L->rhs[O_NMET + O_QE][id] = sE - div[O_QE];
+      double K = U[O_KH][id] + 2.0 * U[O_TH][id];
+      double src[O_NCONS];
+      orc_hydro_source(p, pr, al, U[O_BY][id], W, h, A, K, dal, db, dW, dh, cyl ? x : 0.0, src);
+      for (int v = 0; v < O_NCONS; ++v) L->rhs[O_NMET + v][id] = src[v] - div[v];
     }
 }
 

@@ -135,12 +135,22 @@ int main(int argc, char **argv) {
   const double hydro_all = (double)oc::g.total();
   long long nzf = (long long)N * (N + 1);
   const double div_flops = (hydro_all - face_flops * (nfaces + nzf)) / cells;
-  // cartoon planes (d_y, d_yy of all fields), per cell of the computed patch
+  // the derivatives the right-hand side needs: first derivatives of W, h_ij,
+  // Khat, Gt^i, Theta, alpha, beta^i; second derivatives of W, h_ij, alpha,
+  // beta^i; planes of every field whose d_y or d_yy enters (all but the
+  // scalars Khat and Theta, whose y-derivatives vanish)
+  int need1[O_NMET] = {0}, need2[O_NMET] = {0}, needp[O_NMET];
+  const int f1[] = {O_W, O_HXX, O_HXY, O_HXZ, O_HYY, O_HYZ, O_HZZ, O_KH, O_GX, O_GY, O_GZ, O_TH, O_AL, O_BX, O_BY, O_BZ};
+  const int f2[] = {O_W, O_HXX, O_HXY, O_HXZ, O_HYY, O_HYZ, O_HZZ, O_AL, O_BX, O_BY, O_BZ};
+  for (int f : f1) need1[f] = 1;
+  for (int f : f2) need2[f] = 1;
+  for (int f = 0; f < O_NMET; ++f) needp[f] = (f == O_KH || f == O_TH) ? 0 : 1;
+  // cartoon planes (d_y, d_yy), per cell of the computed patch
   size_t n = np;
   Real *dy[O_NMET], *dyy[O_NMET];
   for (int f = 0; f < O_NMET; ++f) { dy[f] = (Real *)calloc(n, sizeof(Real)); dyy[f] = (Real *)calloc(n, sizeof(Real)); }
   oc::g = base;
-  orc_cartoon_dy(c, l, U, dy, dyy);
+  orc_cartoon_dy_mask(c, l, U, dy, dyy, needp);
   const long long cart_cells = (long long)(N + 7) * (N + 10);
   const double cart_flops = (double)oc::g.total() / cart_cells;
   // derivatives + advection + KO, per cell
@@ -148,7 +158,7 @@ int main(int argc, char **argv) {
   for (int k = 1; k <= N; ++k)
     for (int j = 1; j <= N; ++j) {
       Real Q[O_NMET], dQ[O_NMET][3], ddQ[O_NMET][6], adv[O_NMET], ko[O_NMET];
-      orc_derivs_cell(c, l, U, dy, dyy, j, k, Q, dQ, ddQ, adv);
+      orc_derivs_cell_mask(c, l, U, dy, dyy, j, k, need1, need2, Q, dQ, ddQ, adv);
       orc_ko_cell(c, l, U, j, k, ko);
     }
   const double deriv_flops = (double)oc::g.total() / cells;

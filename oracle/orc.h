@@ -109,8 +109,14 @@ void orc_z4c_point(const orc_params *p, const double Q[O_NMET], const double dQ[
 void orc_constraints_point(const double Q[O_NMET], const double dQ[O_NMET][3], const double ddQ[O_NMET][6],
                            double E, const double Si[3], double *H, double M[3]);
 void orc_ricci_point(const double Q[O_NMET], const double dQ[O_NMET][3], const double ddQ[O_NMET][6], double Rij[6]);
-void orc_derivs_level(const orc_ctx *c, int l, double **U, int j, int k, int cartoon_edge,
-                      double dQ[O_NMET][3], double ddQ[O_NMET][6], double adv[O_NMET]);
+void orc_cartoon_dy(const orc_ctx *c, int l, double **U, double **dy, double **dyy);
+void orc_cartoon_dy_mask(const orc_ctx *c, int l, double **U, double **dy, double **dyy, const int *need);
+void orc_derivs_cell(const orc_ctx *c, int l, double **U, double **dy, double **dyy, int j, int k,
+                     double Q[O_NMET], double dQ[O_NMET][3], double ddQ[O_NMET][6], double adv[O_NMET]);
+void orc_derivs_cell_mask(const orc_ctx *c, int l, double **U, double **dy, double **dyy, int j, int k,
+                          const int *need1, const int *need2, double Q[O_NMET], double dQ[O_NMET][3],
+                          double ddQ[O_NMET][6], double adv[O_NMET]);
+void orc_ko_cell(const orc_ctx *c, int l, double **U, int j, int k, double ko[O_NMET]);
 void orc_matter_point(const orc_params *p, const double pr[O_NPRIM], double W, const double h[6],
                       double *E, double Si[3], double Sij[6]);
 int orc_field_parity_x(int f);
@@ -119,6 +125,9 @@ int orc_prim_parity_x(int f);
 int orc_prim_parity_z(int f);
 
 /* ---- grid.c ---- */
+void orc_hydro_source(const orc_params *p, const double pr[O_NPRIM], double al, double betay, double W,
+                      const double h[6], const double A[6], double K, const double dal[2], const double db[2][3],
+                      const double dW[2], const double dh[2][6], double x, double src[O_NCONS]);
 orc_ctx *orc_create(const orc_params *p);
 void orc_destroy(orc_ctx *c);
 

@@ -70,55 +70,86 @@ static void rotate_ten(double c, double s, const double *in, double *out, int b)
   out[b + 5] = tzz;
 }
 
-/* Values of all metric fields at (x_j, m dy, z_k), dy = dx, m in -3..3.
-   For j >= 1: Lagrange interpolation with the nine points x_{j-4..j+4} at
-   varpi = sqrt(x_j^2 + (m dy)^2), then rotation by phi with cos phi = x/varpi,
-   sin phi = m dy/varpi.  For j <= 0 the value is the rotation by pi of the
-   point (x_{1-j}, -m dy). */
-static void cartoon_point(const orc_ctx *c, int l, double **U, int j, int k, int m, double out[O_NMET]) {
-  const orc_level *L = &c->lv[l];
-  if (m == 0) {
-    for (int f = 0; f < O_NMET; ++f) out[f] = U[f][oidx(L, j, k)];
-    return;
-  }
-  if (j <= 0) {
-    cartoon_point(c, l, U, 1 - j, k, -m, out);
-    for (int f = 0; f < O_NMET; ++f) out[f] *= orc_field_parity_x(f);
-    return;
-  }
-  double x = (j - 0.5) * L->dx, y = m * L->dx;
-  double vp = sqrt(x * x + y * y);
-  double nodes[9], w[9];
+/* Interpolation weights of the cartoon planes (Sec. II.B.2): for x_j and the
+   plane m dy (dy = dx), the nine Lagrange weights on x_{j-4..j+4} at
+   varpi = sqrt(x_j^2 + (m dy)^2) and cos, sin of the azimuth phi of the point;
+   level independent, computed once for j in [1, jmax]. */
+typedef struct { double w[9], cs, sn; } cartoon_coef;
+
+static cartoon_coef *cartoon_table(int jmax) {
+  cartoon_coef *t = (cartoon_coef *)calloc((size_t)(jmax + 1) * 3, sizeof(cartoon_coef));
+  double nodes[9];
   for (int n = 0; n < 9; ++n) nodes[n] = n - 4;
-  orc_lagrange(9, nodes, (vp - x) / L->dx, w);
+  for (int j = 1; j <= jmax; ++j)
+    for (int m = 1; m <= 3; ++m) {
+      cartoon_coef *e = &t[j * 3 + (m - 1)];
+      double x = j - 0.5, y = m;
+      double vp = sqrt(x * x + y * y);
+      orc_lagrange(9, nodes, vp - x, e->w);
+      e->cs = x / vp;
+      e->sn = y / vp;
+    }
+  return t;
+}
+
+/* Values of the metric fields on the planes y = +m dy and y = -m dy at
+   (x_j, z_k), m in 1..3: Lagrange interpolation with x_{j-4..j+4} at varpi
+   (the same for both planes), rotated by +phi and -phi.  For j <= 0 the
+   values are the rotation by pi of the points (x_{1-j}, -+m dy). */
+static void cartoon_planes(const orc_ctx *c, int l, double **U, const cartoon_coef *tab, int j, int k, int m,
+                           double plus[O_NMET], double minus[O_NMET], const int *need) {
+  const orc_level *L = &c->lv[l];
+  if (j <= 0) {
+    cartoon_planes(c, l, U, tab, 1 - j, k, m, minus, plus, need);
+    for (int f = 0; f < O_NMET; ++f) {
+      plus[f] *= orc_field_parity_x(f);
+      minus[f] *= orc_field_parity_x(f);
+    }
+    return;
+  }
+  const cartoon_coef *e = &tab[j * 3 + (m - 1)];
   double base[O_NMET];
   for (int f = 0; f < O_NMET; ++f) {
+    base[f] = 0.0;
+    if (need && !need[f]) continue;
     /* sum_n w_n Q_n written as Q_j + sum_n w_n (Q_n - Q_j) (the weights sum to 1) */
     double q0 = U[f][oidx(L, j, k)], s = 0.0;
-    for (int n = 0; n < 9; ++n) s += w[n] * (U[f][oidx(L, j - 4 + n, k)] - q0);
+    for (int n = 0; n < 9; ++n) s += e->w[n] * (U[f][oidx(L, j - 4 + n, k)] - q0);
     base[f] = q0 + s;
   }
-  double cs = x / vp, sn = y / vp;
-  out[O_W] = base[O_W]; out[O_KH] = base[O_KH]; out[O_TH] = base[O_TH]; out[O_AL] = base[O_AL];
-  rotate_vec(cs, sn, base, out, O_GX, O_GY, O_GZ);
-  rotate_vec(cs, sn, base, out, O_BX, O_BY, O_BZ);
-  rotate_vec(cs, sn, base, out, O_BBX, O_BBY, O_BBZ);
-  rotate_ten(cs, sn, base, out, O_HXX);
-  rotate_ten(cs, sn, base, out, O_AXX);
+  for (int sgn = 0; sgn < 2; ++sgn) {
+    double *out = sgn == 0 ? plus : minus;
+    double sn = sgn == 0 ? e->sn : -e->sn;
+    out[O_W] = base[O_W]; out[O_KH] = base[O_KH]; out[O_TH] = base[O_TH]; out[O_AL] = base[O_AL];
+    rotate_vec(e->cs, sn, base, out, O_GX, O_GY, O_GZ);
+    rotate_vec(e->cs, sn, base, out, O_BX, O_BY, O_BZ);
+    rotate_vec(e->cs, sn, base, out, O_BBX, O_BBY, O_BBZ);
+    rotate_ten(e->cs, sn, base, out, O_HXX);
+    rotate_ten(e->cs, sn, base, out, O_AXX);
+  }
 }
 
 /* d_y Q and d_yy Q from the planes by 6th-order central differences (dy = dx),
    on j in [-2, nx+4], k in [-2, nz+7]; entries outside stay zero. */
 void orc_cartoon_dy(const orc_ctx *c, int l, double **U, double **dy, double **dyy) {
+  orc_cartoon_dy_mask(c, l, U, dy, dyy, NULL);
+}
+
+/* as orc_cartoon_dy, for the fields with need[f] != 0 only (need = NULL: all);
+   the op counter uses it to count the planes the right-hand side needs */
+void orc_cartoon_dy_mask(const orc_ctx *c, int l, double **U, double **dy, double **dyy, const int *need) {
   const orc_level *L = &c->lv[l];
   size_t n = (size_t)L->px * L->pz;
   for (int f = 0; f < O_NMET; ++f) { memset(dy[f], 0, n * sizeof(double)); memset(dyy[f], 0, n * sizeof(double)); }
+  cartoon_coef *tab = cartoon_table(L->nx + 4);
   double pl[7][O_NMET];
   for (int k = -2; k <= L->nz + 7; ++k)
     for (int j = -2; j <= L->nx + 4; ++j) {
-      for (int m = -3; m <= 3; ++m) cartoon_point(c, l, U, j, k, m, pl[m + 3]);
       int id = oidx(L, j, k);
+      for (int f = 0; f < O_NMET; ++f) pl[3][f] = U[f][id];
+      for (int m = 1; m <= 3; ++m) cartoon_planes(c, l, U, tab, j, k, m, pl[3 + m], pl[3 - m], need);
       for (int f = 0; f < O_NMET; ++f) {
+        if (need && !need[f]) continue;
         /* difference form: the weights of a derivative sum to zero */
         double s1 = 0.0, s2 = 0.0;
         for (int m = 0; m < 7; ++m) {
@@ -129,6 +160,7 @@ void orc_cartoon_dy(const orc_ctx *c, int l, double **U, double **dy, double **d
         dyy[f][id] = s2 / (L->dx * L->dx);
       }
     }
+  free(tab);
 }
 
 /* ---------------- derivatives at one cell ---------------- */
@@ -160,6 +192,15 @@ static void cartoon_edge_xy(const double Q[O_NMET], const double dQ[O_NMET][3], 
    planar geometry, where d_y = 0). */
 void orc_derivs_cell(const orc_ctx *c, int l, double **U, double **dy, double **dyy, int j, int k,
                      double Q[O_NMET], double dQ[O_NMET][3], double ddQ[O_NMET][6], double adv[O_NMET]) {
+  orc_derivs_cell_mask(c, l, U, dy, dyy, j, k, NULL, NULL, Q, dQ, ddQ, adv);
+}
+
+/* as orc_derivs_cell, computing first derivatives only where need1[f] and
+   second derivatives only where need2[f] (NULL: all; others left zero); the
+   op counter uses it to count the derivatives the right-hand side needs */
+void orc_derivs_cell_mask(const orc_ctx *c, int l, double **U, double **dy, double **dyy, int j, int k,
+                          const int *need1, const int *need2, double Q[O_NMET], double dQ[O_NMET][3],
+                          double ddQ[O_NMET][6], double adv[O_NMET]) {
   const orc_level *L = &c->lv[l];
   double dx = L->dx, dz = L->dz;
   int id = oidx(L, j, k);
@@ -167,36 +208,53 @@ void orc_derivs_cell(const orc_ctx *c, int l, double **U, double **dy, double **
     const double *u = U[f];
     double u0 = u[id];
     Q[f] = u0;
+    for (int a = 0; a < 3; ++a) dQ[f][a] = 0.0;
+    for (int a = 0; a < 6; ++a) ddQ[f][a] = 0.0;
+    int n1 = !need1 || need1[f], n2 = !need2 || need2[f];
     /* all stencils in difference form sum_n c_n (u_n - u_0): exact zero on constants */
-    double sx = 0, sz = 0, sxx = 0, szz = 0, sxz = 0;
-    for (int n = -3; n <= 3; ++n) {
-      sx += orc_c1[n + 3] * (u[oidx(L, j + n, k)] - u0);
-      sz += orc_c1[n + 3] * (u[oidx(L, j, k + n)] - u0);
-      sxx += orc_c2[n + 3] * (u[oidx(L, j + n, k)] - u0);
-      szz += orc_c2[n + 3] * (u[oidx(L, j, k + n)] - u0);
-      for (int m = -3; m <= 3; ++m) sxz += orc_c1[n + 3] * orc_c1[m + 3] * (u[oidx(L, j + n, k + m)] - u0);
+    if (n1) {
+      double sx = 0, sz = 0;
+      for (int n = -3; n <= 3; ++n) {
+        sx += orc_c1[n + 3] * (u[oidx(L, j + n, k)] - u0);
+        sz += orc_c1[n + 3] * (u[oidx(L, j, k + n)] - u0);
+      }
+      dQ[f][0] = sx / dx;
+      dQ[f][2] = sz / dz;
     }
-    dQ[f][0] = sx / dx;
-    dQ[f][2] = sz / dz;
-    ddQ[f][0] = sxx / (dx * dx);
-    ddQ[f][5] = szz / (dz * dz);
-    ddQ[f][2] = sxz / (dx * dz);
+    if (n2) {
+      double sxx = 0, szz = 0, sxz = 0;
+      for (int n = -3; n <= 3; ++n) {
+        sxx += orc_c2[n + 3] * (u[oidx(L, j + n, k)] - u0);
+        szz += orc_c2[n + 3] * (u[oidx(L, j, k + n)] - u0);
+        for (int m = -3; m <= 3; ++m) sxz += orc_c1[n + 3] * orc_c1[m + 3] * (u[oidx(L, j + n, k + m)] - u0);
+      }
+      ddQ[f][0] = sxx / (dx * dx);
+      ddQ[f][5] = szz / (dz * dz);
+      ddQ[f][2] = sxz / (dx * dz);
+    }
     if (dy) {
       dQ[f][1] = dy[f][id];
-      ddQ[f][3] = dyy[f][id];
-      double sxy = 0, syz = 0, d0 = dy[f][id];
-      for (int n = -3; n <= 3; ++n) {
-        sxy += orc_c1[n + 3] * (dy[f][oidx(L, j + n, k)] - d0);
-        syz += orc_c1[n + 3] * (dy[f][oidx(L, j, k + n)] - d0);
+      if (n2) {
+        ddQ[f][3] = dyy[f][id];
+        double sxy = 0, syz = 0, d0 = dy[f][id];
+        if (!y_zero(f))
+          for (int n = -3; n <= 3; ++n) {
+            sxy += orc_c1[n + 3] * (dy[f][oidx(L, j + n, k)] - d0);
+            syz += orc_c1[n + 3] * (dy[f][oidx(L, j, k + n)] - d0);
+          }
+        ddQ[f][1] = y_zero(f) ? 0.0 : sxy / dx;
+        ddQ[f][4] = y_zero(f) ? 0.0 : syz / dz;
       }
-      ddQ[f][1] = y_zero(f) ? 0.0 : sxy / dx;
-      ddQ[f][4] = y_zero(f) ? 0.0 : syz / dz;
-    } else {
-      dQ[f][1] = 0.0;
-      ddQ[f][1] = ddQ[f][3] = ddQ[f][4] = 0.0;
     }
   }
-  if (dy && j > L->nx) cartoon_edge_xy(Q, dQ, (j - 0.5) * dx, ddQ);
+  if (dy && j > L->nx) {
+    /* the edge formula needs d_x of the tensor/vector components */
+    double ddQe[O_NMET][6];
+    memcpy(ddQe, ddQ, sizeof(ddQe));
+    cartoon_edge_xy(Q, dQ, (j - 0.5) * dx, ddQe);
+    for (int f = 0; f < O_NMET; ++f)
+      if (!need2 || need2[f]) ddQ[f][1] = ddQe[f][1];
+  }
 
   /* advection: 6th-order lopsided in x and z, upwind with the sign of beta;
      central (from the planes) in y */

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
     const double vbary = vu[1] - U[(size_t)fBY * P + id] / al;
     geo = al * iW3 * (rhw2 * vd[1] * vbary + Pp) / x;
   }
-  // K^ij S_ij = rho h w^2 K_ij v^i v^j + P K, K_ij = (At_ij + gt_ij K/3) / W^2
+  // K^ij S_ij = rho h w^2 K_ij v^i v^j + P gamma^ij K_ij, K_ij = (At_ij + gt_ij K/3) / W^2
   const double K = U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id];
   Sym3 Kd;
   Kd.xx = (U[(size_t)fAXX * P + id] + g.xx * K / 3.0) * iW * iW;
@@ -188,7 +188,10 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
   Kd.yy = (U[(size_t)fAYY * P + id] + g.yy * K / 3.0) * iW * iW;
   Kd.yz = (U[(size_t)fAYZ * P + id] + g.yz * K / 3.0) * iW * iW;
   Kd.zz = (U[(size_t)fAZZ * P + id] + g.zz * K / 3.0) * iW * iW;
-  const double KS = rhw2 * s3quad(Kd, vu, vu) + Pp * K;
+  // gamma^ij K_ij = W^2 gt^ij K_ij (equal to K when At is trace-free)
+  const double trK = W * W * (gi.xx * Kd.xx + gi.yy * Kd.yy + gi.zz * Kd.zz
+                              + 2.0 * (gi.xy * Kd.xy + gi.xz * Kd.xz + gi.yz * Kd.yz));
+  const double KS = rhw2 * s3quad(Kd, vu, vu) + Pp * trK;
   const double sE = iW3 * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
   L.rhs[(size_t)fQD * P + id] = -div[0];
   L.rhs[(size_t)fQSX * P + id] = src[0] + geo - div[1];

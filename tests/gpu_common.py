@@ -29,11 +29,15 @@ STATE_GROUPS = [[0, 1, 2, 3, 4, 5, 6, 18],            # W, h_ij, alpha (dimensio
                 [14, 15, 16],                         # Gt^i
                 [19, 20, 21, 22, 23, 24],             # beta^i, B^i
                 [25, 26, 28, 29],                     # q_D, q_Sx, q_Sz, q_E
-                [27]]                                 # q_Sy (x q_Sy in cylindrical geometry)
+                [27]]                                 # q_Sy (x q_Sy in cylindrical geometry: x * group 5)
 PRIM_GROUPS = [[0], [1, 2, 3], [4], [5]]              # rho, u_i, P, eps
 
 
-def group_scale(planes, groups, f):
+def group_scale(planes, groups, f, xmax=1.0):
+    if groups is STATE_GROUPS and f == 27:
+        # q_Sphi = x q_Sy: x times the momentum / energy scale
+        return max(float(np.max(np.abs(planes[27]))),
+                   xmax * max(float(np.max(np.abs(planes[i]))) for i in (25, 26, 28, 29)))
     for g in groups:
         if f in g:
             return max(float(np.max(np.abs(planes[i]))) for i in g)
@@ -52,9 +56,11 @@ def compare_level(gpu, orc, level, tol=1e-11, which=(0, 1, 2), max_frac=1e-3, re
         A = [gpu.read(level, w, f) for f in range(nf)]
         B = [orc.read(level, w, f) for f in range(nf)]
         groups = PRIM_GROUPS if prim else STATE_GROUPS
+        cfg = gpu.cfg
+        xmax = max(1.0, (cfg.nx + 8) * cfg.dx(level)) if cfg.geometry == 1 else 1.0
         for f in range(nf):
             a, b = A[f], B[f]
-            sg = group_scale(B, groups, f)
+            sg = group_scale(B, groups, f, xmax)
             if prim and f in (1, 2, 3):
                 sg = max(sg, 1.0)          # velocities: units of c
             scale = np.maximum(np.abs(b), sg)
