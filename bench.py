@@ -172,25 +172,27 @@ def fp64_peak():
 
 
 def read_traffic():
-    """dram bytes per launch of a kernel from the committed ncu summary
-    (profiles/traffic_tov_stable_3x256.txt) if it was taken on the current
-    kernel sources; None otherwise."""
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    (profiles/traffic_tov_stable_3x256.txt), kept only if the kernel's sources
+    still hash to the recorded value (else the counters are stale)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic_tov_stable_3x256.txt")
     out = {}
     if not os.path.exists(path):
         return out
-    h = hashlib.sha256()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2502_03223_gb300", "csrc"))):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(ROOT, "paper_2502_03223_gb300", "csrc", fn), "rb").read())
-    digest = h.hexdigest()[:16]
     for ln in open(path):
         parts = ln.split()
-        if len(parts) == 4 and not ln.startswith("#"):
-            name, bytes_per_launch, cells_per_launch, src = parts
-            if src == digest:
-                out[name] = (float(bytes_per_launch), float(cells_per_launch))
+        if len(parts) != 5 or ln.startswith("#"):
+            continue
+        name, bytes_per_launch, cells_per_launch, digest, files = parts
+        h = hashlib.sha256()
+        try:
+            for fn in files.split(","):
+                h.update(open(os.path.join(ROOT, "paper_2502_03223_gb300", "csrc", fn), "rb").read())
+        except OSError:
+            continue
+        if h.hexdigest()[:16] == digest:
+            out[name] = (float(bytes_per_launch), float(cells_per_launch))
     return out
 
 
