@@ -159,6 +159,25 @@ sacra_status sacra_profile(sacra_ctx *c, int enable);
 sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_len, double *total_ms,
                                long long *launches, long long *cells);
 
+/* Hydro right-hand side of one level without allocating anything (the paper
+   has no counterpart: this serves callers that cannot call cudaMalloc, e.g.
+   when a host framework's memory pool already owns the device or allocation
+   is not allowed where the call is made).  Same arithmetic as the hydro part
+   of sacra_rk_stage on the region [1, nx] x [1, nz]: face fluxes (PPM,
+   tetrad HLLC/TVDLF), flux divergence and sources; no flux registers.
+   state: DEVICE, 30 padded planes of px*pz doubles (plane stride exactly
+   px*pz), ghosts filled; prims: DEVICE, 6 planes; rhs_out: DEVICE, 5 planes
+   (d_t q_D, q_Sx, q_Sy, q_Sz, q_E), written on the region.  Work is queued on
+   cuda_stream.  px*pz must not exceed SACRA_NOALLOC_MAX_PLANE (up to 256 x 256
+   interior cells), else SACRA_ERR_ARG.  The face-flux scratch is one
+   file-scope device array per GPU (about 5.9 MB, held until the process
+   exits); its device address is looked up on the first call on each device,
+   so that first call should come before any stream capture.  Every call
+   shares the array: calls that overlap on the GPU race (serialize them). */
+#define SACRA_NOALLOC_MAX_PLANE 73984
+sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level, const double *state, const double *prims,
+                                     double *rhs_out, void *cuda_stream);
+
 void sacra_destroy(sacra_ctx *c);
 const char *sacra_last_error(const sacra_ctx *c);
 

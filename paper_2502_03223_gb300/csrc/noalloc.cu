@@ -1,0 +1,85 @@
+// Allocation-free variant of the hydro right-hand side of one level.
+//
+// Some callers cannot call cudaMalloc: code that embeds this library inside
+// a host application whose memory pool already owns the device (a framework
+// caching allocator, a pre-reserved simulation arena), or that runs where
+// allocation is not allowed or its latency is not acceptable.  For them this
+// entry point computes the same face fluxes and flux divergence with sources
+// as the hydro part of sacra_rk_stage, with its scratch (the face fluxes) in
+// a file-scope static device array instead of an arena.  The caller passes
+// inputs and outputs only; nothing is allocated or freed.
+#include <string.h>
+
+#include "kernels.h"
+
+using namespace sacra;
+
+namespace {
+
+constexpr size_t kMaxPlane = SACRA_NOALLOC_MAX_PLANE;   // padded plane of at most 256 x 256 interior cells
+constexpr size_t kScratchDoubles = 2 * NCONS * kMaxPlane + 32;   // x and z face fluxes + a counter
+
+// Shared by every call on a device and kept between calls; every GPU that
+// loads the library holds it (about 5.9 MB) until the process exits.
+static __device__ __align__(256) double g_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+double *g_scratch_addr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level, const double *state,
+                                                const double *prims, double *rhs_out, void *cuda_stream) {
+  if (!p || !state || !prims || !rhs_out) return SACRA_ERR_ARG;
+  if (level < 0 || level >= p->n_levels || p->nx < 8 || p->nz < 4) return SACRA_ERR_ARG;
+  if (p->geometry != SACRA_PLANAR && p->geometry != SACRA_CYLINDRICAL) return SACRA_ERR_ARG;
+  if (p->solver != SACRA_HLLC && p->solver != SACRA_TVDLF) return SACRA_ERR_ARG;
+  if (!(p->dx0 > 0) || !(p->dz0 > 0) || !(p->Gamma_th > 1.0)) return SACRA_ERR_ARG;
+  const size_t px = (size_t)p->nx + 2 * GH, pz = (size_t)p->nz + 2 * GH;
+  if (px * pz > kMaxPlane) return SACRA_ERR_ARG;    // beyond the static scratch
+
+  // set-up, once per device and with that device current: the device address
+  // of the static array (its host-side name is only a stand-in)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return SACRA_ERR_CUDA;
+  }
+  if (!g_scratch_addr[dev]) {
+    double *addr = nullptr;
+    if (cudaGetSymbolAddress((void **)&addr, g_scratch) != cudaSuccess || !addr) {
+      cudaGetLastError();
+      return SACRA_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = addr;
+  }
+  double *scratch = g_scratch_addr[dev];
+
+  DevParams d;
+  memset(&d, 0, sizeof(d));
+  d.geometry = p->geometry; d.evolve = p->evolve_spacetime; d.solver = p->solver; d.rk = p->rk;
+  d.c2p_maxit = p->c2p_maxit; d.n_levels = p->n_levels;
+  d.K = p->K; d.Gamma = p->Gamma; d.Gamma_th = p->Gamma_th; d.rho_atm = p->rho_atm; d.w_max = p->w_max;
+  d.c2p_tol = p->c2p_tol; d.kappa = p->kappa; d.eta_B = p->eta_B; d.eps_ko = p->eps_ko; d.r_z4 = p->r_z4;
+
+  const size_t P = px * pz;   // the caller's plane stride
+  Lev L;
+  memset(&L, 0, sizeof(L));
+  L.nx = p->nx; L.nz = p->nz; L.px = (int)px; L.pz = (int)pz; L.rw = 0;
+  L.dx = p->dx0 / (double)(1 << level);
+  L.dz = p->dz0 / (double)(1 << level);
+  L.P = P;
+  L.un = const_cast<double *>(state);
+  L.prim = const_cast<double *>(prims);
+  L.fx = scratch;
+  L.fz = scratch + NCONS * P;
+  L.rhs = rhs_out - (size_t)fQD * P;       // the kernels write planes fQD..fQE of rhs
+  L.nfb = reinterpret_cast<unsigned long long *>(scratch + 2 * NCONS * kMaxPlane);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // every face a divergence reads is written first, so the scratch needs no clearing
+  launch_flux_x(L, d, state, p->nx, p->nz, 0.0, 0, 0, s);
+  launch_flux_z(L, d, state, p->nx, p->nz, 0.0, 0, 0, s);
+  launch_hydro_div(L, d, state, p->nx, p->nz, s);
+  if (cudaGetLastError() != cudaSuccess) return SACRA_ERR_CUDA;
+  return SACRA_OK;
+}

@@ -25,7 +25,8 @@ STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
 
 EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
            "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync",
-           "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_destroy", "sacra_last_error"]
+           "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_destroy",
+           "sacra_last_error"]
 
 
 class SacraParams(C.Structure):
@@ -73,6 +74,8 @@ def load(path: str = LIB_PATH):
     L.sacra_profile_get.argtypes = [vp, C.c_int, C.c_char_p, C.c_size_t, dp, C.POINTER(C.c_longlong),
                                     C.POINTER(C.c_longlong)]
     L.sacra_profile_get.restype = C.c_int
+    L.sacra_hydro_rhs_noalloc.argtypes = [C.POINTER(SacraParams), C.c_int, vp, vp, vp, vp]
+    L.sacra_hydro_rhs_noalloc.restype = C.c_int
     L.sacra_destroy.argtypes = [vp]
     L.sacra_last_error.argtypes = [vp]
     L.sacra_last_error.restype = C.c_char_p
@@ -93,6 +96,14 @@ def make_params(cfg) -> SacraParams:
     p.K = float(cfg.K); p.Gamma = float(cfg.Gamma); p.Gamma_th = float(cfg.Gamma_th)
     p.rho_atm = float(cfg.rho_atm); p.w_max = float(cfg.w_max); p.c2p_tol = float(cfg.c2p_tol)
     return p
+
+
+def hydro_rhs_noalloc(cfg, level, state_ptr, prims_ptr, rhs_ptr, stream_ptr=0):
+    """sacra_hydro_rhs_noalloc on device pointers (integers); returns the status."""
+    L = load()
+    p = make_params(cfg)
+    return L.sacra_hydro_rhs_noalloc(C.byref(p), int(level), C.c_void_p(state_ptr), C.c_void_p(prims_ptr),
+                                     C.c_void_p(rhs_ptr), C.c_void_p(stream_ptr))
 
 
 class SacraError(RuntimeError):
