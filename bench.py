@@ -242,7 +242,83 @@ def run_reference(args, dist, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(sim, dt, steps, dist):
+    """K graph-replayed steps (plus the constraint diagnostics) bracketed by a
+    barrier and a device synchronize, timed by CUDA events on the library's
+    stream.  Returns (ms, launches, last diagnostics, clocks)."""
+    import torch
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    n0 = sim.launch_count
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(sim.stream)
+    diag = None
+    for _ in range(steps):
+        sim.step(dt, 1, use_graph=True)
+        diag = sim.constraints()
+    ev1.record(sim.stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    return ev0.elapsed_time(ev1), sim.launch_count - n0, diag, clocks
+
+
+def errors_vs_oracle(cfg, datas, sims, steps=1):
+    """Advance the oracle and each simulation `steps` steps from the same
+    initial data; per simulation the rest-mass density L1 error relative to
+    the oracle and, per output field, the largest error relative to the scale
+    of the field's physical group (interior cells of every level)."""
+    import oracle as O
+    from paper_2502_03223_gb300 import sacra2d as S
+    from paper_2502_03223_gb300.workloads import CONS_NAMES, MET_NAMES
+    # physical groups sharing one scale: dimensionless metric, curvature, Gt^i,
+    # shift, hydro (q_Sy: x_max times the hydro scale, as q_Sphi = x q_Sy)
+    groups = [[0, 1, 2, 3, 4, 5, 6, 18], [7, 8, 9, 10, 11, 12, 13, 17], [14, 15, 16],
+              [19, 20, 21, 22, 23, 24], [25, 26, 28, 29]]
+
+    def group_scale(B, f, xmax):
+        if f == 27:
+            return max(float(np.max(np.abs(B[27]))), xmax * max(float(np.max(np.abs(B[i]))) for i in groups[4]))
+        g_ = next(g_ for g_ in groups if f in g_)
+        return max(float(np.max(np.abs(B[i]))) for i in g_)
+
+    names = MET_NAMES + CONS_NAMES
+    o = O.Oracle(cfg)
+    for l, d in enumerate(datas):
+        o.set_level(l, 0, d)
+    o.step(cfg.dt, steps)
+    g = 8
+    out = []
+    for sim in sims:
+        for l, d in enumerate(datas):
+            sim.set_initial_data(l, S.PRIM_METRIC, d)
+        sim.step(cfg.dt, steps, use_graph=False)
+        num = den = 0.0
+        worst = {}
+        for l in range(cfg.n_levels):
+            sl = (slice(g, g + cfg.nz), slice(g, g + cfg.nx))
+            a = sim.read(l, S.PRIMS, 0)[sl]
+            b = o.read(l, 2, 0)[sl]
+            num += float(np.abs(a - b).sum())
+            den += float(np.abs(b).sum())
+            B = [o.read(l, 0, f) for f in range(30)]
+            xmax = (cfg.nx + 8) * cfg.dx(l) if cfg.geometry == 1 else 1.0
+            for f in range(30):
+                sg = group_scale(B, f, xmax)
+                e = float(np.max(np.abs(sim.read(l, S.STATE_STEP, f)[sl] - B[f][sl]))) / sg if sg > 0 else 0.0
+                worst[names[f]] = max(worst.get(names[f], 0.0), e)
+        out.append({"rho_l1_rel": num / den, "steps": steps,
+                    "max_group_rel": {k: float("%.3g" % v) for k, v in worst.items()}})
+    o.close()
+    return out
+
+
 def run_native(args, dist, rank, ws, local):
+    import dataclasses
     import torch
     from paper_2502_03223_gb300 import build as B
     B.build()
@@ -265,25 +341,26 @@ def run_native(args, dist, rank, ws, local):
     diag0 = sim.constraints()
 
     # ---- timed region (device time, CUDA events on the library's stream)
-    sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
-    n0 = sim.launch_count
-    barrier(dist)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(sim.stream)
-    for _ in range(args.steps):
-        diag = one_step()
-    ev1.record(sim.stream)
-    ev1.synchronize()
-    torch.cuda.synchronize()
-    barrier(dist)
-    clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
-    launches = sim.launch_count - n0
+    ms, launches, diag, clocks = timed_steps(sim, dt, args.steps, dist)
     ms_max = max_over_ranks(dist, ms)
     value = ws * cells_per_step * args.steps / (ms_max * 1e-3)
+
+    # ---- the mixed-precision form of the same step, timed the same way
+    mcfg = dataclasses.replace(cfg, precision=S.MIXED)
+    msim = S.Sacra(mcfg)
+    for l, d in enumerate(datas):
+        msim.set_initial_data(l, S.PRIM_METRIC, d)
+    for _ in range(args.warmup):
+        msim.step(dt, 1, use_graph=True)
+        msim.constraints()
+    msim.sync()
+    mms, mlaunches, _, mclocks = timed_steps(msim, dt, args.steps, dist)
+    mms_max = max_over_ranks(dist, mms)
+    mvalue = ws * cells_per_step * args.steps / (mms_max * 1e-3)
+    mixed = {"value": mvalue, "unit": UNIT, "ms_per_step": mms_max / args.steps, "speedup_vs_fp64": mvalue / value,
+             "gpu_launches": mlaunches, "clocks": mclocks,
+             "arith": "FP32 reconstruction, Riemann solver, hydro sources and Z4c algebra; FP64 finite "
+                      "differences, primitive recovery, algebraic constraints, RK and flux accumulation"}
 
     # ---- end to end through the C ABI with host buffers: every step the state
     # of all levels goes host -> device from pinned memory (set_initial_data, RAW),
@@ -343,6 +420,12 @@ def run_native(args, dist, rank, ws, local):
         c, t = oracle_sample(cfg, datas, 1)
         cpu = {"value": c / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "one RK stage (ghost fill + stage) of the whole %s hierarchy, single thread" % cfg.name}
+        if not args.no_errors:
+            # each output's error against the FP64 oracle after one step from the initial data
+            e64, emx = errors_vs_oracle(cfg, datas, [sim, msim], steps=1)
+            mixed["err_vs_oracle"] = emx
+            mixed["fp64_err_vs_oracle"] = {"rho_l1_rel": e64["rho_l1_rel"],
+                                           "max_group_rel": max(e64["max_group_rel"].values())}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -355,6 +438,7 @@ def run_native(args, dist, rank, ws, local):
                            "l2": "working set > L2 (no flush)", "cuda_graph": True},
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "mixed": mixed,
                 "diag": {"H_L2": diag[0], "Mb": diag[4], "rho_max": diag[6], "Mb_drift": (diag[4] - diag0[4]) / diag0[4]}}
         print(json.dumps(line), flush=True)
 
@@ -367,6 +451,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="tov_stable_3x256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-errors", action="store_true", help="skip the per-output error report against the oracle")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist, rank, ws, local = dist_setup()

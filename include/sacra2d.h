@@ -57,6 +57,14 @@ typedef enum {
 enum { SACRA_PLANAR = 0, SACRA_CYLINDRICAL = 1 };
 enum { SACRA_HLLC = 0, SACRA_TVDLF = 1 };
 enum { SACRA_RK4 = 0, SACRA_SSPRK3 = 1 };
+/* precision: FP64 everywhere, or an OR of the parts whose arithmetic runs in FP32 */
+enum {
+  SACRA_FP64 = 0,
+  SACRA_MIXED_FLUX = 1,      /* PPM reconstruction, face metric, tetrad HLLC / TVDLF flux */
+  SACRA_MIXED_SOURCES = 2,   /* geometric and gravitational hydro sources (the divergence stays FP64) */
+  SACRA_MIXED_Z4C = 4,       /* cartoon planes, weighted stencil sums and the pointwise Z4c right-hand side */
+  SACRA_MIXED = 7
+};
 enum { SACRA_PRIM_METRIC = 0, SACRA_RAW = 1 };
 enum { SACRA_FILL = 0, SACRA_RESTRICT_REFLUX = 1 };
 enum { SACRA_STATE_STEP = 0, SACRA_STATE_STAGE = 1, SACRA_PRIMS = 2, SACRA_RHS = 3, SACRA_STATUS = 4 };
@@ -73,7 +81,9 @@ typedef struct {
   int solver;            /* SACRA_HLLC (with TVDLF fallback) or SACRA_TVDLF */
   int rk;                /* SACRA_RK4 (the paper's integrator) or SACRA_SSPRK3 */
   int c2p_maxit;         /* iteration cap of the primitive recovery */
-  int reserved;
+  int precision;         /* SACRA_FP64, or an OR of SACRA_MIXED_* bits (SACRA_MIXED: all of them); every finite
+                            difference of the state, the primitive recovery, the algebraic constraints, the flux
+                            divergence, the RK combination and the flux registers stay FP64 in every mode */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;   /* cold polytrope P = K rho^Gamma plus thermal Gamma_th law (Sec. II.C.3) */

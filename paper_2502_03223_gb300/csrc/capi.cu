@@ -55,6 +55,7 @@ bool valid(const sacra_params *p, std::string *why) {
   if (p->evolve_spacetime && fabs(p->dx0 - p->dz0) > 1e-12 * p->dx0) { *why = "cartoon needs dx0 == dz0"; return false; }
   if (!(p->Gamma_th > 1.0) || (p->K != 0.0 && !(p->Gamma > 1.0))) { *why = "EOS indices must exceed 1"; return false; }
   if (!(p->rho_atm > 0) || !(p->w_max > 1) || !(p->c2p_tol > 0) || p->c2p_maxit < 1) { *why = "bad recovery parameters"; return false; }
+  if (p->precision & ~SACRA_MIXED) { *why = "unknown precision bits"; return false; }
   return true;
 }
 
@@ -236,7 +237,7 @@ void enqueue_stage(sacra_ctx *c, int s, double dt) {
     run(c, K_HYDRO_DIV, cells, [&] { launch_hydro_div(lv, c->dp, U, jmax, kmax, c->stream); });
     if (c->prm.evolve_spacetime) {
       if (c->prm.geometry == SACRA_CYLINDRICAL)
-        run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, U, c->tab, kTabStride, c->stream); });
+        run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, c->dp, U, c->tab, kTabStride, c->stream); });
       run(c, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, c->dp, U, c->ds, jmax, kmax, c->stream); });
       run(c, K_Z4C_POINT, cells, [&] { launch_z4c_point(lv, c->dp, U, c->ds, jmax, kmax, c->stream); });
     }
@@ -323,7 +324,7 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
   }
   DevParams &d = c->dp;
   d.geometry = p->geometry; d.evolve = p->evolve_spacetime; d.solver = p->solver; d.rk = p->rk;
-  d.c2p_maxit = p->c2p_maxit; d.n_levels = p->n_levels;
+  d.c2p_maxit = p->c2p_maxit; d.n_levels = p->n_levels; d.mixed = p->precision & SACRA_MIXED;
   d.K = p->K; d.Gamma = p->Gamma; d.Gamma_th = p->Gamma_th; d.rho_atm = p->rho_atm; d.w_max = p->w_max;
   d.c2p_tol = p->c2p_tol; d.kappa = p->kappa; d.eta_B = p->eta_B; d.eps_ko = p->eps_ko; d.r_z4 = p->r_z4;
 
@@ -533,7 +534,7 @@ sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out) {
     Lev &lv = c->lv[l];
     const long long cells = (long long)lv.nx * lv.nz;
     if (c->prm.evolve_spacetime) {
-      run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, lv.un, c->tab, kTabStride, c->stream); });
+      run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, c->dp, lv.un, c->tab, kTabStride, c->stream); });
       run(c, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, c->dp, lv.un, c->ds, lv.nx, lv.nz, c->stream); });
     }
     const int sl = slot;

@@ -30,6 +30,7 @@ constexpr int ST_NOCONV = 1, ST_COLD = 2, ST_ATM = 4, ST_KRESCALE = 8, ST_BAD = 
 
 struct DevParams {
   int geometry, evolve, solver, rk, c2p_maxit, n_levels;
+  int mixed;             // SACRA_MIXED_* bits: parts whose arithmetic runs in FP32 (FP64 differences and updates)
   double K, Gamma, Gamma_th, rho_atm, w_max, c2p_tol;
   double kappa, eta_B, eps_ko, r_z4;
 };
@@ -52,29 +53,20 @@ __host__ __device__ inline int cid(const Lev &L, int j, int k) { return (k + GH 
 
 // ------------------------------------------------------------------ small tensor helpers
 
-struct Sym3 {
-  double xx, xy, xz, yy, yz, zz;
+template <typename T>
+struct Sym3T {
+  T xx, xy, xz, yy, yz, zz;
 };
+using Sym3 = Sym3T<double>;
 
-__device__ inline double s3get(const Sym3 &m, int i, int j) {
-  const int t = i * 3 + j;
-  switch (t) {
-    case 0: return m.xx;
-    case 1: case 3: return m.xy;
-    case 2: case 6: return m.xz;
-    case 4: return m.yy;
-    case 5: case 7: return m.yz;
-    default: return m.zz;
-  }
-}
-
-__device__ inline Sym3 s3inv(const Sym3 &g, double *detp) {
-  const double cxx = g.yy * g.zz - g.yz * g.yz;
-  const double cxy = g.xz * g.yz - g.xy * g.zz;
-  const double cxz = g.xy * g.yz - g.xz * g.yy;
-  const double det = g.xx * cxx + g.xy * cxy + g.xz * cxz;
-  const double id = 1.0 / det;
-  Sym3 r;
+template <typename T>
+__device__ inline Sym3T<T> s3inv(const Sym3T<T> &g, T *detp) {
+  const T cxx = g.yy * g.zz - g.yz * g.yz;
+  const T cxy = g.xz * g.yz - g.xy * g.zz;
+  const T cxz = g.xy * g.yz - g.xz * g.yy;
+  const T det = g.xx * cxx + g.xy * cxy + g.xz * cxz;
+  const T id = T(1) / det;
+  Sym3T<T> r;
   r.xx = cxx * id; r.xy = cxy * id; r.xz = cxz * id;
   r.yy = (g.xx * g.zz - g.xz * g.xz) * id;
   r.yz = (g.xy * g.xz - g.xx * g.yz) * id;
@@ -84,12 +76,14 @@ __device__ inline Sym3 s3inv(const Sym3 &g, double *detp) {
 }
 
 // a^i b^j m_ij for symmetric m
-__device__ inline double s3quad(const Sym3 &m, const double a[3], const double b[3]) {
+template <typename T>
+__device__ inline T s3quad(const Sym3T<T> &m, const T a[3], const T b[3]) {
   return m.xx * a[0] * b[0] + m.yy * a[1] * b[1] + m.zz * a[2] * b[2]
        + m.xy * (a[0] * b[1] + a[1] * b[0]) + m.xz * (a[0] * b[2] + a[2] * b[0]) + m.yz * (a[1] * b[2] + a[2] * b[1]);
 }
 
-__device__ inline void s3vec(const Sym3 &m, const double a[3], double o[3]) {
+template <typename T>
+__device__ inline void s3vec(const Sym3T<T> &m, const T a[3], T o[3]) {
   o[0] = m.xx * a[0] + m.xy * a[1] + m.xz * a[2];
   o[1] = m.xy * a[0] + m.yy * a[1] + m.yz * a[2];
   o[2] = m.xz * a[0] + m.yz * a[1] + m.zz * a[2];
@@ -110,28 +104,35 @@ __device__ inline Sym3 conf_metric(const double *U, size_t P, int id) {
 
 // The FP64 pow is a long instruction sequence on this part; Gamma = 2 (all
 // the neutron-star workloads) takes the exact product instead, rounded the
-// same way as K * pow(rho, 2).
-__device__ inline double eos_pc(const DevParams &p, double rho) {
-  if (p.K == 0.0) return 0.0;
-  return p.Gamma == 2.0 ? p.K * (rho * rho) : p.K * pow(rho, p.Gamma);
+// same way as K * pow(rho, 2).  Templated on the arithmetic type T (double,
+// or float in the mixed-precision hydro); every constant goes through T(...).
+template <typename T>
+__device__ inline T eos_pc(const DevParams &p, T rho) {
+  if (p.K == 0.0) return T(0);
+  return p.Gamma == 2.0 ? T(p.K) * (rho * rho) : T(p.K) * pow(rho, T(p.Gamma));
 }
-__device__ inline double eos_ec(const DevParams &p, double rho) {
-  if (p.K == 0.0) return 0.0;
-  return p.Gamma == 2.0 ? p.K * rho : p.K * pow(rho, p.Gamma - 1.0) / (p.Gamma - 1.0);
+template <typename T>
+__device__ inline T eos_ec(const DevParams &p, T rho) {
+  if (p.K == 0.0) return T(0);
+  return p.Gamma == 2.0 ? T(p.K) * rho : T(p.K) * pow(rho, T(p.Gamma - 1.0)) / T(p.Gamma - 1.0);
 }
-__device__ inline double eos_p(const DevParams &p, double rho, double eps) {
-  return eos_pc(p, rho) + (p.Gamma_th - 1.0) * rho * (eps - eos_ec(p, rho));
+template <typename T>
+__device__ inline T eos_p(const DevParams &p, T rho, T eps) {
+  return eos_pc(p, rho) + T(p.Gamma_th - 1.0) * rho * (eps - eos_ec(p, rho));
 }
-__device__ inline double eos_eps(const DevParams &p, double rho, double P) {
-  return eos_ec(p, rho) + (P - eos_pc(p, rho)) / ((p.Gamma_th - 1.0) * rho);
+template <typename T>
+__device__ inline T eos_eps(const DevParams &p, T rho, T P) {
+  return eos_ec(p, rho) + (P - eos_pc(p, rho)) / (T(p.Gamma_th - 1.0) * rho);
 }
 // c_s^2 rho h = Gamma P_cold + Gamma_th P_th, clamped to [0, 1)
-__device__ inline double eos_cs2(const DevParams &p, double rho, double eps, double P) {
-  const double pc = eos_pc(p, rho);
-  const double h = 1.0 + eps + P / rho;
-  double c2 = (p.Gamma * pc + p.Gamma_th * (P - pc)) / (rho * h);
-  if (!(c2 > 0.0)) c2 = 0.0;
-  if (c2 >= 1.0) c2 = 1.0 - 1e-15;
+template <typename T>
+__device__ inline T eos_cs2(const DevParams &p, T rho, T eps, T P) {
+  const T pc = eos_pc(p, rho);
+  const T h = T(1) + eps + P / rho;
+  T c2 = (T(p.Gamma) * pc + T(p.Gamma_th) * (P - pc)) / (rho * h);
+  if (!(c2 > T(0))) c2 = T(0);
+  const T cmax = sizeof(T) == 8 ? T(1.0 - 1e-15) : T(1.0f - 1e-6f);
+  if (c2 >= T(1)) c2 = cmax;
   return c2;
 }
 
@@ -140,7 +141,7 @@ __device__ inline double eos_cs2(const DevParams &p, double rho, double eps, dou
 // pr: rho, u_x, u_y, u_z, P, eps; q: psi^6 (D, S_x, S_y or x S_y, S_z, E)
 __device__ inline void prim_to_cons(const DevParams &p, const double pr[NPRIM], double W, const Sym3 &gt, double x,
                                     double q[NCONS]) {
-  const Sym3 gi = s3inv(gt, nullptr);
+  const Sym3 gi = s3inv(gt, (double *)nullptr);
   const double u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
   const double w = sqrt(1.0 + W * W * s3quad(gi, u, u));
   const double rho = pr[pRHO], P = pr[pP];
@@ -217,7 +218,7 @@ __device__ inline void atmosphere(const DevParams &p, double pr[NPRIM]) {
 // had to change.  Returns the status bits.
 __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W, const Sym3 &gt, double x,
                                    double pr[NPRIM]) {
-  const Sym3 gi = s3inv(gt, nullptr);
+  const Sym3 gi = s3inv(gt, (double *)nullptr);
   const double W3 = W * W * W;
   const double D = q[0] * W3;
   double S[3] = {q[1] * W3, q[2] * W3, q[3] * W3};
@@ -279,70 +280,79 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
 
 // ------------------------------------------------------------------ PPM (Colella & Woodward 1984)
 
-__device__ inline double mc_slope(double am, double a0, double ap) {
-  const double dl = a0 - am, dr = ap - a0;
-  if (dl * dr <= 0.0) return 0.0;
-  const double dc = 0.5 * (ap - am);
-  const double lim = fmin(fabs(dc), fmin(2.0 * fabs(dl), 2.0 * fabs(dr)));
-  return dc > 0.0 ? lim : -lim;
+template <typename T>
+__device__ inline T mc_slope(T am, T a0, T ap) {
+  const T dl = a0 - am, dr = ap - a0;
+  if (dl * dr <= T(0)) return T(0);
+  const T dc = T(0.5) * (ap - am);
+  const T lim = fmin(fabs(dc), fmin(T(2) * fabs(dl), T(2) * fabs(dr)));
+  return dc > T(0) ? lim : -lim;
 }
 
-__device__ inline void ppm_limit(double a0, double &aL, double &aR) {
-  if ((aR - a0) * (a0 - aL) <= 0.0) {
+template <typename T>
+__device__ inline void ppm_limit(T a0, T &aL, T &aR) {
+  if ((aR - a0) * (a0 - aL) <= T(0)) {
     aL = a0;
     aR = a0;
     return;
   }
-  const double d = aR - aL;
-  const double a6 = 6.0 * (a0 - 0.5 * (aL + aR));
-  if (d * a6 > d * d) aL = 3.0 * a0 - 2.0 * aR;
-  else if (-d * d > d * a6) aR = 3.0 * a0 - 2.0 * aL;
+  const T d = aR - aL;
+  const T a6 = T(6) * (a0 - T(0.5) * (aL + aR));
+  if (d * a6 > d * d) aL = T(3) * a0 - T(2) * aR;
+  else if (-d * d > d * a6) aR = T(3) * a0 - T(2) * aL;
 }
 
 // face between c[2] and c[3] of the six cells c[0..5]
-__device__ inline void ppm_pair(const double c[6], double &left, double &right) {
-  const double s1 = mc_slope(c[0], c[1], c[2]);
-  const double s2 = mc_slope(c[1], c[2], c[3]);
-  const double s3 = mc_slope(c[2], c[3], c[4]);
-  const double s4 = mc_slope(c[3], c[4], c[5]);
-  const double im = c[1] + 0.5 * (c[2] - c[1]) - (s2 - s1) / 6.0;   // face j-1/2
-  const double i0 = c[2] + 0.5 * (c[3] - c[2]) - (s3 - s2) / 6.0;   // face j+1/2
-  const double ip = c[3] + 0.5 * (c[4] - c[3]) - (s4 - s3) / 6.0;   // face j+3/2
-  double aL = im, aR = i0;
+template <typename T>
+__device__ inline void ppm_pair(const T c[6], T &left, T &right) {
+  const T s1 = mc_slope(c[0], c[1], c[2]);
+  const T s2 = mc_slope(c[1], c[2], c[3]);
+  const T s3 = mc_slope(c[2], c[3], c[4]);
+  const T s4 = mc_slope(c[3], c[4], c[5]);
+  const T im = c[1] + T(0.5) * (c[2] - c[1]) - (s2 - s1) / T(6);   // face j-1/2
+  const T i0 = c[2] + T(0.5) * (c[3] - c[2]) - (s3 - s2) / T(6);   // face j+1/2
+  const T ip = c[3] + T(0.5) * (c[4] - c[3]) - (s4 - s3) / T(6);   // face j+3/2
+  T aL = im, aR = i0;
   ppm_limit(c[2], aL, aR);
   left = aR;
-  double bL = i0, bR = ip;
+  T bL = i0, bR = ip;
   ppm_limit(c[3], bL, bR);
   right = bL;
 }
 
 // ------------------------------------------------------------------ tetrad-frame Riemann solver (Sec. II.C.2)
 
+template <typename T>
 struct SRState {
-  double D, S0, S1, S2, E, P, vx, lm, lp;
+  T D, S0, S1, S2, E, P, vx, lm, lp;
 };
 
-__device__ inline void sr_state(const DevParams &p, double rho, double P, double u0, double u1, double u2, SRState &s) {
-  const double w = sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2);
-  const double eps = eos_eps(p, rho, P);
-  const double h = 1.0 + eps + P / rho;
-  const double c2 = eos_cs2(p, rho, eps, P);
-  const double rhw = rho * h * w;          // rho h w^2 v = rho h w u
+// State of one side in the tetrad frame.  P is the pressure, Poff the value
+// carried in the fluxes: P itself, or P minus a face reference pressure in
+// the mixed-precision form (see face_flux).
+template <typename T>
+__device__ inline void sr_state(const DevParams &p, T rho, T P, T Poff, T u0, T u1, T u2, SRState<T> &s) {
+  const T w = sqrt(T(1) + u0 * u0 + u1 * u1 + u2 * u2);
+  const T eps = eos_eps(p, rho, P);
+  const T h = T(1) + eps + P / rho;
+  const T c2 = eos_cs2(p, rho, eps, P);
+  const T rhw = rho * h * w;          // rho h w^2 v = rho h w u
   s.D = rho * w;
   s.S0 = rhw * u0; s.S1 = rhw * u1; s.S2 = rhw * u2;
   s.E = rhw * w - P;
-  s.P = P;
-  const double v0 = u0 / w, v1 = u1 / w, v2 = u2 / w;
+  s.P = Poff;
+  const T v0 = u0 / w, v1 = u1 / w, v2 = u2 / w;
   s.vx = v0;
-  const double vv = v0 * v0 + v1 * v1 + v2 * v2;
-  double disc = c2 * (1.0 - vv) * (1.0 - vv * c2 - v0 * v0 * (1.0 - c2));
-  disc = disc < 0.0 ? 0.0 : sqrt(disc);
-  const double den = 1.0 / (1.0 - vv * c2);
-  s.lm = (v0 * (1.0 - c2) - disc) * den;
-  s.lp = (v0 * (1.0 - c2) + disc) * den;
+  const T vv = v0 * v0 + v1 * v1 + v2 * v2;
+  T disc = c2 * (T(1) - vv) * (T(1) - vv * c2 - v0 * v0 * (T(1) - c2));
+  disc = disc < T(0) ? T(0) : sqrt(disc);
+  const T den = T(1) / (T(1) - vv * c2);
+  s.lm = (v0 * (T(1) - c2) - disc) * den;
+  s.lp = (v0 * (T(1) - c2) + disc) * den;
 }
 
-__device__ inline void sr_qf(const SRState &s, double q[5], double f[5]) {
+template <typename T>
+__device__ inline void sr_qf(const SRState<T> &s, T q[5], T f[5]) {
   q[0] = s.D; q[1] = s.S0; q[2] = s.S1; q[3] = s.S2; q[4] = s.E;
   f[0] = s.D * s.vx;
   f[1] = s.S0 * s.vx + s.P;
@@ -351,15 +361,26 @@ __device__ inline void sr_qf(const SRState &s, double q[5], double f[5]) {
   f[4] = s.S0;            // (E + P) v^x = S_x
 }
 
-// Flux through a face normal to dir (0 = x, 1 = z).  pl/pr: rho, u_x, u_y,
-// u_z, P; face metric alpha, beta^i, W, gt_ij.  out: alpha psi^6 times the
-// Eulerian flux with Cartesian momentum components.  Returns 1 on a
+// Flux through a face normal to dir (0 = x, 1 = z) in arithmetic T.  pl/pr:
+// rho, u_x, u_y, u_z, P - pref; face metric alpha, beta^i, W, gt_ij.  out:
+// alpha psi^6 times the Eulerian flux with Cartesian momentum components,
+// except that the normal momentum flux lacks alpha W^-3 pref.  Returns 1 on a
 // HLLC -> TVDLF fallback.
-__device__ inline int face_flux(const DevParams &p, int dir, const double pl[5], const double pr[5], double alpha,
-                                const double beta[3], double W, const Sym3 &g, double out[5]) {
+//
+// FP64 (pref = 0): the solver as written in Sec. II.C.2.  FP32 (mixed
+// precision): the same algebra arranged so that rounding scales with what is
+// small in a nearly static flow, not with rho or P: the pressure is carried as
+// an offset from a face reference pref (which the caller adds back in FP64),
+// and the HLLC star states enter as increments q* - q_K, formed from
+// (lambda_c - v_K) and (P_c - P_K) instead of by subtracting two O(rho)
+// numbers.
+template <typename T>
+__device__ inline int face_flux(const DevParams &p, int dir, const T pl[5], const T pr[5], T alpha, const T beta[3],
+                                T W, const Sym3T<T> &g, T out[5], T pref = T(0)) {
+  constexpr bool kDelta = sizeof(T) == 4;
   // work in a frame whose first axis is the face normal: (x,y,z) or (z,x,y)
-  Sym3 m;
-  double bn, uL[3], uR[3];
+  Sym3T<T> m;
+  T bn, uL[3], uR[3];
   if (dir == 0) {
     m = g;
     bn = beta[0];
@@ -371,30 +392,30 @@ __device__ inline int face_flux(const DevParams &p, int dir, const double pl[5],
     uL[0] = pl[3]; uL[1] = pl[1]; uL[2] = pl[2];
     uR[0] = pr[3]; uR[1] = pr[1]; uR[2] = pr[2];
   }
-  const Sym3 mi = s3inv(m, nullptr);
-  const double Bh = rsqrt(mi.xx);                 // 1/sqrt(gt^xx)
-  const double Ch = rsqrt(m.zz);                  // 1/sqrt(gt_zz)
-  const double Dh = Bh * Ch;
+  const Sym3T<T> mi = s3inv(m, (T *)nullptr);
+  const T Bh = rsqrt(mi.xx);                 // 1/sqrt(gt^xx)
+  const T Ch = rsqrt(m.zz);                  // 1/sqrt(gt_zz)
+  const T Dh = Bh * Ch;
   // tetrad components of u: e_(a)^i u_i with the contravariant legs
   //   e_x = W B (gt^xx, gt^xy, gt^xz), e_y = W D (0, gt_zz, -gt_yz), e_z = W C (0, 0, 1)
-  const double tL0 = W * Bh * (mi.xx * uL[0] + mi.xy * uL[1] + mi.xz * uL[2]);
-  const double tL1 = W * Dh * (m.zz * uL[1] - m.yz * uL[2]);
-  const double tL2 = W * Ch * uL[2];
-  const double tR0 = W * Bh * (mi.xx * uR[0] + mi.xy * uR[1] + mi.xz * uR[2]);
-  const double tR1 = W * Dh * (m.zz * uR[1] - m.yz * uR[2]);
-  const double tR2 = W * Ch * uR[2];
-  SRState L, R;
-  sr_state(p, pl[0], pl[4], tL0, tL1, tL2, L);
-  sr_state(p, pr[0], pr[4], tR0, tR1, tR2, R);
-  double qL[5], fL[5], qR[5], fR[5];
+  const T tL0 = W * Bh * (mi.xx * uL[0] + mi.xy * uL[1] + mi.xz * uL[2]);
+  const T tL1 = W * Dh * (m.zz * uL[1] - m.yz * uL[2]);
+  const T tL2 = W * Ch * uL[2];
+  const T tR0 = W * Bh * (mi.xx * uR[0] + mi.xy * uR[1] + mi.xz * uR[2]);
+  const T tR1 = W * Dh * (m.zz * uR[1] - m.yz * uR[2]);
+  const T tR2 = W * Ch * uR[2];
+  SRState<T> L, R;
+  sr_state(p, pl[0], kDelta ? pl[4] + pref : pl[4], pl[4], tL0, tL1, tL2, L);
+  sr_state(p, pr[0], kDelta ? pr[4] + pref : pr[4], pr[4], tR0, tR1, tR2, R);
+  T qL[5], fL[5], qR[5], fR[5];
   sr_qf(L, qL, fL);
   sr_qf(R, qR, fR);
-  const double lamL = fmin(L.lm, R.lm);
-  const double lamR = fmax(L.lp, R.lp);
-  const double sgxx = W * sqrt(mi.xx);
-  const double vint = bn / (alpha * sgxx);
+  const T lamL = fmin(L.lm, R.lm);
+  const T lamR = fmax(L.lp, R.lp);
+  const T sgxx = W * sqrt(mi.xx);
+  const T vint = bn / (alpha * sgxx);
 
-  double F[5];
+  T F[5];
   int fb = 0;
   if (p.solver == SACRA_HLLC) {
     if (lamL >= vint) {
@@ -402,56 +423,73 @@ __device__ inline int face_flux(const DevParams &p, int dir, const double pl[5],
     } else if (lamR <= vint) {
       for (int n = 0; n < 5; ++n) F[n] = fR[n] - vint * qR[n];
     } else {
-      const double idl = 1.0 / (lamR - lamL);
+      const T idl = T(1) / (lamR - lamL);
       // HLL state and flux, only the components the contact speed needs
-      const double Eh = (lamR * qR[4] - lamL * qL[4] + fL[4] - fR[4]) * idl;
-      const double Sh = (lamR * qR[1] - lamL * qL[1] + fL[1] - fR[1]) * idl;
-      const double FEh = (lamR * fL[4] - lamL * fR[4] + lamR * lamL * (qR[4] - qL[4])) * idl;
-      const double FSh = (lamR * fL[1] - lamL * fR[1] + lamR * lamL * (qR[1] - qL[1])) * idl;
-      const double bb = Eh + FSh;
-      const double disc = bb * bb - 4.0 * FEh * Sh;
-      bool bad = !(disc >= 0.0);
-      double lamc = 0.0, Pc = 0.0;
+      const T Eh = (lamR * qR[4] - lamL * qL[4] + fL[4] - fR[4]) * idl;
+      const T Sh = (lamR * qR[1] - lamL * qL[1] + fL[1] - fR[1]) * idl;
+      const T FEh = (lamR * fL[4] - lamL * fR[4] + lamR * lamL * (qR[4] - qL[4])) * idl;
+      const T FSh = (lamR * fL[1] - lamL * fR[1] + lamR * lamL * (qR[1] - qL[1])) * idl;
+      const T bb = Eh + (kDelta ? FSh + pref : FSh);   // FSh (and Pc) are offset by pref in the FP32 form
+      const T disc = bb * bb - T(4) * FEh * Sh;
+      bool bad = !(disc >= T(0));
+      T lamc = T(0), Pc = T(0);
       if (!bad) {
-        lamc = 2.0 * Sh / (bb + sqrt(disc));     // minus root, cancellation free
+        lamc = T(2) * Sh / (bb + sqrt(disc));     // minus root, cancellation free
         Pc = FSh - lamc * FEh;
-        bad = !(lamc >= lamL && lamc <= lamR) || !(Pc > 0.0);
+        bad = !(lamc >= lamL && lamc <= lamR) || !((kDelta ? Pc + pref : Pc) > T(0));
       }
       if (!bad) {
         const bool left = vint <= lamc;
-        const SRState &K = left ? L : R;
-        const double *qK = left ? qL : qR;
-        const double *fK = left ? fL : fR;
-        const double lamK = left ? lamL : lamR;
-        const double fac = lamK - K.vx;
-        const double iden = 1.0 / (lamK - lamc);
-        double qs[5];
-        qs[0] = K.D * fac * iden;
-        qs[1] = (K.S0 * fac + Pc - K.P) * iden;
-        qs[2] = K.S1 * fac * iden;
-        qs[3] = K.S2 * fac * iden;
-        qs[4] = (K.E * fac + Pc * lamc - K.P * K.vx) * iden;
-        for (int n = 0; n < 5; ++n) {
-          const double fs = fK[n] + lamK * (qs[n] - qK[n]);
-          F[n] = fs - vint * qs[n];
-          if (!isfinite(F[n])) bad = true;
+        const SRState<T> &K = left ? L : R;
+        const T *qK = left ? qL : qR;
+        const T *fK = left ? fL : fR;
+        const T lamK = left ? lamL : lamR;
+        const T iden = T(1) / (lamK - lamc);
+        if constexpr (kDelta) {
+          // q* - q_K = [(lambda_c - v_K) q_K + (P_c - P_K) (0, 1, 0, 0, lambda_c)
+          //             + P_K (lambda_c - v_K) (0, 0, 0, 0, 1)] / (lambda_K - lambda_c)
+          const T dv = (lamc - K.vx) * iden;
+          const T dP = (Pc - K.P) * iden;
+          T dq[5];
+          dq[0] = K.D * dv;
+          dq[1] = K.S0 * dv + dP;
+          dq[2] = K.S1 * dv;
+          dq[3] = K.S2 * dv;
+          dq[4] = (K.E + (K.P + pref)) * dv + dP * lamc;
+          for (int n = 0; n < 5; ++n) {
+            F[n] = fK[n] + lamK * dq[n] - vint * (qK[n] + dq[n]);
+            if (!isfinite(F[n])) bad = true;
+          }
+        } else {
+          const T fac = lamK - K.vx;
+          T qs[5];
+          qs[0] = K.D * fac * iden;
+          qs[1] = (K.S0 * fac + Pc - K.P) * iden;
+          qs[2] = K.S1 * fac * iden;
+          qs[3] = K.S2 * fac * iden;
+          qs[4] = (K.E * fac + Pc * lamc - K.P * K.vx) * iden;
+          for (int n = 0; n < 5; ++n) {
+            const T fs = fK[n] + lamK * (qs[n] - qK[n]);
+            F[n] = fs - vint * qs[n];
+            if (!isfinite(F[n])) bad = true;
+          }
         }
       }
       fb = bad ? 1 : 0;
     }
   }
   if (p.solver != SACRA_HLLC || fb) {
-    const double cmax = fmax(fabs(lamL - vint), fabs(lamR - vint));
+    const T cmax = fmax(fabs(lamL - vint), fabs(lamR - vint));
     for (int n = 0; n < 5; ++n)
-      F[n] = 0.5 * ((fL[n] - vint * qL[n]) + (fR[n] - vint * qR[n])) - 0.5 * cmax * (qR[n] - qL[n]);
+      F[n] = T(0.5) * ((fL[n] - vint * qL[n]) + (fR[n] - vint * qR[n])) - T(0.5) * cmax * (qR[n] - qL[n]);
   }
   // back to the Eulerian frame with the covariant legs e_(a)_i:
   //   e_x = (B/W)(1,0,0), e_y = (D/W)(-gt^xy, gt^xx, 0), e_z = (C/W)(gt_xz, gt_yz, gt_zz)
-  const double pre = alpha / (W * W * W) * sgxx;
-  const double iW = 1.0 / W;
-  const double S0 = iW * (Bh * F[1] - Dh * mi.xy * F[2] + Ch * m.xz * F[3]);
-  const double S1 = iW * (Dh * mi.xx * F[2] + Ch * m.yz * F[3]);
-  const double S2 = iW * (Ch * m.zz * F[3]);
+  const T pre = alpha / (W * W * W) * sgxx;
+  const T iW = T(1) / W;
+  const T S0 = iW * (Bh * F[1] - Dh * mi.xy * F[2] + Ch * m.xz * F[3]);
+  const T S1 = iW * (Dh * mi.xx * F[2] + Ch * m.yz * F[3]);
+  const T S2 = iW * (Ch * m.zz * F[3]);
   out[0] = pre * F[0];
   out[4] = pre * F[4];
   if (dir == 0) {

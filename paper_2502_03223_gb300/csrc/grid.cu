@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const doubl
       if (evolve) {
         // DS holds the derivative scratch of the Z4c pass for this level
         constexpr int D1 = 0, D2 = 48;
-        Z4cIn z;
+        Z4cIn<double> z;
         z.W = U[(size_t)fW * P + id]; z.al = U[(size_t)fAL * P + id];
         z.Kh = U[(size_t)fKH * P + id]; z.Th = U[(size_t)fTH * P + id];
         for (int a = 0; a < 6; ++a) { z.h[a] = U[(size_t)(fHXX + a) * P + id]; z.A[a] = U[(size_t)(fAXX + a) * P + id]; }
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const doubl
           z.ddal[q] = DS[(size_t)(D2 + 42 + q) * P + id];
           for (int a = 0; a < 3; ++a) z.ddb[a][q] = DS[(size_t)(D2 + 6 * (8 + a) + q) * P + id];
         }
-        Geo G;
+        Geo<double> G;
         geo_fill(z, G);
         geo_ricci(z, G);
         double pr[NPRIM];

@@ -7,52 +7,103 @@
 namespace sacra {
 
 // 6-point (6th-order) interpolation of a metric field to the face between
-// u[0] and u[s], in difference form about u[0]: (3,-25,150,150,-25,3)/256.
-__device__ __forceinline__ double face6(const double *u, int s) {
-  const double u0 = u[0];
-  return u0 + (3.0 * (u[-2 * s] - u0) - 25.0 * (u[-s] - u0) + 150.0 * (u[s] - u0) - 25.0 * (u[2 * s] - u0)
-               + 3.0 * (u[3 * s] - u0)) * (1.0 / 256.0);
+// u[0] and u[s], in difference form about u[0]: (3,-25,150,150,-25,3)/256,
+// in arithmetic T (interpolation does not amplify rounding, so float is
+// enough in the mixed-precision hydro).
+template <typename T>
+__device__ __forceinline__ T face6(const double *u, int s) {
+  const T u0 = T(u[0]);
+  return u0 + (T(3) * (T(u[-2 * s]) - u0) - T(25) * (T(u[-s]) - u0) + T(150) * (T(u[s]) - u0)
+               - T(25) * (T(u[2 * s]) - u0) + T(3) * (T(u[3 * s]) - u0)) * T(1.0 / 256.0);
 }
 
-// Face j+1/2 (dir 0, stride 1) or k+1/2 (dir 1, stride px) of cell (j, k).
-template <int DIR>
+// Face j+1/2 (dir 0, stride 1) or k+1/2 (dir 1, stride px) of cell (j, k):
+// reconstruction, metric at the face and the flux in arithmetic T.  In FP32
+// the pressure is reconstructed as an offset from the FP64 face reference
+// pref = (P_j + P_j+1) / 2 (PPM commutes with a constant shift), and the
+// pressure part alpha W^-3 pref of the normal momentum flux is added in FP64.
+template <typename T, int DIR>
 __device__ inline void flux_at(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
                                double out[NCONS], int *fb) {
+  constexpr bool kDelta = sizeof(T) == 4;
   const size_t P = L.P;
   const int s = DIR == 0 ? 1 : L.px;
   const int id = cid(L, j, k);
   const int pf[5] = {pRHO, pUX, pUY, pUZ, pP};
-  double pl[5], pr[5];
+  const double *Pc = L.prim + (size_t)pP * P + id;
+  const double pref = kDelta ? 0.5 * (Pc[0] + Pc[s]) : 0.0;
+  T pl[5], pr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const double *a = L.prim + (size_t)pf[v] * P + id;
-    const double c[6] = {a[-2 * s], a[-s], a[0], a[s], a[2 * s], a[3 * s]};
+    const double o = v == 4 ? pref : 0.0;
+    const T c[6] = {T(a[-2 * s] - o), T(a[-s] - o), T(a[0] - o), T(a[s] - o), T(a[2 * s] - o), T(a[3 * s] - o)};
     ppm_pair(c, pl[v], pr[v]);
   }
-  if (!(pl[0] > 0.0) || !(pl[4] > 0.0))
+  const T tref = T(pref);
+  if (!(pl[0] > T(0)) || !(pl[4] + tref > T(0)))
 #pragma unroll
-    for (int v = 0; v < 5; ++v) pl[v] = L.prim[(size_t)pf[v] * P + id];
-  if (!(pr[0] > 0.0) || !(pr[4] > 0.0))
+    for (int v = 0; v < 5; ++v) pl[v] = T(L.prim[(size_t)pf[v] * P + id] - (v == 4 ? pref : 0.0));
+  if (!(pr[0] > T(0)) || !(pr[4] + tref > T(0)))
 #pragma unroll
-    for (int v = 0; v < 5; ++v) pr[v] = L.prim[(size_t)pf[v] * P + id + s];
-  const double alpha = face6(U + (size_t)fAL * P + id, s);
-  const double W = face6(U + (size_t)fW * P + id, s);
-  double beta[3];
+    for (int v = 0; v < 5; ++v) pr[v] = T(L.prim[(size_t)pf[v] * P + id + s] - (v == 4 ? pref : 0.0));
+  const T alpha = face6<T>(U + (size_t)fAL * P + id, s);
+  const T W = face6<T>(U + (size_t)fW * P + id, s);
+  T beta[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) beta[i] = face6(U + (size_t)(fBX + i) * P + id, s);
-  Sym3 g;
-  g.xx = 1.0 + face6(U + (size_t)fHXX * P + id, s);
-  g.xy = face6(U + (size_t)fHXY * P + id, s);
-  g.xz = face6(U + (size_t)fHXZ * P + id, s);
-  g.yy = 1.0 + face6(U + (size_t)fHYY * P + id, s);
-  g.yz = face6(U + (size_t)fHYZ * P + id, s);
-  g.zz = 1.0 + face6(U + (size_t)fHZZ * P + id, s);
-  *fb = face_flux(p, DIR, pl, pr, alpha, beta, W, g, out);
+  for (int i = 0; i < 3; ++i) beta[i] = face6<T>(U + (size_t)(fBX + i) * P + id, s);
+  Sym3T<T> g;
+  g.xx = T(1) + face6<T>(U + (size_t)fHXX * P + id, s);
+  g.xy = face6<T>(U + (size_t)fHXY * P + id, s);
+  g.xz = face6<T>(U + (size_t)fHXZ * P + id, s);
+  g.yy = T(1) + face6<T>(U + (size_t)fHYY * P + id, s);
+  g.yz = face6<T>(U + (size_t)fHYZ * P + id, s);
+  g.zz = T(1) + face6<T>(U + (size_t)fHZZ * P + id, s);
+  T o[5];
+  *fb = face_flux<T>(p, DIR, pl, pr, alpha, beta, W, g, o, tref);
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) out[v] = (double)o[v];
+  if constexpr (kDelta) {
+    const double a64 = face6<double>(U + (size_t)fAL * P + id, s);
+    const double w64 = face6<double>(U + (size_t)fW * P + id, s);
+    out[DIR == 0 ? 1 : 3] += a64 / (w64 * w64 * w64) * pref;
+  }
+}
+
+// The flux of one face in arithmetic T.  The FP32 form hands a face to the
+// FP64 solver where FP32 rounding could change a discrete branch: a stencil
+// with a strong density or pressure contrast (a stellar surface, the
+// atmosphere: reconstructed values of order eps_32 * max decide the
+// positivity fallback there, and the contact pressure of a near-vacuum
+// Riemann problem is of that order too), and every face where the FP32 HLLC
+// fails.  Elsewhere the branches have wide margins.
+constexpr double kMixedContrast = 1e-3;
+
+template <typename T, int DIR>
+__device__ inline void flux_face(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                 double out[NCONS], int *fb) {
+  if constexpr (sizeof(T) == 4) {
+    const int s = DIR == 0 ? 1 : L.px;
+    const double *r = L.prim + (size_t)pRHO * L.P + cid(L, j, k);
+    const double *q = L.prim + (size_t)pP * L.P + cid(L, j, k);
+    double rmin = r[-2 * s], rmax = r[-2 * s], qmin = q[-2 * s], qmax = q[-2 * s];
+#pragma unroll
+    for (int n = -1; n <= 3; ++n) {
+      rmin = fmin(rmin, r[n * s]); rmax = fmax(rmax, r[n * s]);
+      qmin = fmin(qmin, q[n * s]); qmax = fmax(qmax, q[n * s]);
+    }
+    if (rmin > kMixedContrast * rmax && qmin > kMixedContrast * qmax) {
+      flux_at<float, DIR>(L, p, U, j, k, out, fb);
+      if (!*fb) return;
+    }
+  }
+  flux_at<double, DIR>(L, p, U, j, k, out, fb);
 }
 
 // x-faces j+1/2 for j in [0, jmax], rows [1, kmax].  Stores area-weighted
 // fluxes (cylindrical: area x_{j+1/2} dz, and one more factor x for S_phi)
 // and accumulates the flux registers of the refinement boundaries.
+template <typename T>
 __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,7 +111,7 @@ __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
-  flux_at<0>(L, p, U, j, k, f, &fb);
+  flux_face<T, 0>(L, p, U, j, k, f, &fb);
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
   const double xf = j * L.dx;
   const double area = cyl ? xf * L.dz : L.dz;
@@ -79,6 +130,7 @@ __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double
   if (fb) atomicAdd(L.nfb, 1ull);
 }
 
+template <typename T>
 __global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
@@ -86,7 +138,7 @@ __global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
-  flux_at<1>(L, p, U, j, k, f, &fb);
+  flux_face<T, 1>(L, p, U, j, k, f, &fb);
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
   // equatorial mirror plane: D, S_x, S_phi, E are even in z, their z-fluxes vanish there
   if (cyl && k == 0) f[0] = f[1] = f[2] = f[4] = 0.0;
@@ -107,15 +159,19 @@ __global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double
   if (fb) atomicAdd(L.nfb, 1ull);
 }
 
-__device__ __forceinline__ double cd1(const double *u, int s, double idx) {
-  return (45.0 * (u[s] - u[-s]) - 9.0 * (u[2 * s] - u[-2 * s]) + (u[3 * s] - u[-3 * s])) * idx;
+// 6th-order central first derivative: differences in FP64, weighted sum in T
+template <typename T>
+__device__ __forceinline__ T cd1(const double *u, int s, T idx) {
+  return (T(45) * T(u[s] - u[-s]) - T(9) * T(u[2 * s] - u[-2 * s]) + T(u[3 * s] - u[-3 * s])) * idx;
 }
 
-// d_t q = <s> - (1/dV) sum (area-weighted fluxes), Sec. II.C.1.  Sources:
+// d_t q = <s> - (1/dV) sum (area-weighted fluxes), Sec. II.C.1.  The flux
+// divergence is FP64; the sources are evaluated in arithmetic T:
 //   s_Sk = P d_k(alpha W^-3) - W^-3 rho h w^2 [d_k alpha - v_i d_k beta^i
 //          + (W^2/2) alpha v_a v_b d_k gt^ab + (alpha/W) v_i v^i d_k W]
 //        (+ alpha W^-3 (S_y vbar^y + P)/x for k = x, cylindrical),
 //   s_E  = W^-3 (alpha K^ij S_ij - rho h w^2 v^i d_i alpha), s_D = s_Sphi = 0.
+template <typename T>
 __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
@@ -124,8 +180,8 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
   const int id = cid(L, j, k);
   const int sz = L.px;
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
-  const double x = (j - 0.5) * L.dx;
-  const double ivol = 1.0 / (cyl ? x * L.dx * L.dz : L.dx * L.dz);
+  const double xd = (j - 0.5) * L.dx;
+  const double ivol = 1.0 / (cyl ? xd * L.dx * L.dz : L.dx * L.dz);
   double div[NCONS];
 #pragma unroll
   for (int v = 0; v < NCONS; ++v) {
@@ -133,71 +189,78 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
     const double *fz = L.fz + (size_t)v * P + id;
     div[v] = (fx[0] - fx[-1] + fz[0] - fz[-sz]) * ivol;
   }
-  const double W = U[(size_t)fW * P + id], al = U[(size_t)fAL * P + id];
-  const Sym3 g = conf_metric(U, P, id);
-  const Sym3 gi = s3inv(g, nullptr);
-  const double i60[2] = {1.0 / (60.0 * L.dx), 1.0 / (60.0 * L.dz)};
+  const T x = T(xd);
+  const T W = T(U[(size_t)fW * P + id]), al = T(U[(size_t)fAL * P + id]);
+  Sym3T<T> g;
+  g.xx = T(1.0 + U[(size_t)fHXX * P + id]);
+  g.xy = T(U[(size_t)fHXY * P + id]);
+  g.xz = T(U[(size_t)fHXZ * P + id]);
+  g.yy = T(1.0 + U[(size_t)fHYY * P + id]);
+  g.yz = T(U[(size_t)fHYZ * P + id]);
+  g.zz = T(1.0 + U[(size_t)fHZZ * P + id]);
+  const Sym3T<T> gi = s3inv(g, (T *)nullptr);
+  const T i60[2] = {T(1.0 / (60.0 * L.dx)), T(1.0 / (60.0 * L.dz))};
   const int st[2] = {1, sz};
-  double pr[NPRIM];
+  T pr[NPRIM];
 #pragma unroll
-  for (int f = 0; f < NPRIM; ++f) pr[f] = L.prim[(size_t)f * P + id];
-  const double rho = pr[pRHO], Pp = pr[pP];
-  const double u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
-  const double w = sqrt(1.0 + W * W * s3quad(gi, u, u));
-  const double rhw2 = rho * (1.0 + pr[pEPS] + Pp / rho) * w * w;
-  const double vd[3] = {u[0] / w, u[1] / w, u[2] / w};
-  double vu[3];
+  for (int f = 0; f < NPRIM; ++f) pr[f] = T(L.prim[(size_t)f * P + id]);
+  const T rho = pr[pRHO], Pp = pr[pP];
+  const T u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
+  const T w = sqrt(T(1) + W * W * s3quad(gi, u, u));
+  const T rhw2 = rho * (T(1) + pr[pEPS] + Pp / rho) * w * w;
+  const T vd[3] = {u[0] / w, u[1] / w, u[2] / w};
+  T vu[3];
   s3vec(gi, vd, vu);
   vu[0] *= W * W; vu[1] *= W * W; vu[2] *= W * W;
-  const double vv = vd[0] * vu[0] + vd[1] * vu[1] + vd[2] * vu[2];
-  const double iW = 1.0 / W, iW3 = iW * iW * iW;
+  const T vv = vd[0] * vu[0] + vd[1] * vu[1] + vd[2] * vu[2];
+  const T iW = T(1) / W, iW3 = iW * iW * iW;
   // gt^ac v_c, used in v_a v_b d gt^ab = -(gt^ac v_c)(gt^bd v_d) d gt_cd
-  double gv[3];
+  T gv[3];
   s3vec(gi, vd, gv);
-  double src[2], dal[2];
+  T src[2], dal[2];
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
     const int s = st[e];
-    dal[e] = cd1(U + (size_t)fAL * P + id, s, i60[e]);
-    const double dW = cd1(U + (size_t)fW * P + id, s, i60[e]);
-    double vdb = 0.0;
+    dal[e] = cd1<T>(U + (size_t)fAL * P + id, s, i60[e]);
+    const T dW = cd1<T>(U + (size_t)fW * P + id, s, i60[e]);
+    T vdb = T(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) vdb += vd[i] * cd1(U + (size_t)(fBX + i) * P + id, s, i60[e]);
-    Sym3 dg;
-    dg.xx = cd1(U + (size_t)fHXX * P + id, s, i60[e]);
-    dg.xy = cd1(U + (size_t)fHXY * P + id, s, i60[e]);
-    dg.xz = cd1(U + (size_t)fHXZ * P + id, s, i60[e]);
-    dg.yy = cd1(U + (size_t)fHYY * P + id, s, i60[e]);
-    dg.yz = cd1(U + (size_t)fHYZ * P + id, s, i60[e]);
-    dg.zz = cd1(U + (size_t)fHZZ * P + id, s, i60[e]);
-    const double vvdgi = -s3quad(dg, gv, gv);
-    const double dalW3 = iW3 * dal[e] - 3.0 * al * iW3 * iW * dW;
-    src[e] = Pp * dalW3 - iW3 * rhw2 * (dal[e] - vdb + 0.5 * W * W * al * vvdgi + al * iW * vv * dW);
+    for (int i = 0; i < 3; ++i) vdb += vd[i] * cd1<T>(U + (size_t)(fBX + i) * P + id, s, i60[e]);
+    Sym3T<T> dg;
+    dg.xx = cd1<T>(U + (size_t)fHXX * P + id, s, i60[e]);
+    dg.xy = cd1<T>(U + (size_t)fHXY * P + id, s, i60[e]);
+    dg.xz = cd1<T>(U + (size_t)fHXZ * P + id, s, i60[e]);
+    dg.yy = cd1<T>(U + (size_t)fHYY * P + id, s, i60[e]);
+    dg.yz = cd1<T>(U + (size_t)fHYZ * P + id, s, i60[e]);
+    dg.zz = cd1<T>(U + (size_t)fHZZ * P + id, s, i60[e]);
+    const T vvdgi = -s3quad(dg, gv, gv);
+    const T dalW3 = iW3 * dal[e] - T(3) * al * iW3 * iW * dW;
+    src[e] = Pp * dalW3 - iW3 * rhw2 * (dal[e] - vdb + T(0.5) * W * W * al * vvdgi + al * iW * vv * dW);
   }
-  double geo = 0.0;
+  T geo = T(0);
   if (cyl) {
-    const double vbary = vu[1] - U[(size_t)fBY * P + id] / al;
+    const T vbary = vu[1] - T(U[(size_t)fBY * P + id]) / al;
     geo = al * iW3 * (rhw2 * vd[1] * vbary + Pp) / x;
   }
   // K^ij S_ij = rho h w^2 K_ij v^i v^j + P gamma^ij K_ij, K_ij = (At_ij + gt_ij K/3) / W^2
-  const double K = U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id];
-  Sym3 Kd;
-  Kd.xx = (U[(size_t)fAXX * P + id] + g.xx * K / 3.0) * iW * iW;
-  Kd.xy = (U[(size_t)fAXY * P + id] + g.xy * K / 3.0) * iW * iW;
-  Kd.xz = (U[(size_t)fAXZ * P + id] + g.xz * K / 3.0) * iW * iW;
-  Kd.yy = (U[(size_t)fAYY * P + id] + g.yy * K / 3.0) * iW * iW;
-  Kd.yz = (U[(size_t)fAYZ * P + id] + g.yz * K / 3.0) * iW * iW;
-  Kd.zz = (U[(size_t)fAZZ * P + id] + g.zz * K / 3.0) * iW * iW;
+  const T K = T(U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id]);
+  Sym3T<T> Kd;
+  Kd.xx = (T(U[(size_t)fAXX * P + id]) + g.xx * K / T(3)) * iW * iW;
+  Kd.xy = (T(U[(size_t)fAXY * P + id]) + g.xy * K / T(3)) * iW * iW;
+  Kd.xz = (T(U[(size_t)fAXZ * P + id]) + g.xz * K / T(3)) * iW * iW;
+  Kd.yy = (T(U[(size_t)fAYY * P + id]) + g.yy * K / T(3)) * iW * iW;
+  Kd.yz = (T(U[(size_t)fAYZ * P + id]) + g.yz * K / T(3)) * iW * iW;
+  Kd.zz = (T(U[(size_t)fAZZ * P + id]) + g.zz * K / T(3)) * iW * iW;
   // gamma^ij K_ij = W^2 gt^ij K_ij (equal to K when At is trace-free)
-  const double trK = W * W * (gi.xx * Kd.xx + gi.yy * Kd.yy + gi.zz * Kd.zz
-                              + 2.0 * (gi.xy * Kd.xy + gi.xz * Kd.xz + gi.yz * Kd.yz));
-  const double KS = rhw2 * s3quad(Kd, vu, vu) + Pp * trK;
-  const double sE = iW3 * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
+  const T trK = W * W * (gi.xx * Kd.xx + gi.yy * Kd.yy + gi.zz * Kd.zz
+                         + T(2) * (gi.xy * Kd.xy + gi.xz * Kd.xz + gi.yz * Kd.yz));
+  const T KS = rhw2 * s3quad(Kd, vu, vu) + Pp * trK;
+  const T sE = iW3 * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
   L.rhs[(size_t)fQD * P + id] = -div[0];
-  L.rhs[(size_t)fQSX * P + id] = src[0] + geo - div[1];
+  L.rhs[(size_t)fQSX * P + id] = (double)(src[0] + geo) - div[1];
   L.rhs[(size_t)fQSY * P + id] = -div[2];
-  L.rhs[(size_t)fQSZ * P + id] = src[1] - div[3];
-  L.rhs[(size_t)fQE * P + id] = sE - div[4];
+  L.rhs[(size_t)fQSZ * P + id] = (double)src[1] - div[3];
+  L.rhs[(size_t)fQE * P + id] = (double)sE - div[4];
 }
 
 // eps from the EOS and conserved variables on every padded cell (initial data)
@@ -243,16 +306,22 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
 
 void launch_flux_x(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
                    int has_parent, cudaStream_t s) {
-  k_flux_x<<<dim3((jmax + 1 + 31) / 32, (kmax + 3) / 4), dim3(32, 4), 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+  const dim3 g((jmax + 1 + 31) / 32, (kmax + 3) / 4), b(32, 4);
+  if (p.mixed & SACRA_MIXED_FLUX) k_flux_x<float><<<g, b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+  else k_flux_x<double><<<g, b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
 }
 
 void launch_flux_z(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
                    int has_parent, cudaStream_t s) {
-  k_flux_z<<<dim3((jmax + 31) / 32, (kmax + 1 + 3) / 4), dim3(32, 4), 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+  const dim3 g((jmax + 31) / 32, (kmax + 1 + 3) / 4), b(32, 4);
+  if (p.mixed & SACRA_MIXED_FLUX) k_flux_z<float><<<g, b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
+  else k_flux_z<double><<<g, b, 0, s>>>(L, p, U, jmax, kmax, wb, has_child, has_parent);
 }
 
 void launch_hydro_div(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, cudaStream_t s) {
-  k_hydro_rhs<<<dim3((jmax + 31) / 32, (kmax + 3) / 4), dim3(32, 4), 0, s>>>(L, p, U, jmax, kmax);
+  const dim3 g((jmax + 31) / 32, (kmax + 3) / 4), b(32, 4);
+  if (p.mixed & SACRA_MIXED_SOURCES) k_hydro_rhs<float><<<g, b, 0, s>>>(L, p, U, jmax, kmax);
+  else k_hydro_rhs<double><<<g, b, 0, s>>>(L, p, U, jmax, kmax);
 }
 
 void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s) {

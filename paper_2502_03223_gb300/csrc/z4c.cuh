@@ -16,31 +16,34 @@ __device__ __forceinline__ int sp(int i, int j) {
 // Inputs of the pointwise right-hand side.  First derivatives d[k] of the
 // fields that enter undifferentiated-by-advection terms, second derivatives
 // in the pair order xx,xy,xz,yy,yz,zz.
+template <typename T>
 struct Z4cIn {
-  double W, al, Kh, Th;
-  double h[6], A[6], Gt[3], beta[3], B[3];
-  double dW[3], dKh[3], dTh[3], dal[3];
-  double dh[6][3];       // d_k h_ij  -> dh[ij][k]
-  double dGt[3][3];      // d_k Gt^i  -> dGt[i][k]
-  double db[3][3];       // d_k beta^i -> db[i][k]
-  double ddW[6], ddal[6];
-  double ddh[6][6];      // d_kl h_ij -> ddh[ij][kl]
-  double ddb[3][6];      // d_kl beta^i
+  T W, al, Kh, Th;
+  T h[6], A[6], Gt[3], beta[3], B[3];
+  T dW[3], dKh[3], dTh[3], dal[3];
+  T dh[6][3];       // d_k h_ij  -> dh[ij][k]
+  T dGt[3][3];      // d_k Gt^i  -> dGt[i][k]
+  T db[3][3];       // d_k beta^i -> db[i][k]
+  T ddW[6], ddal[6];
+  T ddh[6][6];      // d_kl h_ij -> ddh[ij][kl]
+  T ddb[3][6];      // d_kl beta^i
 };
 
+template <typename T>
 struct Geo {
-  Sym3 g, gi;
-  double Gl[3][6];       // Gt_{k,ij}
-  double G2[3][6];       // Gt^k_ij
-  double Gd[3];          // gt^jk Gt^i_jk
-  double R[6];           // physical Ricci tensor
-  double Rs;             // physical Ricci scalar
+  Sym3T<T> g, gi;
+  T Gl[3][6];       // Gt_{k,ij}
+  T G2[3][6];       // Gt^k_ij
+  T Gd[3];          // gt^jk Gt^i_jk
+  T R[6];           // physical Ricci tensor
+  T Rs;             // physical Ricci scalar
 };
 
-__device__ inline void geo_fill(const Z4cIn &z, Geo &G) {
-  G.g.xx = 1.0 + z.h[0]; G.g.xy = z.h[1]; G.g.xz = z.h[2];
-  G.g.yy = 1.0 + z.h[3]; G.g.yz = z.h[4]; G.g.zz = 1.0 + z.h[5];
-  G.gi = s3inv(G.g, nullptr);
+template <typename T>
+__device__ inline void geo_fill(const Z4cIn<T> &z, Geo<T> &G) {
+  G.g.xx = T(1.0) + z.h[0]; G.g.xy = z.h[1]; G.g.xz = z.h[2];
+  G.g.yy = T(1.0) + z.h[3]; G.g.yz = z.h[4]; G.g.zz = T(1.0) + z.h[5];
+  G.gi = s3inv(G.g, (T *)nullptr);
   // Gt_{k,ij} = (d_i gt_kj + d_j gt_ki - d_k gt_ij) / 2
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -48,7 +51,7 @@ __device__ inline void geo_fill(const Z4cIn &z, Geo &G) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = i; j < 3; ++j)
-        G.Gl[k][sp(i, j)] = 0.5 * (z.dh[sp(k, j)][i] + z.dh[sp(k, i)][j] - z.dh[sp(i, j)][k]);
+        G.Gl[k][sp(i, j)] = T(0.5) * (z.dh[sp(k, j)][i] + z.dh[sp(k, i)][j] - z.dh[sp(i, j)][k]);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
     G.G2[0][a] = G.gi.xx * G.Gl[0][a] + G.gi.xy * G.Gl[1][a] + G.gi.xz * G.Gl[2][a];
@@ -58,67 +61,68 @@ __device__ inline void geo_fill(const Z4cIn &z, Geo &G) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     G.Gd[i] = G.gi.xx * G.G2[i][0] + G.gi.yy * G.G2[i][3] + G.gi.zz * G.G2[i][5]
-            + 2.0 * (G.gi.xy * G.G2[i][1] + G.gi.xz * G.G2[i][2] + G.gi.yz * G.G2[i][4]);
+            + T(2.0) * (G.gi.xy * G.G2[i][1] + G.gi.xz * G.G2[i][2] + G.gi.yz * G.G2[i][4]);
 }
 
 // Ricci tensor of gamma = gt / W^2: Rt_ij (conformal part with d_j Gt^k from
 // the evolved Gt, quadratic term with the computed Gt_d) plus the part from W.
-__device__ inline void geo_ricci(const Z4cIn &z, Geo &G) {
-  const Sym3 &gi = G.gi;
-  const double gim[3][3] = {{gi.xx, gi.xy, gi.xz}, {gi.xy, gi.yy, gi.yz}, {gi.xz, gi.yz, gi.zz}};
-  const double gm[3][3] = {{G.g.xx, G.g.xy, G.g.xz}, {G.g.xy, G.g.yy, G.g.yz}, {G.g.xz, G.g.yz, G.g.zz}};
+template <typename T>
+__device__ inline void geo_ricci(const Z4cIn<T> &z, Geo<T> &G) {
+  const Sym3T<T> &gi = G.gi;
+  const T gim[3][3] = {{gi.xx, gi.xy, gi.xz}, {gi.xy, gi.yy, gi.yz}, {gi.xz, gi.yz, gi.zz}};
+  const T gm[3][3] = {{G.g.xx, G.g.xy, G.g.xz}, {G.g.xy, G.g.yy, G.g.yz}, {G.g.xz, G.g.yz, G.g.zz}};
   // D~_i D~_j W and the traces
-  double DDW[6];
+  T DDW[6];
 #pragma unroll
   for (int a = 0; a < 6; ++a) DDW[a] = z.ddW[a] - (G.G2[0][a] * z.dW[0] + G.G2[1][a] * z.dW[1] + G.G2[2][a] * z.dW[2]);
-  const double trDDW = gi.xx * DDW[0] + gi.yy * DDW[3] + gi.zz * DDW[5] + 2.0 * (gi.xy * DDW[1] + gi.xz * DDW[2] + gi.yz * DDW[4]);
-  const double dW2 = s3quad(gi, z.dW, z.dW);
-  const double iW = 1.0 / z.W;
-  double Rsum = 0.0;
+  const T trDDW = gi.xx * DDW[0] + gi.yy * DDW[3] + gi.zz * DDW[5] + T(2.0) * (gi.xy * DDW[1] + gi.xz * DDW[2] + gi.yz * DDW[4]);
+  const T dW2 = s3quad(gi, z.dW, z.dW);
+  const T iW = T(1.0) / z.W;
+  T Rsum = T(0.0);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int ij = sp(i, j);
-      double r = 0.0;
+      T r = T(0.0);
       // -1/2 gt^lm d_l d_m gt_ij
-      r -= 0.5 * (gi.xx * z.ddh[ij][0] + gi.yy * z.ddh[ij][3] + gi.zz * z.ddh[ij][5]
-                  + 2.0 * (gi.xy * z.ddh[ij][1] + gi.xz * z.ddh[ij][2] + gi.yz * z.ddh[ij][4]));
+      r -= T(0.5) * (gi.xx * z.ddh[ij][0] + gi.yy * z.ddh[ij][3] + gi.zz * z.ddh[ij][5]
+                  + T(2.0) * (gi.xy * z.ddh[ij][1] + gi.xz * z.ddh[ij][2] + gi.yz * z.ddh[ij][4]));
       // gt_k(i d_j) Gt^k
 #pragma unroll
-      for (int k = 0; k < 3; ++k) r += 0.5 * (gm[k][i] * z.dGt[k][j] + gm[k][j] * z.dGt[k][i]);
+      for (int k = 0; k < 3; ++k) r += T(0.5) * (gm[k][i] * z.dGt[k][j] + gm[k][j] * z.dGt[k][i]);
       // Gt_d^k Gt_(ij)k
 #pragma unroll
-      for (int k = 0; k < 3; ++k) r += 0.5 * G.Gd[k] * (G.Gl[i][sp(j, k)] + G.Gl[j][sp(i, k)]);
+      for (int k = 0; k < 3; ++k) r += T(0.5) * G.Gd[k] * (G.Gl[i][sp(j, k)] + G.Gl[j][sp(i, k)]);
       // gt^lm (Gt^k_li Gt_{j,km} + Gt^k_lj Gt_{i,km} + Gt^k_im Gt_{k,lj})
 #pragma unroll
       for (int l = 0; l < 3; ++l)
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          double s = 0.0;
+          T s = T(0.0);
 #pragma unroll
           for (int k = 0; k < 3; ++k)
             s += G.G2[k][sp(l, i)] * G.Gl[j][sp(k, m)] + G.G2[k][sp(l, j)] * G.Gl[i][sp(k, m)]
                + G.G2[k][sp(i, m)] * G.Gl[k][sp(l, j)];
           r += gim[l][m] * s;
         }
-      r += (DDW[ij] + gm[i][j] * trDDW) * iW - 2.0 * gm[i][j] * dW2 * iW * iW;
+      r += (DDW[ij] + gm[i][j] * trDDW) * iW - T(2.0) * gm[i][j] * dW2 * iW * iW;
       G.R[ij] = r;
-      Rsum += (i == j ? 1.0 : 2.0) * gim[i][j] * r;
+      Rsum += (i == j ? T(1.0) : T(2.0)) * gim[i][j] * r;
     }
   G.Rs = z.W * z.W * Rsum;
 }
 
 // Matter terms E, S_i, S_ij from the primitives (rho, u_i, P, eps)
-__device__ inline void matter(const double pr[NPRIM], double W, const Sym3 &g, const Sym3 &gi, double &E, double S[3],
-                              double Sij[6]) {
-  const double u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
-  const double w = sqrt(1.0 + W * W * s3quad(gi, u, u));
-  const double rho = pr[pRHO], P = pr[pP];
-  const double rh = rho * (1.0 + pr[pEPS] + P / rho);
+template <typename T>
+__device__ inline void matter(const T pr[NPRIM], T W, const Sym3T<T> &g, const Sym3T<T> &gi, T &E, T S[3], T Sij[6]) {
+  const T u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
+  const T w = sqrt(T(1.0) + W * W * s3quad(gi, u, u));
+  const T rho = pr[pRHO], P = pr[pP];
+  const T rh = rho * (T(1.0) + pr[pEPS] + P / rho);
   E = rh * w * w - P;
   S[0] = rh * w * u[0]; S[1] = rh * w * u[1]; S[2] = rh * w * u[2];
-  const double iW2 = 1.0 / (W * W);
+  const T iW2 = T(1.0) / (W * W);
   Sij[0] = rh * u[0] * u[0] + P * g.xx * iW2;
   Sij[1] = rh * u[0] * u[1] + P * g.xy * iW2;
   Sij[2] = rh * u[0] * u[2] + P * g.xz * iW2;
@@ -130,21 +134,22 @@ __device__ inline void matter(const double pr[NPRIM], double W, const Sym3 &g, c
 // Source part of the Z4c right-hand side (everything but advection and KO).
 // fz = exp(-r^2/r_Z4^2) multiplies kappa and the Theta source.
 // out[25]; the B^i entries contain only their own source (Gt source - eta B).
-__device__ inline void z4c_source(const DevParams &p, const Z4cIn &z, const Geo &G, double E, const double Si[3],
-                                  const double Sij[6], double fz, double out[NMET]) {
-  constexpr double PI = 3.14159265358979323846;
-  const Sym3 &gi = G.gi;
-  const double gim[3][3] = {{gi.xx, gi.xy, gi.xz}, {gi.xy, gi.yy, gi.yz}, {gi.xz, gi.yz, gi.zz}};
-  const double gm[3][3] = {{G.g.xx, G.g.xy, G.g.xz}, {G.g.xy, G.g.yy, G.g.yz}, {G.g.xz, G.g.yz, G.g.zz}};
-  const double W = z.W, al = z.al;
-  const double K = z.Kh + 2.0 * z.Th;
-  const double kap = p.kappa * fz;
-  const double divb = z.db[0][0] + z.db[1][1] + z.db[2][2];
-  const double iW = 1.0 / W;
+template <typename T>
+__device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const Geo<T> &G, T E, const T Si[3],
+                                  const T Sij[6], T fz, T out[NMET]) {
+  const T PI = T(3.14159265358979323846);
+  const Sym3T<T> &gi = G.gi;
+  const T gim[3][3] = {{gi.xx, gi.xy, gi.xz}, {gi.xy, gi.yy, gi.yz}, {gi.xz, gi.yz, gi.zz}};
+  const T gm[3][3] = {{G.g.xx, G.g.xy, G.g.xz}, {G.g.xy, G.g.yy, G.g.yz}, {G.g.xz, G.g.yz, G.g.zz}};
+  const T W = z.W, al = z.al;
+  const T K = z.Kh + T(2.0) * z.Th;
+  const T kap = T(p.kappa) * fz;
+  const T divb = z.db[0][0] + z.db[1][1] + z.db[2][2];
+  const T iW = T(1.0) / W;
 
   // physical D_i D_j alpha
-  const double daW = s3quad(gi, z.dal, z.dW);
-  double DDa[6];
+  const T daW = s3quad(gi, z.dal, z.dW);
+  T DDa[6];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -153,44 +158,44 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn &z, const Geo 
       DDa[ij] = z.ddal[ij] - (G.G2[0][ij] * z.dal[0] + G.G2[1][ij] * z.dal[1] + G.G2[2][ij] * z.dal[2])
               + (z.dal[i] * z.dW[j] + z.dal[j] * z.dW[i] - gm[i][j] * daW) * iW;
     }
-  const double D2a = W * W * (gi.xx * DDa[0] + gi.yy * DDa[3] + gi.zz * DDa[5]
-                              + 2.0 * (gi.xy * DDa[1] + gi.xz * DDa[2] + gi.yz * DDa[4]));
+  const T D2a = W * W * (gi.xx * DDa[0] + gi.yy * DDa[3] + gi.zz * DDa[5]
+                              + T(2.0) * (gi.xy * DDa[1] + gi.xz * DDa[2] + gi.yz * DDa[4]));
   // At with mixed and raised indices
-  double Am[3][3];   // At_i^k = At_il gt^lk  -> Am[i][k]
+  T Am[3][3];   // At_i^k = At_il gt^lk  -> Am[i][k]
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k)
       Am[i][k] = z.A[sp(i, 0)] * gim[0][k] + z.A[sp(i, 1)] * gim[1][k] + z.A[sp(i, 2)] * gim[2][k];
-  double Au[6];      // At^ij
+  T Au[6];      // At^ij
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) Au[sp(i, j)] = gim[i][0] * Am[0][j] + gim[i][1] * Am[1][j] + gim[i][2] * Am[2][j];
-  double AA = 0.0;
+  T AA = T(0.0);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int k = 0; k < 3; ++k) AA += Am[i][k] * Am[k][i];
-  const double Str = W * W * (gi.xx * Sij[0] + gi.yy * Sij[3] + gi.zz * Sij[5]
-                              + 2.0 * (gi.xy * Sij[1] + gi.xz * Sij[2] + gi.yz * Sij[4]));
+  const T Str = W * W * (gi.xx * Sij[0] + gi.yy * Sij[3] + gi.zz * Sij[5]
+                              + T(2.0) * (gi.xy * Sij[1] + gi.xz * Sij[2] + gi.yz * Sij[4]));
 
-  out[fW] = W * (al * K - divb) / 3.0;
+  out[fW] = W * (al * K - divb) / T(3.0);
 
   // X_ij = alpha R_ij - D_i D_j alpha - 8 pi alpha S_ij and its gt-trace
-  double X[6];
+  T X[6];
 #pragma unroll
-  for (int a = 0; a < 6; ++a) X[a] = al * G.R[a] - DDa[a] - 8.0 * PI * al * Sij[a];
-  const double trX = gi.xx * X[0] + gi.yy * X[3] + gi.zz * X[5] + 2.0 * (gi.xy * X[1] + gi.xz * X[2] + gi.yz * X[4]);
+  for (int a = 0; a < 6; ++a) X[a] = al * G.R[a] - DDa[a] - T(8.0) * PI * al * Sij[a];
+  const T trX = gi.xx * X[0] + gi.yy * X[3] + gi.zz * X[5] + T(2.0) * (gi.xy * X[1] + gi.xz * X[2] + gi.yz * X[4]);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int ij = sp(i, j);
-      double sh = -2.0 * al * z.A[ij] - (2.0 / 3.0) * gm[i][j] * divb;
-      double sa = W * W * (X[ij] - gm[i][j] * trX / 3.0)
-                + al * (K * z.A[ij] - 2.0 * (Am[i][0] * z.A[sp(0, j)] + Am[i][1] * z.A[sp(1, j)] + Am[i][2] * z.A[sp(2, j)]))
-                - (2.0 / 3.0) * z.A[ij] * divb;
+      T sh = -T(2.0) * al * z.A[ij] - (T(2.0) / T(3.0)) * gm[i][j] * divb;
+      T sa = W * W * (X[ij] - gm[i][j] * trX / T(3.0))
+                + al * (K * z.A[ij] - T(2.0) * (Am[i][0] * z.A[sp(0, j)] + Am[i][1] * z.A[sp(1, j)] + Am[i][2] * z.A[sp(2, j)]))
+                - (T(2.0) / T(3.0)) * z.A[ij] * divb;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         sh += gm[i][k] * z.db[k][j] + gm[j][k] * z.db[k][i];
@@ -200,32 +205,32 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn &z, const Geo 
       out[fAXX + ij] = sa;
     }
 
-  out[fKH] = -D2a + al * (AA + K * K / 3.0) + 4.0 * PI * al * (Str + E) + al * kap * z.Th;
+  out[fKH] = -D2a + al * (AA + K * K / T(3.0)) + T(4.0) * PI * al * (Str + E) + al * kap * z.Th;
 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double in = 0.0, s = 0.0, lap = 0.0, grad = 0.0;
+    T in = T(0.0), s = T(0.0), lap = T(0.0), grad = T(0.0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      s -= 2.0 * Au[sp(i, j)] * z.dal[j];
-      in -= gim[i][j] * (2.0 * z.dKh[j] + z.dTh[j]) / 3.0 + 3.0 * iW * Au[sp(i, j)] * z.dW[j]
-          + 8.0 * PI * gim[i][j] * Si[j];
+      s -= T(2.0) * Au[sp(i, j)] * z.dal[j];
+      in -= gim[i][j] * (T(2.0) * z.dKh[j] + z.dTh[j]) / T(3.0) + T(3.0) * iW * Au[sp(i, j)] * z.dW[j]
+          + T(8.0) * PI * gim[i][j] * Si[j];
       grad += gim[i][j] * (z.ddb[0][sp(j, 0)] + z.ddb[1][sp(j, 1)] + z.ddb[2][sp(j, 2)]);
       s -= G.Gd[j] * z.db[i][j];
     }
 #pragma unroll
-    for (int a = 0; a < 6; ++a) in += (a == 0 || a == 3 || a == 5 ? 1.0 : 2.0) * G.G2[i][a] * Au[a];
+    for (int a = 0; a < 6; ++a) in += (a == 0 || a == 3 || a == 5 ? T(1.0) : T(2.0)) * G.G2[i][a] * Au[a];
     lap = gi.xx * z.ddb[i][0] + gi.yy * z.ddb[i][3] + gi.zz * z.ddb[i][5]
-        + 2.0 * (gi.xy * z.ddb[i][1] + gi.xz * z.ddb[i][2] + gi.yz * z.ddb[i][4]);
-    s += 2.0 * al * in + (2.0 / 3.0) * G.Gd[i] * divb + lap + grad / 3.0 - 2.0 * al * kap * (z.Gt[i] - G.Gd[i]);
+        + T(2.0) * (gi.xy * z.ddb[i][1] + gi.xz * z.ddb[i][2] + gi.yz * z.ddb[i][4]);
+    s += T(2.0) * al * in + (T(2.0) / T(3.0)) * G.Gd[i] * divb + lap + grad / T(3.0) - T(2.0) * al * kap * (z.Gt[i] - G.Gd[i]);
     out[fGX + i] = s;
-    out[fBBX + i] = s - p.eta_B * z.B[i];
+    out[fBBX + i] = s - T(p.eta_B) * z.B[i];
   }
 
-  out[fTH] = fz * (0.5 * al * (G.Rs - AA + (2.0 / 3.0) * K * K) - 8.0 * PI * al * E) - 2.0 * al * kap * z.Th;
-  out[fAL] = -2.0 * al * z.Kh;
+  out[fTH] = fz * (T(0.5) * al * (G.Rs - AA + (T(2.0) / T(3.0)) * K * K) - T(8.0) * PI * al * E) - T(2.0) * al * kap * z.Th;
+  out[fAL] = -T(2.0) * al * z.Kh;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) out[fBX + i] = 0.75 * z.B[i];
+  for (int i = 0; i < 3; ++i) out[fBX + i] = T(0.75) * z.B[i];
 }
 
 }  // namespace sacra

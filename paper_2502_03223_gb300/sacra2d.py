@@ -19,6 +19,7 @@ SACRA_OK = 0
 PLANAR, CYLINDRICAL = 0, 1
 HLLC, TVDLF = 0, 1
 RK4, SSPRK3 = 0, 1
+FP64, MIXED_FLUX, MIXED_SOURCES, MIXED_Z4C, MIXED = 0, 1, 2, 4, 7
 PRIM_METRIC, RAW = 0, 1
 FILL, RESTRICT_REFLUX = 0, 1
 STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
@@ -33,7 +34,7 @@ class SacraParams(C.Structure):
     _fields_ = [
         ("n_levels", C.c_int), ("nx", C.c_int), ("nz", C.c_int), ("geometry", C.c_int),
         ("evolve_spacetime", C.c_int), ("solver", C.c_int), ("rk", C.c_int), ("c2p_maxit", C.c_int),
-        ("reserved", C.c_int),
+        ("precision", C.c_int),
         ("dx0", C.c_double), ("dz0", C.c_double),
         ("kappa", C.c_double), ("eta_B", C.c_double), ("eps_ko", C.c_double), ("r_z4", C.c_double),
         ("K", C.c_double), ("Gamma", C.c_double), ("Gamma_th", C.c_double),
@@ -91,6 +92,7 @@ def make_params(cfg) -> SacraParams:
     p.n_levels = int(cfg.n_levels); p.nx = int(cfg.nx); p.nz = int(cfg.nz)
     p.geometry = int(cfg.geometry); p.evolve_spacetime = int(cfg.evolve_spacetime)
     p.solver = int(cfg.solver); p.rk = int(cfg.rk); p.c2p_maxit = int(cfg.c2p_maxit)
+    p.precision = int(getattr(cfg, "precision", 0))
     p.dx0 = float(cfg.dx0); p.dz0 = float(cfg.dz0)
     p.kappa = float(cfg.kappa); p.eta_B = float(cfg.eta_B); p.eps_ko = float(cfg.eps_ko); p.r_z4 = float(cfg.r_z4)
     p.K = float(cfg.K); p.Gamma = float(cfg.Gamma); p.Gamma_th = float(cfg.Gamma_th)

@@ -38,6 +38,7 @@ class RunConfig:
     solver: int = 0            # 0 HLLC (TVDLF fallback), 1 TVDLF
     rk: int = 0                # 0 classical RK4, 1 SSP-RK3
     c2p_maxit: int = 100
+    precision: int = 0         # 0 FP64, 1 mixed FP32/FP64 (GPU library only; the oracle is FP64)
     dx0: float = 1.0
     dz0: float = 1.0
     kappa: float = 0.0
