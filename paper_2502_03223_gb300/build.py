@@ -67,7 +67,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         subprocess.check_call([nvcc(), "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"])
         os.replace(tmp, LIB)
     probe_src = os.path.join(CSRC, "probe.cu")
-    if force or _stale(PROBE, [probe_src]):
+    if force or _stale(PROBE, [probe_src, os.path.join(CSRC, "common.cuh")]):
         tmp = PROBE + ".tmp%d" % os.getpid()
         subprocess.check_call([nvcc(), *_flags(), "-shared", "-o", tmp, probe_src, "-lcudart"])
         os.replace(tmp, PROBE)

@@ -16,7 +16,7 @@ using namespace sacra;
 namespace {
 
 constexpr int kMaxLevels = 12;
-constexpr int kTabStride = 12;   // 9 weights, cos, sin, pad
+constexpr int kTabStride = 12;   // 9 weights, cos, sin, cos - 1
 
 // Lagrange weights over the nodes at position t (product formula)
 void lagrange_weights(int n, const double *nodes, double t, double *w) {
@@ -322,11 +322,7 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
     delete c;
     return SACRA_ERR_CUDA;
   }
-  DevParams &d = c->dp;
-  d.geometry = p->geometry; d.evolve = p->evolve_spacetime; d.solver = p->solver; d.rk = p->rk;
-  d.c2p_maxit = p->c2p_maxit; d.n_levels = p->n_levels; d.mixed = p->precision & SACRA_MIXED;
-  d.K = p->K; d.Gamma = p->Gamma; d.Gamma_th = p->Gamma_th; d.rho_atm = p->rho_atm; d.w_max = p->w_max;
-  d.c2p_tol = p->c2p_tol; d.kappa = p->kappa; d.eta_B = p->eta_B; d.eps_ko = p->eps_ko; d.r_z4 = p->r_z4;
+  fill_dev_params(p, &c->dp);
 
   char *shared = c->arena + c->lay.per_level * p->n_levels;
   c->ds = (double *)(shared + c->lay.ds_off);
@@ -359,7 +355,7 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
     L.nfb = c->nfb;
   }
   // cartoon table: for x_j = (j - 1/2) dx and plane m dy (dy = dx), the
-  // 9 weights on x_{j-4..j+4} at varpi = sqrt(x_j^2 + (m dy)^2), cos, sin of phi
+  // 9 weights on x_{j-4..j+4} at varpi = sqrt(x_j^2 + (m dy)^2), cos, sin of phi, cos - 1
   {
     const int nj = p->nx + 8;
     std::vector<double> tab((size_t)nj * 3 * kTabStride, 0.0);
@@ -372,6 +368,7 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
         lagrange_weights(9, nodes, vp - x, t);
         t[9] = x / vp;
         t[10] = m / vp;
+        t[11] = -(double)(m * m) / (vp * (x + vp));   // cos phi - 1 without cancellation
       }
     cudaMemcpyAsync(c->tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
   }

@@ -31,9 +31,33 @@ constexpr int ST_NOCONV = 1, ST_COLD = 2, ST_ATM = 4, ST_KRESCALE = 8, ST_BAD = 
 struct DevParams {
   int geometry, evolve, solver, rk, c2p_maxit, n_levels;
   int mixed;             // SACRA_MIXED_* bits: parts whose arithmetic runs in FP32 (FP64 differences and updates)
+  int K_zero, gamma2;    // K == 0 (pure Gamma-law), Gamma == 2
   double K, Gamma, Gamma_th, rho_atm, w_max, c2p_tol;
   double kappa, eta_B, eps_ko, r_z4;
+  // FP32 copies for the mixed-precision kernels (no conversions on the device)
+  float fK, fGamma, fGm1, fGamma_th, fGth1, fkappa, feta_B, firz2;
 };
+
+// a parameter in arithmetic T: the FP64 value, or its FP32 copy
+template <typename T>
+__host__ __device__ __forceinline__ T pv(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
+
+// fills every field from the public parameters (host)
+inline void fill_dev_params(const sacra_params *p, DevParams *d) {
+  *d = DevParams{};
+  d->geometry = p->geometry; d->evolve = p->evolve_spacetime; d->solver = p->solver; d->rk = p->rk;
+  d->c2p_maxit = p->c2p_maxit; d->n_levels = p->n_levels; d->mixed = p->precision & SACRA_MIXED;
+  d->K_zero = p->K == 0.0; d->gamma2 = p->Gamma == 2.0;
+  d->K = p->K; d->Gamma = p->Gamma; d->Gamma_th = p->Gamma_th; d->rho_atm = p->rho_atm; d->w_max = p->w_max;
+  d->c2p_tol = p->c2p_tol; d->kappa = p->kappa; d->eta_B = p->eta_B; d->eps_ko = p->eps_ko; d->r_z4 = p->r_z4;
+  d->fK = (float)p->K; d->fGamma = (float)p->Gamma; d->fGm1 = (float)(p->Gamma - 1.0);
+  d->fGamma_th = (float)p->Gamma_th; d->fGth1 = (float)(p->Gamma_th - 1.0);
+  d->fkappa = (float)p->kappa; d->feta_B = (float)p->eta_B;
+  d->firz2 = (float)(1.0 / (p->r_z4 * p->r_z4));
+}
 
 // One refinement level as seen by a kernel: planes of P = px * pz doubles.
 struct Lev {
@@ -50,6 +74,68 @@ struct Lev {
 };
 
 __host__ __device__ inline int cid(const Lev &L, int j, int k) { return (k + GH - 1) * L.px + (j + GH - 1); }
+
+// ------------------------------------------------------------------ FP64 <-> FP32 without the FP64 pipe
+//
+// On this part conversions between double and float issue at the FP64 rate
+// (about 2 per clock per SM, like a DADD), while integer and FP32 operations
+// issue some 30-60x faster.  The mixed-precision kernels therefore take FP32
+// views of FP64 data with integer bit operations:
+//   split_f64(u) = (hi, lo): hi = u truncated to 24 significant bits, lo = the
+//   next 23 bits (u - hi - lo < 2^-46 |u|).  A difference of two nearby FP64
+//   values is then (hi_a - hi_b) + (lo_a - lo_b): the hi part is exact when
+//   the two are within a factor 2 (Sterbenz), so the FP32 result carries one
+//   rounding, the same as rounding the exact FP64 difference.
+//   f32_of(u) = hi + lo, u rounded to FP32.  f64_of(f): exact widening.
+// |u| below 2^-126 flushes to zero, above 2^128 (or NaN) gives +-inf; lo
+// flushes to zero below 2^-103 |u| scale.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 split_f64(double u) {
+  const unsigned hw = (unsigned)__double2hiint(u), lw = (unsigned)__double2loint(u);
+  const unsigned sg = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const int E = e - 896, Fe = e - 919;                   // FP32 exponent fields of hi and of lo's scale
+  const unsigned mh = ((hw & 0xFFFFFu) << 3) | (lw >> 29);   // top 23 mantissa bits
+  const unsigned ml = (lw & 0x1FFFFFFFu) >> 6;               // next 23 bits
+  F2 r;
+  r.hi = E <= 0 ? 0.0f : (E >= 255 ? __uint_as_float(sg | 0x7F800000u) : __uint_as_float(sg | ((unsigned)E << 23) | mh));
+  // 1.ml x 2^k minus 2^k = 0.ml x 2^k: exact in FP32, normalises lo
+  const unsigned lb = sg | ((unsigned)(Fe > 0 ? Fe : 1) << 23);
+  r.lo = (Fe > 0 && E < 255) ? __uint_as_float(lb | ml) - __uint_as_float(lb) : 0.0f;
+  return r;
+}
+
+__device__ __forceinline__ float f32_of(double u) {
+  const F2 s = split_f64(u);
+  return s.hi + s.lo;
+}
+
+__device__ __forceinline__ float f32_diff(const F2 &a, const F2 &b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu, sg = b & 0x80000000u, m = b & 0x7FFFFFu;
+  unsigned hw, lw = m << 29;
+  if (e == 0) { hw = sg; lw = 0; }                                   // zero (subnormals flushed)
+  else if (e == 255) hw = sg | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  else hw = sg | ((e + 896u) << 20) | (m >> 3);
+  return __hiloint2double((int)hw, (int)lw);
+}
+
+// loads and stores of FP64 data in arithmetic T
+template <typename T>
+__device__ __forceinline__ T ld_as(double u) {
+  if constexpr (sizeof(T) == 4) return f32_of(u);
+  else return u;
+}
+template <typename T>
+__device__ __forceinline__ double to_f64(T v) {
+  if constexpr (sizeof(T) == 4) return f64_of(v);
+  else return v;
+}
 
 // ------------------------------------------------------------------ small tensor helpers
 
@@ -108,28 +194,31 @@ __device__ inline Sym3 conf_metric(const double *U, size_t P, int id) {
 // or float in the mixed-precision hydro); every constant goes through T(...).
 template <typename T>
 __device__ inline T eos_pc(const DevParams &p, T rho) {
-  if (p.K == 0.0) return T(0);
-  return p.Gamma == 2.0 ? T(p.K) * (rho * rho) : T(p.K) * pow(rho, T(p.Gamma));
+  if (p.K_zero) return T(0);
+  const T K = pv<T>(p.K, p.fK);
+  return p.gamma2 ? K * (rho * rho) : K * pow(rho, pv<T>(p.Gamma, p.fGamma));
 }
 template <typename T>
 __device__ inline T eos_ec(const DevParams &p, T rho) {
-  if (p.K == 0.0) return T(0);
-  return p.Gamma == 2.0 ? T(p.K) * rho : T(p.K) * pow(rho, T(p.Gamma - 1.0)) / T(p.Gamma - 1.0);
+  if (p.K_zero) return T(0);
+  const T K = pv<T>(p.K, p.fK);
+  const T gm1 = pv<T>(p.Gamma - 1.0, p.fGm1);
+  return p.gamma2 ? K * rho : K * pow(rho, gm1) / gm1;
 }
 template <typename T>
 __device__ inline T eos_p(const DevParams &p, T rho, T eps) {
-  return eos_pc(p, rho) + T(p.Gamma_th - 1.0) * rho * (eps - eos_ec(p, rho));
+  return eos_pc(p, rho) + pv<T>(p.Gamma_th - 1.0, p.fGth1) * rho * (eps - eos_ec(p, rho));
 }
 template <typename T>
 __device__ inline T eos_eps(const DevParams &p, T rho, T P) {
-  return eos_ec(p, rho) + (P - eos_pc(p, rho)) / (T(p.Gamma_th - 1.0) * rho);
+  return eos_ec(p, rho) + (P - eos_pc(p, rho)) / (pv<T>(p.Gamma_th - 1.0, p.fGth1) * rho);
 }
 // c_s^2 rho h = Gamma P_cold + Gamma_th P_th, clamped to [0, 1)
 template <typename T>
 __device__ inline T eos_cs2(const DevParams &p, T rho, T eps, T P) {
   const T pc = eos_pc(p, rho);
   const T h = T(1) + eps + P / rho;
-  T c2 = (T(p.Gamma) * pc + T(p.Gamma_th) * (P - pc)) / (rho * h);
+  T c2 = (pv<T>(p.Gamma, p.fGamma) * pc + pv<T>(p.Gamma_th, p.fGamma_th) * (P - pc)) / (rho * h);
   if (!(c2 > T(0))) c2 = T(0);
   const T cmax = sizeof(T) == 8 ? T(1.0 - 1e-15) : T(1.0f - 1e-6f);
   if (c2 >= T(1)) c2 = cmax;

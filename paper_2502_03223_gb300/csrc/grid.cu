@@ -306,7 +306,10 @@ __global__ void k_reflux(Lev C, Lev Pa, double dt) {
 constexpr int DIAG_Q = 9;   // H^2 dV, Mx^2 dV, My^2 dV, Mz^2 dV, dV, qD dV, qSphi dV, rho_max, n_fail
 constexpr int DIAG_T = 128;
 
-__global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const double *__restrict__ DS, int covered,
+// S: storage type of the derivative scratch and the cartoon planes (FP32 in
+// the mixed-precision Z4c form); the constraint algebra is FP64 either way.
+template <typename S>
+__global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__restrict__ DS, int covered,
                                                  int evolve, double *__restrict__ partials) {
   __shared__ double sh[DIAG_Q][DIAG_T];
   const int t = threadIdx.x;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const doubl
           const double *u = U + (size_t)(fAXX + a) * P + id;
           dA[a][0] = (45.0 * (u[1] - u[-1]) - 9.0 * (u[2] - u[-2]) + (u[3] - u[-3])) * i60x;
           dA[a][2] = (45.0 * (u[L.px] - u[-L.px]) - 9.0 * (u[2 * L.px] - u[-2 * L.px]) + (u[3 * L.px] - u[-3 * L.px])) * i60z;
-          dA[a][1] = (cyl && a != 5) ? L.dy[(size_t)(fAXX + a) * P + id] : 0.0;
+          dA[a][1] = (cyl && a != 5) ? (double)reinterpret_cast<const S *>(L.dy)[(size_t)(fAXX + a) * P + id] : 0.0;
         }
         double M[3];
         for (int ii = 0; ii < 3; ++ii) {
@@ -501,7 +504,11 @@ int diag_blocks(const Lev &L) { return (L.nx * L.nz + DIAG_T - 1) / DIAG_T; }
 
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials, int slot,
                  cudaStream_t s) {
-  k_diag<<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, covered, evolve, partials + (size_t)slot * DIAG_Q);
+  if (p.mixed & SACRA_MIXED_Z4C)
+    k_diag<float><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, reinterpret_cast<const float *>(DS), covered, evolve,
+                                                    partials + (size_t)slot * DIAG_Q);
+  else
+    k_diag<double><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, covered, evolve, partials + (size_t)slot * DIAG_Q);
 }
 
 void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s) {

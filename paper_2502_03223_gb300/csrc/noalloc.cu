@@ -55,12 +55,9 @@ extern "C" sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level
   }
   double *scratch = g_scratch_addr[dev];
 
+  if (p->precision & ~SACRA_MIXED) return SACRA_ERR_ARG;
   DevParams d;
-  memset(&d, 0, sizeof(d));
-  d.geometry = p->geometry; d.evolve = p->evolve_spacetime; d.solver = p->solver; d.rk = p->rk;
-  d.c2p_maxit = p->c2p_maxit; d.n_levels = p->n_levels;
-  d.K = p->K; d.Gamma = p->Gamma; d.Gamma_th = p->Gamma_th; d.rho_atm = p->rho_atm; d.w_max = p->w_max;
-  d.c2p_tol = p->c2p_tol; d.kappa = p->kappa; d.eta_B = p->eta_B; d.eps_ko = p->eps_ko; d.r_z4 = p->r_z4;
+  fill_dev_params(p, &d);
 
   const size_t P = px * pz;   // the caller's plane stride
   Lev L;

@@ -39,3 +39,42 @@ extern "C" int sacra_probe_fp64(int blocks, int threads, int iters, int reps, do
   *tflops = flops / (best * 1e-3) / 1e12;
   return 0;
 }
+
+// Check of the integer-only FP64 <-> FP32 conversions the mixed-precision
+// kernels use (split_f64, f32_of, f64_of of common.cuh) against the hardware
+// conversions: for each input u, hi, lo, f32_of(u), the hardware
+// __double2float_rn(u), and f64_of(f32_of(u)) - (double)f32_of(u).
+#include "common.cuh"
+
+__global__ void k_split(const double *in, int n, float *hi, float *lo, float *f, float *hw, double *dback) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const sacra::F2 s = sacra::split_f64(in[i]);
+  hi[i] = s.hi;
+  lo[i] = s.lo;
+  const float v = sacra::f32_of(in[i]);
+  f[i] = v;
+  hw[i] = __double2float_rn(in[i]);
+  dback[i] = sacra::f64_of(v) - (double)v;
+}
+
+extern "C" int sacra_probe_split(const double *host_in, int n, float *host_hi, float *host_lo, float *host_f32,
+                                 float *host_hw, double *host_back_err) {
+  if (n <= 0) return -1;
+  double *din = nullptr, *dback = nullptr;
+  float *dbuf = nullptr;
+  if (cudaMalloc(&din, sizeof(double) * n) != cudaSuccess) return -1;
+  if (cudaMalloc(&dback, sizeof(double) * n) != cudaSuccess) { cudaFree(din); return -1; }
+  if (cudaMalloc(&dbuf, sizeof(float) * 4 * (size_t)n) != cudaSuccess) { cudaFree(din); cudaFree(dback); return -1; }
+  cudaMemcpy(din, host_in, sizeof(double) * n, cudaMemcpyHostToDevice);
+  k_split<<<(n + 127) / 128, 128>>>(din, n, dbuf, dbuf + n, dbuf + 2 * (size_t)n, dbuf + 3 * (size_t)n, dback);
+  cudaMemcpy(host_hi, dbuf, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  cudaMemcpy(host_lo, dbuf + n, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  cudaMemcpy(host_f32, dbuf + 2 * (size_t)n, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  cudaMemcpy(host_hw, dbuf + 3 * (size_t)n, sizeof(float) * n, cudaMemcpyDeviceToHost);
+  cudaMemcpy(host_back_err, dback, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  cudaFree(din);
+  cudaFree(dback);
+  cudaFree(dbuf);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}

@@ -5,6 +5,8 @@
 //   k_cartoon:    interpolate-and-rotate planes y = +-m dy -> d_y, d_yy scratch
 //   k_z4c_derivs: all x/z/mixed derivatives, advection + KO -> derivative scratch
 //   k_z4c_point:  pointwise Z4c algebra -> rhs
+#include <type_traits>
+
 #include "kernels.h"
 #include "z4c.cuh"
 
@@ -22,6 +24,12 @@ __device__ __forceinline__ double par_x(int f) {
     default:
       return 1.0;
   }
+}
+
+// x-parity of the cartoon fields in kCartoonFields order (compile-time form)
+__host__ __device__ constexpr float par_x_slot(int a) {
+  return (a == 4 || a == 6 || a == 10 || a == 12 || a == 13 || a == 14 || a == 16 || a == 17 || a == 18 || a == 19)
+             ? -1.0f : 1.0f;
 }
 
 // rotate interpolated base values v[20] (ordered as kCartoonFields) by phi
@@ -130,7 +138,8 @@ __device__ __forceinline__ void deltas_ten(float c1, float sn, const float u[5],
   d[4] = sn * u[2] + c1 * u[4] + (sn * s[2] + c * s[4]);
 }
 
-__global__ void k_cartoon_f32(Lev L, const double *__restrict__ U, const double *__restrict__ tab, int tab_stride) {
+__global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
+                                                     int tab_stride) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x - 2;
   const int k = blockIdx.y * blockDim.y + threadIdx.y - 2;
   if (j > L.nx + 4 || k > L.nz + 7) return;
@@ -138,69 +147,81 @@ __global__ void k_cartoon_f32(Lev L, const double *__restrict__ U, const double 
   const int jj = flip ? 1 - j : j;
   const size_t P = L.P;
   const int c0 = cid(L, jj, k);
-  double base0[20];
-  float u0[20];
+  float w[3][9], cm1[3], sn[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const double *t = tab + (size_t)(jj * 3 + m) * tab_stride;   // 9 weights, cos, sin, cos - 1
+#pragma unroll
+    for (int n = 0; n < 9; ++n) w[m][n] = f32_of(t[n]);
+    sn[m] = f32_of(t[10]);
+    cm1[m] = f32_of(t[11]);
+  }
+  // interpolated minus centre value on the three planes, from exact FP64 differences
+  float u0[20], sv[3][20];
 #pragma unroll
   for (int a = 0; a < 20; ++a) {
-    base0[a] = U[(size_t)kCartoonFields[a] * P + c0];
-    u0[a] = (float)base0[a];
+    const double *u = U + (size_t)kCartoonFields[a] * P + c0 - 4;
+    const F2 c = split_f64(u[4]);
+    u0[a] = c.hi + c.lo;
+    float dn[9];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) dn[n] = n == 4 ? 0.0f : f32_diff(split_f64(u[n]), c);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int n = 0; n < 9; ++n) acc += w[m][n] * dn[n];
+      sv[m][a] = acc;
+    }
   }
   float d1[20], d2[20];
 #pragma unroll
   for (int a = 0; a < 20; ++a) { d1[a] = 0.0f; d2[a] = 0.0f; }
   const float c1w[3] = {45.0f, -9.0f, 1.0f}, c2w[3] = {270.0f, -27.0f, 2.0f};
-  for (int m = 1; m <= 3; ++m) {
-    const double *t = tab + (size_t)(jj * 3 + (m - 1)) * tab_stride;   // 9 weights, cos, sin
-    float w[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) w[n] = (float)t[n];
-    float sv[20];
-#pragma unroll
-    for (int a = 0; a < 20; ++a) {
-      const double *u = U + (size_t)kCartoonFields[a] * P + c0 - 4;
-      float acc = 0.0f;
-#pragma unroll
-      for (int n = 0; n < 9; ++n) acc += w[n] * (float)(u[n] - base0[a]);
-      sv[a] = acc;
-    }
-    const float c1 = (float)(t[9] - 1.0), sn = (float)t[10];
+  for (int m = 0; m < 3; ++m) {
+    const float c1 = cm1[m], s1 = sn[m];
+    const float *v = sv[m];
     float dp[20], dm[20];   // plane (+m), plane (-m) minus centre, at jj
-    dp[0] = dm[0] = sv[0];
-    dp[1] = dm[1] = sv[1];
-    deltas_ten(c1, sn, u0 + 2, sv + 2, dp + 2);
-    deltas_ten(c1, -sn, u0 + 2, sv + 2, dm + 2);
-    dp[7] = dm[7] = sv[7];                 // h_zz
-    deltas_ten(c1, sn, u0 + 8, sv + 8, dp + 8);
-    deltas_ten(c1, -sn, u0 + 8, sv + 8, dm + 8);
-    deltas_vec(c1, sn, u0[13], u0[14], sv[13], sv[14], dp[13], dp[14]);
-    deltas_vec(c1, -sn, u0[13], u0[14], sv[13], sv[14], dm[13], dm[14]);
-    dp[15] = dm[15] = sv[15];              // beta^z
-    deltas_vec(c1, sn, u0[16], u0[17], sv[16], sv[17], dp[16], dp[17]);
-    deltas_vec(c1, -sn, u0[16], u0[17], sv[16], sv[17], dm[16], dm[17]);
-    deltas_vec(c1, sn, u0[18], u0[19], sv[18], sv[19], dp[18], dp[19]);
-    deltas_vec(c1, -sn, u0[18], u0[19], sv[18], sv[19], dm[18], dm[19]);
-    const float w1 = c1w[m - 1], w2 = c2w[m - 1];
+    dp[0] = dm[0] = v[0];
+    dp[1] = dm[1] = v[1];
+    deltas_ten(c1, s1, u0 + 2, v + 2, dp + 2);
+    deltas_ten(c1, -s1, u0 + 2, v + 2, dm + 2);
+    dp[7] = dm[7] = v[7];                 // h_zz
+    deltas_ten(c1, s1, u0 + 8, v + 8, dp + 8);
+    deltas_ten(c1, -s1, u0 + 8, v + 8, dm + 8);
+    deltas_vec(c1, s1, u0[13], u0[14], v[13], v[14], dp[13], dp[14]);
+    deltas_vec(c1, -s1, u0[13], u0[14], v[13], v[14], dm[13], dm[14]);
+    dp[15] = dm[15] = v[15];              // beta^z
+    deltas_vec(c1, s1, u0[16], u0[17], v[16], v[17], dp[16], dp[17]);
+    deltas_vec(c1, -s1, u0[16], u0[17], v[16], v[17], dm[16], dm[17]);
+    deltas_vec(c1, s1, u0[18], u0[19], v[18], v[19], dp[18], dp[19]);
+    deltas_vec(c1, -s1, u0[18], u0[19], v[18], v[19], dm[18], dm[19]);
+    const float w1 = c1w[m], w2 = c2w[m];
 #pragma unroll
     for (int a = 0; a < 20; ++a) {
       // at flipped points the +m plane is par * (-m plane of jj) and vice versa
-      const float pr = (float)par_x(kCartoonFields[a]);
+      const float pr = par_x_slot(a);
       const float plus = flip ? pr * dm[a] : dp[a];
       const float minus = flip ? pr * dp[a] : dm[a];
       d1[a] += w1 * (plus - minus);
       d2[a] += w2 * (plus + minus);
     }
   }
+  // FP32 planes (same plane stride as the FP64 layout)
+  float *dyf = reinterpret_cast<float *>(L.dy);
+  float *dyyf = reinterpret_cast<float *>(L.dyy);
   const int o = cid(L, j, k);
   const float i1 = (float)(1.0 / (60.0 * L.dx)), i2 = (float)(1.0 / (180.0 * L.dx * L.dx));
 #pragma unroll
   for (int a = 2; a < 20; ++a) {
     const int f = kCartoonFields[a];
     if (f == fHZZ || f == fBZ) continue;
-    L.dy[(size_t)f * P + o] = (double)(d1[a] * i1);
+    dyf[(size_t)f * P + o] = d1[a] * i1;
   }
   const int sec[11] = {0, 1, 2, 3, 4, 5, 6, 7, 13, 14, 15};
 #pragma unroll
-  for (int b = 0; b < 11; ++b) L.dyy[(size_t)kCartoonFields[sec[b]] * P + o] = (double)(d2[sec[b]] * i2);
+  for (int b = 0; b < 11; ++b) dyyf[(size_t)kCartoonFields[sec[b]] * P + o] = d2[sec[b]] * i2;
 }
 
 // ---------------------------------------------------------------- derivative pass
@@ -329,28 +350,180 @@ __global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const do
   }
 }
 
+// Mixed-precision derivative pass.  The block stages each field's tile with
+// a 4-cell halo in shared memory as FP32 (hi, lo) splits (integer bit
+// operations, no FP64 instruction), so every stencil difference is one
+// rounding of the exact FP64 difference, and the weighted sums run in FP32.
+// Outputs (the derivative scratch, same plane layout as the FP64 pass) are
+// FP32; the cartoon planes it reads are FP32 as well.
+constexpr int DTX = 32, DTZ = 8, DHX = DTX + 8, DHZ = DTZ + 8;
+
+__host__ __device__ constexpr int d1_of(int f) {
+  return f <= fHZZ ? f : (f == fKH ? 7 : (f >= fGX && f <= fGZ ? 8 + f - fGX : (f == fTH ? 11 : (f == fAL ? 12 : (f >= fBX && f <= fBZ ? 13 + f - fBX : -1)))));
+}
+__host__ __device__ constexpr int d2_of(int f) {
+  return f <= fHZZ ? f : (f == fAL ? 7 : (f >= fBX && f <= fBZ ? 8 + f - fBX : -1));
+}
+// calls fn(std::integral_constant<int, F>) for F = F0 .. NMET - 1 (compile-time field loop)
+template <int F0>
+struct FieldLoop {
+  template <class Fn>
+  __device__ __forceinline__ static void run(Fn &&fn) {
+    fn(std::integral_constant<int, F0>{});
+    FieldLoop<F0 + 1>::run(fn);
+  }
+};
+template <>
+struct FieldLoop<NMET> {
+  template <class Fn>
+  __device__ __forceinline__ static void run(Fn &&) {}
+};
+
+__host__ __device__ constexpr bool y_zero_c(int f) {
+  return f == fW || f == fKH || f == fTH || f == fAL || f == fGZ || f == fBZ || f == fBBZ || f == fHZZ || f == fAZZ;
+}
+
+__global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,
+                                                              float *__restrict__ DS, int jmax, int kmax, int cyl) {
+  __shared__ float2 tile[DHZ][DHX];
+  const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * DTX + tx;
+  const int j0 = blockIdx.x * DTX + 1, k0 = blockIdx.y * DTZ + 1;
+  const int j = j0 + tx, k = k0 + tz;
+  const bool live = j <= jmax && k <= kmax;
+  const size_t P = L.P;
+  const int id = cid(L, live ? j : 1, live ? k : 1);
+  const int jlim = L.nx + GH, klim = L.nz + GH;
+  const float *dyf = reinterpret_cast<const float *>(L.dy);
+  const float *dyyf = reinterpret_cast<const float *>(L.dyy);
+  const float i60x = (float)(1.0 / (60.0 * L.dx)), i60z = (float)(1.0 / (60.0 * L.dz));
+  const float i180x = (float)(1.0 / (180.0 * L.dx * L.dx)), i180z = (float)(1.0 / (180.0 * L.dz * L.dz));
+  const float ixz = (float)(1.0 / (3600.0 * L.dx * L.dz));
+  const float ko = (float)(-p.eps_ko / 256.0);
+  const float ikx = (float)(1.0 / L.dx), ikz = (float)(1.0 / L.dz);
+  const bool edge = cyl && j > L.nx;
+  const float bx = f32_of(U[(size_t)fBX * P + id]), by = f32_of(U[(size_t)fBY * P + id]),
+              bz = f32_of(U[(size_t)fBZ * P + id]);
+  float ev[7], ed[7];   // edge formula: values and d_x of h_xx, h_xy, h_xz, h_yy, h_yz, beta^x, beta^y
+#pragma unroll
+  for (int q = 0; q < 7; ++q) ev[q] = ed[q] = 0.0f;
+
+  FieldLoop<0>::run([&](auto fc) {
+    constexpr int f = decltype(fc)::value;
+    const double *Uf = U + (size_t)f * P;
+    for (int e = tid; e < DHX * DHZ; e += DTX * DTZ) {
+      const int ex = e % DHX, ez = e / DHX;
+      const int gj = j0 - 4 + ex, gk = k0 - 4 + ez;
+      F2 v = {0.0f, 0.0f};
+      if (gj <= jlim && gk <= klim) v = split_f64(Uf[cid(L, gj, gk)]);
+      tile[ez][ex] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    if (live) {
+      const int cx = tx + 4, cz = tz + 4;
+      const float2 c = tile[cz][cx];
+      auto at = [&](int dx, int dz) { return tile[cz + dz][cx + dx]; };
+      auto df = [&](float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); };
+      float Dx[9], Dz[9];   // u(n) - u(0), n = -4..4
+#pragma unroll
+      for (int n = -4; n <= 4; ++n) {
+        Dx[n + 4] = n == 0 ? 0.0f : df(at(n, 0), c);
+        Dz[n + 4] = n == 0 ? 0.0f : df(at(0, n), c);
+      }
+      constexpr int a1 = d1_of(f), a2 = d2_of(f);
+      float d1x = 0.0f;
+      if constexpr (a1 >= 0) {
+        d1x = (45.0f * df(at(1, 0), at(-1, 0)) - 9.0f * df(at(2, 0), at(-2, 0)) + df(at(3, 0), at(-3, 0))) * i60x;
+        const float d1z = (45.0f * df(at(0, 1), at(0, -1)) - 9.0f * df(at(0, 2), at(0, -2)) + df(at(0, 3), at(0, -3))) * i60z;
+        DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = d1x;
+        DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = d1z;
+        DS[(size_t)(DS_D1 + 3 * a1 + 1) * P + id] = (cyl && !y_zero_c(f)) ? dyf[(size_t)f * P + id] : 0.0f;
+      }
+      if constexpr (a2 >= 0) {
+        float dxz = 0.0f;
+#pragma unroll
+        for (int n = 1; n <= 3; ++n) {
+          const float w = n == 1 ? 45.0f : (n == 2 ? -9.0f : 1.0f);
+          const float zp = 45.0f * df(at(n, 1), at(n, -1)) - 9.0f * df(at(n, 2), at(n, -2)) + df(at(n, 3), at(n, -3));
+          const float zm = 45.0f * df(at(-n, 1), at(-n, -1)) - 9.0f * df(at(-n, 2), at(-n, -2)) + df(at(-n, 3), at(-n, -3));
+          dxz += w * (zp - zm);
+        }
+        float dxy = 0.0f, dyz = 0.0f, dyy = 0.0f;
+        if (cyl) {
+          dyy = dyyf[(size_t)f * P + id];
+          if (!y_zero_c(f)) {
+            const float *q = dyf + (size_t)f * P + id;
+            const int sz = L.px;
+            dyz = (45.0f * (q[sz] - q[-sz]) - 9.0f * (q[2 * sz] - q[-2 * sz]) + (q[3 * sz] - q[-3 * sz])) * i60z;
+            if (!edge) dxy = (45.0f * (q[1] - q[-1]) - 9.0f * (q[2] - q[-2]) + (q[3] - q[-3])) * i60x;
+          }
+        }
+        float *o = DS + (size_t)(DS_D2 + 6 * a2) * P + id;
+        o[0] = (270.0f * (Dx[5] + Dx[3]) - 27.0f * (Dx[6] + Dx[2]) + 2.0f * (Dx[7] + Dx[1])) * i180x;
+        o[P] = dxy;
+        o[2 * P] = dxz * ixz;
+        o[3 * P] = dyy;
+        o[4 * P] = dyz;
+        o[5 * P] = (270.0f * (Dz[5] + Dz[3]) - 27.0f * (Dz[6] + Dz[2]) + 2.0f * (Dz[7] + Dz[1])) * i180z;
+      }
+      // advection: lopsided in x and z (upwind side of the shift), central in y from the planes; KO
+      float adv = 0.0f;
+      auto lop = [](const float *D, float v) {   // upwind-biased stencil, side of sign(v)
+        if (v > 0.0f) return 2.0f * D[2] - 24.0f * D[3] + 80.0f * D[5] - 30.0f * D[6] + 8.0f * D[7] - D[8];
+        if (v < 0.0f) return -(2.0f * D[6] - 24.0f * D[5] + 80.0f * D[3] - 30.0f * D[2] + 8.0f * D[1] - D[0]);
+        return 0.0f;
+      };
+      adv += bx * lop(Dx, bx) * i60x + bz * lop(Dz, bz) * i60z;
+      if (cyl && !y_zero_c(f)) adv += by * dyf[(size_t)f * P + id];
+      const float kx = (Dx[8] + Dx[0]) - 8.0f * (Dx[7] + Dx[1]) + 28.0f * (Dx[6] + Dx[2]) - 56.0f * (Dx[5] + Dx[3]);
+      const float kz = (Dz[8] + Dz[0]) - 8.0f * (Dz[7] + Dz[1]) + 28.0f * (Dz[6] + Dz[2]) - 56.0f * (Dz[5] + Dz[3]);
+      adv += ko * (kx * ikx + kz * ikz);
+      DS[(size_t)(DS_AK + f) * P + id] = adv;
+      constexpr int eq = f == fHXX ? 0 : f == fHXY ? 1 : f == fHXZ ? 2 : f == fHYY ? 3 : f == fHYZ ? 4 : f == fBX ? 5 : f == fBY ? 6 : -1;
+      if constexpr (eq >= 0) {
+        ev[eq] = c.x + c.y;
+        ed[eq] = d1x;
+      }
+    }
+    __syncthreads();
+  });
+  if (live && edge) {
+    // Eq. cartoon_bnd for cells beyond the level edge: d_xy from d_x and values
+    const float x = (float)((j - 0.5) * L.dx);
+    const float ix = 1.0f / x, ix2 = ix * ix;
+    auto put = [&](int a, float v) { DS[(size_t)(DS_D2 + 6 * a + 1) * P + id] = v; };
+    put(8, ev[6] * ix2 - ed[6] * ix);
+    put(9, -ev[5] * ix2 + ed[5] * ix);
+    put(3, ev[4] * ix2 - ed[4] * ix);
+    put(5, -ev[2] * ix2 + ed[2] * ix);
+    const float txy = ev[1] * ix2 - ed[1] * ix;
+    put(1, 2.0f * txy);
+    put(4, -2.0f * txy);
+    put(2, (ev[3] - ev[0]) * ix2 + (ed[0] - ed[3]) * ix);
+  }
+}
+
 // ---------------------------------------------------------------- pointwise pass
 
 template <typename T>
-__device__ inline void load_z4c_in(const Lev &L, const double *__restrict__ U, const double *__restrict__ DS, int id,
+__device__ inline void load_z4c_in(const Lev &L, const double *__restrict__ U, const T *__restrict__ DS, int id,
                                    Z4cIn<T> &z) {
   const size_t P = L.P;
-  z.W = T(U[(size_t)fW * P + id]);
-  z.al = T(U[(size_t)fAL * P + id]);
-  z.Kh = T(U[(size_t)fKH * P + id]);
-  z.Th = T(U[(size_t)fTH * P + id]);
+  z.W = ld_as<T>(U[(size_t)fW * P + id]);
+  z.al = ld_as<T>(U[(size_t)fAL * P + id]);
+  z.Kh = ld_as<T>(U[(size_t)fKH * P + id]);
+  z.Th = ld_as<T>(U[(size_t)fTH * P + id]);
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    z.h[a] = T(U[(size_t)(fHXX + a) * P + id]);
-    z.A[a] = T(U[(size_t)(fAXX + a) * P + id]);
+    z.h[a] = ld_as<T>(U[(size_t)(fHXX + a) * P + id]);
+    z.A[a] = ld_as<T>(U[(size_t)(fAXX + a) * P + id]);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    z.Gt[i] = T(U[(size_t)(fGX + i) * P + id]);
-    z.beta[i] = T(U[(size_t)(fBX + i) * P + id]);
-    z.B[i] = T(U[(size_t)(fBBX + i) * P + id]);
+    z.Gt[i] = ld_as<T>(U[(size_t)(fGX + i) * P + id]);
+    z.beta[i] = ld_as<T>(U[(size_t)(fBX + i) * P + id]);
+    z.B[i] = ld_as<T>(U[(size_t)(fBBX + i) * P + id]);
   }
-  auto d1 = [&](int a, int k) { return T(DS[(size_t)(DS_D1 + 3 * a + k) * P + id]); };
+  auto d1 = [&](int a, int k) { return DS[(size_t)(DS_D1 + 3 * a + k) * P + id]; };
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     z.dW[k] = d1(0, k);
@@ -364,7 +537,7 @@ __device__ inline void load_z4c_in(const Lev &L, const double *__restrict__ U, c
 #pragma unroll
     for (int i = 0; i < 3; ++i) z.db[i][k] = d1(13 + i, k);
   }
-  auto d2 = [&](int a, int q) { return T(DS[(size_t)(DS_D2 + 6 * a + q) * P + id]); };
+  auto d2 = [&](int a, int q) { return DS[(size_t)(DS_D2 + 6 * a + q) * P + id]; };
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     z.ddW[q] = d2(0, q);
@@ -378,7 +551,7 @@ __device__ inline void load_z4c_in(const Lev &L, const double *__restrict__ U, c
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const double *__restrict__ U,
-                                                    const double *__restrict__ DS, int jmax, int kmax) {
+                                                    const T *__restrict__ DS, int jmax, int kmax) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
   const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
   if (j > jmax || k > kmax) return;
@@ -391,15 +564,23 @@ __global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const dou
   geo_ricci(z, G);
   T pr[NPRIM];
 #pragma unroll
-  for (int f = 0; f < NPRIM; ++f) pr[f] = T(L.prim[(size_t)f * P + id]);
+  for (int f = 0; f < NPRIM; ++f) pr[f] = ld_as<T>(L.prim[(size_t)f * P + id]);
   T E, Si[3], Sij[6];
   matter(pr, z.W, G.g, G.gi, E, Si, Sij);
-  const double x = (j - 0.5) * L.dx, zc = (k - 0.5) * L.dz;
-  const T fz = T(exp(-(x * x + zc * zc) / (p.r_z4 * p.r_z4)));
+  T fz;
+  if constexpr (sizeof(T) == 4) {
+    const float x = ((float)j - 0.5f) * f32_of(L.dx), zc = ((float)k - 0.5f) * f32_of(L.dz);
+    fz = expf(-(x * x + zc * zc) * p.firz2);
+  } else {
+    const double x = (j - 0.5) * L.dx, zc = (k - 0.5) * L.dz;
+    fz = exp(-(x * x + zc * zc) / (p.r_z4 * p.r_z4));
+  }
   T src[NMET];
   z4c_source(p, z, G, E, Si, Sij, fz, src);
 #pragma unroll
-  for (int f = 0; f < NMET; ++f) L.rhs[(size_t)f * P + id] = (double)src[f] + DS[(size_t)(DS_AK + f) * P + id];
+  // FP64: source + advection/KO in FP64; FP32: their FP32 sum, widened exactly
+#pragma unroll
+  for (int f = 0; f < NMET; ++f) L.rhs[(size_t)f * P + id] = to_f64<T>(src[f] + DS[(size_t)(DS_AK + f) * P + id]);
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -407,7 +588,7 @@ __global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const dou
 void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const double *DS, int jmax, int kmax,
                       cudaStream_t s) {
   dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
-  if (p.mixed & SACRA_MIXED_Z4C) k_z4c_point<float><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax);
+  if (p.mixed & SACRA_MIXED_Z4C) k_z4c_point<float><<<g, b, 0, s>>>(L, p, U, reinterpret_cast<const float *>(DS), jmax, kmax);
   else k_z4c_point<double><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax);
 }
 
@@ -418,9 +599,13 @@ void launch_cartoon(const Lev &L, const DevParams &p, const double *U, const dou
 }
 
 void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s) {
-  dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
-  if (p.mixed & SACRA_MIXED_Z4C) k_z4c_derivs<float><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax, p.geometry == SACRA_CYLINDRICAL);
-  else k_z4c_derivs<double><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax, p.geometry == SACRA_CYLINDRICAL);
+  if (p.mixed & SACRA_MIXED_Z4C) {
+    dim3 b(DTX, DTZ), g((jmax + DTX - 1) / DTX, (kmax + DTZ - 1) / DTZ);
+    k_z4c_derivs_f32<<<g, b, 0, s>>>(L, p, U, reinterpret_cast<float *>(DS), jmax, kmax, p.geometry == SACRA_CYLINDRICAL);
+  } else {
+    dim3 b(32, 4), g((jmax + 31) / 32, (kmax + 3) / 4);
+    k_z4c_derivs<double><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax, p.geometry == SACRA_CYLINDRICAL);
+  }
 }
 
 int z4c_scratch_planes() { return DS_N; }

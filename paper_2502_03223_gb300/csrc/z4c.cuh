@@ -143,7 +143,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
   const T gm[3][3] = {{G.g.xx, G.g.xy, G.g.xz}, {G.g.xy, G.g.yy, G.g.yz}, {G.g.xz, G.g.yz, G.g.zz}};
   const T W = z.W, al = z.al;
   const T K = z.Kh + T(2.0) * z.Th;
-  const T kap = T(p.kappa) * fz;
+  const T kap = pv<T>(p.kappa, p.fkappa) * fz;
   const T divb = z.db[0][0] + z.db[1][1] + z.db[2][2];
   const T iW = T(1.0) / W;
 
@@ -224,7 +224,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
         + T(2.0) * (gi.xy * z.ddb[i][1] + gi.xz * z.ddb[i][2] + gi.yz * z.ddb[i][4]);
     s += T(2.0) * al * in + (T(2.0) / T(3.0)) * G.Gd[i] * divb + lap + grad / T(3.0) - T(2.0) * al * kap * (z.Gt[i] - G.Gd[i]);
     out[fGX + i] = s;
-    out[fBBX + i] = s - T(p.eta_B) * z.B[i];
+    out[fBBX + i] = s - pv<T>(p.eta_B, p.feta_B) * z.B[i];
   }
 
   out[fTH] = fz * (T(0.5) * al * (G.Rs - AA + (T(2.0) / T(3.0)) * K * K) - T(8.0) * PI * al * E) - T(2.0) * al * kap * z.Th;
