@@ -262,9 +262,9 @@ void enqueue_restrict(sacra_ctx *c) {
     const int nh = Pa.nx / 2;
     run(c, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, c->stream); });
     run(c, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, c->dt_step, c->stream); });
-    run(c, K_C2P, (long long)nh * nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, 1, nh, c->stream); });
-    run(c, K_C2P, nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, nh + 1, nh + 1, 1, nh, c->stream); });
-    run(c, K_C2P, nh, [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh, nh + 1, nh + 1, c->stream); });
+    // the restricted cells [1, N/2]^2 and the refluxed strips next to them (not the corner)
+    run(c, K_C2P, (long long)(nh + 1) * (nh + 1) - 1,
+        [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh + 1, 1, nh + 1, c->stream, 1); });
   }
   // the parents' axis/equator ghosts mirror their restricted interiors
   for (int l = 0; l < L - 1; ++l) enqueue_parity(c, l, c->lv[l].un);
@@ -340,6 +340,8 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
     L.nx = p->nx; L.nz = p->nz; L.px = p->nx + 2 * GH; L.pz = p->nz + 2 * GH; L.rw = (int)rwp;
     L.dx = p->dx0 / (double)(1 << l);
     L.dz = p->dz0 / (double)(1 << l);
+    L.i60x = 1.0 / (60.0 * L.dx);
+    L.i60z = 1.0 / (60.0 * L.dz);
     L.P = P;
     double *dp = (double *)b;
     L.un = dp; dp += NST * P;

@@ -34,6 +34,7 @@ struct DevParams {
   int K_zero, gamma2;    // K == 0 (pure Gamma-law), Gamma == 2
   double K, Gamma, Gamma_th, rho_atm, w_max, c2p_tol;
   double kappa, eta_B, eps_ko, r_z4;
+  double c2p_kmax;       // 2 v_max / (1 + v_max^2), v_max = sqrt(1 - 1 / w_max^2)
   // FP32 copies for the mixed-precision kernels (no conversions on the device)
   float fK, fGamma, fGm1, fGamma_th, fGth1, fkappa, feta_B, firz2;
 };
@@ -57,12 +58,15 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->fGamma_th = (float)p->Gamma_th; d->fGth1 = (float)(p->Gamma_th - 1.0);
   d->fkappa = (float)p->kappa; d->feta_B = (float)p->eta_B;
   d->firz2 = (float)(1.0 / (p->r_z4 * p->r_z4));
+  const double vmax = sqrt(1.0 - 1.0 / (p->w_max * p->w_max));
+  d->c2p_kmax = 2.0 * vmax / (1.0 + vmax * vmax);
 }
 
 // One refinement level as seen by a kernel: planes of P = px * pz doubles.
 struct Lev {
   int nx, nz, px, pz, rw;
   double dx, dz;
+  double i60x, i60z;            // 1 / (60 dx), 1 / (60 dz)
   size_t P;
   double *un, *us, *ka, *rhs;   // NST planes each
   double *prim;                 // NPRIM planes
@@ -323,8 +327,7 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
   double r = sqrt(W * W * s3quad(gi, S, S)) / D;
   const double qq = E / D - 1.0;
   double k = r / (1.0 + qq);
-  const double vmax = sqrt(1.0 - 1.0 / (p.w_max * p.w_max));
-  const double kmax = 2.0 * vmax / (1.0 + vmax * vmax);
+  const double kmax = p.c2p_kmax;
   if (k > kmax) {
     const double s = kmax / k;
     S[0] *= s; S[1] *= s; S[2] *= s;

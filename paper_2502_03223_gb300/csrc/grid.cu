@@ -30,29 +30,39 @@ __device__ __forceinline__ double sgn_z(int f) {
   }
 }
 
-// axis ghosts j in [-7, 0] for rows [1, nz+8] (metric + primitives)
+// axis ghosts j in [-7, 0] for rows [1, nz+8]; blockIdx.z: plane (25 metric
+// fields, then the 6 primitives)
 __global__ void k_parity_x(Lev L, double *__restrict__ U) {
   const int j = -7 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
   if (j > 0 || k > L.nz + GH) return;
-  const size_t P = L.P;
+  const int f = blockIdx.z;
   const int d = cid(L, j, k), s = cid(L, 1 - j, k);
-  for (int f = 0; f < NMET; ++f) U[(size_t)f * P + d] = sgn_x(f) * U[(size_t)f * P + s];
-#pragma unroll
-  for (int f = 0; f < NPRIM; ++f)
-    L.prim[(size_t)f * P + d] = ((f == pUX || f == pUY) ? -1.0 : 1.0) * L.prim[(size_t)f * P + s];
+  if (f < NMET) {
+    double *u = U + (size_t)f * L.P;
+    u[d] = sgn_x(f) * u[s];
+  } else {
+    const int q = f - NMET;
+    double *u = L.prim + (size_t)q * L.P;
+    u[d] = ((q == pUX || q == pUY) ? -1.0 : 1.0) * u[s];
+  }
 }
 
-// equator ghosts k in [-7, 0] for all columns
+// equator ghosts k in [-7, 0] for all columns; blockIdx.z as above
 __global__ void k_parity_z(Lev L, double *__restrict__ U) {
   const int j = -7 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   const int k = -7 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
   if (j > L.nx + GH || k > 0) return;
-  const size_t P = L.P;
+  const int f = blockIdx.z;
   const int d = cid(L, j, k), s = cid(L, j, 1 - k);
-  for (int f = 0; f < NMET; ++f) U[(size_t)f * P + d] = sgn_z(f) * U[(size_t)f * P + s];
-#pragma unroll
-  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = (f == pUZ ? -1.0 : 1.0) * L.prim[(size_t)f * P + s];
+  if (f < NMET) {
+    double *u = U + (size_t)f * L.P;
+    u[d] = sgn_z(f) * u[s];
+  } else {
+    const int q = f - NMET;
+    double *u = L.prim + (size_t)q * L.P;
+    u[d] = (q == pUZ ? -1.0 : 1.0) * u[s];
+  }
 }
 
 // planar slab: zero-gradient copy into every ghost cell
@@ -72,10 +82,24 @@ __global__ void k_outflow(Lev L, double *__restrict__ U) {
 // Outer boundary of the coarsest level (Sec. II.B.3): Q = Q_inf + (1 - tau/r)
 // (Q^n - Q_inf)(r - tau), quadratic (3x3) Lagrange interpolation of the step-
 // start state Un; hydro primitives copied from the nearest interior cell.
+// Threads: the L-shaped strip {j > nx or k > nz} of [1, nx+8] x [1, nz+8],
+// indexed compactly (rows k > nz first), times kOuterGroups groups of fields
+// (blockIdx.y) that share the interpolation weights.
+constexpr int kOuterGroups = 5;
+
 __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict__ U, double tau) {
-  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
-  if (j > L.nx + GH || k > L.nz + GH || (j <= L.nx && k <= L.nz)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = L.nx + GH, top = GH * w;
+  int j, k;
+  if (i < top) {
+    j = 1 + i % w;
+    k = L.nz + 1 + i / w;
+  } else {
+    i -= top;
+    if (i >= GH * L.nz) return;
+    j = L.nx + 1 + i % GH;
+    k = 1 + i / GH;
+  }
   const size_t P = L.P;
   const double x = (j - 0.5) * L.dx, z = (k - 0.5) * L.dz;
   const double r = sqrt(x * x + z * z);
@@ -86,7 +110,7 @@ __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict
   const double wx[3] = {0.5 * tx * (tx - 1.0), (1.0 - tx) * (1.0 + tx), 0.5 * tx * (tx + 1.0)};
   const double wz[3] = {0.5 * tz * (tz - 1.0), (1.0 - tz) * (1.0 + tz), 0.5 * tz * (tz + 1.0)};
   const int d = cid(L, j, k), c0 = cid(L, i0, k0);
-  for (int f = 0; f < NMET; ++f) {
+  for (int f = blockIdx.y; f < NMET; f += kOuterGroups) {
     const double qinf = (f == fW || f == fAL) ? 1.0 : 0.0;
     const double *u = Un + (size_t)f * P + c0;
     const double u0 = u[0] - qinf;
@@ -97,9 +121,11 @@ __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict
       for (int a = 0; a < 3; ++a) s += wx[a] * wz[b] * (u[(b - 1) * L.px + (a - 1)] - qinf - u0);
     U[(size_t)f * P + d] = qinf + fac * (u0 + s);
   }
-  const int sc = cid(L, min(j, L.nx), min(k, L.nz));
+  if (blockIdx.y == 0) {
+    const int sc = cid(L, min(j, L.nx), min(k, L.nz));
 #pragma unroll
-  for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = L.prim[(size_t)f * P + sc];
+    for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = L.prim[(size_t)f * P + sc];
+  }
 }
 
 __device__ __forceinline__ double minmod(double a, double b) {
@@ -246,21 +272,24 @@ __global__ void __launch_bounds__(128) k_rk_update(Lev L, DevParams p, const dou
 // Restriction of child level C onto parent cells [1, N/2]^2 (Sec. II.D):
 // q as the volume-weighted average of the 2x2 children, the metric by 8th-
 // order Lagrange (nodes shifted inward so that none passes the child edge N).
+// blockIdx.z: the field (metric 0..24, conserved 25..29).
 __global__ void k_restrict(Lev C, Lev Pa) {
   const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
   const int nh = Pa.nx / 2;
   if (j > nh || k > nh) return;
+  const int f = blockIdx.z;
   const size_t P = C.P, PP = Pa.P;
   const int d = cid(Pa, j, k);
-  const double xp = (j - 0.5) * Pa.dx;
-  const double xa = (2 * j - 1.5) * C.dx, xb = (2 * j - 0.5) * C.dx;
   const int c00 = cid(C, 2 * j - 1, 2 * k - 1);
-  for (int v = 0; v < NCONS; ++v) {
-    const double *q = C.un + (size_t)(fQD + v) * P + c00;
+  if (f >= NMET) {
+    const double xp = (j - 0.5) * Pa.dx;
+    const double xa = (2 * j - 1.5) * C.dx, xb = (2 * j - 0.5) * C.dx;
+    const double *q = C.un + (size_t)f * P + c00;
     // (x-weighted sum of 4 children) * dxc dzc / (x_p dxp dzp); dxp dzp = 4 dxc dzc
     const double s = xa * (q[0] + q[C.px]) + xb * (q[1] + q[C.px + 1]);
-    Pa.un[(size_t)(fQD + v) * PP + d] = s / (4.0 * xp);
+    Pa.un[(size_t)f * PP + d] = s / (4.0 * xp);
+    return;
   }
   const double *wx, *wz;
   int bx, bz;
@@ -268,18 +297,16 @@ __global__ void k_restrict(Lev C, Lev Pa) {
   if (j <= nh - 2) { wx = cW.rest_c; bx = 2 * j - 4; } else { wx = (j == nh) ? cW.rest_s0 : cW.rest_s1; bx = N - 7; }
   if (k <= nh - 2) { wz = cW.rest_c; bz = 2 * k - 4; } else { wz = (k == nh) ? cW.rest_s0 : cW.rest_s1; bz = N - 7; }
   const int cb = cid(C, bx, bz);
-  for (int f = 0; f < NMET; ++f) {
-    const double *u = C.un + (size_t)f * P;
-    const double u0 = u[c00];
-    double s = 0.0;
-    for (int b = 0; b < 8; ++b) {
-      double r = 0.0;
+  const double *u = C.un + (size_t)f * P;
+  const double u0 = u[c00];
+  double s = 0.0;
+  for (int b = 0; b < 8; ++b) {
+    double r = 0.0;
 #pragma unroll
-      for (int a = 0; a < 8; ++a) r += wx[a] * (u[cb + b * C.px + a] - u0);
-      s += wz[b] * r;
-    }
-    Pa.un[(size_t)f * PP + d] = u0 + s;
+    for (int a = 0; a < 8; ++a) r += wx[a] * (u[cb + b * C.px + a] - u0);
+    s += wz[b] * r;
   }
+  Pa.un[(size_t)f * PP + d] = u0 + s;
 }
 
 // Reflux (Sec. II.D): parent cells next to the child's outer faces get the
@@ -453,11 +480,11 @@ __global__ void k_diag_final(const double *__restrict__ partials, int n, double 
 // ---------------------------------------------------------------- host launchers
 
 void launch_parity_x(const Lev &L, double *U, cudaStream_t s) {
-  k_parity_x<<<dim3(1, (L.nz + GH + 31) / 32), dim3(8, 32), 0, s>>>(L, U);
+  k_parity_x<<<dim3(1, (L.nz + GH + 15) / 16, NMET + NPRIM), dim3(8, 16), 0, s>>>(L, U);
 }
 
 void launch_parity_z(const Lev &L, double *U, cudaStream_t s) {
-  k_parity_z<<<dim3((L.nx + 2 * GH + 31) / 32, 1), dim3(32, 8), 0, s>>>(L, U);
+  k_parity_z<<<dim3((L.nx + 2 * GH + 31) / 32, 1, NMET + NPRIM), dim3(32, 8), 0, s>>>(L, U);
 }
 
 void launch_outflow(const Lev &L, double *U, cudaStream_t s) {
@@ -465,8 +492,8 @@ void launch_outflow(const Lev &L, double *U, cudaStream_t s) {
 }
 
 void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s) {
-  dim3 b(32, 4), g((L.nx + GH + 31) / 32, (L.nz + GH + 3) / 4);
-  k_outer<<<g, b, 0, s>>>(L, Un, U, tau);
+  const int n = GH * (L.nx + GH) + GH * L.nz;
+  k_outer<<<dim3((n + 127) / 128, kOuterGroups), 128, 0, s>>>(L, Un, U, tau);
 }
 
 int prolong_cells(const Lev &L, int full) {
@@ -491,7 +518,7 @@ void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, 
 
 void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s) {
   const int nh = Pa.nx / 2;
-  dim3 b(32, 4), g((nh + 31) / 32, (nh + 3) / 4);
+  dim3 b(32, 4), g((nh + 31) / 32, (nh + 3) / 4, NST);
   k_restrict<<<g, b, 0, s>>>(C, Pa);
 }
 

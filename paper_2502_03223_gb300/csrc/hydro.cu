@@ -7,67 +7,136 @@
 namespace sacra {
 
 // 6-point (6th-order) interpolation of a metric field to the face between
-// u[0] and u[s], in difference form about u[0]: (3,-25,150,150,-25,3)/256,
-// in arithmetic T (interpolation does not amplify rounding, so float is
-// enough in the mixed-precision hydro).
-template <typename T>
-__device__ __forceinline__ T face6(const double *u, int s) {
-  const T u0 = T(u[0]);
-  return u0 + (T(3) * (T(u[-2 * s]) - u0) - T(25) * (T(u[-s]) - u0) + T(150) * (T(u[s]) - u0)
-               - T(25) * (T(u[2 * s]) - u0) + T(3) * (T(u[3 * s]) - u0)) * T(1.0 / 256.0);
+// u[0] and u[s], in difference form about u[0]: (3,-25,150,150,-25,3)/256.
+__device__ __forceinline__ double face6(const double *u, int s) {
+  const double u0 = u[0];
+  return u0 + (3.0 * (u[-2 * s] - u0) - 25.0 * (u[-s] - u0) + 150.0 * (u[s] - u0) - 25.0 * (u[2 * s] - u0)
+               + 3.0 * (u[3 * s] - u0)) * (1.0 / 256.0);
 }
 
 // Face j+1/2 (dir 0, stride 1) or k+1/2 (dir 1, stride px) of cell (j, k):
-// reconstruction, metric at the face and the flux in arithmetic T.  In FP32
-// the pressure is reconstructed as an offset from the FP64 face reference
-// pref = (P_j + P_j+1) / 2 (PPM commutes with a constant shift), and the
-// pressure part alpha W^-3 pref of the normal momentum flux is added in FP64.
-template <typename T, int DIR>
-__device__ inline void flux_at(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
-                               double out[NCONS], int *fb) {
-  constexpr bool kDelta = sizeof(T) == 4;
+// reconstruction, metric at the face and the flux, FP64.
+template <int DIR>
+__device__ inline void flux_at_f64(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                   double out[NCONS], int *fb) {
   const size_t P = L.P;
   const int s = DIR == 0 ? 1 : L.px;
   const int id = cid(L, j, k);
   const int pf[5] = {pRHO, pUX, pUY, pUZ, pP};
-  const double *Pc = L.prim + (size_t)pP * P + id;
-  const double pref = kDelta ? 0.5 * (Pc[0] + Pc[s]) : 0.0;
-  T pl[5], pr[5];
+  double pl[5], pr[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
     const double *a = L.prim + (size_t)pf[v] * P + id;
-    const double o = v == 4 ? pref : 0.0;
-    const T c[6] = {T(a[-2 * s] - o), T(a[-s] - o), T(a[0] - o), T(a[s] - o), T(a[2 * s] - o), T(a[3 * s] - o)};
+    const double c[6] = {a[-2 * s], a[-s], a[0], a[s], a[2 * s], a[3 * s]};
     ppm_pair(c, pl[v], pr[v]);
   }
-  const T tref = T(pref);
-  if (!(pl[0] > T(0)) || !(pl[4] + tref > T(0)))
+  if (!(pl[0] > 0.0) || !(pl[4] > 0.0))
 #pragma unroll
-    for (int v = 0; v < 5; ++v) pl[v] = T(L.prim[(size_t)pf[v] * P + id] - (v == 4 ? pref : 0.0));
-  if (!(pr[0] > T(0)) || !(pr[4] + tref > T(0)))
+    for (int v = 0; v < 5; ++v) pl[v] = L.prim[(size_t)pf[v] * P + id];
+  if (!(pr[0] > 0.0) || !(pr[4] > 0.0))
 #pragma unroll
-    for (int v = 0; v < 5; ++v) pr[v] = T(L.prim[(size_t)pf[v] * P + id + s] - (v == 4 ? pref : 0.0));
-  const T alpha = face6<T>(U + (size_t)fAL * P + id, s);
-  const T W = face6<T>(U + (size_t)fW * P + id, s);
-  T beta[3];
+    for (int v = 0; v < 5; ++v) pr[v] = L.prim[(size_t)pf[v] * P + id + s];
+  const double alpha = face6(U + (size_t)fAL * P + id, s);
+  const double W = face6(U + (size_t)fW * P + id, s);
+  double beta[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) beta[i] = face6<T>(U + (size_t)(fBX + i) * P + id, s);
-  Sym3T<T> g;
-  g.xx = T(1) + face6<T>(U + (size_t)fHXX * P + id, s);
-  g.xy = face6<T>(U + (size_t)fHXY * P + id, s);
-  g.xz = face6<T>(U + (size_t)fHXZ * P + id, s);
-  g.yy = T(1) + face6<T>(U + (size_t)fHYY * P + id, s);
-  g.yz = face6<T>(U + (size_t)fHYZ * P + id, s);
-  g.zz = T(1) + face6<T>(U + (size_t)fHZZ * P + id, s);
-  T o[5];
-  *fb = face_flux<T>(p, DIR, pl, pr, alpha, beta, W, g, o, tref);
+  for (int i = 0; i < 3; ++i) beta[i] = face6(U + (size_t)(fBX + i) * P + id, s);
+  Sym3 g;
+  g.xx = 1.0 + face6(U + (size_t)fHXX * P + id, s);
+  g.xy = face6(U + (size_t)fHXY * P + id, s);
+  g.xz = face6(U + (size_t)fHXZ * P + id, s);
+  g.yy = 1.0 + face6(U + (size_t)fHYY * P + id, s);
+  g.yz = face6(U + (size_t)fHYZ * P + id, s);
+  g.zz = 1.0 + face6(U + (size_t)fHZZ * P + id, s);
+  *fb = face_flux<double>(p, DIR, pl, pr, alpha, beta, W, g, out);
+}
+
+// The FP32 face interpolation as an increment over the cell value u[0],
+// from exact differences (integer splits, no FP64 instruction).
+__device__ __forceinline__ float face6_delta(const double *u, int s, F2 &c) {
+  c = split_f64(u[0]);
+  return (3.0f * f32_diff(split_f64(u[-2 * s]), c) - 25.0f * f32_diff(split_f64(u[-s]), c)
+          + 150.0f * f32_diff(split_f64(u[s]), c) - 25.0f * f32_diff(split_f64(u[2 * s]), c)
+          + 3.0f * f32_diff(split_f64(u[3 * s]), c)) * (1.0f / 256.0f);
+}
+
+// The same face in FP32 (mixed precision), arranged so that rounding scales
+// with what varies across the face, not with rho or P:
+//  * the pressure is reconstructed as the offset P - P_j (PPM commutes with a
+//    constant shift) from exact differences, and the HLLC solver carries it
+//    as that offset (face_flux with pref = P_j);
+//  * the normal momentum flux then lacks g_f P_j, g = alpha W^-3 at the face;
+//    it is split as g_j P_j (cell j, FP64: the large part, which cancels
+//    between the faces of a cell in FP64) plus (g_f - g_j) P_j in FP32 from
+//    the face increments of alpha and W, in a form without cancellation:
+//      g_f / g_j - 1 = [x - 3y - 3y^2 - y^3] / (1 + y)^3,
+//      x = dalpha / alpha_j, y = dW / W_j.
+// The only FP64 instructions are the 5 of g_j P_j and the final addition.
+template <int DIR>
+__device__ inline void flux_at_f32(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                   double out[NCONS], int *fb) {
+  const size_t P = L.P;
+  const int s = DIR == 0 ? 1 : L.px;
+  const int id = cid(L, j, k);
+  const int pf[4] = {pRHO, pUX, pUY, pUZ};
+  float pl[5], pr[5];
 #pragma unroll
-  for (int v = 0; v < NCONS; ++v) out[v] = (double)o[v];
-  if constexpr (kDelta) {
-    const double a64 = face6<double>(U + (size_t)fAL * P + id, s);
-    const double w64 = face6<double>(U + (size_t)fW * P + id, s);
-    out[DIR == 0 ? 1 : 3] += a64 / (w64 * w64 * w64) * pref;
+  for (int v = 0; v < 4; ++v) {
+    const double *a = L.prim + (size_t)pf[v] * P + id;
+    const float c[6] = {f32_of(a[-2 * s]), f32_of(a[-s]), f32_of(a[0]), f32_of(a[s]), f32_of(a[2 * s]), f32_of(a[3 * s])};
+    ppm_pair(c, pl[v], pr[v]);
   }
+  const double *aP = L.prim + (size_t)pP * P + id;
+  const double Pj = aP[0];
+  const F2 Ps = split_f64(Pj);
+  const float pref = Ps.hi + Ps.lo;
+  {
+    const float c[6] = {f32_diff(split_f64(aP[-2 * s]), Ps), f32_diff(split_f64(aP[-s]), Ps), 0.0f,
+                        f32_diff(split_f64(aP[s]), Ps), f32_diff(split_f64(aP[2 * s]), Ps), f32_diff(split_f64(aP[3 * s]), Ps)};
+    ppm_pair(c, pl[4], pr[4]);
+    if (!(pl[0] > 0.0f) || !(pl[4] + pref > 0.0f)) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) pl[v] = f32_of(L.prim[(size_t)pf[v] * P + id]);
+      pl[4] = 0.0f;
+    }
+    if (!(pr[0] > 0.0f) || !(pr[4] + pref > 0.0f)) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) pr[v] = f32_of(L.prim[(size_t)pf[v] * P + id + s]);
+      pr[4] = c[3];
+    }
+  }
+  F2 ca, cw, cb;
+  const float da = face6_delta(U + (size_t)fAL * P + id, s, ca);
+  const float dW = face6_delta(U + (size_t)fW * P + id, s, cw);
+  const float aj = ca.hi + ca.lo, Wj = cw.hi + cw.lo;
+  const float alpha = aj + da, W = Wj + dW;
+  float beta[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float d = face6_delta(U + (size_t)(fBX + i) * P + id, s, cb);
+    beta[i] = (cb.hi + cb.lo) + d;
+  }
+  Sym3T<float> g;
+  float gv[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const float d = face6_delta(U + (size_t)(fHXX + a) * P + id, s, cb);
+    gv[a] = (cb.hi + cb.lo) + d;
+  }
+  g.xx = 1.0f + gv[0]; g.xy = gv[1]; g.xz = gv[2]; g.yy = 1.0f + gv[3]; g.yz = gv[4]; g.zz = 1.0f + gv[5];
+  float o[5];
+  *fb = face_flux<float>(p, DIR, pl, pr, alpha, beta, W, g, o, pref);
+  // (g_f - g_j) P_j in FP32
+  const float x = da / aj, y = dW / Wj, y1 = 1.0f + y;
+  const float rel = (x - y * (3.0f + y * (3.0f + y))) / (y1 * y1 * y1);
+  const float gj32 = aj / (Wj * Wj * Wj);
+  constexpr int n = DIR == 0 ? 1 : 3;
+  o[n] += gj32 * rel * pref;
+#pragma unroll
+  for (int v = 0; v < NCONS; ++v) out[v] = f64_of(o[v]);
+  // g_j P_j in FP64
+  const double aj64 = U[(size_t)fAL * P + id], Wj64 = U[(size_t)fW * P + id];
+  out[n] += aj64 * Pj / (Wj64 * Wj64 * Wj64);
 }
 
 // The flux of one face in arithmetic T.  The FP32 form hands a face to the
@@ -77,7 +146,7 @@ __device__ inline void flux_at(const Lev &L, const DevParams &p, const double *_
 // positivity fallback there, and the contact pressure of a near-vacuum
 // Riemann problem is of that order too), and every face where the FP32 HLLC
 // fails.  Elsewhere the branches have wide margins.
-constexpr double kMixedContrast = 1e-3;
+constexpr float kMixedContrast = 1e-3f;
 
 template <typename T, int DIR>
 __device__ inline void flux_face(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
@@ -86,18 +155,19 @@ __device__ inline void flux_face(const Lev &L, const DevParams &p, const double 
     const int s = DIR == 0 ? 1 : L.px;
     const double *r = L.prim + (size_t)pRHO * L.P + cid(L, j, k);
     const double *q = L.prim + (size_t)pP * L.P + cid(L, j, k);
-    double rmin = r[-2 * s], rmax = r[-2 * s], qmin = q[-2 * s], qmax = q[-2 * s];
+    float rmin = split_f64(r[-2 * s]).hi, rmax = rmin, qmin = split_f64(q[-2 * s]).hi, qmax = qmin;
 #pragma unroll
     for (int n = -1; n <= 3; ++n) {
-      rmin = fmin(rmin, r[n * s]); rmax = fmax(rmax, r[n * s]);
-      qmin = fmin(qmin, q[n * s]); qmax = fmax(qmax, q[n * s]);
+      const float rv = split_f64(r[n * s]).hi, qv = split_f64(q[n * s]).hi;
+      rmin = fminf(rmin, rv); rmax = fmaxf(rmax, rv);
+      qmin = fminf(qmin, qv); qmax = fmaxf(qmax, qv);
     }
     if (rmin > kMixedContrast * rmax && qmin > kMixedContrast * qmax) {
-      flux_at<float, DIR>(L, p, U, j, k, out, fb);
+      flux_at_f32<DIR>(L, p, U, j, k, out, fb);
       if (!*fb) return;
     }
   }
-  flux_at<double, DIR>(L, p, U, j, k, out, fb);
+  flux_at_f64<DIR>(L, p, U, j, k, out, fb);
 }
 
 // x-faces j+1/2 for j in [0, jmax], rows [1, kmax].  Stores area-weighted
@@ -159,10 +229,16 @@ __global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double
   if (fb) atomicAdd(L.nfb, 1ull);
 }
 
-// 6th-order central first derivative: differences in FP64, weighted sum in T
+// 6th-order central first derivative: exact differences (FP64, or FP32 from
+// integer splits), weighted sum in T
 template <typename T>
 __device__ __forceinline__ T cd1(const double *u, int s, T idx) {
-  return (T(45) * T(u[s] - u[-s]) - T(9) * T(u[2 * s] - u[-2 * s]) + T(u[3 * s] - u[-3 * s])) * idx;
+  if constexpr (sizeof(T) == 4) {
+    return (45.0f * f32_diff(split_f64(u[s]), split_f64(u[-s])) - 9.0f * f32_diff(split_f64(u[2 * s]), split_f64(u[-2 * s]))
+            + f32_diff(split_f64(u[3 * s]), split_f64(u[-3 * s]))) * idx;
+  } else {
+    return (45.0 * (u[s] - u[-s]) - 9.0 * (u[2 * s] - u[-2 * s]) + (u[3 * s] - u[-3 * s])) * idx;
+  }
 }
 
 // d_t q = <s> - (1/dV) sum (area-weighted fluxes), Sec. II.C.1.  The flux
@@ -189,21 +265,22 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
     const double *fz = L.fz + (size_t)v * P + id;
     div[v] = (fx[0] - fx[-1] + fz[0] - fz[-sz]) * ivol;
   }
-  const T x = T(xd);
-  const T W = T(U[(size_t)fW * P + id]), al = T(U[(size_t)fAL * P + id]);
+  auto ld = [&](int f) { return ld_as<T>(U[(size_t)f * P + id]); };
+  const T x = sizeof(T) == 4 ? T(((float)j - 0.5f) * f32_of(L.dx)) : T(xd);
+  const T W = ld(fW), al = ld(fAL);
   Sym3T<T> g;
-  g.xx = T(1.0 + U[(size_t)fHXX * P + id]);
-  g.xy = T(U[(size_t)fHXY * P + id]);
-  g.xz = T(U[(size_t)fHXZ * P + id]);
-  g.yy = T(1.0 + U[(size_t)fHYY * P + id]);
-  g.yz = T(U[(size_t)fHYZ * P + id]);
-  g.zz = T(1.0 + U[(size_t)fHZZ * P + id]);
+  if constexpr (sizeof(T) == 4) {
+    g.xx = 1.0f + ld(fHXX); g.yy = 1.0f + ld(fHYY); g.zz = 1.0f + ld(fHZZ);
+  } else {
+    g.xx = 1.0 + U[(size_t)fHXX * P + id]; g.yy = 1.0 + U[(size_t)fHYY * P + id]; g.zz = 1.0 + U[(size_t)fHZZ * P + id];
+  }
+  g.xy = ld(fHXY); g.xz = ld(fHXZ); g.yz = ld(fHYZ);
   const Sym3T<T> gi = s3inv(g, (T *)nullptr);
-  const T i60[2] = {T(1.0 / (60.0 * L.dx)), T(1.0 / (60.0 * L.dz))};
+  const T i60[2] = {ld_as<T>(L.i60x), ld_as<T>(L.i60z)};
   const int st[2] = {1, sz};
   T pr[NPRIM];
 #pragma unroll
-  for (int f = 0; f < NPRIM; ++f) pr[f] = T(L.prim[(size_t)f * P + id]);
+  for (int f = 0; f < NPRIM; ++f) pr[f] = ld_as<T>(L.prim[(size_t)f * P + id]);
   const T rho = pr[pRHO], Pp = pr[pP];
   const T u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
   const T w = sqrt(T(1) + W * W * s3quad(gi, u, u));
@@ -239,28 +316,30 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
   }
   T geo = T(0);
   if (cyl) {
-    const T vbary = vu[1] - T(U[(size_t)fBY * P + id]) / al;
+    const T vbary = vu[1] - ld(fBY) / al;
     geo = al * iW3 * (rhw2 * vd[1] * vbary + Pp) / x;
   }
   // K^ij S_ij = rho h w^2 K_ij v^i v^j + P gamma^ij K_ij, K_ij = (At_ij + gt_ij K/3) / W^2
-  const T K = T(U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id]);
+  T K;
+  if constexpr (sizeof(T) == 4) K = ld(fKH) + 2.0f * ld(fTH);
+  else K = U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id];
   Sym3T<T> Kd;
-  Kd.xx = (T(U[(size_t)fAXX * P + id]) + g.xx * K / T(3)) * iW * iW;
-  Kd.xy = (T(U[(size_t)fAXY * P + id]) + g.xy * K / T(3)) * iW * iW;
-  Kd.xz = (T(U[(size_t)fAXZ * P + id]) + g.xz * K / T(3)) * iW * iW;
-  Kd.yy = (T(U[(size_t)fAYY * P + id]) + g.yy * K / T(3)) * iW * iW;
-  Kd.yz = (T(U[(size_t)fAYZ * P + id]) + g.yz * K / T(3)) * iW * iW;
-  Kd.zz = (T(U[(size_t)fAZZ * P + id]) + g.zz * K / T(3)) * iW * iW;
+  Kd.xx = (ld(fAXX) + g.xx * K / T(3)) * iW * iW;
+  Kd.xy = (ld(fAXY) + g.xy * K / T(3)) * iW * iW;
+  Kd.xz = (ld(fAXZ) + g.xz * K / T(3)) * iW * iW;
+  Kd.yy = (ld(fAYY) + g.yy * K / T(3)) * iW * iW;
+  Kd.yz = (ld(fAYZ) + g.yz * K / T(3)) * iW * iW;
+  Kd.zz = (ld(fAZZ) + g.zz * K / T(3)) * iW * iW;
   // gamma^ij K_ij = W^2 gt^ij K_ij (equal to K when At is trace-free)
   const T trK = W * W * (gi.xx * Kd.xx + gi.yy * Kd.yy + gi.zz * Kd.zz
                          + T(2) * (gi.xy * Kd.xy + gi.xz * Kd.xz + gi.yz * Kd.yz));
   const T KS = rhw2 * s3quad(Kd, vu, vu) + Pp * trK;
   const T sE = iW3 * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
   L.rhs[(size_t)fQD * P + id] = -div[0];
-  L.rhs[(size_t)fQSX * P + id] = (double)(src[0] + geo) - div[1];
+  L.rhs[(size_t)fQSX * P + id] = to_f64<T>(src[0] + geo) - div[1];
   L.rhs[(size_t)fQSY * P + id] = -div[2];
-  L.rhs[(size_t)fQSZ * P + id] = (double)src[1] - div[3];
-  L.rhs[(size_t)fQE * P + id] = (double)sE - div[4];
+  L.rhs[(size_t)fQSZ * P + id] = to_f64<T>(src[1]) - div[3];
+  L.rhs[(size_t)fQE * P + id] = to_f64<T>(sE) - div[4];
 }
 
 // eps from the EOS and conserved variables on every padded cell (initial data)
@@ -283,10 +362,10 @@ __global__ void k_prim2cons_all(Lev L, DevParams p, double *__restrict__ U) {
 }
 
 // primitive recovery on [j0, j1] x [k0, k1] of state U
-__global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0, int j1, int k0, int k1) {
+__global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0, int j1, int k0, int k1, int skip_corner) {
   const int j = j0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   const int k = k0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
-  if (j > j1 || k > k1) return;
+  if (j > j1 || k > k1 || (skip_corner && j == j1 && k == k1)) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
   double q[NCONS], pr[NPRIM];
@@ -328,9 +407,10 @@ void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStrea
   k_prim2cons_all<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(L, p, U);
 }
 
-void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s) {
+void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s,
+                       int skip_corner) {
   dim3 b(32, 4), g((j1 - j0 + 1 + 31) / 32, (k1 - k0 + 1 + 3) / 4);
-  k_c2p_region<<<g, b, 0, s>>>(L, p, U, j0, j1, k0, k1);
+  k_c2p_region<<<g, b, 0, s>>>(L, p, U, j0, j1, k0, k1, skip_corner);
 }
 
 }  // namespace sacra

@@ -20,7 +20,8 @@ void launch_flux_z(const Lev &L, const DevParams &p, const double *U, int jmax, 
                    int has_parent, cudaStream_t s);
 void launch_hydro_div(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, cudaStream_t s);
 void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStream_t s);
-void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s);
+void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s,
+                       int skip_corner = 0);
 
 void launch_cartoon(const Lev &L, const DevParams &p, const double *U, const double *tab, int tab_stride, cudaStream_t s);
 void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s);

@@ -26,6 +26,13 @@ __device__ __forceinline__ double par_x(int f) {
   }
 }
 
+// field of cartoon slot a (kCartoonFields, compile-time form)
+__host__ __device__ constexpr int cartoon_field(int a) {
+  constexpr int f[20] = {fW, fAL, fHXX, fHXY, fHXZ, fHYY, fHYZ, fHZZ, fAXX, fAXY,
+                         fAXZ, fAYY, fAYZ, fBX, fBY, fBZ, fGX, fGY, fBBX, fBBY};
+  return f[a];
+}
+
 // x-parity of the cartoon fields in kCartoonFields order (compile-time form)
 __host__ __device__ constexpr float par_x_slot(int a) {
   return (a == 4 || a == 6 || a == 10 || a == 12 || a == 13 || a == 14 || a == 16 || a == 17 || a == 18 || a == 19)
@@ -61,7 +68,36 @@ __device__ __forceinline__ void rotate20(const double v[20], double c, double s,
 // Planes y = +-m dy at (x_j, z_k): 9-point Lagrange in x at varpi, rotated by
 // +-phi (Sec. II.B.2); j <= 0 from the rotation by pi of (x_{1-j}, -+m dy).
 // d_y and d_yy by 6th-order central differences over m = -3..3 (dy = dx).
-__global__ void k_cartoon_f64(Lev L, const double *__restrict__ U, const double *__restrict__ tab, int tab_stride) {
+// The fields are taken group by group (scalars, the h and At tensors, the
+// beta, Gt and B vectors): each group's three planes come from one pass over
+// its 9-point stencils, and only the group's components are live at a time.
+struct CartoonOut {
+  Lev L;
+  int o;
+  bool flip;
+  double i1, i2;
+};
+
+// accumulate the d_y / d_yy sums of slot a from its +m / -m plane values
+__device__ __forceinline__ void cartoon_acc(int a, bool flip, double w1, double w2, double pp, double pm, double base,
+                                            double &d1, double &d2) {
+  const double pr = par_x_slot(a);
+  const double plus = flip ? pr * pm : pp;
+  const double minus = flip ? pr * pp : pm;
+  const double centre = flip ? pr * base : base;
+  d1 += w1 * (plus - minus);
+  d2 += w2 * ((plus - centre) + (minus - centre));
+}
+
+__device__ __forceinline__ void cartoon_store(const CartoonOut &c, int a, double d1, double d2) {
+  const int f = cartoon_field(a);
+  const size_t P = c.L.P;
+  if (f != fHZZ && f != fBZ && a >= 2) c.L.dy[(size_t)f * P + c.o] = d1 * c.i1;
+  if (a <= 7 || (a >= 13 && a <= 15)) c.L.dyy[(size_t)f * P + c.o] = d2 * c.i2;
+}
+
+__global__ void __launch_bounds__(128) k_cartoon_f64(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
+                                                     int tab_stride) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x - 2;
   const int k = blockIdx.y * blockDim.y + threadIdx.y - 2;
   if (j > L.nx + 4 || k > L.nz + 7) return;
@@ -69,51 +105,80 @@ __global__ void k_cartoon_f64(Lev L, const double *__restrict__ U, const double 
   const int jj = flip ? 1 - j : j;
   const size_t P = L.P;
   const int c0 = cid(L, jj, k);
-  double base0[20];
-#pragma unroll
-  for (int a = 0; a < 20; ++a) base0[a] = U[(size_t)kCartoonFields[a] * P + c0];
-  double d1[20], d2[20];
-#pragma unroll
-  for (int a = 0; a < 20; ++a) { d1[a] = 0.0; d2[a] = 0.0; }
+  const double *t0 = tab + (size_t)(jj * 3) * tab_stride;   // per m: 9 weights, cos, sin
+  CartoonOut co{L, cid(L, j, k), flip, 1.0 / (60.0 * L.dx), 1.0 / (180.0 * L.dx * L.dx)};
   const double c1w[3] = {45.0, -9.0, 1.0}, c2w[3] = {270.0, -27.0, 2.0};
-  for (int m = 1; m <= 3; ++m) {
-    const double *t = tab + (size_t)(jj * 3 + (m - 1)) * tab_stride;   // 9 weights, cos, sin
-    double v[20];
+  // the three planes of slot a: v[m] = base + sum_n t_m[n] (u[n] - base)
+  auto planes = [&](int a, double &base, double v[3]) {
+    const double *u = U + (size_t)cartoon_field(a) * P + c0 - 4;
+    base = u[4];
+    double s[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int a = 0; a < 20; ++a) {
-      const double *u = U + (size_t)kCartoonFields[a] * P + c0 - 4;
-      double s = 0.0;
+    for (int n = 0; n < 9; ++n) {
+      const double d = u[n] - base;
 #pragma unroll
-      for (int n = 0; n < 9; ++n) s += t[n] * (u[n] - base0[a]);
-      v[a] = base0[a] + s;
+      for (int m = 0; m < 3; ++m) s[m] += t0[m * tab_stride + n] * d;
     }
-    double pp[20], pm[20];
-    rotate20(v, t[9], t[10], pp);
-    rotate20(v, t[9], -t[10], pm);
-    const double w1 = c1w[m - 1], w2 = c2w[m - 1];
 #pragma unroll
-    for (int a = 0; a < 20; ++a) {
-      // at flipped points the +m plane is par * (-m plane of jj) and vice versa
-      const double plus = flip ? par_x(kCartoonFields[a]) * pm[a] : pp[a];
-      const double minus = flip ? par_x(kCartoonFields[a]) * pp[a] : pm[a];
-      const double centre = flip ? par_x(kCartoonFields[a]) * base0[a] : base0[a];
-      d1[a] += w1 * (plus - minus);
-      d2[a] += w2 * ((plus - centre) + (minus - centre));
+    for (int m = 0; m < 3; ++m) v[m] = base + s[m];
+  };
+  // scalars under the rotation: W, alpha, h_zz, beta^z
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int a = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 7 : 15));
+    double base, v[3], d1 = 0.0, d2 = 0.0;
+    planes(a, base, v);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) cartoon_acc(a, flip, c1w[m], c2w[m], v[m], v[m], base, d1, d2);
+    cartoon_store(co, a, d1, d2);
+  }
+  // vectors (x, y components): beta, Gt, B
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int a = q == 0 ? 13 : (q == 1 ? 16 : 18);
+    double bx, by, vx[3], vy[3];
+    planes(a, bx, vx);
+    planes(a + 1, by, vy);
+    double d1x = 0.0, d2x = 0.0, d1y = 0.0, d2y = 0.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double c = t0[m * tab_stride + 9], sn = t0[m * tab_stride + 10];
+      const double px = c * vx[m] - sn * vy[m], py = sn * vx[m] + c * vy[m];
+      const double mx = c * vx[m] - (-sn) * vy[m], my = (-sn) * vx[m] + c * vy[m];
+      cartoon_acc(a, flip, c1w[m], c2w[m], px, mx, bx, d1x, d2x);
+      cartoon_acc(a + 1, flip, c1w[m], c2w[m], py, my, by, d1y, d2y);
     }
+    cartoon_store(co, a, d1x, d2x);
+    cartoon_store(co, a + 1, d1y, d2y);
   }
-  const int o = cid(L, j, k);
-  const double i1 = 1.0 / (60.0 * L.dx), i2 = 1.0 / (180.0 * L.dx * L.dx);
-  // d_y of the fields whose y-derivative is not forced to zero
+  // symmetric tensors h_ij (slots 2..6) and At_ij (8..12): xx, xy, xz, yy, yz
 #pragma unroll
-  for (int a = 2; a < 20; ++a) {
-    const int f = kCartoonFields[a];
-    if (f == fHZZ || f == fBZ) continue;
-    L.dy[(size_t)f * P + o] = d1[a] * i1;
+  for (int q = 0; q < 2; ++q) {
+    const int a0 = q == 0 ? 2 : 8;
+    double b[5], v[5][3];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) planes(a0 + i, b[i], v[i]);
+    double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, d2[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double c = t0[m * tab_stride + 9];
+      double pp[5], pm[5];
+#pragma unroll
+      for (int sg = 0; sg < 2; ++sg) {
+        const double sn = sg == 0 ? t0[m * tab_stride + 10] : -t0[m * tab_stride + 10];
+        double *r = sg == 0 ? pp : pm;
+        r[0] = c * c * v[0][m] - 2.0 * c * sn * v[1][m] + sn * sn * v[3][m];
+        r[1] = c * sn * (v[0][m] - v[3][m]) + (c * c - sn * sn) * v[1][m];
+        r[2] = c * v[2][m] - sn * v[4][m];
+        r[3] = sn * sn * v[0][m] + 2.0 * c * sn * v[1][m] + c * c * v[3][m];
+        r[4] = sn * v[2][m] + c * v[4][m];
+      }
+#pragma unroll
+      for (int i = 0; i < 5; ++i) cartoon_acc(a0 + i, flip, c1w[m], c2w[m], pp[i], pm[i], b[i], d1[i], d2[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) cartoon_store(co, a0 + i, d1[i], d2[i]);
   }
-  // d_yy of W, h_ij, alpha, beta^i
-  const int sec[11] = {0, 1, 2, 3, 4, 5, 6, 7, 13, 14, 15};
-#pragma unroll
-  for (int b = 0; b < 11; ++b) L.dyy[(size_t)kCartoonFields[sec[b]] * P + o] = d2[sec[b]] * i2;
 }
 
 // Mixed precision: the same planes in FP32, formed as differences from the
