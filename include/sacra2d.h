@@ -45,6 +45,7 @@ extern "C" {
 #endif
 
 typedef struct sacra_ctx sacra_ctx;
+typedef struct sacra_batch sacra_batch;
 
 typedef enum {
   SACRA_OK = 0,
@@ -188,8 +189,48 @@ sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_le
 sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level, const double *state, const double *prims,
                                      double *rhs_out, void *cuda_stream);
 
+/* Autotuner (no counterpart in the paper).  Every RK stage runs as one
+   persistent launch per kernel kind over the tiles of all levels; for each
+   kind this times every tile shape the kernel allows and every persistent
+   grid size (blocks per SM) on the current state (reps launches each, CUDA
+   events on the context's stream) and keeps the fastest.  The state is not
+   changed.  Needs initial data on every level.  sacra_get_tuning reports the
+   choice for kernel kind `kind` (0 x-fluxes, 1 z-fluxes, 2 hydro divergence
+   and sources, 3 cartoon planes, 4 Z4c derivatives, 5 Z4c pointwise, 6 stage
+   update); SACRA_ERR_ARG past the last kind. */
+sacra_status sacra_tune(sacra_ctx *c, int reps);
+sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *tile_y, int *blocks_per_sm);
+
 void sacra_destroy(sacra_ctx *c);
 const char *sacra_last_error(const sacra_ctx *c);
+
+/* ---- Batches of independent stars (no counterpart in the paper: many
+   hierarchies advanced together).  Each star has its own sacra_params; the
+   stars may differ in n_levels, nx = nz and dx0 = dz0 and must agree in
+   everything else (else SACRA_ERR_ARG).  All stars take the same dt.  Every
+   RK stage is one persistent launch per kernel kind over the tiles of every
+   level of every star (ghost fill, restriction and reflux stay per level);
+   sacra_batch_step with use_graph != 0 replays whole steps of all stars as
+   one CUDA graph.  Arena, stream, error and ownership rules are those of the
+   single-star calls; `star` is 0-based. */
+sacra_status sacra_batch_arena_bytes(const sacra_params *per_star, int n_stars, size_t *bytes);
+sacra_status sacra_init_batch(const sacra_params *per_star, int n_stars, void *cuda_stream, void *arena,
+                              size_t arena_bytes, sacra_batch **out);
+sacra_status sacra_batch_set_initial_data(sacra_batch *b, int star, int level, int kind, const double *host_planes,
+                                          int n_fields);
+sacra_status sacra_batch_step(sacra_batch *b, double dt, int n_steps, int use_graph);
+sacra_status sacra_batch_read_state(sacra_batch *b, int star, int level, int which, int field, double *host_out,
+                                    size_t n);
+sacra_status sacra_batch_constraints(sacra_batch *b, int star, sacra_diag *out);
+sacra_status sacra_batch_tune(sacra_batch *b, int reps);
+sacra_status sacra_batch_get_tuning(const sacra_batch *b, int kind, int *tile_x, int *tile_y, int *blocks_per_sm);
+sacra_status sacra_batch_sync(sacra_batch *b);
+long long sacra_batch_launch_count(const sacra_batch *b);
+sacra_status sacra_batch_profile(sacra_batch *b, int enable);
+sacra_status sacra_batch_profile_get(sacra_batch *b, int idx, char *name, size_t name_len, double *total_ms,
+                                     long long *launches, long long *cells);
+void sacra_batch_destroy(sacra_batch *b);
+const char *sacra_batch_last_error(const sacra_batch *b);
 
 #ifdef __cplusplus
 }

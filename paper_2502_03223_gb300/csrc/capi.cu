@@ -1,11 +1,14 @@
-// C ABI of the SACRA-2D hot path (include/sacra2d.h): context, device arena,
-// the stage sequence of Sec. II.D (lockstep levels), CUDA-graph replay of
-// whole steps.  All arithmetic runs in the kernels of hydro.cu, z4c.cu and
-// grid.cu; the host only orders launches and computes interpolation weights.
+// C ABI of the SACRA-2D hot path (include/sacra2d.h): contexts, device arena,
+// the stage sequence of Sec. II.D (lockstep levels), batched persistent
+// launches over all levels of one star or of many stars, the autotuner of
+// their tile shapes and grid sizes, and CUDA-graph replay of whole steps.  All
+// arithmetic runs in the kernels of hydro.cu, z4c.cu and grid.cu; the host
+// orders launches, builds tile lists and computes interpolation weights.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -30,14 +33,35 @@ void lagrange_weights(int n, const double *nodes, double t, double *w) {
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
+// Device memory of one star (hierarchy): per level the state registers,
+// primitives, face fluxes, its own derivative and cartoon scratch (the levels
+// of a stage run concurrently), flux registers and status; then the
+// diagnostic partial sums.
 struct Layout {
   size_t P;          // plane stride (doubles), multiple of 32
   int rw;            // flux register row width
   size_t per_level;  // bytes
-  size_t shared;     // bytes after the levels
-  size_t ds_off, dy_off, dyy_off, tab_off, part_off, dout_off, nfb_off;
-  int n_part;        // diag partial blocks (all levels)
+  size_t part_bytes; // diagnostic partials
+  int n_part;
 };
+
+Layout layout(const sacra_params *p) {
+  Layout o;
+  const size_t px = p->nx + 2 * GH, pz = p->nz + 2 * GH;
+  o.P = round_up(px * pz, 32);
+  o.rw = (p->nx > p->nz ? p->nx : p->nz) + 2;
+  const size_t rwp = round_up((size_t)o.rw, 32);
+  const size_t planes = 4 * NST + NPRIM + 2 * NCONS + (size_t)z4c_scratch_planes() + 2 * NMET;
+  o.per_level = round_up(planes * o.P * 8 + o.P * 4 /* status */ + 4 * NCONS * rwp * 8, 256);
+  o.n_part = p->n_levels * ((p->nx * p->nz + 127) / 128);
+  o.part_bytes = round_up((size_t)o.n_part * 9 * 8, 256);
+  return o;
+}
+
+size_t star_bytes(const sacra_params *p) {
+  const Layout o = layout(p);
+  return o.per_level * p->n_levels + o.part_bytes;
+}
 
 bool valid(const sacra_params *p, std::string *why) {
   if (!p) { *why = "params is NULL"; return false; }
@@ -59,39 +83,24 @@ bool valid(const sacra_params *p, std::string *why) {
   return true;
 }
 
-Layout layout(const sacra_params *p) {
-  Layout o;
-  const size_t px = p->nx + 2 * GH, pz = p->nz + 2 * GH;
-  o.P = round_up(px * pz, 32);
-  o.rw = (p->nx > p->nz ? p->nx : p->nz) + 2;
-  const size_t rwp = round_up((size_t)o.rw, 32);
-  const size_t planes = 4 * NST + NPRIM + 2 * NCONS;
-  o.per_level = planes * o.P * 8 + o.P * 4 /* status */ + 4 * NCONS * rwp * 8;
-  o.per_level = round_up(o.per_level, 256);
-  size_t off = 0;
-  o.ds_off = off; off += round_up((size_t)z4c_scratch_planes() * o.P * 8, 256);
-  o.dy_off = off; off += round_up((size_t)NMET * o.P * 8, 256);
-  o.dyy_off = off; off += round_up((size_t)NMET * o.P * 8, 256);
-  o.tab_off = off; off += round_up((size_t)(p->nx + 8) * 3 * kTabStride * 8, 256);
-  o.n_part = p->n_levels * ((p->nx * p->nz + 127) / 128);
-  o.part_off = off; off += round_up((size_t)o.n_part * 9 * 8, 256);
-  o.dout_off = off; off += 256;
-  o.nfb_off = off; off += 256;
-  o.shared = off;
-  return o;
+// stars of one batch share the choices that select kernels (geometry, spacetime
+// evolution, Riemann solver, integrator, precision); every other parameter
+// (grid, EOS, gauge, atmosphere, recovery) is the star's own
+bool compatible(const sacra_params *a, const sacra_params *b) {
+  return a->geometry == b->geometry && a->evolve_spacetime == b->evolve_spacetime && a->solver == b->solver &&
+         a->rk == b->rk && a->precision == b->precision;
 }
-
-}  // namespace
 
 // kernel kinds for launch counting and the optional per-kernel profile
 enum Kid {
   K_OUTFLOW, K_OUTER, K_PROLONG, K_PARITY_X, K_PARITY_Z, K_FLUX_X, K_FLUX_Z, K_HYDRO_DIV, K_CARTOON, K_Z4C_DERIVS,
   K_Z4C_POINT, K_RK_UPDATE, K_RESTRICT, K_REFLUX, K_C2P, K_PRIM2CONS, K_DIAG, K_DIAG_FINAL, K_COUNT
 };
-static const char *kKidName[K_COUNT] = {"k_outflow", "k_outer", "k_prolong", "k_parity_x", "k_parity_z", "k_flux_x",
-                                        "k_flux_z", "k_hydro_rhs", "k_cartoon", "k_z4c_derivs", "k_z4c_point",
-                                        "k_rk_update", "k_restrict", "k_reflux", "k_c2p_region", "k_prim2cons_all",
-                                        "k_diag", "k_diag_final"};
+const char *kKidName[K_COUNT] = {"k_outflow", "k_outer", "k_prolong", "k_parity_x", "k_parity_z", "k_flux_x",
+                                 "k_flux_z", "k_hydro_rhs", "k_cartoon", "k_z4c_derivs", "k_z4c_point",
+                                 "k_rk_update", "k_restrict", "k_reflux", "k_c2p_region", "k_prim2cons_all",
+                                 "k_diag", "k_diag_final"};
+const Kid kKindKid[B_NKIND] = {K_FLUX_X, K_FLUX_Z, K_HYDRO_DIV, K_CARTOON, K_Z4C_DERIVS, K_Z4C_POINT, K_RK_UPDATE};
 
 struct ProfRec {
   int kid;
@@ -99,249 +108,491 @@ struct ProfRec {
   long long cells;
 };
 
-struct sacra_ctx {
+// one hierarchy of levels
+struct Star {
   sacra_params prm;
   DevParams dp;
   Layout lay;
+  Lev lv[kMaxLevels];
+  void *ds[kMaxLevels];
+  double *part = nullptr;
+  double dt_step = 0.0;
+  bool have_data[kMaxLevels] = {};
+};
+
+// ---- tile shapes and the autotuner's choice per kernel kind
+struct Shape {
+  int x, y;
+};
+const Shape kShapes128[] = {{32, 4}, {64, 2}, {16, 8}, {128, 1}};
+const Shape kShapes256[] = {{32, 4}, {64, 2}, {16, 8}, {128, 1}, {32, 8}, {64, 4}};
+const int kBlocksPerSm[] = {1, 2, 3, 4, 6, 8, 12};
+
+// the launch bounds (threads per block) of the batched kernels
+int max_threads(int kind) {
+  switch (kind) {
+    case B_FLUX_X: case B_FLUX_Z: case B_HYDRO: case B_DERIVS: return 256;
+    default: return 128;
+  }
+}
+
+struct KindCfg {
+  Shape shape{32, 4};
+  int blocks_per_sm = 8;
+};
+
+struct Region {
+  int j0, j1, k0, k1;
+};
+
+// cells a kind covers on level l of a star at stage s
+Region kind_region(const sacra_params &p, int l, int s, int S, int kind) {
+  const int ext = (l > 0 && s < S - 1) ? 4 : 0;
+  const int jmax = p.nx + ext, kmax = p.nz + ext;
+  switch (kind) {
+    case B_FLUX_X: return {0, jmax, 1, kmax};
+    case B_FLUX_Z: return {1, jmax, 0, kmax};
+    case B_CARTOON: return {-2, p.nx + 4, -2, p.nz + 7};
+    default: return {1, jmax, 1, kmax};
+  }
+}
+
+long long tile_count(const Region &r, Shape sh) {
+  return (long long)((r.j1 - r.j0 + sh.x) / sh.x) * ((r.k1 - r.k0 + sh.y) / sh.y);
+}
+
+}  // namespace
+
+// The execution engine behind both public handles: one star (sacra_ctx) or a
+// batch of stars advanced together (sacra_batch).
+struct Engine {
+  std::vector<Star> stars;
+  DevParams dp;
+  int S = 4;                      // stages per step
   cudaStream_t stream = nullptr;
   char *arena = nullptr;
   bool own_arena = false;
-  Lev lv[kMaxLevels];
-  double *ds = nullptr, *tab = nullptr, *part = nullptr, *dout = nullptr;
+  double *tab = nullptr, *dout = nullptr;
   unsigned long long *nfb = nullptr;
-  double dt_step = 0.0;
-  bool have_data[kMaxLevels] = {};
+  int sms = 1;
+  // plan of the batched launches
+  std::vector<std::pair<int, int>> slots;   // (star, level)
+  BL *bl_dev = nullptr;           // [2 parities][S][slots], then 2 x slots tuning copies
+  Tile *tiles_dev = nullptr;
+  size_t tiles_cap = 0, tune_cap = 0;
+  long long toff[4][B_NKIND] = {}, tcnt[4][B_NKIND] = {};
+  long long cells[4][B_NKIND] = {};
+  KindCfg cfg[B_NKIND];
+  // bookkeeping
   long long launches = 0;
   std::string err;
-  // graph replay: one graph per parity of the register swap
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   double gdt[2] = {0.0, 0.0};
   long long glaunch[2] = {0, 0};
   int parity = 0;    // number of register swaps mod 2
   bool capturing = false;
-  // per-kernel profile (eager launches only)
   bool prof = false;
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> pool;
   size_t pool_used = 0;
 };
 
+struct sacra_ctx {
+  Engine e;
+};
+struct sacra_batch {
+  Engine e;
+};
+
 namespace {
 
-sacra_status fail(sacra_ctx *c, sacra_status s, const std::string &m) {
-  if (c) c->err = m;
+sacra_status fail(Engine &e, sacra_status s, const std::string &m) {
+  e.err = m;
   return s;
 }
 
-sacra_status cuda_check(sacra_ctx *c, const char *where) {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(c, SACRA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+sacra_status cuda_check(Engine &e, const char *where) {
+  cudaError_t x = cudaGetLastError();
+  if (x != cudaSuccess) return fail(e, SACRA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(x));
   return SACRA_OK;
 }
 
-cudaEvent_t pool_event(sacra_ctx *c) {
-  if (c->pool_used == c->pool.size()) {
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    c->pool.push_back(e);
+cudaEvent_t pool_event(Engine &e) {
+  if (e.pool_used == e.pool.size()) {
+    cudaEvent_t x;
+    cudaEventCreate(&x);
+    e.pool.push_back(x);
   }
-  return c->pool[c->pool_used++];
+  return e.pool[e.pool_used++];
 }
 
 // every kernel launch goes through here: count it, and bracket it with
 // events when profiling (not while a graph is being captured)
 template <class F>
-void run(sacra_ctx *c, Kid k, long long cells, F &&launch) {
-  if (c->prof && !c->capturing) {
-    ProfRec r{(int)k, pool_event(c), pool_event(c), cells};
-    cudaEventRecord(r.a, c->stream);
+void run(Engine &e, Kid k, long long cells, F &&launch) {
+  if (e.prof && !e.capturing) {
+    ProfRec r{(int)k, pool_event(e), pool_event(e), cells};
+    cudaEventRecord(r.a, e.stream);
     launch();
-    cudaEventRecord(r.b, c->stream);
-    c->recs.push_back(r);
+    cudaEventRecord(r.b, e.stream);
+    e.recs.push_back(r);
   } else {
     launch();
   }
-  ++c->launches;
+  ++e.launches;
 }
 
-int n_stages(const sacra_ctx *c) { return c->prm.rk == SACRA_RK4 ? 4 : 3; }
-double stage_c(const sacra_ctx *c, int s) {
+double stage_c(int rk, int s) {
   static const double c4[4] = {0.0, 0.5, 0.5, 1.0}, c3[3] = {0.0, 1.0, 0.5};
-  return c->prm.rk == SACRA_RK4 ? c4[s] : c3[s];
+  return rk == SACRA_RK4 ? c4[s] : c3[s];
 }
-double stage_b(const sacra_ctx *c, int s) {
+double stage_b(int rk, int s) {
   static const double b4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0}, b3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
-  return c->prm.rk == SACRA_RK4 ? b4[s] : b3[s];
+  return rk == SACRA_RK4 ? b4[s] : b3[s];
 }
-double *stage_state(sacra_ctx *c, int l, int s) { return s == 0 ? c->lv[l].un : c->lv[l].us; }
+double *stage_state(Star &st, int l, int s) { return s == 0 ? st.lv[l].un : st.lv[l].us; }
 
-void region(const sacra_ctx *c, int l, int s, int *jmax, int *kmax) {
-  const int ext = (l > 0 && s < n_stages(c) - 1) ? 4 : 0;
-  *jmax = c->prm.nx + ext;
-  *kmax = c->prm.nz + ext;
-}
-
-void enqueue_parity(sacra_ctx *c, int l, double *U) {
-  const Lev &L = c->lv[l];
-  run(c, K_PARITY_X, 8LL * (L.nz + GH), [&] { launch_parity_x(L, U, c->stream); });
-  run(c, K_PARITY_Z, 8LL * (L.nx + 2 * GH), [&] { launch_parity_z(L, U, c->stream); });
+bool kind_used(const Engine &e, int kind) {
+  const sacra_params &p = e.stars[0].prm;
+  if (kind == B_CARTOON) return p.evolve_spacetime && p.geometry == SACRA_CYLINDRICAL;
+  if (kind == B_DERIVS || kind == B_POINT) return p.evolve_spacetime != 0;
+  return true;
 }
 
-void enqueue_fill(sacra_ctx *c, int s, double dt) {
-  for (int l = 0; l < c->prm.n_levels; ++l) {
-    double *U = stage_state(c, l, s);
-    const Lev &L = c->lv[l];
-    if (c->prm.geometry == SACRA_PLANAR) {
-      run(c, K_OUTFLOW, (long long)L.px * L.pz, [&] { launch_outflow(L, U, c->stream); });
+bool fixed_shape(const Engine &e, int kind) { return kind == B_DERIVS && (e.dp.mixed & SACRA_MIXED_Z4C); }
+
+Shape kind_shape(const Engine &e, int kind) {
+  if (fixed_shape(e, kind)) {
+    const dim3 b = z4c_derivs_f32_block();
+    return {(int)b.x, (int)b.y};
+  }
+  return e.cfg[kind].shape;
+}
+
+// ---------------------------------------------------------------- plan
+
+// level views as stage s at register parity par sees them
+BL make_bl(const Engine &e, int slot, int par, int s) {
+  const Star &st = e.stars[e.slots[slot].first];
+  const int l = e.slots[slot].second;
+  BL b;
+  b.L = st.lv[l];
+  b.P = st.dp;
+  if (par != e.parity) std::swap(b.L.un, b.L.us);   // st.lv holds the registers of the current parity
+  b.U = s == 0 ? b.L.un : b.L.us;
+  b.DS = st.ds[l];
+  const int ext = (l > 0 && s < e.S - 1) ? 4 : 0;
+  b.jmax = st.prm.nx + ext;
+  b.kmax = st.prm.nz + ext;
+  b.has_child = l < st.prm.n_levels - 1;
+  b.has_parent = l > 0;
+  b.wb = stage_b(st.prm.rk, s);
+  return b;
+}
+
+void build_tiles(const Engine &e, int s, int kind, Shape sh, std::vector<Tile> &out) {
+  out.clear();
+  for (int i = 0; i < (int)e.slots.size(); ++i) {
+    const Region r = kind_region(e.stars[e.slots[i].first].prm, e.slots[i].second, s, e.S, kind);
+    for (int k0 = r.k0; k0 <= r.k1; k0 += sh.y)
+      for (int j0 = r.j0; j0 <= r.j1; j0 += sh.x) out.push_back(Tile{i, j0, k0, 0});
+  }
+}
+
+long long region_cells(const Engine &e, int s, int kind) {
+  long long n = 0;
+  for (const auto &sl : e.slots) {
+    const Region r = kind_region(e.stars[sl.first].prm, sl.second, s, e.S, kind);
+    n += (long long)(r.j1 - r.j0 + 1) * (r.k1 - r.k0 + 1);
+  }
+  return n;
+}
+
+// tiles of (stage s, kind) over all stars at shape sh
+long long count_tiles(const std::vector<sacra_params> &ps, int S, int s, int kind, Shape sh) {
+  long long n = 0;
+  for (const sacra_params &p : ps)
+    for (int l = 0; l < p.n_levels; ++l) n += tile_count(kind_region(p, l, s, S, kind), sh);
+  return n;
+}
+
+// the largest tile count of (stage s, kind) over every shape a launch may use
+long long max_tiles(const std::vector<sacra_params> &ps, int S, int s, int kind) {
+  long long m = 0;
+  for (const Shape &sh : kShapes256) m = std::max(m, count_tiles(ps, S, s, kind, sh));
+  const dim3 f = z4c_derivs_f32_block();
+  return std::max(m, count_tiles(ps, S, s, kind, Shape{(int)f.x, (int)f.y}));
+}
+
+// tile capacity: every stage and kind at its largest count, then a tuning area
+void plan_caps(const std::vector<sacra_params> &ps, size_t *cap, size_t *tune) {
+  const int S = ps[0].rk == SACRA_RK4 ? 4 : 3;
+  *cap = 0;
+  *tune = 0;
+  for (int s = 0; s < S; ++s)
+    for (int kind = 0; kind < B_NKIND; ++kind) {
+      const long long m = max_tiles(ps, S, s, kind);
+      *cap += (size_t)m;
+      if (s == 0) *tune = std::max(*tune, (size_t)m);
+    }
+}
+
+size_t plan_bytes(const std::vector<sacra_params> &ps) {
+  const int S = ps[0].rk == SACRA_RK4 ? 4 : 3;
+  size_t nl = 0;
+  for (const sacra_params &p : ps) nl += p.n_levels;
+  size_t cap, tune;
+  plan_caps(ps, &cap, &tune);
+  return round_up((2 * (size_t)S + 2) * nl * sizeof(BL), 256) + round_up((cap + tune) * sizeof(Tile), 256);
+}
+
+// upload the level views and the tile lists of the current choice of shapes
+sacra_status upload_plan(Engine &e) {
+  const int NL = (int)e.slots.size();
+  std::vector<BL> bls((size_t)2 * e.S * NL);
+  for (int par = 0; par < 2; ++par)
+    for (int s = 0; s < e.S; ++s)
+      for (int i = 0; i < NL; ++i) bls[((size_t)par * e.S + s) * NL + i] = make_bl(e, i, par, s);
+  cudaMemcpyAsync(e.bl_dev, bls.data(), bls.size() * sizeof(BL), cudaMemcpyHostToDevice, e.stream);
+  std::vector<Tile> all, t;
+  for (int s = 0; s < e.S; ++s)
+    for (int kind = 0; kind < B_NKIND; ++kind) {
+      build_tiles(e, s, kind, kind_shape(e, kind), t);
+      e.toff[s][kind] = (long long)all.size();
+      e.tcnt[s][kind] = (long long)t.size();
+      e.cells[s][kind] = region_cells(e, s, kind);
+      all.insert(all.end(), t.begin(), t.end());
+    }
+  if (all.size() > e.tiles_cap) return fail(e, SACRA_ERR_OOM, "tile capacity exceeded");
+  cudaMemcpyAsync(e.tiles_dev, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice, e.stream);
+  // the host vectors must live until the copies are done
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "upload plan");
+  return cuda_check(e, "upload plan");
+}
+
+Batch batch_of(const Engine &e, int s, int kind) {
+  Batch b;
+  b.bl = e.bl_dev + ((size_t)e.parity * e.S + s) * e.slots.size();
+  b.tiles = e.tiles_dev + e.toff[s][kind];
+  b.ntiles = (int)e.tcnt[s][kind];
+  const Shape sh = kind_shape(e, kind);
+  b.block = dim3(sh.x, sh.y);
+  const long long g = (long long)e.sms * e.cfg[kind].blocks_per_sm;
+  b.grid = (int)std::max(1LL, std::min<long long>(g, b.ntiles));
+  return b;
+}
+
+void launch_kind(Engine &e, int kind, const Batch &b, int s, double dt) {
+  switch (kind) {
+    case B_FLUX_X: launch_b_flux_x(b, e.dp, e.stream); break;
+    case B_FLUX_Z: launch_b_flux_z(b, e.dp, e.stream); break;
+    case B_HYDRO: launch_b_hydro_div(b, e.dp, e.stream); break;
+    case B_CARTOON: launch_b_cartoon(b, e.dp, e.tab, kTabStride, e.stream); break;
+    case B_DERIVS: launch_b_z4c_derivs(b, e.dp, e.stream); break;
+    case B_POINT: launch_b_z4c_point(b, e.dp, e.stream); break;
+    case B_RK: launch_b_rk_update(b, e.dp, s, dt, e.stream); break;
+  }
+}
+
+// ---------------------------------------------------------------- stage sequence
+
+void enqueue_parity(Engine &e, Star &st, int l, double *U) {
+  const Lev &L = st.lv[l];
+  run(e, K_PARITY_X, 8LL * (L.nz + GH), [&] { launch_parity_x(L, U, e.stream); });
+  run(e, K_PARITY_Z, 8LL * (L.nx + 2 * GH), [&] { launch_parity_z(L, U, e.stream); });
+}
+
+void enqueue_fill(Engine &e, Star &st, int s, double dt) {
+  for (int l = 0; l < st.prm.n_levels; ++l) {
+    double *U = stage_state(st, l, s);
+    const Lev &L = st.lv[l];
+    if (st.prm.geometry == SACRA_PLANAR) {
+      run(e, K_OUTFLOW, (long long)L.px * L.pz, [&] { launch_outflow(L, U, e.stream); });
       continue;
     }
     if (l == 0) {
-      run(c, K_OUTER, (long long)(L.nx + GH) * (L.nz + GH) - (long long)L.nx * L.nz,
-          [&] { launch_outer(L, L.un, U, stage_c(c, s) * dt, c->stream); });
+      run(e, K_OUTER, (long long)(L.nx + GH) * (L.nz + GH) - (long long)L.nx * L.nz,
+          [&] { launch_outer(L, L.un, U, stage_c(st.prm.rk, s) * dt, e.stream); });
     } else {
-      double *Up = stage_state(c, l - 1, s);
-      run(c, K_PROLONG, prolong_cells(L, s == 0), [&] { launch_prolong(L, c->lv[l - 1], c->dp, U, Up, s == 0, c->stream); });
-      ++c->launches;   // the prolongation is two kernels
+      double *Up = stage_state(st, l - 1, s);
+      run(e, K_PROLONG, prolong_cells(L, s == 0), [&] { launch_prolong(L, st.lv[l - 1], st.dp, U, Up, s == 0, e.stream); });
+      ++e.launches;   // the prolongation is two kernels
     }
-    enqueue_parity(c, l, U);
+    enqueue_parity(e, st, l, U);
   }
 }
 
-void swap_registers(sacra_ctx *c) {
-  for (int l = 0; l < c->prm.n_levels; ++l) {
-    double *t = c->lv[l].un;
-    c->lv[l].un = c->lv[l].us;
-    c->lv[l].us = t;
-  }
-  c->parity ^= 1;
+void swap_registers(Engine &e) {
+  for (Star &st : e.stars)
+    for (int l = 0; l < st.prm.n_levels; ++l) std::swap(st.lv[l].un, st.lv[l].us);
+  e.parity ^= 1;
 }
 
-void enqueue_stage(sacra_ctx *c, int s, double dt) {
-  const int S = n_stages(c);
-  const int L = c->prm.n_levels;
-  if (s == 0) {
-    c->dt_step = dt;
-    for (int l = 0; l < L; ++l)
-      cudaMemsetAsync(c->lv[l].freg, 0, (size_t)4 * NCONS * c->lv[l].rw * sizeof(double), c->stream);
-  }
-  for (int l = 0; l < L; ++l) {
-    Lev &lv = c->lv[l];
-    double *U = stage_state(c, l, s);
-    int jmax, kmax;
-    region(c, l, s, &jmax, &kmax);
-    const long long cells = (long long)jmax * kmax;
-    const double wb = stage_b(c, s);
-    const int hc = l < L - 1, hp = l > 0;
-    run(c, K_FLUX_X, cells, [&] { launch_flux_x(lv, c->dp, U, jmax, kmax, wb, hc, hp, c->stream); });
-    run(c, K_FLUX_Z, cells, [&] { launch_flux_z(lv, c->dp, U, jmax, kmax, wb, hc, hp, c->stream); });
-    run(c, K_HYDRO_DIV, cells, [&] { launch_hydro_div(lv, c->dp, U, jmax, kmax, c->stream); });
-    if (c->prm.evolve_spacetime) {
-      if (c->prm.geometry == SACRA_CYLINDRICAL)
-        run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, c->dp, U, c->tab, kTabStride, c->stream); });
-      run(c, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, c->dp, U, c->ds, jmax, kmax, c->stream); });
-      run(c, K_Z4C_POINT, cells, [&] { launch_z4c_point(lv, c->dp, U, c->ds, jmax, kmax, c->stream); });
+// one RK stage of every level of every star: one batched launch per kernel kind
+void enqueue_stage(Engine &e, int s, double dt) {
+  if (s == 0)
+    for (Star &st : e.stars) {
+      st.dt_step = dt;
+      for (int l = 0; l < st.prm.n_levels; ++l)
+        cudaMemsetAsync(st.lv[l].freg, 0, (size_t)4 * NCONS * st.lv[l].rw * sizeof(double), e.stream);
     }
-    run(c, K_RK_UPDATE, cells, [&] { launch_rk_update(lv, c->dp, U, s, dt, jmax, kmax, c->stream); });
+  for (int kind = 0; kind < B_NKIND; ++kind) {
+    if (!kind_used(e, kind)) continue;
+    const Batch b = batch_of(e, s, kind);
+    run(e, kKindKid[kind], e.cells[s][kind], [&] { launch_kind(e, kind, b, s, dt); });
   }
-  if (s == S - 1) {
-    if (c->prm.geometry == SACRA_CYLINDRICAL) {
-      const Lev &L0 = c->lv[0];
-      run(c, K_OUTER, (long long)(L0.nx + GH) * (L0.nz + GH) - (long long)L0.nx * L0.nz,
-          [&] { launch_outer(L0, L0.un, L0.us, dt, c->stream); });
-    }
-    swap_registers(c);
+  if (s == e.S - 1) {
+    for (Star &st : e.stars)
+      if (st.prm.geometry == SACRA_CYLINDRICAL) {
+        const Lev &L0 = st.lv[0];
+        run(e, K_OUTER, (long long)(L0.nx + GH) * (L0.nz + GH) - (long long)L0.nx * L0.nz,
+            [&] { launch_outer(L0, L0.un, L0.us, dt, e.stream); });
+      }
+    swap_registers(e);
   }
 }
 
-void enqueue_restrict(sacra_ctx *c) {
-  const int L = c->prm.n_levels;
+void enqueue_restrict(Engine &e, Star &st) {
+  const int L = st.prm.n_levels;
   if (L < 2) return;
   for (int l = L - 1; l >= 1; --l) {
-    Lev &C = c->lv[l], &Pa = c->lv[l - 1];
-    enqueue_parity(c, l, C.un);
+    Lev &C = st.lv[l], &Pa = st.lv[l - 1];
+    enqueue_parity(e, st, l, C.un);
     const int nh = Pa.nx / 2;
-    run(c, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, c->stream); });
-    run(c, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, c->dt_step, c->stream); });
+    run(e, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, e.stream); });
+    run(e, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, st.dt_step, e.stream); });
     // the restricted cells [1, N/2]^2 and the refluxed strips next to them (not the corner)
-    run(c, K_C2P, (long long)(nh + 1) * (nh + 1) - 1,
-        [&] { launch_c2p_region(Pa, c->dp, Pa.un, 1, nh + 1, 1, nh + 1, c->stream, 1); });
+    run(e, K_C2P, (long long)(nh + 1) * (nh + 1) - 1,
+        [&] { launch_c2p_region(Pa, st.dp, Pa.un, 1, nh + 1, 1, nh + 1, e.stream, 1); });
   }
   // the parents' axis/equator ghosts mirror their restricted interiors
-  for (int l = 0; l < L - 1; ++l) enqueue_parity(c, l, c->lv[l].un);
+  for (int l = 0; l < L - 1; ++l) enqueue_parity(e, st, l, st.lv[l].un);
 }
 
-void enqueue_step(sacra_ctx *c, double dt) {
-  const int S = n_stages(c);
-  for (int s = 0; s < S; ++s) {
-    enqueue_fill(c, s, dt);
-    enqueue_stage(c, s, dt);
+void enqueue_step(Engine &e, double dt) {
+  for (int s = 0; s < e.S; ++s) {
+    for (Star &st : e.stars) enqueue_fill(e, st, s, dt);
+    enqueue_stage(e, s, dt);
   }
-  enqueue_restrict(c);
+  for (Star &st : e.stars) enqueue_restrict(e, st);
 }
 
-}  // namespace
-
-extern "C" {
-
-sacra_status sacra_arena_bytes(const sacra_params *p, size_t *bytes) {
-  std::string why;
-  if (!bytes || !valid(p, &why)) return SACRA_ERR_ARG;
-  const Layout o = layout(p);
-  *bytes = o.per_level * p->n_levels + o.shared;
-  return SACRA_OK;
+bool ready(const Engine &e) {
+  for (const Star &st : e.stars)
+    for (int l = 0; l < st.prm.n_levels; ++l)
+      if (!st.have_data[l]) return false;
+  return true;
 }
 
-sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *arena, size_t arena_bytes,
-                             sacra_ctx **out) {
-  if (!out) return SACRA_ERR_ARG;
-  *out = nullptr;
-  std::string why;
-  if (!valid(p, &why)) return SACRA_ERR_ARG;
-  sacra_ctx *c = new sacra_ctx();
-  c->prm = *p;
-  c->lay = layout(p);
-  c->stream = (cudaStream_t)cuda_stream;
-  const size_t need = c->lay.per_level * p->n_levels + c->lay.shared;
-  if (arena) {
-    if (arena_bytes < need || ((uintptr_t)arena & 255)) {
-      delete c;
-      return SACRA_ERR_OOM;
+void drop_graphs(Engine &e) {
+  for (int i = 0; i < 2; ++i)
+    if (e.gexec[i]) {
+      cudaGraphExecDestroy(e.gexec[i]);
+      e.gexec[i] = nullptr;
     }
-    c->arena = (char *)arena;
-  } else {
-    if (cudaMalloc(&c->arena, need) != cudaSuccess) {
-      cudaGetLastError();
-      delete c;
-      return SACRA_ERR_OOM;
-    }
-    c->own_arena = true;
-  }
-  if (cudaMemsetAsync(c->arena, 0, need, c->stream) != cudaSuccess) {
-    cudaGetLastError();
-    if (c->own_arena) cudaFree(c->arena);
-    delete c;
-    return SACRA_ERR_CUDA;
-  }
-  fill_dev_params(p, &c->dp);
+}
 
-  char *shared = c->arena + c->lay.per_level * p->n_levels;
-  c->ds = (double *)(shared + c->lay.ds_off);
-  double *dy = (double *)(shared + c->lay.dy_off);
-  double *dyy = (double *)(shared + c->lay.dyy_off);
-  c->tab = (double *)(shared + c->lay.tab_off);
-  c->part = (double *)(shared + c->lay.part_off);
-  c->dout = (double *)(shared + c->lay.dout_off);
-  c->nfb = (unsigned long long *)(shared + c->lay.nfb_off);
-  const size_t P = c->lay.P;
-  const size_t rwp = round_up((size_t)c->lay.rw, 32);
+// ---------------------------------------------------------------- autotuner
+//
+// Per kernel kind: every tile shape the kernel's launch bounds allow, times
+// every persistent grid size (blocks per SM), each timed by CUDA events over
+// `reps` stage-0 launches on the current state.  These launches change no
+// state: the flux registers are off, the stage update writes into the level's
+// derivative scratch, the fallback counter is restored afterwards, and every
+// buffer they do write (face fluxes, right-hand sides, scratch) is recomputed
+// by the next stage.
+sacra_status tune(Engine &e, int reps) {
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  if (reps < 1) reps = 1;
+  drop_graphs(e);
+  const int NL = (int)e.slots.size();
+  std::vector<BL> tv(2 * (size_t)NL);
+  for (int i = 0; i < NL; ++i) {
+    BL b = make_bl(e, i, e.parity, 0);
+    b.has_child = b.has_parent = 0;
+    tv[i] = b;
+    double *scr = reinterpret_cast<double *>(b.DS);
+    const size_t P = b.L.P;
+    b.L.us = scr;
+    b.L.ka = scr + (size_t)NST * P;
+    b.L.prim = scr + (size_t)2 * NST * P;
+    b.L.status = reinterpret_cast<int *>(scr + (size_t)(2 * NST + NPRIM) * P);
+    tv[NL + i] = b;
+  }
+  BL *tv_dev = e.bl_dev + (size_t)2 * e.S * NL;
+  cudaMemcpyAsync(tv_dev, tv.data(), tv.size() * sizeof(BL), cudaMemcpyHostToDevice, e.stream);
+  unsigned long long nfb0 = 0;
+  cudaMemcpyAsync(&nfb0, e.nfb, sizeof(nfb0), cudaMemcpyDeviceToHost, e.stream);
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "tune");
+  Tile *tune_tiles = e.tiles_dev + e.tiles_cap;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  std::vector<Tile> t;
+  sacra_status status = SACRA_OK;
+  // coordinate descent per kind: the grid size at the current shape, then the shape at that grid size
+  auto time_cfg = [&](int kind, Shape sh, int m, float *ms) -> sacra_status {
+    build_tiles(e, 0, kind, sh, t);
+    if (t.size() > e.tune_cap) { *ms = 1e30f; return SACRA_OK; }
+    cudaMemcpyAsync(tune_tiles, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, e.stream);
+    Batch bt;
+    bt.bl = tv_dev + (kind == B_RK ? NL : 0);
+    bt.tiles = tune_tiles;
+    bt.ntiles = (int)t.size();
+    bt.block = dim3(sh.x, sh.y);
+    bt.grid = (int)std::max(1LL, std::min<long long>((long long)e.sms * m, bt.ntiles));
+    launch_kind(e, kind, bt, 0, 0.0);   // warm-up
+    cudaEventRecord(a, e.stream);
+    for (int r = 0; r < reps; ++r) launch_kind(e, kind, bt, 0, 0.0);
+    cudaEventRecord(b, e.stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) return cuda_check(e, "tune");
+    e.launches += reps + 1;
+    cudaEventElapsedTime(ms, a, b);
+    return SACRA_OK;
+  };
+  for (int kind = 0; kind < B_NKIND && status == SACRA_OK; ++kind) {
+    if (!kind_used(e, kind)) continue;
+    std::vector<Shape> shapes;
+    if (fixed_shape(e, kind)) shapes.push_back(kind_shape(e, kind));
+    else if (max_threads(kind) >= 256) shapes.assign(std::begin(kShapes256), std::end(kShapes256));
+    else shapes.assign(std::begin(kShapes128), std::end(kShapes128));
+    KindCfg pick = e.cfg[kind];
+    pick.shape = kind_shape(e, kind);
+    float best = 1e30f;
+    for (int m : kBlocksPerSm) {
+      float ms = 0.f;
+      if ((status = time_cfg(kind, pick.shape, m, &ms)) != SACRA_OK) break;
+      if (ms < best) { best = ms; pick.blocks_per_sm = m; }
+    }
+    for (const Shape &sh : shapes) {
+      if (status != SACRA_OK || (sh.x == pick.shape.x && sh.y == pick.shape.y)) continue;
+      float ms = 0.f;
+      if ((status = time_cfg(kind, sh, pick.blocks_per_sm, &ms)) != SACRA_OK) break;
+      if (ms < best) { best = ms; pick.shape = sh; }
+    }
+    e.cfg[kind] = pick;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (status != SACRA_OK) return status;
+  cudaMemcpyAsync(e.nfb, &nfb0, sizeof(nfb0), cudaMemcpyHostToDevice, e.stream);
+  status = upload_plan(e);
+  if (status != SACRA_OK) return status;
+  return cuda_check(e, "tune");
+}
+
+// ---------------------------------------------------------------- set-up
+
+void init_star_levels(Star &st, char *base) {
+  const sacra_params *p = &st.prm;
+  const size_t P = st.lay.P;
+  const size_t rwp = round_up((size_t)st.lay.rw, 32);
   for (int l = 0; l < p->n_levels; ++l) {
-    Lev &L = c->lv[l];
-    char *b = c->arena + c->lay.per_level * l;
+    Lev &L = st.lv[l];
+    memset(&L, 0, sizeof(L));
+    char *b = base + st.lay.per_level * l;
     L.nx = p->nx; L.nz = p->nz; L.px = p->nx + 2 * GH; L.pz = p->nz + 2 * GH; L.rw = (int)rwp;
-    L.dx = p->dx0 / (double)(1 << l);
-    L.dz = p->dz0 / (double)(1 << l);
-    L.i60x = 1.0 / (60.0 * L.dx);
-    L.i60z = 1.0 / (60.0 * L.dz);
+    set_spacing(L, p->dx0 / (double)(1 << l), p->dz0 / (double)(1 << l));
     L.P = P;
     double *dp = (double *)b;
     L.un = dp; dp += NST * P;
@@ -351,201 +602,248 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
     L.prim = dp; dp += NPRIM * P;
     L.fx = dp; dp += NCONS * P;
     L.fz = dp; dp += NCONS * P;
+    st.ds[l] = dp; dp += (size_t)z4c_scratch_planes() * P;
+    L.dy = dp; dp += NMET * P;
+    L.dyy = dp; dp += NMET * P;
     L.freg = dp; dp += 4 * NCONS * rwp;
     L.status = (int *)dp;
-    L.dy = dy; L.dyy = dyy;
-    L.nfb = c->nfb;
   }
-  // cartoon table: for x_j = (j - 1/2) dx and plane m dy (dy = dx), the
-  // 9 weights on x_{j-4..j+4} at varpi = sqrt(x_j^2 + (m dy)^2), cos, sin of phi, cos - 1
-  {
-    const int nj = p->nx + 8;
-    std::vector<double> tab((size_t)nj * 3 * kTabStride, 0.0);
-    double nodes[9];
-    for (int n = 0; n < 9; ++n) nodes[n] = n - 4;
-    for (int j = 1; j < nj; ++j)
-      for (int m = 1; m <= 3; ++m) {
-        const double x = j - 0.5, vp = sqrt(x * x + (double)(m * m));
-        double *t = &tab[(size_t)(j * 3 + m - 1) * kTabStride];
-        lagrange_weights(9, nodes, vp - x, t);
-        t[9] = x / vp;
-        t[10] = m / vp;
-        t[11] = -(double)(m * m) / (vp * (x + vp));   // cos phi - 1 without cancellation
-      }
-    cudaMemcpyAsync(c->tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  st.part = (double *)(base + st.lay.per_level * p->n_levels);
+}
+
+// shared tables: cartoon weights (for the largest nx) and the grid weights
+void upload_tables(Engine &e, int max_nx) {
+  // cartoon table: for x_j = (j - 1/2) dx and plane m dy (dy = dx), the 9
+  // weights on x_{j-4..j+4} at varpi = sqrt(x_j^2 + (m dy)^2), cos, sin of phi, cos - 1
+  const int nj = max_nx + 8;
+  std::vector<double> tab((size_t)nj * 3 * kTabStride, 0.0);
+  double nodes[9];
+  for (int n = 0; n < 9; ++n) nodes[n] = n - 4;
+  for (int j = 1; j < nj; ++j)
+    for (int m = 1; m <= 3; ++m) {
+      const double x = j - 0.5, vp = sqrt(x * x + (double)(m * m));
+      double *t = &tab[(size_t)(j * 3 + m - 1) * kTabStride];
+      lagrange_weights(9, nodes, vp - x, t);
+      t[9] = x / vp;
+      t[10] = m / vp;
+      t[11] = -(double)(m * m) / (vp * (x + vp));   // cos phi - 1 without cancellation
+    }
+  cudaMemcpyAsync(e.tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, e.stream);
+  GridWeights w;
+  double n8[8];
+  for (int n = 0; n < 8; ++n) n8[n] = n - 3;
+  lagrange_weights(8, n8, 0.25, w.prol);
+  lagrange_weights(8, n8, 0.5, w.rest_c);          // nodes 2j-4..2j+3 relative to 2j-1
+  for (int n = 0; n < 8; ++n) n8[n] = n;
+  lagrange_weights(8, n8, 4.5, w.rest_s1);         // N-7..N -> N - 5/2
+  lagrange_weights(8, n8, 6.5, w.rest_s0);         // N-7..N -> N - 1/2
+  set_grid_weights(w);
+  cudaStreamSynchronize(e.stream);                 // tab lives on the host stack
+}
+
+size_t engine_bytes(const std::vector<sacra_params> &ps) {
+  size_t n = 0;
+  int max_nx = 0;
+  for (const sacra_params &p : ps) {
+    n += star_bytes(&p);
+    max_nx = std::max(max_nx, p.nx);
   }
-  {
-    GridWeights w;
-    double n8[8];
-    for (int n = 0; n < 8; ++n) n8[n] = n - 3;
-    lagrange_weights(8, n8, 0.25, w.prol);
-    lagrange_weights(8, n8, 0.5, w.rest_c);          // nodes 2j-4..2j+3 relative to 2j-1
-    for (int n = 0; n < 8; ++n) n8[n] = n;
-    lagrange_weights(8, n8, 4.5, w.rest_s1);         // N-7..N -> N - 5/2
-    lagrange_weights(8, n8, 6.5, w.rest_s0);         // N-7..N -> N - 1/2
-    set_grid_weights(w);
+  return n + round_up((size_t)(max_nx + 8) * 3 * kTabStride * 8, 256) + 256 /* dout */ + 256 /* nfb */ +
+         plan_bytes(ps);
+}
+
+sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *stream, void *arena, size_t arena_bytes) {
+  e.stream = (cudaStream_t)stream;
+  const size_t need = engine_bytes(ps);
+  if (arena) {
+    if (arena_bytes < need || ((uintptr_t)arena & 255)) return SACRA_ERR_OOM;
+    e.arena = (char *)arena;
+  } else {
+    if (cudaMalloc(&e.arena, need) != cudaSuccess) {
+      cudaGetLastError();
+      return SACRA_ERR_OOM;
+    }
+    e.own_arena = true;
   }
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-    if (c->own_arena) cudaFree(c->arena);
-    delete c;
+  if (cudaMemsetAsync(e.arena, 0, need, e.stream) != cudaSuccess) {
+    cudaGetLastError();
     return SACRA_ERR_CUDA;
   }
-  *out = c;
+  fill_dev_params(&ps[0], &e.dp);
+  e.S = ps[0].rk == SACRA_RK4 ? 4 : 3;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&e.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e.sms < 1) e.sms = 1;
+  char *p = e.arena;
+  e.stars.resize(ps.size());
+  int max_nx = 0;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    Star &st = e.stars[i];
+    st.prm = ps[i];
+    fill_dev_params(&ps[i], &st.dp);
+    st.lay = layout(&ps[i]);
+    init_star_levels(st, p);
+    p += star_bytes(&ps[i]);
+    max_nx = std::max(max_nx, ps[i].nx);
+    for (int l = 0; l < ps[i].n_levels; ++l) e.slots.push_back({(int)i, l});
+  }
+  e.tab = (double *)p;
+  p += round_up((size_t)(max_nx + 8) * 3 * kTabStride * 8, 256);
+  e.dout = (double *)p;
+  p += 256;
+  e.nfb = (unsigned long long *)p;
+  p += 256;
+  const size_t nl = e.slots.size();
+  e.bl_dev = (BL *)p;
+  p += round_up((2 * (size_t)e.S + 2) * nl * sizeof(BL), 256);
+  e.tiles_dev = (Tile *)p;
+  plan_caps(ps, &e.tiles_cap, &e.tune_cap);
+  for (Star &st : e.stars)
+    for (int l = 0; l < st.prm.n_levels; ++l) st.lv[l].nfb = e.nfb;
+  upload_tables(e, max_nx);
+  const sacra_status s = upload_plan(e);
+  if (s != SACRA_OK) return s;
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SACRA_ERR_CUDA;
   return SACRA_OK;
 }
 
-sacra_status sacra_set_initial_data(sacra_ctx *c, int level, int kind, const double *host, int n_fields) {
-  if (!c) return SACRA_ERR_ARG;
-  if (level < 0 || level >= c->prm.n_levels || !host) return fail(c, SACRA_ERR_ARG, "bad level or buffer");
-  if (n_fields != 30) return fail(c, SACRA_ERR_ARG, "n_fields must be 30");
-  Lev &L = c->lv[level];
+void engine_free(Engine &e) {
+  cudaStreamSynchronize(e.stream);
+  drop_graphs(e);
+  for (cudaEvent_t x : e.pool) cudaEventDestroy(x);
+  if (e.own_arena && e.arena) cudaFree(e.arena);
+}
+
+// ---------------------------------------------------------------- operations shared by both handles
+
+sacra_status set_initial_data(Engine &e, int star, int level, int kind, const double *host, int n_fields) {
+  if (star < 0 || star >= (int)e.stars.size()) return fail(e, SACRA_ERR_ARG, "bad star");
+  Star &st = e.stars[star];
+  if (level < 0 || level >= st.prm.n_levels || !host) return fail(e, SACRA_ERR_ARG, "bad level or buffer");
+  if (n_fields != 30) return fail(e, SACRA_ERR_ARG, "n_fields must be 30");
+  Lev &L = st.lv[level];
   const size_t np = (size_t)L.px * L.pz;
   if (kind == SACRA_PRIM_METRIC) {
     for (int f = 0; f < NMET; ++f)
-      cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, e.stream);
     for (int v = 0; v < 5; ++v)
       cudaMemcpyAsync(L.prim + (size_t)v * L.P, host + (size_t)(NMET + v) * np, np * 8, cudaMemcpyHostToDevice,
-                      c->stream);
-    run(c, K_PRIM2CONS, (long long)np, [&] { launch_prim2cons_all(L, c->dp, L.un, c->stream); });
+                      e.stream);
+    run(e, K_PRIM2CONS, (long long)np, [&] { launch_prim2cons_all(L, st.dp, L.un, e.stream); });
   } else if (kind == SACRA_RAW) {
     for (int f = 0; f < NST; ++f)
-      cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, c->stream);
-    run(c, K_C2P, (long long)np, [&] { launch_c2p_region(L, c->dp, L.un, 1 - GH, L.nx + GH, 1 - GH, L.nz + GH, c->stream); });
+      cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, e.stream);
+    run(e, K_C2P, (long long)np, [&] { launch_c2p_region(L, st.dp, L.un, 1 - GH, L.nx + GH, 1 - GH, L.nz + GH, e.stream); });
   } else {
-    return fail(c, SACRA_ERR_ARG, "unknown kind");
+    return fail(e, SACRA_ERR_ARG, "unknown kind");
   }
-  cudaMemcpyAsync(L.us, L.un, (size_t)NST * L.P * 8, cudaMemcpyDeviceToDevice, c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "set_initial_data");
-  c->have_data[level] = true;
-  return cuda_check(c, "set_initial_data");
+  cudaMemcpyAsync(L.us, L.un, (size_t)NST * L.P * 8, cudaMemcpyDeviceToDevice, e.stream);
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "set_initial_data");
+  st.have_data[level] = true;
+  return cuda_check(e, "set_initial_data");
 }
 
-static bool ready(sacra_ctx *c) {
-  for (int l = 0; l < c->prm.n_levels; ++l)
-    if (!c->have_data[l]) return false;
-  return true;
-}
-
-sacra_status sacra_regrid_ghosts(sacra_ctx *c, int what, int stage, double dt) {
-  if (!c) return SACRA_ERR_ARG;
-  if (!ready(c)) return fail(c, SACRA_ERR_STATE, "initial data missing on some level");
-  if (what == SACRA_FILL) {
-    if (stage < 0 || stage >= n_stages(c)) return fail(c, SACRA_ERR_ARG, "bad stage");
-    enqueue_fill(c, stage, dt);
-  } else if (what == SACRA_RESTRICT_REFLUX) {
-    enqueue_restrict(c);
-  } else {
-    return fail(c, SACRA_ERR_ARG, "unknown regrid request");
-  }
-  return cuda_check(c, "regrid_ghosts");
-}
-
-sacra_status sacra_rk_stage(sacra_ctx *c, int stage, double dt) {
-  if (!c) return SACRA_ERR_ARG;
-  if (!ready(c)) return fail(c, SACRA_ERR_STATE, "initial data missing on some level");
-  if (stage < 0 || stage >= n_stages(c) || !(dt > 0)) return fail(c, SACRA_ERR_ARG, "bad stage or dt");
-  enqueue_stage(c, stage, dt);
-  return cuda_check(c, "rk_stage");
-}
-
-sacra_status sacra_step(sacra_ctx *c, double dt, int n_steps, int use_graph) {
-  if (!c) return SACRA_ERR_ARG;
-  if (!ready(c)) return fail(c, SACRA_ERR_STATE, "initial data missing on some level");
-  if (!(dt > 0) || n_steps < 0) return fail(c, SACRA_ERR_ARG, "bad dt or n_steps");
+sacra_status step(Engine &e, double dt, int n_steps, int use_graph) {
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  if (!(dt > 0) || n_steps < 0) return fail(e, SACRA_ERR_ARG, "bad dt or n_steps");
   for (int it = 0; it < n_steps; ++it) {
     if (!use_graph) {
-      enqueue_step(c, dt);
+      enqueue_step(e, dt);
       continue;
     }
-    const int par = c->parity;
-    if (!c->gexec[par] || c->gdt[par] != dt) {
-      if (c->gexec[par]) { cudaGraphExecDestroy(c->gexec[par]); c->gexec[par] = nullptr; }
+    const int par = e.parity;
+    if (!e.gexec[par] || e.gdt[par] != dt) {
+      if (e.gexec[par]) { cudaGraphExecDestroy(e.gexec[par]); e.gexec[par] = nullptr; }
       cudaGraph_t g;
-      const long long before = c->launches;
-      if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return cuda_check(c, "graph capture (the stream must be a non-default stream)");
-      c->capturing = true;
-      enqueue_step(c, dt);       // swaps the registers on the host side
-      c->capturing = false;
-      if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess) return cuda_check(c, "graph capture");
-      c->glaunch[par] = c->launches - before;
-      c->launches = before;
-      swap_registers(c);         // undo: the graph has not run yet
-      if (cudaGraphInstantiate(&c->gexec[par], g, 0) != cudaSuccess) {
+      const long long before = e.launches;
+      if (cudaStreamBeginCapture(e.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cuda_check(e, "graph capture (the stream must be a non-default stream)");
+      e.capturing = true;
+      enqueue_step(e, dt);       // swaps the registers on the host side
+      e.capturing = false;
+      if (cudaStreamEndCapture(e.stream, &g) != cudaSuccess) return cuda_check(e, "graph capture");
+      e.glaunch[par] = e.launches - before;
+      e.launches = before;
+      swap_registers(e);         // undo: the graph has not run yet
+      if (cudaGraphInstantiate(&e.gexec[par], g, 0) != cudaSuccess) {
         cudaGraphDestroy(g);
-        return cuda_check(c, "graph instantiate");
+        return cuda_check(e, "graph instantiate");
       }
       cudaGraphDestroy(g);
-      c->gdt[par] = dt;
+      e.gdt[par] = dt;
     }
-    if (cudaGraphLaunch(c->gexec[par], c->stream) != cudaSuccess) return cuda_check(c, "graph launch");
-    c->launches += c->glaunch[par];
-    c->dt_step = dt;
-    swap_registers(c);
+    if (cudaGraphLaunch(e.gexec[par], e.stream) != cudaSuccess) return cuda_check(e, "graph launch");
+    e.launches += e.glaunch[par];
+    for (Star &st : e.stars) st.dt_step = dt;
+    swap_registers(e);
   }
-  return cuda_check(c, "step");
+  return cuda_check(e, "step");
 }
 
-sacra_status sacra_read_state(sacra_ctx *c, int level, int which, int field, double *host, size_t n) {
-  if (!c) return SACRA_ERR_ARG;
-  if (level < 0 || level >= c->prm.n_levels || !host) return fail(c, SACRA_ERR_ARG, "bad level or buffer");
-  Lev &L = c->lv[level];
+sacra_status read_state(Engine &e, int star, int level, int which, int field, double *host, size_t n) {
+  if (star < 0 || star >= (int)e.stars.size()) return fail(e, SACRA_ERR_ARG, "bad star");
+  Star &st = e.stars[star];
+  if (level < 0 || level >= st.prm.n_levels || !host) return fail(e, SACRA_ERR_ARG, "bad level or buffer");
+  Lev &L = st.lv[level];
   const size_t np = (size_t)L.px * L.pz;
   const double *src = nullptr;
   std::vector<double> tmp;
   if (which == SACRA_STATE_STEP || which == SACRA_STATE_STAGE || which == SACRA_RHS) {
-    if (field < 0 || field >= NST) return fail(c, SACRA_ERR_ARG, "bad field");
+    if (field < 0 || field >= NST) return fail(e, SACRA_ERR_ARG, "bad field");
     const double *base = which == SACRA_STATE_STEP ? L.un : (which == SACRA_STATE_STAGE ? L.us : L.rhs);
     src = base + (size_t)field * L.P;
   } else if (which == SACRA_PRIMS) {
-    if (field < 0 || field >= NPRIM) return fail(c, SACRA_ERR_ARG, "bad field");
+    if (field < 0 || field >= NPRIM) return fail(e, SACRA_ERR_ARG, "bad field");
     src = L.prim + (size_t)field * L.P;
   } else if (which != SACRA_STATUS) {
-    return fail(c, SACRA_ERR_ARG, "unknown plane");
+    return fail(e, SACRA_ERR_ARG, "unknown plane");
   }
   tmp.resize(np);
   if (which == SACRA_STATUS) {
-    std::vector<int> st(np);
-    cudaMemcpyAsync(st.data(), L.status, np * 4, cudaMemcpyDeviceToHost, c->stream);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "read_state");
-    for (size_t i = 0; i < np; ++i) tmp[i] = st[i];
+    std::vector<int> sv(np);
+    cudaMemcpyAsync(sv.data(), L.status, np * 4, cudaMemcpyDeviceToHost, e.stream);
+    if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "read_state");
+    for (size_t i = 0; i < np; ++i) tmp[i] = sv[i];
   } else {
-    cudaMemcpyAsync(tmp.data(), src, np * 8, cudaMemcpyDeviceToHost, c->stream);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "read_state");
+    cudaMemcpyAsync(tmp.data(), src, np * 8, cudaMemcpyDeviceToHost, e.stream);
+    if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "read_state");
   }
   if (n == np) {
     memcpy(host, tmp.data(), np * 8);
   } else if (n == (size_t)L.nx * L.nz) {
     for (int k = 1; k <= L.nz; ++k) memcpy(host + (size_t)(k - 1) * L.nx, tmp.data() + cid(L, 1, k), (size_t)L.nx * 8);
   } else {
-    return fail(c, SACRA_ERR_ARG, "n must be nx*nz or px*pz");
+    return fail(e, SACRA_ERR_ARG, "n must be nx*nz or px*pz");
   }
-  return cuda_check(c, "read_state");
+  return cuda_check(e, "read_state");
 }
 
-sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out) {
-  if (!c || !out) return SACRA_ERR_ARG;
-  if (!ready(c)) return fail(c, SACRA_ERR_STATE, "initial data missing on some level");
-  enqueue_fill(c, 0, 0.0);
-  const int L = c->prm.n_levels;
+sacra_status constraints(Engine &e, int star, sacra_diag *out) {
+  if (star < 0 || star >= (int)e.stars.size() || !out) return fail(e, SACRA_ERR_ARG, "bad star or output");
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  Star &st = e.stars[star];
+  enqueue_fill(e, st, 0, 0.0);
+  const int L = st.prm.n_levels;
   int slot = 0;
   for (int l = 0; l < L; ++l) {
-    Lev &lv = c->lv[l];
+    Lev &lv = st.lv[l];
     const long long cells = (long long)lv.nx * lv.nz;
-    if (c->prm.evolve_spacetime) {
-      run(c, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, c->dp, lv.un, c->tab, kTabStride, c->stream); });
-      run(c, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, c->dp, lv.un, c->ds, lv.nx, lv.nz, c->stream); });
+    double *ds = reinterpret_cast<double *>(st.ds[l]);
+    if (st.prm.evolve_spacetime) {
+      run(e, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, st.dp, lv.un, e.tab, kTabStride, e.stream); });
+      run(e, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, st.dp, lv.un, ds, lv.nx, lv.nz, e.stream); });
     }
     const int sl = slot;
-    run(c, K_DIAG, cells, [&] { launch_diag(lv, c->dp, c->ds, l < L - 1, c->prm.evolve_spacetime, c->part, sl, c->stream); });
+    run(e, K_DIAG, cells, [&] { launch_diag(lv, st.dp, ds, l < L - 1, st.prm.evolve_spacetime, st.part, sl, e.stream); });
     slot += diag_blocks(lv);
   }
-  run(c, K_DIAG_FINAL, slot, [&] { launch_diag_final(c->part, slot, c->dout, c->stream); });
+  run(e, K_DIAG_FINAL, slot, [&] { launch_diag_final(st.part, slot, e.dout, e.stream); });
   double h[9];
   unsigned long long nfb = 0;
-  cudaMemcpyAsync(h, c->dout, sizeof(h), cudaMemcpyDeviceToHost, c->stream);
-  cudaMemcpyAsync(&nfb, c->nfb, sizeof(nfb), cudaMemcpyDeviceToHost, c->stream);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "constraints");
+  cudaMemcpyAsync(h, e.dout, sizeof(h), cudaMemcpyDeviceToHost, e.stream);
+  cudaMemcpyAsync(&nfb, e.nfb, sizeof(nfb), cudaMemcpyDeviceToHost, e.stream);
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "constraints");
   out->H_L2 = sqrt(h[0] / h[4]);
   for (int a = 0; a < 3; ++a) out->M_L2[a] = sqrt(h[1 + a] / h[4]);
   out->Mb = h[5];
@@ -553,32 +851,16 @@ sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out) {
   out->rho_max = h[7];
   out->n_c2p_fail = h[8];
   out->n_fallback = (double)nfb;
-  return cuda_check(c, "constraints");
+  return cuda_check(e, "constraints");
 }
 
-sacra_status sacra_sync(sacra_ctx *c) {
-  if (!c) return SACRA_ERR_ARG;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "sync");
-  return cuda_check(c, "sync");
-}
-
-long long sacra_launch_count(const sacra_ctx *c) { return c ? c->launches : -1; }
-
-sacra_status sacra_profile(sacra_ctx *c, int enable) {
-  if (!c) return SACRA_ERR_ARG;
-  c->prof = enable != 0;
-  c->recs.clear();
-  c->pool_used = 0;
-  return SACRA_OK;
-}
-
-sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_len, double *total_ms,
-                               long long *launches, long long *cells) {
-  if (!c || idx < 0 || idx >= K_COUNT || !name || name_len == 0) return SACRA_ERR_ARG;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_check(c, "profile_get");
+sacra_status profile_get(Engine &e, int idx, char *name, size_t name_len, double *total_ms, long long *launches,
+                         long long *cells) {
+  if (idx < 0 || idx >= K_COUNT || !name || name_len == 0) return SACRA_ERR_ARG;
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "profile_get");
   double ms = 0.0;
   long long n = 0, cl = 0;
-  for (const ProfRec &r : c->recs) {
+  for (const ProfRec &r : e.recs) {
     if (r.kid != idx) continue;
     float t = 0.f;
     cudaEventElapsedTime(&t, r.a, r.b);
@@ -590,19 +872,202 @@ sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_le
   if (total_ms) *total_ms = ms;
   if (launches) *launches = n;
   if (cells) *cells = cl;
-  return cuda_check(c, "profile_get");
+  return cuda_check(e, "profile_get");
+}
+
+sacra_status get_tuning(const Engine &e, int kind, int *tile_x, int *tile_y, int *blocks_per_sm) {
+  if (kind < 0 || kind >= B_NKIND) return SACRA_ERR_ARG;
+  const Shape sh = kind_shape(e, kind);
+  if (tile_x) *tile_x = sh.x;
+  if (tile_y) *tile_y = sh.y;
+  if (blocks_per_sm) *blocks_per_sm = e.cfg[kind].blocks_per_sm;
+  return SACRA_OK;
+}
+
+sacra_status set_profile(Engine &e, int enable) {
+  e.prof = enable != 0;
+  e.recs.clear();
+  e.pool_used = 0;
+  return SACRA_OK;
+}
+
+sacra_status sync(Engine &e) {
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "sync");
+  return cuda_check(e, "sync");
+}
+
+bool params_ok(const sacra_params *per_star, int n) {
+  if (!per_star || n < 1) return false;
+  std::string why;
+  for (int i = 0; i < n; ++i)
+    if (!valid(&per_star[i], &why) || !compatible(&per_star[i], &per_star[0])) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------- one star
+
+sacra_status sacra_arena_bytes(const sacra_params *p, size_t *bytes) {
+  if (!bytes || !params_ok(p, 1)) return SACRA_ERR_ARG;
+  *bytes = engine_bytes({*p});
+  return SACRA_OK;
+}
+
+sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *arena, size_t arena_bytes,
+                             sacra_ctx **out) {
+  if (!out) return SACRA_ERR_ARG;
+  *out = nullptr;
+  if (!params_ok(p, 1)) return SACRA_ERR_ARG;
+  sacra_ctx *c = new sacra_ctx();
+  const sacra_status s = engine_init(c->e, {*p}, cuda_stream, arena, arena_bytes);
+  if (s != SACRA_OK) {
+    engine_free(c->e);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return SACRA_OK;
+}
+
+sacra_status sacra_set_initial_data(sacra_ctx *c, int level, int kind, const double *host, int n_fields) {
+  if (!c) return SACRA_ERR_ARG;
+  return set_initial_data(c->e, 0, level, kind, host, n_fields);
+}
+
+sacra_status sacra_regrid_ghosts(sacra_ctx *c, int what, int stage, double dt) {
+  if (!c) return SACRA_ERR_ARG;
+  Engine &e = c->e;
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  if (what == SACRA_FILL) {
+    if (stage < 0 || stage >= e.S) return fail(e, SACRA_ERR_ARG, "bad stage");
+    enqueue_fill(e, e.stars[0], stage, dt);
+  } else if (what == SACRA_RESTRICT_REFLUX) {
+    enqueue_restrict(e, e.stars[0]);
+  } else {
+    return fail(e, SACRA_ERR_ARG, "unknown regrid request");
+  }
+  return cuda_check(e, "regrid_ghosts");
+}
+
+sacra_status sacra_rk_stage(sacra_ctx *c, int stage, double dt) {
+  if (!c) return SACRA_ERR_ARG;
+  Engine &e = c->e;
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  if (stage < 0 || stage >= e.S || !(dt > 0)) return fail(e, SACRA_ERR_ARG, "bad stage or dt");
+  enqueue_stage(e, stage, dt);
+  return cuda_check(e, "rk_stage");
+}
+
+sacra_status sacra_step(sacra_ctx *c, double dt, int n_steps, int use_graph) {
+  if (!c) return SACRA_ERR_ARG;
+  return step(c->e, dt, n_steps, use_graph);
+}
+
+sacra_status sacra_read_state(sacra_ctx *c, int level, int which, int field, double *host, size_t n) {
+  if (!c) return SACRA_ERR_ARG;
+  return read_state(c->e, 0, level, which, field, host, n);
+}
+
+sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out) {
+  if (!c || !out) return SACRA_ERR_ARG;
+  return constraints(c->e, 0, out);
+}
+
+sacra_status sacra_sync(sacra_ctx *c) { return c ? sync(c->e) : SACRA_ERR_ARG; }
+
+long long sacra_launch_count(const sacra_ctx *c) { return c ? c->e.launches : -1; }
+
+sacra_status sacra_profile(sacra_ctx *c, int enable) { return c ? set_profile(c->e, enable) : SACRA_ERR_ARG; }
+
+sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_len, double *total_ms,
+                               long long *launches, long long *cells) {
+  if (!c) return SACRA_ERR_ARG;
+  return profile_get(c->e, idx, name, name_len, total_ms, launches, cells);
+}
+
+sacra_status sacra_tune(sacra_ctx *c, int reps) { return c ? tune(c->e, reps) : SACRA_ERR_ARG; }
+
+sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *tile_y, int *blocks_per_sm) {
+  return c ? get_tuning(c->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
 }
 
 void sacra_destroy(sacra_ctx *c) {
   if (!c) return;
-  cudaStreamSynchronize(c->stream);
-  for (int i = 0; i < 2; ++i)
-    if (c->gexec[i]) cudaGraphExecDestroy(c->gexec[i]);
-  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
-  if (c->own_arena) cudaFree(c->arena);
+  engine_free(c->e);
   delete c;
 }
 
-const char *sacra_last_error(const sacra_ctx *c) { return c ? c->err.c_str() : "null context"; }
+const char *sacra_last_error(const sacra_ctx *c) { return c ? c->e.err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------- a batch of stars
+
+sacra_status sacra_batch_arena_bytes(const sacra_params *per_star, int n_stars, size_t *bytes) {
+  if (!bytes || !params_ok(per_star, n_stars)) return SACRA_ERR_ARG;
+  *bytes = engine_bytes(std::vector<sacra_params>(per_star, per_star + n_stars));
+  return SACRA_OK;
+}
+
+sacra_status sacra_init_batch(const sacra_params *per_star, int n_stars, void *cuda_stream, void *arena,
+                              size_t arena_bytes, sacra_batch **out) {
+  if (!out) return SACRA_ERR_ARG;
+  *out = nullptr;
+  if (!params_ok(per_star, n_stars)) return SACRA_ERR_ARG;
+  sacra_batch *b = new sacra_batch();
+  const sacra_status s =
+      engine_init(b->e, std::vector<sacra_params>(per_star, per_star + n_stars), cuda_stream, arena, arena_bytes);
+  if (s != SACRA_OK) {
+    engine_free(b->e);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return SACRA_OK;
+}
+
+sacra_status sacra_batch_set_initial_data(sacra_batch *b, int star, int level, int kind, const double *host,
+                                          int n_fields) {
+  return b ? set_initial_data(b->e, star, level, kind, host, n_fields) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_step(sacra_batch *b, double dt, int n_steps, int use_graph) {
+  return b ? step(b->e, dt, n_steps, use_graph) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_read_state(sacra_batch *b, int star, int level, int which, int field, double *host,
+                                    size_t n) {
+  return b ? read_state(b->e, star, level, which, field, host, n) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_constraints(sacra_batch *b, int star, sacra_diag *out) {
+  return b ? constraints(b->e, star, out) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_tune(sacra_batch *b, int reps) { return b ? tune(b->e, reps) : SACRA_ERR_ARG; }
+
+sacra_status sacra_batch_get_tuning(const sacra_batch *b, int kind, int *tile_x, int *tile_y, int *blocks_per_sm) {
+  return b ? get_tuning(b->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_sync(sacra_batch *b) { return b ? sync(b->e) : SACRA_ERR_ARG; }
+
+long long sacra_batch_launch_count(const sacra_batch *b) { return b ? b->e.launches : -1; }
+
+sacra_status sacra_batch_profile(sacra_batch *b, int enable) { return b ? set_profile(b->e, enable) : SACRA_ERR_ARG; }
+
+sacra_status sacra_batch_profile_get(sacra_batch *b, int idx, char *name, size_t name_len, double *total_ms,
+                                     long long *launches, long long *cells) {
+  return b ? profile_get(b->e, idx, name, name_len, total_ms, launches, cells) : SACRA_ERR_ARG;
+}
+
+void sacra_batch_destroy(sacra_batch *b) {
+  if (!b) return;
+  engine_free(b->e);
+  delete b;
+}
+
+const char *sacra_batch_last_error(const sacra_batch *b) { return b ? b->e.err.c_str() : "null batch"; }
 
 }  // extern "C"

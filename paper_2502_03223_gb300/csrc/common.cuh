@@ -36,7 +36,7 @@ struct DevParams {
   double kappa, eta_B, eps_ko, r_z4;
   double c2p_kmax;       // 2 v_max / (1 + v_max^2), v_max = sqrt(1 - 1 / w_max^2)
   // FP32 copies for the mixed-precision kernels (no conversions on the device)
-  float fK, fGamma, fGm1, fGamma_th, fGth1, fkappa, feta_B, firz2;
+  float fK, fGamma, fGm1, fGamma_th, fGth1, fkappa, feta_B, firz2, fko;
 };
 
 // a parameter in arithmetic T: the FP64 value, or its FP32 copy
@@ -58,15 +58,21 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->fGamma_th = (float)p->Gamma_th; d->fGth1 = (float)(p->Gamma_th - 1.0);
   d->fkappa = (float)p->kappa; d->feta_B = (float)p->eta_B;
   d->firz2 = (float)(1.0 / (p->r_z4 * p->r_z4));
+  d->fko = (float)(-p->eps_ko / 256.0);
   const double vmax = sqrt(1.0 - 1.0 / (p->w_max * p->w_max));
   d->c2p_kmax = 2.0 * vmax / (1.0 + vmax * vmax);
 }
 
 // One refinement level as seen by a kernel: planes of P = px * pz doubles.
+struct LevF {                   // FP32 copies of the spacing constants
+  float dx, dz, idx, idz, i60x, i60z, i180x, i180z, ixz;
+};
+
 struct Lev {
   int nx, nz, px, pz, rw;
   double dx, dz;
-  double i60x, i60z;            // 1 / (60 dx), 1 / (60 dz)
+  double i60x, i60z, i180x;     // 1 / (60 dx), 1 / (60 dz), 1 / (180 dx^2)
+  LevF f;
   size_t P;
   double *un, *us, *ka, *rhs;   // NST planes each
   double *prim;                 // NPRIM planes
@@ -78,6 +84,16 @@ struct Lev {
 };
 
 __host__ __device__ inline int cid(const Lev &L, int j, int k) { return (k + GH - 1) * L.px + (j + GH - 1); }
+
+// spacing and the constants derived from it (host)
+inline void set_spacing(Lev &L, double dx, double dz) {
+  L.dx = dx; L.dz = dz;
+  L.i60x = 1.0 / (60.0 * dx); L.i60z = 1.0 / (60.0 * dz); L.i180x = 1.0 / (180.0 * dx * dx);
+  L.f.dx = (float)dx; L.f.dz = (float)dz; L.f.idx = (float)(1.0 / dx); L.f.idz = (float)(1.0 / dz);
+  L.f.i60x = (float)L.i60x; L.f.i60z = (float)L.i60z;
+  L.f.i180x = (float)(1.0 / (180.0 * dx * dx)); L.f.i180z = (float)(1.0 / (180.0 * dz * dz));
+  L.f.ixz = (float)(1.0 / (3600.0 * dx * dz));
+}
 
 // ------------------------------------------------------------------ FP64 <-> FP32 without the FP64 pipe
 //

@@ -229,10 +229,8 @@ __device__ inline void enforce_algebraic(double m[NST]) {
 // RK stage combination on [1, jmax] x [1, kmax], then algebraic constraints
 // and primitive recovery.  Ust = stage state read (Un at stage 0, Us after);
 // the result is written to Us.
-__global__ void __launch_bounds__(128) k_rk_update(Lev L, DevParams p, const double *__restrict__ Ust, int stage, double dt,
-                                                   int jmax, int kmax) {
-  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+__device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p, const double *__restrict__ Ust, int stage, double dt,
+                                                   int jmax, int kmax, int j, int k) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -267,6 +265,22 @@ __global__ void __launch_bounds__(128) k_rk_update(Lev L, DevParams p, const dou
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + id] = pr[f];
   L.status[id] = st;
+}
+
+__global__ void __launch_bounds__(128) k_rk_update(Lev L, DevParams p, const double *__restrict__ Ust, int stage, double dt,
+                                                   int jmax, int kmax) {
+  rk_update_cell(L, p, Ust, stage, dt, jmax, kmax, 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x), 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y));
+}
+
+__global__ void __launch_bounds__(128) kb_rk_update(Batch b, DevParams p, int stage, double dt) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    rk_update_cell(q.L, q.P, q.U, stage, dt, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+  });
+}
+
+void launch_b_rk_update(const Batch &b, const DevParams &p, int stage, double dt, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  kb_rk_update<<<b.grid, b.block, 0, s>>>(b, p, stage, dt);
 }
 
 // Restriction of child level C onto parent cells [1, N/2]^2 (Sec. II.D):

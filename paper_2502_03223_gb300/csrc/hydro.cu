@@ -174,10 +174,8 @@ __device__ inline void flux_face(const Lev &L, const DevParams &p, const double 
 // fluxes (cylindrical: area x_{j+1/2} dz, and one more factor x for S_phi)
 // and accumulates the flux registers of the refinement boundaries.
 template <typename T>
-__global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
-                                                 double wb, int has_child, int has_parent) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
+__device__ __forceinline__ void flux_x_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
+                                                 double wb, int has_child, int has_parent, int j, int k) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
@@ -201,10 +199,14 @@ __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
+__global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y;
+  flux_x_cell<T>(L, p, U, jmax, kmax, wb, has_child, has_parent, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void flux_z_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
+                                                 double wb, int has_child, int has_parent, int j, int k) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
@@ -229,6 +231,12 @@ __global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double
   if (fb) atomicAdd(L.nfb, 1ull);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
+                                                 double wb, int has_child, int has_parent) {
+  flux_z_cell<T>(L, p, U, jmax, kmax, wb, has_child, has_parent, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y);
+}
+
 // 6th-order central first derivative: exact differences (FP64, or FP32 from
 // integer splits), weighted sum in T
 template <typename T>
@@ -248,9 +256,7 @@ __device__ __forceinline__ T cd1(const double *u, int s, T idx) {
 //        (+ alpha W^-3 (S_y vbar^y + P)/x for k = x, cylindrical),
 //   s_E  = W^-3 (alpha K^ij S_ij - rho h w^2 v^i d_i alpha), s_D = s_Sphi = 0.
 template <typename T>
-__global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
+__device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax, int j, int k) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -342,6 +348,11 @@ __global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const dou
   L.rhs[(size_t)fQE * P + id] = to_f64<T>(sE) - div[4];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_hydro_rhs(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax) {
+  hydro_rhs_cell<T>(L, p, U, jmax, kmax, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
 // eps from the EOS and conserved variables on every padded cell (initial data)
 __global__ void k_prim2cons_all(Lev L, DevParams p, double *__restrict__ U) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -379,6 +390,50 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
 #pragma unroll
     for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + id] = q[v];
   L.status[id] = st;
+}
+
+// ---------------------------------------------------------------- batched persistent kernels
+//
+// One launch covers the tiles of every level of every star in a batch: each
+// block walks the tile list with a grid stride; a tile is one block's worth of
+// cells of one level (origin j0, k0; extent = the block shape).
+template <typename T>
+__global__ void __launch_bounds__(256) kb_flux_x(Batch b, DevParams p) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    flux_x_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_flux_z(Batch b, DevParams p) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    flux_z_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_hydro_rhs(Batch b, DevParams p) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    hydro_rhs_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+  });
+}
+
+void launch_b_flux_x(const Batch &b, const DevParams &p, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_FLUX) kb_flux_x<float><<<b.grid, b.block, 0, s>>>(b, p);
+  else kb_flux_x<double><<<b.grid, b.block, 0, s>>>(b, p);
+}
+
+void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_FLUX) kb_flux_z<float><<<b.grid, b.block, 0, s>>>(b, p);
+  else kb_flux_z<double><<<b.grid, b.block, 0, s>>>(b, p);
+}
+
+void launch_b_hydro_div(const Batch &b, const DevParams &p, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_SOURCES) kb_hydro_rhs<float><<<b.grid, b.block, 0, s>>>(b, p);
+  else kb_hydro_rhs<double><<<b.grid, b.block, 0, s>>>(b, p);
 }
 
 // ---------------------------------------------------------------- host launchers

@@ -14,6 +14,57 @@ struct GridWeights {
 };
 void set_grid_weights(const GridWeights &w);
 
+// ---- batched launches: one persistent launch per kernel kind and stage over
+// the tiles of all levels of all stars of a batch (see capi.cu)
+struct BL {                 // one level of one star as a stage sees it
+  Lev L;
+  DevParams P;              // the star's parameters (EOS, gauge, atmosphere, ...)
+  const double *U;          // stage state read (Un at stage 0, Us after)
+  void *DS;                 // this level's derivative scratch (FP64 or FP32 planes)
+  int jmax, kmax;           // update region [1, jmax] x [1, kmax]
+  int has_child, has_parent;
+  double wb;                // RK weight of this stage's fluxes in the flux registers
+};
+struct Tile {               // one block's worth of cells of one level
+  int bl, j0, k0, pad;
+};
+struct Batch {
+  const BL *bl;             // device array
+  const Tile *tiles;        // device array
+  int ntiles;
+  int grid;                 // persistent blocks
+  dim3 block;               // tile shape = block shape
+};
+// Grid-stride walk over the tiles of a batched launch: the block copies the
+// tile's level view into shared memory (so that every thread reads the level
+// and its parameters from there) and calls f(view, tile) with all threads.
+template <class F>
+__device__ __forceinline__ void for_tiles(const Batch &b, F &&f) {
+  __shared__ BL sb;
+  const int nth = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+    const Tile tl = b.tiles[t];
+    const int *src = reinterpret_cast<const int *>(b.bl + tl.bl);
+    int *dst = reinterpret_cast<int *>(&sb);
+    for (int i = tid; i < (int)(sizeof(BL) / sizeof(int)); i += nth) dst[i] = src[i];
+    __syncthreads();
+    f(sb, tl);
+    __syncthreads();
+  }
+}
+static_assert(sizeof(BL) % sizeof(int) == 0, "BL is copied as ints");
+
+enum BKind { B_FLUX_X = 0, B_FLUX_Z, B_HYDRO, B_CARTOON, B_DERIVS, B_POINT, B_RK, B_NKIND };
+void launch_b_flux_x(const Batch &b, const DevParams &p, cudaStream_t s);
+void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s);
+void launch_b_hydro_div(const Batch &b, const DevParams &p, cudaStream_t s);
+void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, cudaStream_t s);
+void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s);
+void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s);
+void launch_b_rk_update(const Batch &b, const DevParams &p, int stage, double dt, cudaStream_t s);
+// the FP32 derivative pass has a fixed tile shape
+dim3 z4c_derivs_f32_block();
+
 void launch_flux_x(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
                    int has_parent, cudaStream_t s);
 void launch_flux_z(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,

@@ -63,10 +63,7 @@ extern "C" sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level
   Lev L;
   memset(&L, 0, sizeof(L));
   L.nx = p->nx; L.nz = p->nz; L.px = (int)px; L.pz = (int)pz; L.rw = 0;
-  L.dx = p->dx0 / (double)(1 << level);
-  L.dz = p->dz0 / (double)(1 << level);
-  L.i60x = 1.0 / (60.0 * L.dx);
-  L.i60z = 1.0 / (60.0 * L.dz);
+  set_spacing(L, p->dx0 / (double)(1 << level), p->dz0 / (double)(1 << level));
   L.P = P;
   L.un = const_cast<double *>(state);
   L.prim = const_cast<double *>(prims);

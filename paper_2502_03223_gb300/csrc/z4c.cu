@@ -72,9 +72,9 @@ __device__ __forceinline__ void rotate20(const double v[20], double c, double s,
 // beta, Gt and B vectors): each group's three planes come from one pass over
 // its 9-point stencils, and only the group's components are live at a time.
 struct CartoonOut {
-  Lev L;
+  double *dy, *dyy;
+  size_t P;
   int o;
-  bool flip;
   double i1, i2;
 };
 
@@ -91,22 +91,19 @@ __device__ __forceinline__ void cartoon_acc(int a, bool flip, double w1, double 
 
 __device__ __forceinline__ void cartoon_store(const CartoonOut &c, int a, double d1, double d2) {
   const int f = cartoon_field(a);
-  const size_t P = c.L.P;
-  if (f != fHZZ && f != fBZ && a >= 2) c.L.dy[(size_t)f * P + c.o] = d1 * c.i1;
-  if (a <= 7 || (a >= 13 && a <= 15)) c.L.dyy[(size_t)f * P + c.o] = d2 * c.i2;
+  if (f != fHZZ && f != fBZ && a >= 2) c.dy[(size_t)f * c.P + c.o] = d1 * c.i1;
+  if (a <= 7 || (a >= 13 && a <= 15)) c.dyy[(size_t)f * c.P + c.o] = d2 * c.i2;
 }
 
-__global__ void __launch_bounds__(128) k_cartoon_f64(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
-                                                     int tab_stride) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x - 2;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y - 2;
+__device__ __forceinline__ void cartoon_f64_cell(const Lev &L, const double *__restrict__ U, const double *__restrict__ tab,
+                                                     int tab_stride, int j, int k) {
   if (j > L.nx + 4 || k > L.nz + 7) return;
   const bool flip = j <= 0;
   const int jj = flip ? 1 - j : j;
   const size_t P = L.P;
   const int c0 = cid(L, jj, k);
   const double *t0 = tab + (size_t)(jj * 3) * tab_stride;   // per m: 9 weights, cos, sin
-  CartoonOut co{L, cid(L, j, k), flip, 1.0 / (60.0 * L.dx), 1.0 / (180.0 * L.dx * L.dx)};
+  CartoonOut co{L.dy, L.dyy, P, cid(L, j, k), L.i60x, L.i180x};
   const double c1w[3] = {45.0, -9.0, 1.0}, c2w[3] = {270.0, -27.0, 2.0};
   // the three planes of slot a: v[m] = base + sum_n t_m[n] (u[n] - base)
   auto planes = [&](int a, double &base, double v[3]) {
@@ -181,6 +178,11 @@ __global__ void __launch_bounds__(128) k_cartoon_f64(Lev L, const double *__rest
   }
 }
 
+__global__ void __launch_bounds__(128) k_cartoon_f64(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
+                                                     int tab_stride) {
+  cartoon_f64_cell(L, U, tab, tab_stride, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
+}
+
 // Mixed precision: the same planes in FP32, formed as differences from the
 // centre value so that their small variations keep FP32 relative precision:
 // the interpolation sums FP64 differences u_n - u_j with FP32 weights, and the
@@ -203,10 +205,8 @@ __device__ __forceinline__ void deltas_ten(float c1, float sn, const float u[5],
   d[4] = sn * u[2] + c1 * u[4] + (sn * s[2] + c * s[4]);
 }
 
-__global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
-                                                     int tab_stride) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x - 2;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y - 2;
+__device__ __forceinline__ void cartoon_f32_cell(const Lev &L, const double *__restrict__ U, const double *__restrict__ tab,
+                                                     int tab_stride, int j, int k) {
   if (j > L.nx + 4 || k > L.nz + 7) return;
   const bool flip = j <= 0;
   const int jj = flip ? 1 - j : j;
@@ -289,6 +289,11 @@ __global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__rest
   for (int b = 0; b < 11; ++b) dyyf[(size_t)kCartoonFields[sec[b]] * P + o] = d2[sec[b]] * i2;
 }
 
+__global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
+                                                     int tab_stride) {
+  cartoon_f32_cell(L, U, tab, tab_stride, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
+}
+
 // ---------------------------------------------------------------- derivative pass
 
 // derivative scratch layout (planes): D1 first derivatives of the 16 fields
@@ -332,10 +337,8 @@ __device__ __forceinline__ T fdko(const double *u, int s) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const double *__restrict__ U,
-                                                     double *__restrict__ DS, int jmax, int kmax, int cyl) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
+__device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
+                                                     double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -415,6 +418,12 @@ __global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const do
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const double *__restrict__ U,
+                                                     double *__restrict__ DS, int jmax, int kmax, int cyl) {
+  z4c_derivs_cell<T>(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
 // Mixed-precision derivative pass.  The block stages each field's tile with
 // a 4-cell halo in shared memory as FP32 (hi, lo) splits (integer bit
 // operations, no FP64 instruction), so every stencil difference is one
@@ -448,11 +457,11 @@ __host__ __device__ constexpr bool y_zero_c(int f) {
   return f == fW || f == fKH || f == fTH || f == fAL || f == fGZ || f == fBZ || f == fBBZ || f == fHZZ || f == fAZZ;
 }
 
-__global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,
-                                                              float *__restrict__ DS, int jmax, int kmax, int cyl) {
-  __shared__ float2 tile[DHZ][DHX];
+// one block = one tile of DTX x DTZ cells with origin (j0, k0)
+__device__ __forceinline__ void z4c_derivs_f32_tile(const Lev &L, const DevParams &p, const double *__restrict__ U,
+                                                    float *__restrict__ DS, int jmax, int kmax, int cyl, int j0, int k0,
+                                                    float2 (*tile)[DHX]) {
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * DTX + tx;
-  const int j0 = blockIdx.x * DTX + 1, k0 = blockIdx.y * DTZ + 1;
   const int j = j0 + tx, k = k0 + tz;
   const bool live = j <= jmax && k <= kmax;
   const size_t P = L.P;
@@ -460,11 +469,9 @@ __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParam
   const int jlim = L.nx + GH, klim = L.nz + GH;
   const float *dyf = reinterpret_cast<const float *>(L.dy);
   const float *dyyf = reinterpret_cast<const float *>(L.dyy);
-  const float i60x = (float)(1.0 / (60.0 * L.dx)), i60z = (float)(1.0 / (60.0 * L.dz));
-  const float i180x = (float)(1.0 / (180.0 * L.dx * L.dx)), i180z = (float)(1.0 / (180.0 * L.dz * L.dz));
-  const float ixz = (float)(1.0 / (3600.0 * L.dx * L.dz));
-  const float ko = (float)(-p.eps_ko / 256.0);
-  const float ikx = (float)(1.0 / L.dx), ikz = (float)(1.0 / L.dz);
+  const float i60x = L.f.i60x, i60z = L.f.i60z, i180x = L.f.i180x, i180z = L.f.i180z, ixz = L.f.ixz;
+  const float ko = p.fko;
+  const float ikx = L.f.idx, ikz = L.f.idz;
   const bool edge = cyl && j > L.nx;
   const float bx = f32_of(U[(size_t)fBX * P + id]), by = f32_of(U[(size_t)fBY * P + id]),
               bz = f32_of(U[(size_t)fBZ * P + id]);
@@ -553,7 +560,7 @@ __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParam
   });
   if (live && edge) {
     // Eq. cartoon_bnd for cells beyond the level edge: d_xy from d_x and values
-    const float x = (float)((j - 0.5) * L.dx);
+    const float x = ((float)j - 0.5f) * L.f.dx;
     const float ix = 1.0f / x, ix2 = ix * ix;
     auto put = [&](int a, float v) { DS[(size_t)(DS_D2 + 6 * a + 1) * P + id] = v; };
     put(8, ev[6] * ix2 - ed[6] * ix);
@@ -565,6 +572,20 @@ __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParam
     put(4, -2.0f * txy);
     put(2, (ev[3] - ev[0]) * ix2 + (ed[0] - ed[3]) * ix);
   }
+}
+
+__global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,
+                                                              float *__restrict__ DS, int jmax, int kmax, int cyl) {
+  __shared__ float2 tile[DHZ][DHX];
+  z4c_derivs_f32_tile(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * DTX + 1, blockIdx.y * DTZ + 1, tile);
+}
+
+__global__ void __launch_bounds__(DTX * DTZ, 3) kb_z4c_derivs_f32(Batch b, DevParams p) {
+  __shared__ float2 tile[DHZ][DHX];
+  const int cyl = p.geometry == SACRA_CYLINDRICAL;
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    z4c_derivs_f32_tile(q.L, q.P, q.U, reinterpret_cast<float *>(q.DS), q.jmax, q.kmax, cyl, tl.j0, tl.k0, tile);
+  });
 }
 
 // ---------------------------------------------------------------- pointwise pass
@@ -615,10 +636,8 @@ __device__ inline void load_z4c_in(const Lev &L, const double *__restrict__ U, c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const double *__restrict__ U,
-                                                    const T *__restrict__ DS, int jmax, int kmax) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y + 1;
+__device__ __forceinline__ void z4c_point_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
+                                                    const T *__restrict__ DS, int jmax, int kmax, int j, int k) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -648,6 +667,12 @@ __global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const dou
   for (int f = 0; f < NMET; ++f) L.rhs[(size_t)f * P + id] = to_f64<T>(src[f] + DS[(size_t)(DS_AK + f) * P + id]);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(128) k_z4c_point(Lev L, DevParams p, const double *__restrict__ U,
+                                                    const T *__restrict__ DS, int jmax, int kmax) {
+  z4c_point_cell<T>(L, p, U, DS, jmax, kmax, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
+}
+
 // ---------------------------------------------------------------- host launchers
 
 void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const double *DS, int jmax, int kmax,
@@ -672,6 +697,56 @@ void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double
     k_z4c_derivs<double><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax, p.geometry == SACRA_CYLINDRICAL);
   }
 }
+
+// ---------------------------------------------------------------- batched persistent kernels
+
+__global__ void __launch_bounds__(128) kb_cartoon_f64(Batch b, const double *__restrict__ tab, int tab_stride) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    cartoon_f64_cell(q.L, q.U, tab, tab_stride, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+  });
+}
+
+__global__ void __launch_bounds__(128) kb_cartoon_f32(Batch b, const double *__restrict__ tab, int tab_stride) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    cartoon_f32_cell(q.L, q.U, tab, tab_stride, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+  });
+}
+
+__global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
+  const int cyl = p.geometry == SACRA_CYLINDRICAL;
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    z4c_derivs_cell<double>(q.L, q.P, q.U, reinterpret_cast<double *>(q.DS), q.jmax, q.kmax, cyl, tl.j0 + threadIdx.x,
+                            tl.k0 + threadIdx.y);
+  });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) kb_z4c_point(Batch b, DevParams p) {
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    z4c_point_cell<T>(q.L, q.P, q.U, reinterpret_cast<const T *>(q.DS), q.jmax, q.kmax, tl.j0 + threadIdx.x,
+                      tl.k0 + threadIdx.y);
+  });
+}
+
+void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_Z4C) kb_cartoon_f32<<<b.grid, b.block, 0, s>>>(b, tab, tab_stride);
+  else kb_cartoon_f64<<<b.grid, b.block, 0, s>>>(b, tab, tab_stride);
+}
+
+void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_Z4C) kb_z4c_derivs_f32<<<b.grid, dim3(DTX, DTZ), 0, s>>>(b, p);
+  else kb_z4c_derivs<<<b.grid, b.block, 0, s>>>(b, p);
+}
+
+void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s) {
+  if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_Z4C) kb_z4c_point<float><<<b.grid, b.block, 0, s>>>(b, p);
+  else kb_z4c_point<double><<<b.grid, b.block, 0, s>>>(b, p);
+}
+
+dim3 z4c_derivs_f32_block() { return dim3(DTX, DTZ); }
 
 int z4c_scratch_planes() { return DS_N; }
 

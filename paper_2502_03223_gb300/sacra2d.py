@@ -26,8 +26,14 @@ STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
 
 EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
            "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync",
-           "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_destroy",
-           "sacra_last_error"]
+           "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_tune",
+           "sacra_get_tuning", "sacra_destroy", "sacra_last_error",
+           "sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
+           "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
+           "sacra_batch_sync", "sacra_batch_launch_count", "sacra_batch_profile", "sacra_batch_profile_get",
+           "sacra_batch_destroy", "sacra_batch_last_error"]
+EXPORTS = sorted(EXPORTS)
+KIND_NAMES = ["flux_x", "flux_z", "hydro_rhs", "cartoon", "z4c_derivs", "z4c_point", "rk_update"]
 
 
 class SacraParams(C.Structure):
@@ -77,9 +83,37 @@ def load(path: str = LIB_PATH):
     L.sacra_profile_get.restype = C.c_int
     L.sacra_hydro_rhs_noalloc.argtypes = [C.POINTER(SacraParams), C.c_int, vp, vp, vp, vp]
     L.sacra_hydro_rhs_noalloc.restype = C.c_int
+    ip = C.POINTER(C.c_int)
+    L.sacra_tune.argtypes = [vp, C.c_int]
+    L.sacra_tune.restype = C.c_int
+    L.sacra_get_tuning.argtypes = [vp, C.c_int, ip, ip, ip]
+    L.sacra_get_tuning.restype = C.c_int
     L.sacra_destroy.argtypes = [vp]
     L.sacra_last_error.argtypes = [vp]
     L.sacra_last_error.restype = C.c_char_p
+    # batches
+    PP = C.POINTER(SacraParams)
+    L.sacra_batch_arena_bytes.argtypes = [PP, C.c_int, C.POINTER(C.c_size_t)]
+    L.sacra_init_batch.argtypes = [PP, C.c_int, vp, vp, C.c_size_t, C.POINTER(vp)]
+    L.sacra_batch_set_initial_data.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, C.c_int]
+    L.sacra_batch_step.argtypes = [vp, C.c_double, C.c_int, C.c_int]
+    L.sacra_batch_read_state.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, C.c_size_t]
+    L.sacra_batch_constraints.argtypes = [vp, C.c_int, C.POINTER(SacraDiag)]
+    L.sacra_batch_tune.argtypes = [vp, C.c_int]
+    L.sacra_batch_get_tuning.argtypes = [vp, C.c_int, ip, ip, ip]
+    L.sacra_batch_sync.argtypes = [vp]
+    L.sacra_batch_launch_count.argtypes = [vp]
+    L.sacra_batch_launch_count.restype = C.c_longlong
+    L.sacra_batch_profile.argtypes = [vp, C.c_int]
+    L.sacra_batch_profile_get.argtypes = [vp, C.c_int, C.c_char_p, C.c_size_t, dp, C.POINTER(C.c_longlong),
+                                          C.POINTER(C.c_longlong)]
+    L.sacra_batch_destroy.argtypes = [vp]
+    L.sacra_batch_last_error.argtypes = [vp]
+    L.sacra_batch_last_error.restype = C.c_char_p
+    for name in ("sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
+                 "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
+                 "sacra_batch_sync", "sacra_batch_profile", "sacra_batch_profile_get"):
+        getattr(L, name).restype = C.c_int
     for name in ("sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
                  "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync"):
         getattr(L, name).restype = C.c_int
@@ -214,3 +248,117 @@ class Sacra:
     @property
     def n_stages(self):
         return 4 if self.cfg.rk == 0 else 3
+
+    def tune(self, reps=3):
+        """Run the autotuner of the batched launches; returns {kind: (tile_x, tile_y, blocks_per_sm)}."""
+        self._chk(self._L.sacra_tune(self._c, reps), "tune")
+        return self.tuning()
+
+    def tuning(self):
+        out = {}
+        for k, name in enumerate(KIND_NAMES):
+            x, y, m = C.c_int(0), C.c_int(0), C.c_int(0)
+            self._chk(self._L.sacra_get_tuning(self._c, k, C.byref(x), C.byref(y), C.byref(m)), "get_tuning")
+            out[name] = (x.value, y.value, m.value)
+        return out
+
+
+class SacraBatch:
+    """Many independent stars advanced together (one persistent launch per
+    kernel kind and RK stage over all of them).  cfgs: one RunConfig per star;
+    they may differ in n_levels, nx = nz and dx0 only."""
+
+    def __init__(self, cfgs, stream=None):
+        import torch
+        self.cfgs = list(cfgs)
+        self._L = load()
+        n = len(self.cfgs)
+        self._p = (SacraParams * n)(*[make_params(c) for c in self.cfgs])
+        nbytes = C.c_size_t(0)
+        if self._L.sacra_batch_arena_bytes(self._p, n, C.byref(nbytes)) != SACRA_OK:
+            raise SacraError("configuration rejected by sacra_batch_arena_bytes")
+        self.arena_bytes = nbytes.value
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._arena = torch.empty(self.arena_bytes, dtype=torch.uint8, device="cuda")
+        b = C.c_void_p()
+        rc = self._L.sacra_init_batch(self._p, n, C.c_void_p(self.stream.cuda_stream),
+                                      C.c_void_p(self._arena.data_ptr()), nbytes, C.byref(b))
+        if rc != SACRA_OK:
+            raise SacraError("sacra_init_batch failed with status %d" % rc)
+        self._b = b
+
+    def _chk(self, rc, what):
+        if rc != SACRA_OK:
+            raise SacraError("%s failed (%d): %s" % (what, rc, self._L.sacra_batch_last_error(self._b).decode()))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._L.sacra_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_initial_data(self, star, level, kind, planes):
+        a = np.ascontiguousarray(planes, dtype=np.float64)
+        c = self.cfgs[star]
+        assert a.size == 30 * (c.nx + 16) * (c.nz + 16)
+        self._chk(self._L.sacra_batch_set_initial_data(self._b, star, level, kind,
+                                                       a.ctypes.data_as(C.POINTER(C.c_double)), 30),
+                  "batch_set_initial_data")
+
+    def step(self, dt, n=1, use_graph=False):
+        self._chk(self._L.sacra_batch_step(self._b, dt, n, 1 if use_graph else 0), "batch_step")
+
+    def sync(self):
+        self._chk(self._L.sacra_batch_sync(self._b), "batch_sync")
+
+    def read(self, star, level, which, field):
+        c = self.cfgs[star]
+        px, pz = c.nx + 16, c.nz + 16
+        out = np.zeros(px * pz)
+        self._chk(self._L.sacra_batch_read_state(self._b, star, level, which, field,
+                                                 out.ctypes.data_as(C.POINTER(C.c_double)), px * pz),
+                  "batch_read_state")
+        return out.reshape(pz, px)
+
+    def constraints(self, star):
+        d = SacraDiag()
+        self._chk(self._L.sacra_batch_constraints(self._b, star, C.byref(d)), "batch_constraints")
+        return np.array([d.H_L2, d.M_L2[0], d.M_L2[1], d.M_L2[2], d.Mb, d.J, d.rho_max, d.n_c2p_fail, d.n_fallback])
+
+    def tune(self, reps=3):
+        self._chk(self._L.sacra_batch_tune(self._b, reps), "batch_tune")
+        return self.tuning()
+
+    def tuning(self):
+        out = {}
+        for k, name in enumerate(KIND_NAMES):
+            x, y, m = C.c_int(0), C.c_int(0), C.c_int(0)
+            self._chk(self._L.sacra_batch_get_tuning(self._b, k, C.byref(x), C.byref(y), C.byref(m)), "get_tuning")
+            out[name] = (x.value, y.value, m.value)
+        return out
+
+    def profile(self, enable=True):
+        self._chk(self._L.sacra_batch_profile(self._b, 1 if enable else 0), "batch_profile")
+
+    def profile_report(self):
+        out = {}
+        idx = 0
+        buf = C.create_string_buffer(64)
+        while True:
+            ms = C.c_double(0.0); n = C.c_longlong(0); cells = C.c_longlong(0)
+            rc = self._L.sacra_batch_profile_get(self._b, idx, buf, 64, C.byref(ms), C.byref(n), C.byref(cells))
+            if rc != SACRA_OK:
+                break
+            if n.value:
+                out[buf.value.decode()] = (ms.value, n.value, cells.value)
+            idx += 1
+        return out
+
+    @property
+    def launch_count(self):
+        return self._L.sacra_batch_launch_count(self._b)

@@ -259,6 +259,24 @@ def config_migration(N=512, n_levels=5, dx_fine=0.1):
     return tov_config("migration_5x512", rho_c=7.993e-3, n_levels=n_levels, N=N, dx_fine=dx_fine, rk=0)
 
 
+def config_batch_sweep(n_stars=64, seed=20250203, precision=7, rk=1, dx_fine=0.25,
+                       sizes=(128, 256, 384, 512), levels=(2, 3, 4, 5), rho_c=(1e-3, 8e-3)):
+    """Batched sweep of independent TOV / migration stars (K=100, Gamma=2):
+    central densities uniform in rho_c, grids drawn from `sizes` with a level
+    count drawn from `levels`, finest dx = dx_fine, all with one dt.  Returns
+    [(RunConfig, TOVSolution)], seeded."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_stars):
+        rc = float(rng.uniform(*rho_c))
+        N = int(rng.choice(sizes))
+        L = int(rng.choice(levels))
+        cfg, tov = tov_config("sweep_%02d" % i, rho_c=rc, n_levels=L, N=N, dx_fine=dx_fine, rk=rk)
+        cfg.precision = precision
+        out.append((cfg, tov))
+    return out
+
+
 # ------------------------------------------------------------------ random inputs
 
 def random_metric_perturbation(cfg: RunConfig, level: int, rng: np.random.Generator, amp=1e-2, nbump=3):
