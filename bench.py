@@ -317,6 +317,55 @@ def errors_vs_oracle(cfg, datas, sims, steps=1):
     return out
 
 
+def run_batch(args, dist, ws):
+    """Time whole steps of the batched sweep: n stars of grids {128..512}^2
+    with 2-5 levels each (seeded), mixed precision, autotuned, graph-replayed.
+    No diagnostics in these steps (the sweep reports throughput only)."""
+    import torch
+    from paper_2502_03223_gb300 import sacra2d as S
+    from paper_2502_03223_gb300 import workloads as W
+    stars = W.config_batch_sweep(n_stars=args.batch_stars)
+    cfgs = [c for c, _ in stars]
+    dt = min(c.dt for c in cfgs)
+    t0 = time.perf_counter()
+    b = S.SacraBatch(cfgs)
+    for i, (c, tov) in enumerate(stars):
+        for l in range(c.n_levels):
+            b.set_initial_data(i, l, S.PRIM_METRIC, W.tov_level_data(c, tov, l, p_deplete=0.99 if tov.rho_c > 3.2e-3 else 1.0))
+    t_init = time.perf_counter() - t0
+    b.step(dt, 1, use_graph=False)
+    b.sync()
+    tuning = b.tune(reps=1) if not args.no_tune else None
+    for _ in range(max(args.warmup - 1, 2)):
+        b.step(dt, 1, use_graph=True)
+    b.sync()
+    steps = max(3, min(args.steps, args.batch_steps))
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    n0 = b.launch_count
+    barrier(dist)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(b.stream)
+    b.step(dt, steps, use_graph=True)
+    ev1.record(b.stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    barrier(dist)
+    clocks = sampler.stop()
+    ms = max_over_ranks(dist, ev0.elapsed_time(ev1))
+    cells = sum(c.interior_cells * c.n_stages for c in cfgs)
+    launches = b.launch_count - n0
+    diag = b.constraints(0)
+    b.close()
+    return {"workload": "batch_sweep_%d" % len(cfgs), "value": ws * cells * steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps, "n_stars": len(cfgs),
+            "cell_updates_per_step": cells, "precision": "mixed", "cuda_graph": True, "tuning": tuning,
+            "gpu_launches": launches, "clocks": clocks, "init_s": t_init,
+            "star0_H_L2": diag[0], "sizes": sorted(set((c.nx, c.n_levels) for c in cfgs))[:40]}
+
+
 def run_native(args, dist, rank, ws, local):
     import dataclasses
     import torch
@@ -338,6 +387,10 @@ def run_native(args, dist, rank, ws, local):
     for _ in range(args.warmup):
         one_step()
     sim.sync()
+    tuning = sim.tune(reps=2) if not args.no_tune else None   # autotuner, outside the timed region
+    for _ in range(2):
+        one_step()
+    sim.sync()
     diag0 = sim.constraints()
 
     # ---- timed region (device time, CUDA events on the library's stream)
@@ -354,13 +407,24 @@ def run_native(args, dist, rank, ws, local):
         msim.step(dt, 1, use_graph=True)
         msim.constraints()
     msim.sync()
+    mtuning = msim.tune(reps=2) if not args.no_tune else None
+    for _ in range(2):
+        msim.step(dt, 1, use_graph=True)
+        msim.constraints()
+    msim.sync()
     mms, mlaunches, _, mclocks = timed_steps(msim, dt, args.steps, dist)
     mms_max = max_over_ranks(dist, mms)
     mvalue = ws * cells_per_step * args.steps / (mms_max * 1e-3)
     mixed = {"value": mvalue, "unit": UNIT, "ms_per_step": mms_max / args.steps, "speedup_vs_fp64": mvalue / value,
-             "gpu_launches": mlaunches, "clocks": mclocks,
+             "gpu_launches": mlaunches, "clocks": mclocks, "tuning": mtuning,
              "arith": "FP32 reconstruction, Riemann solver, hydro sources and Z4c algebra; FP64 finite "
                       "differences, primitive recovery, algebraic constraints, RK and flux accumulation"}
+
+    # ---- the batched sweep (independent stars of mixed sizes in one set of
+    # persistent launches per stage), mixed precision, one graph per step
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, dist, ws)
 
     # ---- end to end through the C ABI with host buffers: every step the state
     # of all levels goes host -> device from pinned memory (set_initial_data, RAW),
@@ -438,7 +502,7 @@ def run_native(args, dist, rank, ws, local):
                            "l2": "working set > L2 (no flush)", "cuda_graph": True},
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mixed": mixed,
+                "mixed": mixed, "batch": batch, "tuning": tuning,
                 "diag": {"H_L2": diag[0], "Mb": diag[4], "rho_max": diag[6], "Mb_drift": (diag[4] - diag0[4]) / diag0[4]}}
         print(json.dumps(line), flush=True)
 
@@ -452,6 +516,10 @@ def main():
     ap.add_argument("--workload", default="tov_stable_3x256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-errors", action="store_true", help="skip the per-output error report against the oracle")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default launch shapes)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
+    ap.add_argument("--batch-stars", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist, rank, ws, local = dist_setup()
