@@ -201,6 +201,49 @@ sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level, const dou
 sacra_status sacra_tune(sacra_ctx *c, int reps);
 sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *tile_y, int *blocks_per_sm);
 
+/* ---- Learned seed of the primitive recovery (no counterpart in the paper).
+   A 9 -> 64 -> 64 -> 1 tanh network (BF16 weights, FP32 arithmetic) predicts
+   log10(P / D) from the conserved variables and metric invariants; the
+   predicted pressure gives a first value z0 of the recovery's unknown, the
+   FP64 Illinois iteration runs on the bracket z0 (1 -+ delta) and, whenever
+   that bracket does not enclose the root or the iteration reaches its cap,
+   on the plain bracket.  Converged primitives therefore equal those of the
+   unseeded recovery to its tolerance (c2p_tol).
+
+   sacra_mlp_bytes: size of the packed network (a device buffer the caller owns).
+   sacra_mlp_collect: write tuples (9 features, then log10(P / D); 10 floats
+   each) of every interior cell of every level whose recovery is non-trivial
+   (moving fluid above the atmosphere, no cold or atmosphere branch) into
+   DEVICE buffer dev_tuples (capacity tuples); *n = tuples written.
+   sacra_mlp_train: train a fresh network (Glorot-uniform start from `seed`)
+   on DEVICE tuples (every fifth tuple, index % 5 == 4, is held out) with Adam
+   for `steps` minibatches of batch_blocks x 128 tuples, lr decaying by a
+   cosine to lr / 100; writes the packed network to DEVICE dev_net.
+   host_loss: NULL or `steps` floats (minibatch loss per step); host_report:
+   NULL or 3 floats (held-out RMS error of log10(P / D), 99.9th percentile of
+   the seed's relative z error, the bracket half-width delta chosen as four
+   times that percentile, in [1e-5, 0.05]).  Runs on cuda_stream; allocates
+   its scratch with cudaMalloc and frees it before returning.
+   sacra_mlp_grad: the gradient (flat order w1 64x9, b1, w2 64x64, b2, w3, b3;
+   MLP_NPARAM = 4865 floats to host_grad) of the mean squared error over all
+   n DEVICE tuples at the network dev_net, and that loss (host_loss).
+   sacra_set_mlp: use network dev_net (DEVICE, must outlive its use) in every
+   later recovery of the context; NULL restores the plain bracket.
+   sacra_c2p_counting / sacra_c2p_counts: count, from now on, Illinois
+   function evaluations, recoveries where a seed was tried, seeded brackets
+   that held, and recoveries; out4 receives the four counts (reset != 0
+   zeroes them). */
+size_t sacra_mlp_bytes(void);
+sacra_status sacra_mlp_collect(sacra_ctx *c, float *dev_tuples, long long capacity, long long *n);
+sacra_status sacra_mlp_train(const float *dev_tuples, long long n, int steps, int batch_blocks, float lr,
+                             unsigned long long seed, void *dev_net, float *host_loss, float *host_report,
+                             void *cuda_stream);
+sacra_status sacra_mlp_grad(const float *dev_tuples, long long n, const void *dev_net, float *host_grad,
+                            float *host_loss, void *cuda_stream);
+sacra_status sacra_set_mlp(sacra_ctx *c, const void *dev_net);
+sacra_status sacra_c2p_counting(sacra_ctx *c, int enable);
+sacra_status sacra_c2p_counts(sacra_ctx *c, long long *out4, int reset);
+
 void sacra_destroy(sacra_ctx *c);
 const char *sacra_last_error(const sacra_ctx *c);
 
@@ -229,6 +272,8 @@ long long sacra_batch_launch_count(const sacra_batch *b);
 sacra_status sacra_batch_profile(sacra_batch *b, int enable);
 sacra_status sacra_batch_profile_get(sacra_batch *b, int idx, char *name, size_t name_len, double *total_ms,
                                      long long *launches, long long *cells);
+sacra_status sacra_batch_set_mlp(sacra_batch *b, const void *dev_net);
+sacra_status sacra_batch_mlp_collect(sacra_batch *b, float *dev_tuples, long long capacity, long long *n);
 void sacra_batch_destroy(sacra_batch *b);
 const char *sacra_batch_last_error(const sacra_batch *b);
 

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["hydro.cu", "z4c.cu", "grid.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["hydro.cu", "z4c.cu", "grid.cu", "capi.cu", "noalloc.cu", "mlp.cu"]
 HEADERS = ["common.cuh", "z4c.cuh", "kernels.h"]
 LIB = os.path.join(BUILD, "libsacra2d.so")
 PROBE = os.path.join(BUILD, "libsacra_probe.so")

@@ -896,6 +896,50 @@ sacra_status sync(Engine &e) {
   return cuda_check(e, "sync");
 }
 
+// ---- learned seed of the primitive recovery
+
+unsigned long long *c2p_counters(Engine &e) { return e.nfb + 1; }   // 4 counters next to the fallback count
+unsigned long long *collect_counter(Engine &e) { return e.nfb + 8; }
+
+sacra_status set_mlp(Engine &e, const void *dev_net) {
+  const MlpNet *net = reinterpret_cast<const MlpNet *>(dev_net);
+  e.dp.mlp = net;
+  for (Star &st : e.stars) st.dp.mlp = net;
+  drop_graphs(e);
+  return upload_plan(e);
+}
+
+sacra_status set_counting(Engine &e, int on) {
+  unsigned long long *c = on ? c2p_counters(e) : nullptr;
+  e.dp.c2p_stats = c;
+  for (Star &st : e.stars) st.dp.c2p_stats = c;
+  if (on) cudaMemsetAsync(c2p_counters(e), 0, 4 * sizeof(unsigned long long), e.stream);
+  drop_graphs(e);
+  return upload_plan(e);
+}
+
+sacra_status get_counts(Engine &e, long long out[4], int reset) {
+  unsigned long long h[4];
+  cudaMemcpyAsync(h, c2p_counters(e), sizeof(h), cudaMemcpyDeviceToHost, e.stream);
+  if (reset) cudaMemsetAsync(c2p_counters(e), 0, sizeof(h), e.stream);
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "c2p counts");
+  for (int a = 0; a < 4; ++a) out[a] = (long long)h[a];
+  return cuda_check(e, "c2p counts");
+}
+
+sacra_status mlp_collect(Engine &e, float *dev_out, long long cap, long long *n) {
+  if (!dev_out || cap < 0 || !n) return fail(e, SACRA_ERR_ARG, "bad buffer");
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  cudaMemsetAsync(collect_counter(e), 0, sizeof(unsigned long long), e.stream);
+  for (Star &st : e.stars)
+    for (int l = 0; l < st.prm.n_levels; ++l) launch_mlp_collect(st.lv[l], st.dp, dev_out, cap, collect_counter(e), e.stream);
+  unsigned long long h = 0;
+  cudaMemcpyAsync(&h, collect_counter(e), sizeof(h), cudaMemcpyDeviceToHost, e.stream);
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "mlp_collect");
+  *n = std::min<long long>((long long)h, cap);
+  return cuda_check(e, "mlp_collect");
+}
+
 bool params_ok(const sacra_params *per_star, int n) {
   if (!per_star || n < 1) return false;
   std::string why;
@@ -994,6 +1038,39 @@ sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *ti
   return c ? get_tuning(c->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
 }
 
+size_t sacra_mlp_bytes(void) { return sizeof(MlpNet); }
+
+sacra_status sacra_mlp_collect(sacra_ctx *c, float *dev_tuples, long long capacity, long long *n) {
+  return c ? mlp_collect(c->e, dev_tuples, capacity, n) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_mlp_train(const float *dev_tuples, long long n, int steps, int batch_blocks, float lr,
+                             unsigned long long seed, void *dev_net, float *host_loss, float *host_report,
+                             void *cuda_stream) {
+  const int rc = mlp_train(dev_tuples, n, steps, batch_blocks, lr, seed, reinterpret_cast<MlpNet *>(dev_net),
+                           host_loss, host_report, (cudaStream_t)cuda_stream);
+  if (rc == -1) return SACRA_ERR_ARG;
+  if (rc == -3) return SACRA_ERR_OOM;
+  return rc == 0 && cudaGetLastError() == cudaSuccess ? SACRA_OK : SACRA_ERR_CUDA;
+}
+
+sacra_status sacra_mlp_grad(const float *dev_tuples, long long n, const void *dev_net, float *host_grad,
+                            float *host_loss, void *cuda_stream) {
+  const int rc = mlp_grad(dev_tuples, n, reinterpret_cast<const MlpNet *>(dev_net), host_grad, host_loss,
+                          (cudaStream_t)cuda_stream);
+  if (rc == -1) return SACRA_ERR_ARG;
+  if (rc == -3) return SACRA_ERR_OOM;
+  return rc == 0 && cudaGetLastError() == cudaSuccess ? SACRA_OK : SACRA_ERR_CUDA;
+}
+
+sacra_status sacra_set_mlp(sacra_ctx *c, const void *dev_net) { return c ? set_mlp(c->e, dev_net) : SACRA_ERR_ARG; }
+
+sacra_status sacra_c2p_counting(sacra_ctx *c, int enable) { return c ? set_counting(c->e, enable) : SACRA_ERR_ARG; }
+
+sacra_status sacra_c2p_counts(sacra_ctx *c, long long *out4, int reset) {
+  return c && out4 ? get_counts(c->e, out4, reset) : SACRA_ERR_ARG;
+}
+
 void sacra_destroy(sacra_ctx *c) {
   if (!c) return;
   engine_free(c->e);
@@ -1060,6 +1137,14 @@ sacra_status sacra_batch_profile(sacra_batch *b, int enable) { return b ? set_pr
 sacra_status sacra_batch_profile_get(sacra_batch *b, int idx, char *name, size_t name_len, double *total_ms,
                                      long long *launches, long long *cells) {
   return b ? profile_get(b->e, idx, name, name_len, total_ms, launches, cells) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_set_mlp(sacra_batch *b, const void *dev_net) {
+  return b ? set_mlp(b->e, dev_net) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_mlp_collect(sacra_batch *b, float *dev_tuples, long long capacity, long long *n) {
+  return b ? mlp_collect(b->e, dev_tuples, capacity, n) : SACRA_ERR_ARG;
 }
 
 void sacra_batch_destroy(sacra_batch *b) {

@@ -28,6 +28,8 @@ enum : int { pRHO = 0, pUX, pUY, pUZ, pP, pEPS };
 // recovery status bits
 constexpr int ST_NOCONV = 1, ST_COLD = 2, ST_ATM = 4, ST_KRESCALE = 8, ST_BAD = 16;
 
+struct MlpNet;
+
 struct DevParams {
   int geometry, evolve, solver, rk, c2p_maxit, n_levels;
   int mixed;             // SACRA_MIXED_* bits: parts whose arithmetic runs in FP32 (FP64 differences and updates)
@@ -37,6 +39,10 @@ struct DevParams {
   double c2p_kmax;       // 2 v_max / (1 + v_max^2), v_max = sqrt(1 - 1 / w_max^2)
   // FP32 copies for the mixed-precision kernels (no conversions on the device)
   float fK, fGamma, fGm1, fGamma_th, fGth1, fkappa, feta_B, firz2, fko;
+  // learned seed of the primitive recovery (null: plain bracket) and its counters
+  // [Illinois evaluations, recoveries with a seed tried, seeded brackets that held, recoveries]
+  const MlpNet *mlp;
+  unsigned long long *c2p_stats;
 };
 
 // a parameter in arithmetic T: the FP64 value, or its FP32 copy
@@ -245,6 +251,10 @@ __device__ inline T eos_cs2(const DevParams &p, T rho, T eps, T P) {
   return c2;
 }
 
+}  // namespace sacra
+#include "mlp.cuh"
+namespace sacra {
+
 // ------------------------------------------------------------------ primitive <-> conserved (Eq. cons_var)
 
 // pr: rho, u_x, u_y, u_z, P, eps; q: psi^6 (D, S_x, S_y or x S_y, S_z, E)
@@ -281,10 +291,11 @@ __device__ inline double c2p_fun(const DevParams &p, double z, double D, double 
   return z - r / ((1.0 + eps) * (1.0 + a));
 }
 
-// Illinois bracketing iteration on [a, b]; *ok = 0 on no sign change or cap
+// Illinois bracketing iteration from the bracket [a, b] with the master
+// function's values fa, fb there; *ok = 0 on no sign change or at the cap
 template <bool COLD>
-__device__ double illinois(const DevParams &p, double a, double b, double D, double qq, double r, int *its, int *ok) {
-  double fa = c2p_fun<COLD>(p, a, D, qq, r), fb = c2p_fun<COLD>(p, b, D, qq, r);
+__device__ double illinois_from(const DevParams &p, double a, double fa, double b, double fb, double D, double qq,
+                                double r, int *its, int *ok) {
   *its = 0;
   *ok = 1;
   if (fa == 0.0) return a;
@@ -313,6 +324,13 @@ __device__ double illinois(const DevParams &p, double a, double b, double D, dou
   }
   *ok = 0;
   return c;
+}
+
+// Illinois bracketing iteration on [a, b]
+template <bool COLD>
+__device__ double illinois(const DevParams &p, double a, double b, double D, double qq, double r, int *its, int *ok) {
+  const double fa = c2p_fun<COLD>(p, a, D, qq, r), fb = c2p_fun<COLD>(p, b, D, qq, r);
+  return illinois_from<COLD>(p, a, fa, b, fb, D, qq, r, its, ok);
 }
 
 __device__ inline void atmosphere(const DevParams &p, double pr[NPRIM]) {
@@ -354,7 +372,51 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
   const double zlo = 0.5 * k / sqrt(1.0 - 0.25 * k * k);
   const double zhi = k / sqrt(1.0 - k * k);
   int its, ok;
-  double z = illinois<false>(p, zlo, zhi, D, qq, r, &its, &ok);
+  double z = 0.0;
+  bool solved = false;
+  unsigned long long ev = 0, tried = 0, held = 0;
+  if (p.mlp && r > 0.0) {
+    // learned seed: P / D -> v = r / (1 + q + P / D) -> z0 = v / sqrt(1 - v^2) (FP32).  The master
+    // function at z0 tells the side of the root; the bracket is [z0, z0 (1 + delta)] or
+    // [z0 (1 - delta), z0] inside [zlo, zhi], and the Illinois iteration itself is unchanged
+    float x[MLP_IN];
+    c2p_features(p, D, qq, r, k, W, gt, gi, x);
+    const float pd = exp10f(mlp_forward(p.mlp, x));
+    const float v = f32_of(r) / (1.0f + f32_of(qq) + pd);
+    tried = 1;
+    if (v > 0.0f && v < 1.0f) {
+      const float z0 = v * rsqrtf(1.0f - v * v), dl = p.mlp->delta;
+      const double zs = fmin(fmax(f64_of(z0), zlo), zhi);
+      const double f0 = c2p_fun<false>(p, zs, D, qq, r);
+      double a, fa, b, fb;
+      if (f0 < 0.0) {
+        a = zs; fa = f0;
+        b = fmin(zhi, f64_of(z0 * (1.0f + dl)));
+        fb = c2p_fun<false>(p, b, D, qq, r);
+      } else {
+        b = zs; fb = f0;
+        a = fmax(zlo, f64_of(z0 * (1.0f - dl)));
+        fa = c2p_fun<false>(p, a, D, qq, r);
+      }
+      ev += 2;
+      if (a <= b) {
+        z = illinois_from<false>(p, a, fa, b, fb, D, qq, r, &its, &ok);
+        ev += its;
+        solved = ok != 0;
+        held = solved ? 1 : 0;
+      }
+    }
+  }
+  if (!solved) {
+    z = illinois<false>(p, zlo, zhi, D, qq, r, &its, &ok);
+    ev += its + 2;
+  }
+  if (p.c2p_stats) {
+    atomicAdd(p.c2p_stats + 0, ev);
+    if (tried) atomicAdd(p.c2p_stats + 1, tried);
+    if (held) atomicAdd(p.c2p_stats + 2, held);
+    atomicAdd(p.c2p_stats + 3, 1ull);
+  }
   if (!ok) st |= ST_NOCONV;
   double w = sqrt(1.0 + z * z);
   double rho = D / w;

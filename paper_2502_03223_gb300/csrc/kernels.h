@@ -97,4 +97,13 @@ void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered
 int diag_blocks(const Lev &L);
 void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s);
 
+// learned seed of the primitive recovery (mlp.cu): tuples from a level's state,
+// training (forward, backward, Adam) and the full-batch gradient
+void launch_mlp_collect(const Lev &L, const DevParams &p, float *out, long long cap, unsigned long long *count,
+                        cudaStream_t s);
+int mlp_train(const float *samples, long long n, int steps, int batch_blocks, float lr, unsigned long long seed,
+              MlpNet *dev_net, float *host_loss, float *host_report, cudaStream_t s);
+int mlp_grad(const float *samples, long long n, const MlpNet *dev_net, float *host_grad, float *host_loss,
+             cudaStream_t s);
+
 }  // namespace sacra

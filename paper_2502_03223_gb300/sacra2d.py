@@ -31,8 +31,11 @@ EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sa
            "sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
            "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
            "sacra_batch_sync", "sacra_batch_launch_count", "sacra_batch_profile", "sacra_batch_profile_get",
-           "sacra_batch_destroy", "sacra_batch_last_error"]
+           "sacra_batch_destroy", "sacra_batch_last_error", "sacra_mlp_bytes", "sacra_mlp_collect",
+           "sacra_mlp_train", "sacra_mlp_grad", "sacra_set_mlp", "sacra_c2p_counting", "sacra_c2p_counts",
+           "sacra_batch_set_mlp", "sacra_batch_mlp_collect"]
 EXPORTS = sorted(EXPORTS)
+MLP_NPARAM = 4865
 KIND_NAMES = ["flux_x", "flux_z", "hydro_rhs", "cartoon", "z4c_derivs", "z4c_point", "rk_update"]
 
 
@@ -110,6 +113,20 @@ def load(path: str = LIB_PATH):
     L.sacra_batch_destroy.argtypes = [vp]
     L.sacra_batch_last_error.argtypes = [vp]
     L.sacra_batch_last_error.restype = C.c_char_p
+    fp = C.POINTER(C.c_float)
+    L.sacra_mlp_bytes.argtypes = []
+    L.sacra_mlp_bytes.restype = C.c_size_t
+    L.sacra_mlp_collect.argtypes = [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
+    L.sacra_mlp_train.argtypes = [vp, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_ulonglong, vp, fp, fp, vp]
+    L.sacra_mlp_grad.argtypes = [vp, C.c_longlong, vp, fp, fp, vp]
+    L.sacra_set_mlp.argtypes = [vp, vp]
+    L.sacra_c2p_counting.argtypes = [vp, C.c_int]
+    L.sacra_c2p_counts.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
+    L.sacra_batch_set_mlp.argtypes = [vp, vp]
+    L.sacra_batch_mlp_collect.argtypes = [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
+    for name in ("sacra_mlp_collect", "sacra_mlp_train", "sacra_mlp_grad", "sacra_set_mlp", "sacra_c2p_counting",
+                 "sacra_c2p_counts", "sacra_batch_set_mlp", "sacra_batch_mlp_collect"):
+        getattr(L, name).restype = C.c_int
     for name in ("sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
                  "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
                  "sacra_batch_sync", "sacra_batch_profile", "sacra_batch_profile_get"):
@@ -249,6 +266,27 @@ class Sacra:
     def n_stages(self):
         return 4 if self.cfg.rk == 0 else 3
 
+    def mlp_collect(self, out):
+        """Append-free dump of recovery tuples into `out` (CUDA float32 (cap, 10)); returns the count."""
+        n = C.c_longlong(0)
+        self._chk(self._L.sacra_mlp_collect(self._c, C.c_void_p(out.data_ptr()), out.shape[0], C.byref(n)),
+                  "mlp_collect")
+        return n.value
+
+    def set_mlp(self, net):
+        """Use a trained seed network (CUDA uint8 tensor, kept alive by the caller); None disables."""
+        self._net = net
+        self._chk(self._L.sacra_set_mlp(self._c, C.c_void_p(net.data_ptr()) if net is not None else None), "set_mlp")
+
+    def c2p_counting(self, enable=True):
+        self._chk(self._L.sacra_c2p_counting(self._c, 1 if enable else 0), "c2p_counting")
+
+    def c2p_counts(self, reset=False):
+        """(Illinois evaluations, seeded tries, seeded brackets that held, recoveries)."""
+        out = (C.c_longlong * 4)()
+        self._chk(self._L.sacra_c2p_counts(self._c, out, 1 if reset else 0), "c2p_counts")
+        return tuple(out)
+
     def tune(self, reps=3):
         """Run the autotuner of the batched launches; returns {kind: (tile_x, tile_y, blocks_per_sm)}."""
         self._chk(self._L.sacra_tune(self._c, reps), "tune")
@@ -261,6 +299,61 @@ class Sacra:
             self._chk(self._L.sacra_get_tuning(self._c, k, C.byref(x), C.byref(y), C.byref(m)), "get_tuning")
             out[name] = (x.value, y.value, m.value)
         return out
+
+
+def mlp_train(tuples, steps=2000, batch_blocks=32, lr=3e-3, seed=1, record_loss=False, stream=None):
+    """Train the recovery seed on the GPU.  tuples: a CUDA float32 tensor of
+    shape (n, 10).  Returns (net: CUDA uint8 tensor, report: dict, loss history)."""
+    import torch
+    L = load()
+    assert tuples.is_cuda and tuples.dtype == torch.float32 and tuples.shape[1] == 10
+    net = torch.zeros(L.sacra_mlp_bytes(), dtype=torch.uint8, device="cuda")
+    hist = np.zeros(max(steps, 1), dtype=np.float32) if record_loss else None
+    rep = np.zeros(3, dtype=np.float32)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    fpp = C.POINTER(C.c_float)
+    rc = L.sacra_mlp_train(C.c_void_p(tuples.data_ptr()), tuples.shape[0], steps, batch_blocks, lr, seed,
+                           C.c_void_p(net.data_ptr()), hist.ctypes.data_as(fpp) if record_loss else None,
+                           rep.ctypes.data_as(fpp), C.c_void_p(st.cuda_stream))
+    if rc != SACRA_OK:
+        raise SacraError("sacra_mlp_train failed with status %d" % rc)
+    return net, {"val_rms_log10": float(rep[0]), "z_err_q999": float(rep[1]), "delta": float(rep[2])}, hist
+
+
+def mlp_grad(tuples, net, stream=None):
+    """Full-batch gradient (4865 floats, the oracle's flat order) and loss."""
+    import torch
+    L = load()
+    g = np.zeros(MLP_NPARAM, dtype=np.float32)
+    loss = C.c_float(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = L.sacra_mlp_grad(C.c_void_p(tuples.data_ptr()), tuples.shape[0], C.c_void_p(net.data_ptr()),
+                          g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss), C.c_void_p(st.cuda_stream))
+    if rc != SACRA_OK:
+        raise SacraError("sacra_mlp_grad failed with status %d" % rc)
+    return g, float(loss.value)
+
+
+def mlp_unpack(net_bytes):
+    """Host view of a packed network (numpy uint8 array): dict of float64 arrays."""
+    b = np.asarray(net_bytes, dtype=np.uint8)
+    def bf(o, n):
+        u = b[o:o + 2 * n].view(np.uint16).astype(np.uint32) << 16
+        return u.view(np.float32).astype(np.float64)
+    def f(o, n):
+        return b[o:o + 4 * n].view(np.float32).astype(np.float64)
+    o = 0
+    w1 = bf(o, 576).reshape(64, 9); o += 1152
+    w2 = bf(o, 4096).reshape(64, 64); o += 8192
+    w3 = bf(o, 64); o += 128 + 8
+    b1 = f(o, 64); o += 256
+    b2 = f(o, 64); o += 256
+    b3 = f(o, 1)[0]; o += 4
+    in_mu = f(o, 9); o += 36
+    in_sd = f(o, 9); o += 36
+    out_mu, out_sd, delta = f(o, 3)
+    return {"w1": w1, "b1": b1, "w2": w2, "b2": b2, "w3": w3, "b3": b3, "in_mu": in_mu, "in_sd": in_sd,
+            "out_mu": out_mu, "out_sd": out_sd, "delta": delta}
 
 
 class SacraBatch:

@@ -19,7 +19,7 @@ def lib_path():
 
 def _declared():
     txt = open(os.path.join(ROOT, "include", "sacra2d.h")).read()
-    return sorted(set(re.findall(r"\b(sacra_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(sacra_[a-z_0-9]+)\s*\(", txt)))
 
 
 def test_header_declares_the_binding_exports():
