@@ -340,29 +340,47 @@ def run_batch(args, dist, ws):
         b.step(dt, 1, use_graph=True)
     b.sync()
     steps = max(3, min(args.steps, args.batch_steps))
-    sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
-    n0 = b.launch_count
-    barrier(dist)
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(b.stream)
-    b.step(dt, steps, use_graph=True)
-    ev1.record(b.stream)
-    ev1.synchronize()
-    torch.cuda.synchronize()
-    barrier(dist)
-    clocks = sampler.stop()
-    ms = max_over_ranks(dist, ev0.elapsed_time(ev1))
+
+    def timed(nsteps):
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        n0 = b.launch_count
+        barrier(dist)
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(b.stream)
+        b.step(dt, nsteps, use_graph=True)
+        ev1.record(b.stream)
+        ev1.synchronize()
+        torch.cuda.synchronize()
+        barrier(dist)
+        return max_over_ranks(dist, ev0.elapsed_time(ev1)), b.launch_count - n0, sampler.stop()
+
+    ms, launches, clocks = timed(steps)
+    # the learned recovery seed, trained on tuples of this batch's own state
+    learned = None
+    if not args.no_learned:
+        buf = torch.zeros((2_000_000, 10), dtype=torch.float32, device="cuda")
+        n = b.mlp_collect(buf)
+        if n >= 1000:
+            net, rep, _ = S.mlp_train(buf[:n], steps=3000, batch_blocks=32, lr=1e-2, seed=1, kmin=0.2)
+            del buf
+            b.set_mlp(net)
+            b.step(dt, 2, use_graph=True)
+            lms, _, lclocks = timed(steps)
+            learned = {"ms_per_step": lms / steps, "tuples": n, "train": rep, "clocks": lclocks}
+            b.set_mlp(None)
     cells = sum(c.interior_cells * c.n_stages for c in cfgs)
-    launches = b.launch_count - n0
+    if learned is not None:
+        learned["value"] = ws * cells * steps / (learned["ms_per_step"] * steps * 1e-3)
+        learned["unit"] = UNIT
     diag = b.constraints(0)
     b.close()
     return {"workload": "batch_sweep_%d" % len(cfgs), "value": ws * cells * steps / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms / steps, "steps": steps, "n_stars": len(cfgs),
             "cell_updates_per_step": cells, "precision": "mixed", "cuda_graph": True, "tuning": tuning,
-            "gpu_launches": launches, "clocks": clocks, "init_s": t_init,
+            "gpu_launches": launches, "clocks": clocks, "init_s": t_init, "learned_seed": learned,
             "star0_H_L2": diag[0], "sizes": sorted(set((c.nx, c.n_levels) for c in cfgs))[:40]}
 
 
@@ -519,6 +537,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default launch shapes)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
     ap.add_argument("--batch-stars", type=int, default=64)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned recovery seed")
     ap.add_argument("--batch-steps", type=int, default=5)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

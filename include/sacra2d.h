@@ -218,7 +218,9 @@ sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *ti
    sacra_mlp_train: train a fresh network (Glorot-uniform start from `seed`)
    on DEVICE tuples (every fifth tuple, index % 5 == 4, is held out) with Adam
    for `steps` minibatches of batch_blocks x 128 tuples, lr decaying by a
-   cosine to lr / 100; writes the packed network to DEVICE dev_net.
+   cosine to lr / 100; writes the packed network to DEVICE dev_net.  The
+   seed is tried only where k = r / (1 + q) >= kmin (slow flows, where the
+   plain bracket already converges in 2-3 evaluations, can skip it).
    host_loss: NULL or `steps` floats (minibatch loss per step); host_report:
    NULL or 3 floats (held-out RMS error of log10(P / D), 99.9th percentile of
    the seed's relative z error, the bracket half-width delta chosen as four
@@ -236,7 +238,7 @@ sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *ti
 size_t sacra_mlp_bytes(void);
 sacra_status sacra_mlp_collect(sacra_ctx *c, float *dev_tuples, long long capacity, long long *n);
 sacra_status sacra_mlp_train(const float *dev_tuples, long long n, int steps, int batch_blocks, float lr,
-                             unsigned long long seed, void *dev_net, float *host_loss, float *host_report,
+                             unsigned long long seed, float kmin, void *dev_net, float *host_loss, float *host_report,
                              void *cuda_stream);
 sacra_status sacra_mlp_grad(const float *dev_tuples, long long n, const void *dev_net, float *host_grad,
                             float *host_loss, void *cuda_stream);

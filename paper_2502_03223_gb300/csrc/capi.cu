@@ -1045,9 +1045,9 @@ sacra_status sacra_mlp_collect(sacra_ctx *c, float *dev_tuples, long long capaci
 }
 
 sacra_status sacra_mlp_train(const float *dev_tuples, long long n, int steps, int batch_blocks, float lr,
-                             unsigned long long seed, void *dev_net, float *host_loss, float *host_report,
+                             unsigned long long seed, float kmin, void *dev_net, float *host_loss, float *host_report,
                              void *cuda_stream) {
-  const int rc = mlp_train(dev_tuples, n, steps, batch_blocks, lr, seed, reinterpret_cast<MlpNet *>(dev_net),
+  const int rc = mlp_train(dev_tuples, n, steps, batch_blocks, lr, seed, kmin, reinterpret_cast<MlpNet *>(dev_net),
                            host_loss, host_report, (cudaStream_t)cuda_stream);
   if (rc == -1) return SACRA_ERR_ARG;
   if (rc == -3) return SACRA_ERR_OOM;

@@ -343,8 +343,10 @@ __device__ inline void atmosphere(const DevParams &p, double pr[NPRIM]) {
 // Conserved -> primitive for one cell (Galeazzi et al. 2013, App. C; cold
 // fallback and atmosphere of Sec. II.C.4).  q is rewritten when the state
 // had to change.  Returns the status bits.
+// SEED: the learned seed is compiled in (and used when net is not null)
+template <bool SEED = false>
 __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W, const Sym3 &gt, double x,
-                                   double pr[NPRIM]) {
+                                   double pr[NPRIM], const MlpNet *net = nullptr) {
   const Sym3 gi = s3inv(gt, (double *)nullptr);
   const double W3 = W * W * W;
   const double D = q[0] * W3;
@@ -375,17 +377,17 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
   double z = 0.0;
   bool solved = false;
   unsigned long long ev = 0, tried = 0, held = 0;
-  if (p.mlp && r > 0.0) {
+  if (SEED && net && r > 0.0 && k >= net->kmin) {
     // learned seed: P / D -> v = r / (1 + q + P / D) -> z0 = v / sqrt(1 - v^2) (FP32).  The master
     // function at z0 tells the side of the root; the bracket is [z0, z0 (1 + delta)] or
     // [z0 (1 - delta), z0] inside [zlo, zhi], and the Illinois iteration itself is unchanged
     float x[MLP_IN];
     c2p_features(p, D, qq, r, k, W, gt, gi, x);
-    const float pd = exp10f(mlp_forward(p.mlp, x));
+    const float pd = exp10f(mlp_forward(net, x));
     const float v = f32_of(r) / (1.0f + f32_of(qq) + pd);
     tried = 1;
     if (v > 0.0f && v < 1.0f) {
-      const float z0 = v * rsqrtf(1.0f - v * v), dl = p.mlp->delta;
+      const float z0 = v * rsqrtf(1.0f - v * v), dl = net->delta;
       const double zs = fmin(fmax(f64_of(z0), zlo), zhi);
       const double f0 = c2p_fun<false>(p, zs, D, qq, r);
       double a, fa, b, fb;

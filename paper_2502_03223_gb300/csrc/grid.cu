@@ -229,8 +229,9 @@ __device__ inline void enforce_algebraic(double m[NST]) {
 // RK stage combination on [1, jmax] x [1, kmax], then algebraic constraints
 // and primitive recovery.  Ust = stage state read (Un at stage 0, Us after);
 // the result is written to Us.
+template <bool SEED = false>
 __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p, const double *__restrict__ Ust, int stage, double dt,
-                                                   int jmax, int kmax, int j, int k) {
+                                                   int jmax, int kmax, int j, int k, const MlpNet *net = nullptr) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -260,7 +261,7 @@ __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p,
   Sym3 g;
   g.xx = 1.0 + m[fHXX]; g.xy = m[fHXY]; g.xz = m[fHXZ]; g.yy = 1.0 + m[fHYY]; g.yz = m[fHYZ]; g.zz = 1.0 + m[fHZZ];
   double pr[NPRIM];
-  const int st = cons_to_prim(p, m + fQD, m[fW], g, (j - 0.5) * L.dx, pr);
+  const int st = cons_to_prim<SEED>(p, m + fQD, m[fW], g, (j - 0.5) * L.dx, pr, net);
   for (int f = f0; f < NST; ++f) L.us[(size_t)f * P + id] = m[f];
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + id] = pr[f];
@@ -272,15 +273,30 @@ __global__ void __launch_bounds__(128) k_rk_update(Lev L, DevParams p, const dou
   rk_update_cell(L, p, Ust, stage, dt, jmax, kmax, 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x), 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y));
 }
 
+template <bool SEED>
 __global__ void __launch_bounds__(128) kb_rk_update(Batch b, DevParams p, int stage, double dt) {
-  for_tiles(b, [&](const BL &q, const Tile &tl) {
-    rk_update_cell(q.L, q.P, q.U, stage, dt, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
-  });
+  if constexpr (SEED) {
+    // the learned recovery seed (one network for the batch) staged in shared memory
+    __shared__ MlpNet snet;
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.mlp);
+    uint4 *dst = reinterpret_cast<uint4 *>(&snet);
+    const int nth = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int i = tid; i < (int)(sizeof(MlpNet) / sizeof(uint4)); i += nth) dst[i] = src[i];
+    __syncthreads();
+    for_tiles(b, [&](const BL &q, const Tile &tl) {
+      rk_update_cell<true>(q.L, q.P, q.U, stage, dt, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y, &snet);
+    });
+  } else {
+    for_tiles(b, [&](const BL &q, const Tile &tl) {
+      rk_update_cell<false>(q.L, q.P, q.U, stage, dt, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+    });
+  }
 }
 
 void launch_b_rk_update(const Batch &b, const DevParams &p, int stage, double dt, cudaStream_t s) {
   if (b.ntiles <= 0) return;
-  kb_rk_update<<<b.grid, b.block, 0, s>>>(b, p, stage, dt);
+  if (p.mlp) kb_rk_update<true><<<b.grid, b.block, 0, s>>>(b, p, stage, dt);
+  else kb_rk_update<false><<<b.grid, b.block, 0, s>>>(b, p, stage, dt);
 }
 
 // Restriction of child level C onto parent cells [1, N/2]^2 (Sec. II.D):

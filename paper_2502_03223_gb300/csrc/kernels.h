@@ -102,7 +102,7 @@ void launch_diag_final(const double *partials, int n, double *out, cudaStream_t 
 void launch_mlp_collect(const Lev &L, const DevParams &p, float *out, long long cap, unsigned long long *count,
                         cudaStream_t s);
 int mlp_train(const float *samples, long long n, int steps, int batch_blocks, float lr, unsigned long long seed,
-              MlpNet *dev_net, float *host_loss, float *host_report, cudaStream_t s);
+              float kmin, MlpNet *dev_net, float *host_loss, float *host_report, cudaStream_t s);
 int mlp_grad(const float *samples, long long n, const MlpNet *dev_net, float *host_grad, float *host_loss,
              cudaStream_t s);
 

@@ -292,7 +292,7 @@ void pack(const std::vector<float> &theta, MlpNet &net) {
 }  // namespace
 
 int mlp_train(const float *samples, long long n, int steps, int batch_blocks, float lr, unsigned long long seed,
-              MlpNet *dev_net, float *host_loss, float *host_report, cudaStream_t s) {
+              float kmin, MlpNet *dev_net, float *host_loss, float *host_report, cudaStream_t s) {
   if (!samples || n < 50 || steps < 0 || batch_blocks < 1 || !dev_net || !(lr > 0)) return -1;
   // moments of the training samples -> normalisation
   const int mb = 256;
@@ -321,6 +321,7 @@ int mlp_train(const float *samples, long long n, int steps, int batch_blocks, fl
   init_theta(seed, theta);
   pack(theta, net);
   net.delta = 0.05f;
+  net.kmin = kmin;
   cudaMemcpyAsync(dev_net, &net, sizeof(net), cudaMemcpyHostToDevice, s);
   DevBuf th, m, v, part, ploss;
   const size_t P = MLP_NPARAM;

@@ -19,7 +19,7 @@ constexpr int MLP_IN = 9, MLP_H = 64;
 constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
 
 // the packed network as the kernels read it (one device copy per context)
-struct MlpNet {
+struct alignas(16) MlpNet {
   uint16_t w1[MLP_H * MLP_IN];   // BF16, row-major (hidden unit, input)
   uint16_t w2[MLP_H * MLP_H];    // BF16, row-major (out, in)
   uint16_t w3[MLP_H];            // BF16
@@ -27,6 +27,7 @@ struct MlpNet {
   float b1[MLP_H], b2[MLP_H], b3;
   float in_mu[MLP_IN], in_sd[MLP_IN], out_mu, out_sd;
   float delta;                   // relative half-width of the seeded bracket
+  float kmin;                    // the seed is tried where k = r / (1 + q) >= kmin
 };
 
 __host__ __device__ inline float bf16_to_f32(uint16_t b) {
@@ -71,26 +72,52 @@ __device__ __forceinline__ void c2p_features(const DevParams &p, double D, doubl
   x[8] = p.K_zero ? 0.0f : log10f(eos_pc<float>(p, Df) / Df);
 }
 
-// y = log10(P / D) predicted (FP32 accumulation over BF16 weights)
+// two BF16 values packed in a 32-bit word -> floats (low half first)
+__device__ __forceinline__ void bf16x2(unsigned u, float &lo, float &hi) {
+  lo = __uint_as_float(u << 16);
+  hi = __uint_as_float(u & 0xFFFF0000u);
+}
+
+// y = log10(P / D) predicted (FP32 accumulation over BF16 weights, read 8 at a time)
 __device__ inline float mlp_forward(const MlpNet *__restrict__ net, const float x[MLP_IN]) {
   float xh[MLP_IN];
 #pragma unroll
   for (int i = 0; i < MLP_IN; ++i) xh[i] = (x[i] - net->in_mu[i]) / net->in_sd[i];
   float h1[MLP_H];
-#pragma unroll 4
-  for (int j = 0; j < MLP_H; ++j) {
-    float a = net->b1[j];
+  const unsigned *w1 = reinterpret_cast<const unsigned *>(net->w1);   // 9 inputs per row: pairs span rows
 #pragma unroll
-    for (int i = 0; i < MLP_IN; ++i) a += bf16_to_f32(net->w1[j * MLP_IN + i]) * xh[i];
-    h1[j] = tanhf(a);
+  for (int j = 0; j < MLP_H; ++j) h1[j] = net->b1[j];
+#pragma unroll
+  for (int q = 0; q < MLP_H * MLP_IN / 2; ++q) {
+    float lo, hi;
+    bf16x2(w1[q], lo, hi);
+    const int e0 = 2 * q, e1 = 2 * q + 1;
+    h1[e0 / MLP_IN] += lo * xh[e0 % MLP_IN];
+    h1[e1 / MLP_IN] += hi * xh[e1 % MLP_IN];
   }
+#pragma unroll
+  for (int j = 0; j < MLP_H; ++j) h1[j] = tanhf(h1[j]);
   float y = net->b3;
-  for (int j = 0; j < MLP_H; ++j) {
-    float a = net->b2[j];
-    const uint16_t *w = net->w2 + j * MLP_H;
-#pragma unroll 8
-    for (int i = 0; i < MLP_H; ++i) a += bf16_to_f32(w[i]) * h1[i];
-    y += bf16_to_f32(net->w3[j]) * tanhf(a);
+  const uint4 *w2 = reinterpret_cast<const uint4 *>(net->w2);
+  const unsigned *w3 = reinterpret_cast<const unsigned *>(net->w3);
+  for (int j = 0; j < MLP_H; j += 2) {
+    float a0 = net->b2[j], a1 = net->b2[j + 1];
+#pragma unroll
+    for (int c = 0; c < MLP_H / 8; ++c) {
+      const uint4 u = w2[j * (MLP_H / 8) + c], v = w2[(j + 1) * (MLP_H / 8) + c];
+      float l, h;
+      bf16x2(u.x, l, h); a0 += l * h1[8 * c + 0] + h * h1[8 * c + 1];
+      bf16x2(u.y, l, h); a0 += l * h1[8 * c + 2] + h * h1[8 * c + 3];
+      bf16x2(u.z, l, h); a0 += l * h1[8 * c + 4] + h * h1[8 * c + 5];
+      bf16x2(u.w, l, h); a0 += l * h1[8 * c + 6] + h * h1[8 * c + 7];
+      bf16x2(v.x, l, h); a1 += l * h1[8 * c + 0] + h * h1[8 * c + 1];
+      bf16x2(v.y, l, h); a1 += l * h1[8 * c + 2] + h * h1[8 * c + 3];
+      bf16x2(v.z, l, h); a1 += l * h1[8 * c + 4] + h * h1[8 * c + 5];
+      bf16x2(v.w, l, h); a1 += l * h1[8 * c + 6] + h * h1[8 * c + 7];
+    }
+    float o0, o1;
+    bf16x2(w3[j / 2], o0, o1);
+    y += o0 * tanhf(a0) + o1 * tanhf(a1);
   }
   return net->out_mu + net->out_sd * y;
 }

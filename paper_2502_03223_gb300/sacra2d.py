@@ -117,7 +117,7 @@ def load(path: str = LIB_PATH):
     L.sacra_mlp_bytes.argtypes = []
     L.sacra_mlp_bytes.restype = C.c_size_t
     L.sacra_mlp_collect.argtypes = [vp, vp, C.c_longlong, C.POINTER(C.c_longlong)]
-    L.sacra_mlp_train.argtypes = [vp, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_ulonglong, vp, fp, fp, vp]
+    L.sacra_mlp_train.argtypes = [vp, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_ulonglong, C.c_float, vp, fp, fp, vp]
     L.sacra_mlp_grad.argtypes = [vp, C.c_longlong, vp, fp, fp, vp]
     L.sacra_set_mlp.argtypes = [vp, vp]
     L.sacra_c2p_counting.argtypes = [vp, C.c_int]
@@ -301,7 +301,7 @@ class Sacra:
         return out
 
 
-def mlp_train(tuples, steps=2000, batch_blocks=32, lr=3e-3, seed=1, record_loss=False, stream=None):
+def mlp_train(tuples, steps=2000, batch_blocks=32, lr=3e-3, seed=1, record_loss=False, stream=None, kmin=0.0):
     """Train the recovery seed on the GPU.  tuples: a CUDA float32 tensor of
     shape (n, 10).  Returns (net: CUDA uint8 tensor, report: dict, loss history)."""
     import torch
@@ -312,7 +312,7 @@ def mlp_train(tuples, steps=2000, batch_blocks=32, lr=3e-3, seed=1, record_loss=
     rep = np.zeros(3, dtype=np.float32)
     st = stream if stream is not None else torch.cuda.current_stream()
     fpp = C.POINTER(C.c_float)
-    rc = L.sacra_mlp_train(C.c_void_p(tuples.data_ptr()), tuples.shape[0], steps, batch_blocks, lr, seed,
+    rc = L.sacra_mlp_train(C.c_void_p(tuples.data_ptr()), tuples.shape[0], steps, batch_blocks, lr, seed, kmin,
                            C.c_void_p(net.data_ptr()), hist.ctypes.data_as(fpp) if record_loss else None,
                            rep.ctypes.data_as(fpp), C.c_void_p(st.cuda_stream))
     if rc != SACRA_OK:
@@ -351,9 +351,9 @@ def mlp_unpack(net_bytes):
     b3 = f(o, 1)[0]; o += 4
     in_mu = f(o, 9); o += 36
     in_sd = f(o, 9); o += 36
-    out_mu, out_sd, delta = f(o, 3)
+    out_mu, out_sd, delta, kmin = f(o, 4)
     return {"w1": w1, "b1": b1, "w2": w2, "b2": b2, "w3": w3, "b3": b3, "in_mu": in_mu, "in_sd": in_sd,
-            "out_mu": out_mu, "out_sd": out_sd, "delta": delta}
+            "out_mu": out_mu, "out_sd": out_sd, "delta": delta, "kmin": kmin}
 
 
 class SacraBatch:
@@ -426,6 +426,17 @@ class SacraBatch:
     def tune(self, reps=3):
         self._chk(self._L.sacra_batch_tune(self._b, reps), "batch_tune")
         return self.tuning()
+
+    def mlp_collect(self, out):
+        n = C.c_longlong(0)
+        self._chk(self._L.sacra_batch_mlp_collect(self._b, C.c_void_p(out.data_ptr()), out.shape[0], C.byref(n)),
+                  "batch_mlp_collect")
+        return n.value
+
+    def set_mlp(self, net):
+        self._net = net
+        self._chk(self._L.sacra_batch_set_mlp(self._b, C.c_void_p(net.data_ptr()) if net is not None else None),
+                  "batch_set_mlp")
 
     def tuning(self):
         out = {}

@@ -30,7 +30,7 @@ def _oracle_inputs(tuples, p):
 
 
 def test_network_size():
-    assert S.load().sacra_mlp_bytes() == 10080
+    assert S.load().sacra_mlp_bytes() == 10096        # 16-byte aligned
     assert M.n_params() == S.MLP_NPARAM
 
 
