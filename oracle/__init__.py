@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
         if all(os.path.getmtime(s) <= t for s in srcs):
             return out
     tmp = out + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-o", tmp]
     cmd += [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, out)
@@ -121,6 +121,8 @@ def lib():
             L = C.CDLL(path)
             P = C.POINTER(Params)
             L.orc_create.restype = C.c_void_p
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
             L.orc_create.argtypes = [P]
             L.orc_destroy.argtypes = [C.c_void_p]
             L.orc_set_level.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp]
@@ -196,6 +198,15 @@ def eos_eps(cfg, rho, press):
 
 def eos_cs2(cfg, rho, eps, press):
     return lib().orc_eos_cs2(C.byref(make_params(cfg)), rho, eps, press)
+
+
+def set_threads(n):
+    """Worker threads of the oracle's parallel loops (0: all processors)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return lib().orc_get_threads()
 
 
 def prim2cons(cfg, prim, W, h, x=1.0):

@@ -343,13 +343,16 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
   int cyl = p->geometry == 1;
   double wb = stage_b(p, s);
   int has_child = l < p->n_levels - 1, has_parent = l > 0;
-  /* x-faces j+1/2, j in [0, jmax], rows [1, kmax] */
+  /* x-faces j+1/2, j in [0, jmax], rows [1, kmax] (rows in parallel: each
+     flux-register entry belongs to one row) */
+  int nfb = 0;
+#pragma omp parallel for schedule(static) reduction(+ : nfb)
   for (int k = 1; k <= kmax; ++k)
     for (int j = 0; j <= jmax; ++j) {
       double pl[5], prr[5], al, be[3], W, h[6], f[O_NCONS];
       face_prims(L, j, k, 0, pl, prr);
       face_metric(L, U, j, k, 0, &al, be, &W, h);
-      c->n_fallback += orc_riemann_flux(p, 0, pl, prr, al, be, W, h, f);
+      nfb += orc_riemann_flux(p, 0, pl, prr, al, be, W, h, f);
       double xf = j * L->dx;  /* x_{j+1/2} */
       double area = cyl ? xf * L->dz : L->dz;
       int id = oidx(L, j, k);
@@ -360,13 +363,14 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
       if (has_parent && j == L->nx && k <= L->nz)
         for (int v = 0; v < O_NCONS; ++v) L->freg[1][v][k] += wb * L->fx[v][id];
     }
-  /* z-faces k+1/2 */
+  /* z-faces k+1/2 (the register rows k = nz/2, nz are each one iteration) */
+#pragma omp parallel for schedule(static) reduction(+ : nfb)
   for (int k = 0; k <= kmax; ++k)
     for (int j = 1; j <= jmax; ++j) {
       double pl[5], prr[5], al, be[3], W, h[6], f[O_NCONS];
       face_prims(L, j, k, 1, pl, prr);
       face_metric(L, U, j, k, 1, &al, be, &W, h);
-      c->n_fallback += orc_riemann_flux(p, 1, pl, prr, al, be, W, h, f);
+      nfb += orc_riemann_flux(p, 1, pl, prr, al, be, W, h, f);
       /* equatorial mirror face: D, S_x, S_phi and E are even in z, so their
          z-fluxes vanish on the symmetry plane (only the pressure term of the
          S_z flux remains); the solver reproduces this only up to rounding */
@@ -381,7 +385,9 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
       if (has_parent && k == L->nz && j <= L->nx)
         for (int v = 0; v < O_NCONS; ++v) L->freg[3][v][j] += wb * L->fz[v][id];
     }
+  c->n_fallback += nfb;
   /* divergence and sources */
+#pragma omp parallel for schedule(static)
   for (int k = 1; k <= kmax; ++k)
     for (int j = 1; j <= jmax; ++j) {
       int id = oidx(L, j, k);
@@ -441,6 +447,7 @@ static void z4c_rhs(orc_ctx *c, int l, double **U, int jmax, int kmax) {
     for (int f = 0; f < O_NMET; ++f) { dy[f] = alloc_arr(n); dyy[f] = alloc_arr(n); }
     orc_cartoon_dy(c, l, U, dy, dyy);
   }
+#pragma omp parallel for schedule(static)
   for (int k = 1; k <= kmax; ++k)
     for (int j = 1; j <= jmax; ++j) {
       int id = oidx(L, j, k);
@@ -486,6 +493,7 @@ static void enforce(double **U, int id) {
 
 static void c2p_region(orc_ctx *c, int l, double **U, int j0, int j1, int k0, int k1) {
   orc_level *L = &c->lv[l];
+#pragma omp parallel for schedule(static)
   for (int k = k0; k <= k1; ++k)
     for (int j = j0; j <= j1; ++j) {
       int id = oidx(L, j, k);
@@ -518,6 +526,7 @@ void orc_stage(orc_ctx *c, int s, double dt) {
     region(c, l, s, &jmax, &kmax);
     hydro_rhs(c, l, s, U, jmax, kmax);
     if (p->evolve_spacetime) z4c_rhs(c, l, U, jmax, kmax);
+#pragma omp parallel for schedule(static)
     for (int k = 1; k <= kmax; ++k)
       for (int j = 1; j <= jmax; ++j) {
         int id = oidx(L, j, k);
@@ -741,6 +750,17 @@ void orc_step(orc_ctx *c, double dt, int nsteps) {
 }
 
 int orc_fallbacks(const orc_ctx *c) { return c->n_fallback; }
+
+/* Worker threads of the parallel loops (OpenMP builds; the per-cell
+   arithmetic, hence every result, is the same for any count). */
+#ifdef _OPENMP
+#include <omp.h>
+void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : omp_get_num_procs()); }
+int orc_get_threads(void) { return omp_get_max_threads(); }
+#else
+void orc_set_threads(int n) { (void)n; }
+int orc_get_threads(void) { return 1; }
+#endif
 
 /* Derivatives (central first, second, advection) of every metric field of the
    step-start state at n cells, with the cartoon y-derivatives; for tests. */

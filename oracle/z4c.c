@@ -142,9 +142,10 @@ void orc_cartoon_dy_mask(const orc_ctx *c, int l, double **U, double **dy, doubl
   size_t n = (size_t)L->px * L->pz;
   for (int f = 0; f < O_NMET; ++f) { memset(dy[f], 0, n * sizeof(double)); memset(dyy[f], 0, n * sizeof(double)); }
   cartoon_coef *tab = cartoon_table(L->nx + 4);
-  double pl[7][O_NMET];
+#pragma omp parallel for schedule(static)
   for (int k = -2; k <= L->nz + 7; ++k)
     for (int j = -2; j <= L->nx + 4; ++j) {
+      double pl[7][O_NMET];
       int id = oidx(L, j, k);
       for (int f = 0; f < O_NMET; ++f) pl[3][f] = U[f][id];
       for (int m = 1; m <= 3; ++m) cartoon_planes(c, l, U, tab, j, k, m, pl[3 + m], pl[3 - m], need);
