@@ -39,6 +39,7 @@ struct DevParams {
   double c2p_kmax;       // 2 v_max / (1 + v_max^2), v_max = sqrt(1 - 1 / w_max^2)
   // FP32 copies for the mixed-precision kernels (no conversions on the device)
   float fK, fGamma, fGm1, fGamma_th, fGth1, fkappa, feta_B, firz2, fko;
+  double ko;             // -eps_KO / 256
   // learned seed of the primitive recovery (null: plain bracket) and its counters
   // [Illinois evaluations, recoveries with a seed tried, seeded brackets that held, recoveries]
   const MlpNet *mlp;
@@ -65,6 +66,7 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->fkappa = (float)p->kappa; d->feta_B = (float)p->eta_B;
   d->firz2 = (float)(1.0 / (p->r_z4 * p->r_z4));
   d->fko = (float)(-p->eps_ko / 256.0);
+  d->ko = -p->eps_ko / 256.0;
   const double vmax = sqrt(1.0 - 1.0 / (p->w_max * p->w_max));
   d->c2p_kmax = 2.0 * vmax / (1.0 + vmax * vmax);
 }
@@ -78,6 +80,7 @@ struct Lev {
   int nx, nz, px, pz, rw;
   double dx, dz;
   double i60x, i60z, i180x;     // 1 / (60 dx), 1 / (60 dz), 1 / (180 dx^2)
+  double i180z, ixz, idx, idz;  // 1 / (180 dz^2), 1 / (3600 dx dz), 1 / dx, 1 / dz
   LevF f;
   size_t P;
   double *un, *us, *ka, *rhs;   // NST planes each
@@ -95,6 +98,7 @@ __host__ __device__ inline int cid(const Lev &L, int j, int k) { return (k + GH 
 inline void set_spacing(Lev &L, double dx, double dz) {
   L.dx = dx; L.dz = dz;
   L.i60x = 1.0 / (60.0 * dx); L.i60z = 1.0 / (60.0 * dz); L.i180x = 1.0 / (180.0 * dx * dx);
+  L.i180z = 1.0 / (180.0 * dz * dz); L.ixz = 1.0 / (3600.0 * dx * dz); L.idx = 1.0 / dx; L.idz = 1.0 / dz;
   L.f.dx = (float)dx; L.f.dz = (float)dz; L.f.idx = (float)(1.0 / dx); L.f.idz = (float)(1.0 / dz);
   L.f.i60x = (float)L.i60x; L.f.i60z = (float)L.i60z;
   L.f.i180x = (float)(1.0 / (180.0 * dx * dx)); L.f.i180z = (float)(1.0 / (180.0 * dz * dz));

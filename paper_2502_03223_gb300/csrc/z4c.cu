@@ -336,93 +336,6 @@ __device__ __forceinline__ T fdko(const double *u, int s) {
        + T(28) * (T(u[2 * s] - u0) + T(u[-2 * s] - u0)) - T(56) * (T(u[s] - u0) + T(u[-s] - u0));
 }
 
-template <typename T>
-__device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
-                                                     double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k) {
-  if (j > jmax || k > kmax) return;
-  const size_t P = L.P;
-  const int id = cid(L, j, k);
-  const int sz = L.px;
-  const T i60x = T(1.0 / (60.0 * L.dx)), i60z = T(1.0 / (60.0 * L.dz));
-  const T i180x = T(1.0 / (180.0 * L.dx * L.dx)), i180z = T(1.0 / (180.0 * L.dz * L.dz));
-  const T ixz = T(1.0 / (3600.0 * L.dx * L.dz));
-  const bool edge = cyl && j > L.nx;
-  const T x = T((j - 0.5) * L.dx);
-
-  // first derivatives
-  for (int a = 0; a < 16; ++a) {
-    const int f = kD1Fields[a];
-    const double *u = U + (size_t)f * P + id;
-    DS[(size_t)(DS_D1 + 3 * a + 0) * P + id] = (double)fd1<T>(u, 1, i60x);
-    DS[(size_t)(DS_D1 + 3 * a + 2) * P + id] = (double)fd1<T>(u, sz, i60z);
-    DS[(size_t)(DS_D1 + 3 * a + 1) * P + id] = (cyl && !y_zero(f)) ? L.dy[(size_t)f * P + id] : 0.0;
-  }
-  // second derivatives: xx, xy, xz, yy, yz, zz
-  for (int a = 0; a < 11; ++a) {
-    const int f = kD2Fields[a];
-    const double *u = U + (size_t)f * P + id;
-    T dxz = T(0);
-#pragma unroll
-    for (int n = 1; n <= 3; ++n) {
-      const T w = n == 1 ? T(45) : (n == 2 ? T(-9) : T(1));
-      // d_z at j+n minus d_z at j-n (pair form in both directions, FP64 differences)
-      const T zp = T(45) * T(u[n + sz] - u[n - sz]) - T(9) * T(u[n + 2 * sz] - u[n - 2 * sz]) + T(u[n + 3 * sz] - u[n - 3 * sz]);
-      const T zm = T(45) * T(u[-n + sz] - u[-n - sz]) - T(9) * T(u[-n + 2 * sz] - u[-n - 2 * sz]) + T(u[-n + 3 * sz] - u[-n - 3 * sz]);
-      dxz += w * (zp - zm);
-    }
-    T dxy = T(0), dyz = T(0), dyy = T(0);
-    if (cyl) {
-      dyy = T(L.dyy[(size_t)f * P + id]);
-      if (!y_zero(f) && !edge) {
-        const double *dyf = L.dy + (size_t)f * P + id;
-        dxy = fd1<T>(dyf, 1, i60x);
-        dyz = fd1<T>(dyf, sz, i60z);
-      } else if (!y_zero(f)) {
-        dyz = fd1<T>(L.dy + (size_t)f * P + id, sz, i60z);
-      }
-    }
-    double *o = DS + (size_t)(DS_D2 + 6 * a) * P + id;
-    o[0] = (double)fd2<T>(u, 1, i180x);
-    o[P] = (double)dxy;
-    o[2 * P] = (double)(dxz * ixz);
-    o[3 * P] = (double)dyy;
-    o[4 * P] = (double)dyz;
-    o[5 * P] = (double)fd2<T>(u, sz, i180z);
-  }
-  if (edge) {
-    // Eq. cartoon_bnd for cells beyond the level edge: d_xy from d_x and values
-    const T ix = T(1) / x, ix2 = ix * ix;
-    auto val = [&](int f) { return T(U[(size_t)f * P + id]); };
-    auto ddx = [&](int f) { return fd1<T>(U + (size_t)f * P + id, 1, i60x); };
-    auto put = [&](int a, T v) { DS[(size_t)(DS_D2 + 6 * a + 1) * P + id] = (double)v; };
-    // beta^x, beta^y are D2 entries 8, 9; h_ij entries 1..6 (xx,xy,xz,yy,yz,zz)
-    put(8, val(fBY) * ix2 - ddx(fBY) * ix);
-    put(9, -val(fBX) * ix2 + ddx(fBX) * ix);
-    put(3, val(fHYZ) * ix2 - ddx(fHYZ) * ix);
-    put(5, -val(fHXZ) * ix2 + ddx(fHXZ) * ix);
-    const T txy = val(fHXY) * ix2 - ddx(fHXY) * ix;
-    put(1, T(2) * txy);
-    put(4, T(-2) * txy);
-    put(2, (val(fHYY) - val(fHXX)) * ix2 + (ddx(fHXX) - ddx(fHYY)) * ix);
-  }
-  // advection (lopsided in x, z; central in y from the planes) + KO
-  const T bx = T(U[(size_t)fBX * P + id]), by = T(U[(size_t)fBY * P + id]), bz = T(U[(size_t)fBZ * P + id]);
-  const T ko = T(-p.eps_ko / 256.0);
-  const T ikx = T(1.0 / L.dx), ikz = T(1.0 / L.dz);
-  for (int f = 0; f < NMET; ++f) {
-    const double *u = U + (size_t)f * P + id;
-    T adv = bx * fdlop<T>(u, 1, bx, i60x) + bz * fdlop<T>(u, sz, bz, i60z);
-    if (cyl && !y_zero(f)) adv += by * T(L.dy[(size_t)f * P + id]);
-    adv += ko * (fdko<T>(u, 1) * ikx + fdko<T>(u, sz) * ikz);
-    DS[(size_t)(DS_AK + f) * P + id] = (double)adv;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const double *__restrict__ U,
-                                                     double *__restrict__ DS, int jmax, int kmax, int cyl) {
-  z4c_derivs_cell<T>(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
-}
 
 // Mixed-precision derivative pass.  The block stages each field's tile with
 // a 4-cell halo in shared memory as FP32 (hi, lo) splits (integer bit
@@ -572,6 +485,106 @@ __device__ __forceinline__ void z4c_derivs_f32_tile(const Lev &L, const DevParam
     put(4, -2.0f * txy);
     put(2, (ev[3] - ev[0]) * ix2 + (ed[0] - ed[3]) * ix);
   }
+}
+
+// FP64 derivative pass, one thread per cell: per field the differences
+// u(n) - u(0), n = -4..4, along x and z are formed once and shared by the
+// first and second derivatives, the lopsided advection and the Kreiss-Oliger
+// term (difference form: exact zero on constants).
+__constant__ signed char kD1Of[NMET] = {0, 1, 2, 3, 4, 5, 6, -1, -1, -1, -1, -1, -1, 7, 8, 9, 10, 11, 12, 13, 14, 15, -1, -1, -1};
+__constant__ signed char kD2Of[NMET] = {0, 1, 2, 3, 4, 5, 6, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 7, 8, 9, 10, -1, -1, -1};
+
+template <typename T>
+__device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
+                                                double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k) {
+  static_assert(sizeof(T) == 8, "the FP32 form is z4c_derivs_f32_tile");
+  if (j > jmax || k > kmax) return;
+  const size_t P = L.P;
+  const int id = cid(L, j, k);
+  const int sz = L.px;
+  const double i60x = L.i60x, i60z = L.i60z, i180x = L.i180x, i180z = L.i180z, ixz = L.ixz;
+  const bool edge = cyl && j > L.nx;
+  const double bx = U[(size_t)fBX * P + id], by = U[(size_t)fBY * P + id], bz = U[(size_t)fBZ * P + id];
+  const double ko = p.ko, ikx = L.idx, ikz = L.idz;
+#pragma unroll 1
+  for (int f = 0; f < NMET; ++f) {
+    const double *u = U + (size_t)f * P + id;
+    const double u0 = u[0];
+    double Dx[9], Dz[9];
+#pragma unroll
+    for (int n = -4; n <= 4; ++n) {
+      Dx[n + 4] = n == 0 ? 0.0 : u[n] - u0;
+      Dz[n + 4] = n == 0 ? 0.0 : u[n * sz] - u0;
+    }
+    const int a1 = kD1Of[f], a2 = kD2Of[f];
+    const bool yz = y_zero(f);
+    if (a1 >= 0) {
+      DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (45.0 * (Dx[5] - Dx[3]) - 9.0 * (Dx[6] - Dx[2]) + (Dx[7] - Dx[1])) * i60x;
+      DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (45.0 * (Dz[5] - Dz[3]) - 9.0 * (Dz[6] - Dz[2]) + (Dz[7] - Dz[1])) * i60z;
+      DS[(size_t)(DS_D1 + 3 * a1 + 1) * P + id] = (cyl && !yz) ? L.dy[(size_t)f * P + id] : 0.0;
+    }
+    if (a2 >= 0) {
+      double dxz = 0.0;
+#pragma unroll
+      for (int n = 1; n <= 3; ++n) {
+        const double w = n == 1 ? 45.0 : (n == 2 ? -9.0 : 1.0);
+        // d_z at j+n minus d_z at j-n (pair form in both directions)
+        const double zp = 45.0 * (u[n + sz] - u[n - sz]) - 9.0 * (u[n + 2 * sz] - u[n - 2 * sz]) + (u[n + 3 * sz] - u[n - 3 * sz]);
+        const double zm = 45.0 * (u[-n + sz] - u[-n - sz]) - 9.0 * (u[-n + 2 * sz] - u[-n - 2 * sz]) + (u[-n + 3 * sz] - u[-n - 3 * sz]);
+        dxz += w * (zp - zm);
+      }
+      double dxy = 0.0, dyz = 0.0, dyy = 0.0;
+      if (cyl) {
+        dyy = L.dyy[(size_t)f * P + id];
+        if (!yz) {
+          const double *q = L.dy + (size_t)f * P + id;
+          dyz = (45.0 * (q[sz] - q[-sz]) - 9.0 * (q[2 * sz] - q[-2 * sz]) + (q[3 * sz] - q[-3 * sz])) * i60z;
+          if (!edge) dxy = (45.0 * (q[1] - q[-1]) - 9.0 * (q[2] - q[-2]) + (q[3] - q[-3])) * i60x;
+        }
+      }
+      double *o = DS + (size_t)(DS_D2 + 6 * a2) * P + id;
+      o[0] = (270.0 * (Dx[5] + Dx[3]) - 27.0 * (Dx[6] + Dx[2]) + 2.0 * (Dx[7] + Dx[1])) * i180x;
+      o[P] = dxy;
+      o[2 * P] = dxz * ixz;
+      o[3 * P] = dyy;
+      o[4 * P] = dyz;
+      o[5 * P] = (270.0 * (Dz[5] + Dz[3]) - 27.0 * (Dz[6] + Dz[2]) + 2.0 * (Dz[7] + Dz[1])) * i180z;
+    }
+    // advection: lopsided in x and z (upwind side of the shift), central in y; KO
+    auto lop = [](const double *D, double v) {
+      if (v > 0.0) return 2.0 * D[2] - 24.0 * D[3] + 80.0 * D[5] - 30.0 * D[6] + 8.0 * D[7] - D[8];
+      if (v < 0.0) return -(2.0 * D[6] - 24.0 * D[5] + 80.0 * D[3] - 30.0 * D[2] + 8.0 * D[1] - D[0]);
+      return 0.0;
+    };
+    double adv = bx * (lop(Dx, bx) * i60x) + bz * (lop(Dz, bz) * i60z);
+    if (cyl && !yz) adv += by * L.dy[(size_t)f * P + id];
+    const double kx = (Dx[8] + Dx[0]) - 8.0 * (Dx[7] + Dx[1]) + 28.0 * (Dx[6] + Dx[2]) - 56.0 * (Dx[5] + Dx[3]);
+    const double kz = (Dz[8] + Dz[0]) - 8.0 * (Dz[7] + Dz[1]) + 28.0 * (Dz[6] + Dz[2]) - 56.0 * (Dz[5] + Dz[3]);
+    adv += ko * (kx * ikx + kz * ikz);
+    DS[(size_t)(DS_AK + f) * P + id] = adv;
+  }
+  if (edge) {
+    // Eq. cartoon_bnd for cells beyond the level edge: d_xy from d_x and values
+    const double x = (j - 0.5) * L.dx;
+    const double ix = 1.0 / x, ix2 = ix * ix;
+    auto val = [&](int f) { return U[(size_t)f * P + id]; };
+    auto ddx = [&](int f) { return DS[(size_t)(DS_D1 + 3 * kD1Of[f]) * P + id]; };
+    auto put = [&](int a, double v) { DS[(size_t)(DS_D2 + 6 * a + 1) * P + id] = v; };
+    put(8, val(fBY) * ix2 - ddx(fBY) * ix);
+    put(9, -val(fBX) * ix2 + ddx(fBX) * ix);
+    put(3, val(fHYZ) * ix2 - ddx(fHYZ) * ix);
+    put(5, -val(fHXZ) * ix2 + ddx(fHXZ) * ix);
+    const double txy = val(fHXY) * ix2 - ddx(fHXY) * ix;
+    put(1, 2.0 * txy);
+    put(4, -2.0 * txy);
+    put(2, (val(fHYY) - val(fHXX)) * ix2 + (ddx(fHXX) - ddx(fHYY)) * ix);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const double *__restrict__ U,
+                                                     double *__restrict__ DS, int jmax, int kmax, int cyl) {
+  z4c_derivs_cell<T>(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
 }
 
 __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,
