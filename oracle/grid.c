@@ -37,6 +37,10 @@ orc_ctx *orc_create(const orc_params *p) {
       L->fx[f] = alloc_arr(n); L->fz[f] = alloc_arr(n);
       for (int r = 0; r < 4; ++r) L->freg[r][f] = alloc_arr((size_t)(p->nx > p->nz ? p->nx : p->nz) + 2);
     }
+    for (int f = 0; f < O_NSTATE; ++f) L->uold[f] = alloc_arr(n);
+    for (int f = 0; f < O_NMET; ++f) L->ut[f] = alloc_arr(n);
+    for (int f = 0; f < O_NPRIM; ++f) { L->pold[f] = alloc_arr(n); L->pnow[f] = alloc_arr(n); L->pt[f] = alloc_arr(n); }
+    L->wpar = 1.0;
   }
   return c;
 }
@@ -52,6 +56,9 @@ void orc_destroy(orc_ctx *c) {
       free(L->fx[f]); free(L->fz[f]);
       for (int r = 0; r < 4; ++r) free(L->freg[r][f]);
     }
+    for (int f = 0; f < O_NSTATE; ++f) free(L->uold[f]);
+    for (int f = 0; f < O_NMET; ++f) free(L->ut[f]);
+    for (int f = 0; f < O_NPRIM; ++f) { free(L->pold[f]); free(L->pnow[f]); free(L->pt[f]); }
   }
   free(c);
 }
@@ -179,7 +186,7 @@ static void prol_weights(int j, int *base, double w[8]) {
    Lagrange for the metric, minmod-limited linear for the primitives, then
    conserved variables rebuilt from the primitives. full = refill [N+1, N+8]
    (start of the step), else only [N+5, N+8]. */
-static void prolong_fill(orc_ctx *c, int l, double **U, double **Up, int full) {
+static void prolong_from(orc_ctx *c, int l, double **U, double **Up, double **Pprim, int full) {
   orc_level *L = &c->lv[l], *P = &c->lv[l - 1];
   int lo = full ? L->nx + 1 : L->nx + 5;
   for (int k = 1; k <= L->nz + ORC_G; ++k)
@@ -204,7 +211,7 @@ static void prolong_fill(orc_ctx *c, int l, double **U, double **Up, int full) {
       child_to_parent(k, &mz, &oz);
       double pr[O_NPRIM];
       for (int f = 0; f < O_NPRIM; ++f) {
-        double *a = P->prim[f];
+        double *a = Pprim[f];
         double a0 = a[oidx(P, mx, mz)];
         double sx = minmod(a[oidx(P, mx + 1, mz)] - a0, a0 - a[oidx(P, mx - 1, mz)]);
         double sz = minmod(a[oidx(P, mx, mz + 1)] - a0, a0 - a[oidx(P, mx, mz - 1)]);
@@ -218,6 +225,33 @@ static void prolong_fill(orc_ctx *c, int l, double **U, double **Up, int full) {
       cell_h(U, d, h);
       orc_prim2cons(&c->p, pr, U[O_W][d], h, xc(L, j), q);
       for (int f = 0; f < O_NCONS; ++f) U[O_NMET + f][d] = q[f];
+    }
+}
+
+static void prolong_fill(orc_ctx *c, int l, double **U, double **Up, int full) {
+  prolong_from(c, l, U, Up, c->lv[l - 1].prim, full);
+}
+
+/* Parent data of a sub-cycled level at time t^n + theta (t^{n+1} - t^n) of the
+   parent's step (Sec. II.D): second-order Lagrange through the parent's time
+   slices t^{n-1}, t^n, t^{n+1}; for the primitives first order through
+   t^n, t^{n+1} where (p^{n+1} - p^n)(p^n - p^{n-1}) < 0; first order
+   everywhere while no t^{n-1} slice exists yet. */
+static void time_interp(orc_ctx *c, int lp, double theta) {
+  orc_level *P = &c->lv[lp];
+  size_t n = (size_t)P->px * P->pz;
+  double wm = 0.5 * theta * (theta - 1.0), wp = 0.5 * theta * (theta + 1.0);   /* weights of t^{n-1}, t^{n+1} */
+  /* after the parent's step: un holds t^{n+1}, us holds t^n */
+  for (int f = 0; f < O_NMET; ++f)
+    for (size_t i = 0; i < n; ++i) {
+      double q0 = P->us[f][i], q1 = P->un[f][i];
+      P->ut[f][i] = P->have_old ? q0 + wm * (P->uold[f][i] - q0) + wp * (q1 - q0) : q0 + theta * (q1 - q0);
+    }
+  for (int f = 0; f < O_NPRIM; ++f)
+    for (size_t i = 0; i < n; ++i) {
+      double q0 = P->pnow[f][i], q1 = P->prim[f][i];
+      int quad = P->have_old && !((q1 - q0) * (q0 - P->pold[f][i]) < 0.0);
+      P->pt[f][i] = quad ? q0 + wm * (P->pold[f][i] - q0) + wp * (q1 - q0) : q0 + theta * (q1 - q0);
     }
 }
 
@@ -361,7 +395,7 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
       if (has_child && j == L->nx / 2 && k <= L->nz / 2)
         for (int v = 0; v < O_NCONS; ++v) L->freg[0][v][k] += wb * L->fx[v][id];
       if (has_parent && j == L->nx && k <= L->nz)
-        for (int v = 0; v < O_NCONS; ++v) L->freg[1][v][k] += wb * L->fx[v][id];
+        for (int v = 0; v < O_NCONS; ++v) L->freg[1][v][k] += wb * L->wpar * L->fx[v][id];
     }
   /* z-faces k+1/2 (the register rows k = nz/2, nz are each one iteration) */
 #pragma omp parallel for schedule(static) reduction(+ : nfb)
@@ -383,7 +417,7 @@ static void hydro_rhs(orc_ctx *c, int l, int s, double **U, int jmax, int kmax) 
       if (has_child && k == L->nz / 2 && j <= L->nx / 2)
         for (int v = 0; v < O_NCONS; ++v) L->freg[2][v][j] += wb * L->fz[v][id];
       if (has_parent && k == L->nz && j <= L->nx)
-        for (int v = 0; v < O_NCONS; ++v) L->freg[3][v][j] += wb * L->fz[v][id];
+        for (int v = 0; v < O_NCONS; ++v) L->freg[3][v][j] += wb * L->wpar * L->fz[v][id];
     }
   c->n_fallback += nfb;
   /* divergence and sources */
@@ -510,55 +544,68 @@ static void c2p_region(orc_ctx *c, int l, double **U, int j0, int j1, int k0, in
 
 /* ---------------- one RK stage on all levels ---------------- */
 
+/* One RK stage of level l with step dt.  At stage 0 the level's flux
+   registers at its own child boundary (0, 2) are cleared, those at its parent
+   boundary (1, 3) when reset_parent is set (a sub-cycled level sums them over
+   both of its steps inside one parent step). */
+static void stage_level(orc_ctx *c, int l, int s, double dt, int reset_parent) {
+  const orc_params *p = &c->p;
+  orc_level *L = &c->lv[l];
+  if (s == 0) {
+    size_t rn = sizeof(double) * ((p->nx > p->nz ? p->nx : p->nz) + 2);
+    for (int f = 0; f < O_NCONS; ++f) {
+      memset(L->freg[0][f], 0, rn);
+      memset(L->freg[2][f], 0, rn);
+      if (reset_parent) { memset(L->freg[1][f], 0, rn); memset(L->freg[3][f], 0, rn); }
+    }
+  }
+  double **U = stage_state(c, l, s);
+  int jmax, kmax;
+  region(c, l, s, &jmax, &kmax);
+  hydro_rhs(c, l, s, U, jmax, kmax);
+  if (p->evolve_spacetime) z4c_rhs(c, l, U, jmax, kmax);
+#pragma omp parallel for schedule(static)
+  for (int k = 1; k <= kmax; ++k)
+    for (int j = 1; j <= jmax; ++j) {
+      int id = oidx(L, j, k);
+      for (int f = 0; f < O_NSTATE; ++f) {
+        if (f < O_NMET && !p->evolve_spacetime) continue;
+        double un = L->un[f][id], us = U[f][id], kk = L->rhs[f][id];
+        double out;
+        if (p->rk == 0) {
+          static const double a4[3] = {0.5, 0.5, 1.0};
+          if (s < 3) {
+            L->ka[f][id] = (s == 0 ? 0.0 : L->ka[f][id]) + stage_b(p, s) * kk;
+            out = un + a4[s] * dt * kk;
+          } else {
+            out = un + dt * (L->ka[f][id] + kk / 6.0);
+          }
+        } else {
+          if (s == 0) out = un + dt * kk;
+          else if (s == 1) out = 0.75 * un + 0.25 * us + 0.25 * dt * kk;
+          else out = un / 3.0 + 2.0 / 3.0 * us + 2.0 / 3.0 * dt * kk;
+        }
+        L->us[f][id] = out;
+      }
+      if (p->evolve_spacetime) enforce(L->us, id);
+    }
+  c2p_region(c, l, L->us, 1, jmax, 1, kmax);
+}
+
+static void swap_level(orc_ctx *c, int l) {
+  for (int f = 0; f < O_NSTATE; ++f) {
+    double *t = c->lv[l].un[f]; c->lv[l].un[f] = c->lv[l].us[f]; c->lv[l].us[f] = t;
+  }
+}
+
 void orc_stage(orc_ctx *c, int s, double dt) {
   const orc_params *p = &c->p;
   int S = n_stages(p);
-  if (s == 0) {
-    c->dt_step = dt;
-    for (int l = 0; l < p->n_levels; ++l)
-      for (int r = 0; r < 4; ++r)
-        for (int f = 0; f < O_NCONS; ++f) memset(c->lv[l].freg[r][f], 0, sizeof(double) * ((p->nx > p->nz ? p->nx : p->nz) + 2));
-  }
-  for (int l = 0; l < p->n_levels; ++l) {
-    orc_level *L = &c->lv[l];
-    double **U = stage_state(c, l, s);
-    int jmax, kmax;
-    region(c, l, s, &jmax, &kmax);
-    hydro_rhs(c, l, s, U, jmax, kmax);
-    if (p->evolve_spacetime) z4c_rhs(c, l, U, jmax, kmax);
-#pragma omp parallel for schedule(static)
-    for (int k = 1; k <= kmax; ++k)
-      for (int j = 1; j <= jmax; ++j) {
-        int id = oidx(L, j, k);
-        for (int f = 0; f < O_NSTATE; ++f) {
-          if (f < O_NMET && !p->evolve_spacetime) continue;
-          double un = L->un[f][id], us = U[f][id], kk = L->rhs[f][id];
-          double out;
-          if (p->rk == 0) {
-            static const double a4[3] = {0.5, 0.5, 1.0};
-            if (s < 3) {
-              L->ka[f][id] = (s == 0 ? 0.0 : L->ka[f][id]) + stage_b(p, s) * kk;
-              out = un + a4[s] * dt * kk;
-            } else {
-              out = un + dt * (L->ka[f][id] + kk / 6.0);
-            }
-          } else {
-            if (s == 0) out = un + dt * kk;
-            else if (s == 1) out = 0.75 * un + 0.25 * us + 0.25 * dt * kk;
-            else out = un / 3.0 + 2.0 / 3.0 * us + 2.0 / 3.0 * dt * kk;
-          }
-          L->us[f][id] = out;
-        }
-        if (p->evolve_spacetime) enforce(L->us, id);
-      }
-    c2p_region(c, l, L->us, 1, jmax, 1, kmax);
-  }
+  if (s == 0) c->dt_step = dt;
+  for (int l = 0; l < p->n_levels; ++l) stage_level(c, l, s, dt, 1);
   if (s == S - 1) {
     if (p->geometry == 1) outer_fill(c, c->lv[0].us, dt);
-    for (int l = 0; l < p->n_levels; ++l)
-      for (int f = 0; f < O_NSTATE; ++f) {
-        double *t = c->lv[l].un[f]; c->lv[l].un[f] = c->lv[l].us[f]; c->lv[l].us[f] = t;
-      }
+    for (int l = 0; l < p->n_levels; ++l) swap_level(c, l);
   }
 }
 
@@ -575,10 +622,11 @@ static void rest_weights(int j, int N, int *base, double w[8]) {
   *base = b;
 }
 
-void orc_restrict_reflux(orc_ctx *c) {
-  const orc_params *p = &c->p;
-  if (p->n_levels < 2) return;
-  for (int l = p->n_levels - 1; l >= 1; --l) {
+/* Restriction of level l onto its parent, reflux of the parent cells next to
+   the refinement boundary with the parent's step dt, recovery there, and the
+   parent's axis/equator ghosts. */
+static void restrict_pair(orc_ctx *c, int l, double dt) {
+  {
     orc_level *C = &c->lv[l], *P = &c->lv[l - 1];
     double **Uc = C->un, **Up = P->un;
     /* the child's axis/equator ghosts mirror its final (already restricted) interior */
@@ -611,8 +659,8 @@ void orc_restrict_reflux(orc_ctx *c) {
         }
       }
     /* reflux on the parent cells just outside the child: replace the coarse
-       face flux by the sum of the fine face fluxes (RK-weighted over the step) */
-    double dt = c->dt_step;
+       face flux by the sum of the fine face fluxes (RK-weighted over the step;
+       a sub-cycled child's registers carry dt_child / dt over its two steps) */
     for (int k = 1; k <= Nh; ++k) {
       int d = oidx(P, Nh + 1, k);
       double vp = xc(P, Nh + 1) * P->dx * P->dz;
@@ -632,9 +680,13 @@ void orc_restrict_reflux(orc_ctx *c) {
     c2p_region(c, l - 1, Up, 1, Nh, 1, Nh);
     c2p_region(c, l - 1, Up, Nh + 1, Nh + 1, 1, Nh);
     c2p_region(c, l - 1, Up, 1, Nh, Nh + 1, Nh + 1);
+    /* ghosts of the parent mirror its restricted interior */
+    parity_fill(c, l - 1, Up);
   }
-  /* ghosts of the parents mirror their restricted interiors */
-  for (int l = 0; l < p->n_levels - 1; ++l) parity_fill(c, l, c->lv[l].un);
+}
+
+void orc_restrict_reflux(orc_ctx *c) {
+  for (int l = c->p.n_levels - 1; l >= 1; --l) restrict_pair(c, l, c->dt_step);
 }
 
 /* ---------------- diagnostics, Sec. II.F.1 ---------------- */
@@ -738,14 +790,87 @@ int orc_read(orc_ctx *c, int l, int which, int field, double *out) {
   return 0;
 }
 
-void orc_step(orc_ctx *c, double dt, int nsteps) {
-  int S = n_stages(&c->p);
-  for (int it = 0; it < nsteps; ++it) {
+/* ---------------- Berger-Oliger sub-cycling, Sec. II.D ---------------- */
+
+/* levels [0, G) share the coarse step; levels >= G take half their parent's step */
+static int lockstep_levels(const orc_params *p) {
+  int K = p->subcycle_from;
+  return (K <= 0 || K >= p->n_levels) ? p->n_levels : K;
+}
+
+static void save_now(orc_ctx *c, int l) {
+  orc_level *L = &c->lv[l];
+  size_t n = (size_t)L->px * L->pz;
+  for (int f = 0; f < O_NPRIM; ++f) memcpy(L->pnow[f], L->prim[f], n * sizeof(double));
+}
+
+/* after a parent step and its children's: t^n becomes t^{n-1} (a copy: the
+   stage register keeps fields a frozen-metric run never rewrites) */
+static void rotate_slices(orc_ctx *c, int l) {
+  orc_level *L = &c->lv[l];
+  size_t n = (size_t)L->px * L->pz;
+  for (int f = 0; f < O_NSTATE; ++f) memcpy(L->uold[f], L->us[f], n * sizeof(double));
+  for (int f = 0; f < O_NPRIM; ++f) { double *t = L->pold[f]; L->pold[f] = L->pnow[f]; L->pnow[f] = t; }
+  L->have_old = 1;
+}
+
+/* two steps of dtl of sub-cycled level l inside one step of its parent */
+static void advance_sub(orc_ctx *c, int l, double dtl) {
+  const orc_params *p = &c->p;
+  int S = n_stages(p), L = p->n_levels;
+  c->lv[l].wpar = 0.5;
+  for (int m = 0; m < 2; ++m) {
     for (int s = 0; s < S; ++s) {
-      orc_fill(c, s, dt);
-      orc_stage(c, s, dt);
+      double **U = stage_state(c, l, s);
+      time_interp(c, l - 1, 0.5 * (m + stage_c(p, s)));
+      prolong_from(c, l, U, c->lv[l - 1].ut, c->lv[l - 1].pt, s == 0);
+      parity_fill(c, l, U);
+      if (s == 0 && l + 1 < L) save_now(c, l);
+      stage_level(c, l, s, dtl, m == 0);
     }
-    orc_restrict_reflux(c);
+    swap_level(c, l);
+    if (l + 1 < L) {
+      parity_fill(c, l, c->lv[l].un);
+      advance_sub(c, l + 1, 0.5 * dtl);
+      restrict_pair(c, l + 1, dtl);
+      rotate_slices(c, l);
+    }
+  }
+}
+
+/* nsteps steps of the coarse step dt: levels below subcycle_from in lockstep,
+   then each deeper level twice per step of its parent, restriction and
+   reflux whenever a child has caught up with its parent */
+void orc_step(orc_ctx *c, double dt, int nsteps) {
+  const orc_params *p = &c->p;
+  int S = n_stages(p), L = p->n_levels, G = lockstep_levels(p);
+  for (int it = 0; it < nsteps; ++it) {
+    if (G == L) {
+      for (int s = 0; s < S; ++s) {
+        orc_fill(c, s, dt);
+        orc_stage(c, s, dt);
+      }
+      orc_restrict_reflux(c);
+      continue;
+    }
+    c->dt_step = dt;
+    for (int s = 0; s < S; ++s) {
+      for (int l = 0; l < G; ++l) {
+        double **U = stage_state(c, l, s);
+        if (l == 0) outer_fill(c, U, stage_c(p, s) * dt);
+        else prolong_fill(c, l, U, stage_state(c, l - 1, s), s == 0);
+        parity_fill(c, l, U);
+      }
+      if (s == 0) save_now(c, G - 1);
+      for (int l = 0; l < G; ++l) stage_level(c, l, s, dt, 1);
+    }
+    outer_fill(c, c->lv[0].us, dt);
+    for (int l = 0; l < G; ++l) swap_level(c, l);
+    parity_fill(c, G - 1, c->lv[G - 1].un);
+    advance_sub(c, G, 0.5 * dt);
+    restrict_pair(c, G, dt);
+    rotate_slices(c, G - 1);
+    for (int l = G - 1; l >= 1; --l) restrict_pair(c, l, dt);
   }
 }
 

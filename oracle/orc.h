@@ -48,7 +48,7 @@ typedef struct {
   int solver;            /* 0: HLLC with TVDLF fallback, 1: TVDLF */
   int rk;                /* 0: classical RK4, 1: SSP-RK3 */
   int c2p_maxit;
-  int pad_;
+  int subcycle_from;     /* 0: all levels share one dt (lockstep); K >= 1: levels >= K take dt / 2 of their parent */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;
@@ -69,6 +69,14 @@ typedef struct {
   /* flux registers, RK-weighted sums over the stages of one step:
      0: x-face nx/2+1/2, 1: x-face nx+1/2 (indexed by k), 2: z-face nz/2+1/2, 3: z-face nz+1/2 (indexed by j) */
   double *freg[4][O_NCONS];
+  /* Berger-Oliger sub-cycling (Sec. II.D): this level's state and primitives at
+     t^{n-1} and its primitives at t^n (time slices for a sub-cycled child), and
+     its data interpolated to a stage time of its sub-cycled child */
+  double *uold[O_NSTATE];
+  double *pold[O_NPRIM], *pnow[O_NPRIM];
+  double *ut[O_NMET], *pt[O_NPRIM];
+  int have_old;
+  double wpar;            /* weight of this level's parent-boundary flux registers: dt_l / dt_(l-1) */
 } orc_level;
 
 typedef struct {

@@ -39,6 +39,7 @@ class RunConfig:
     rk: int = 0                # 0 classical RK4, 1 SSP-RK3
     c2p_maxit: int = 100
     precision: int = 0         # 0 FP64, 1 mixed FP32/FP64 (GPU library only; the oracle is FP64)
+    subcycle_from: int = 0     # 0 lockstep; K >= 1: levels >= K take half their parent's step
     dx0: float = 1.0
     dz0: float = 1.0
     kappa: float = 0.0
@@ -74,8 +75,12 @@ class RunConfig:
 
     @property
     def dt(self):
+        """Step of the coarse (lockstep) levels: the finest level's CFL step
+        times 2 per sub-cycled level."""
         f = self.n_levels - 1
-        return self.cfl * min(self.dx(f), self.dz(f))
+        K = self.subcycle_from
+        nsub = 0 if (K <= 0 or K >= self.n_levels) else self.n_levels - K
+        return self.cfl * min(self.dx(f), self.dz(f)) * (1 << nsub)
 
     @property
     def interior_cells(self):
