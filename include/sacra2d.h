@@ -85,6 +85,14 @@ typedef struct {
   int precision;         /* SACRA_FP64, or an OR of SACRA_MIXED_* bits (SACRA_MIXED: all of them); every finite
                             difference of the state, the primitive recovery, the algebraic constraints, the flux
                             divergence, the RK combination and the flux registers stay FP64 in every mode */
+  int subcycle_from;     /* Berger-Oliger sub-cycling (Sec. II.D): 0 = every level takes the step dt given to
+                            sacra_step (lockstep); K >= 1 = levels >= K take half their parent's step
+                            (the paper's l_fix = K - 1), dt being the step of the levels below K.
+                            K >= n_levels is lockstep too.  Single contexts only (a batch star with
+                            1 <= K < n_levels: SACRA_ERR_ARG); on a sub-cycled context the stage-wise
+                            calls (sacra_regrid_ghosts, sacra_rk_stage) return SACRA_ERR_STATE.  Each
+                            parent of a sub-cycled level keeps 2 x 25 metric and 3 x 6 primitive
+                            planes more (its t^{n-1} and t^n slices and their interpolant) */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;   /* cold polytrope P = K rho^Gamma plus thermal Gamma_th law (Sec. II.C.3) */

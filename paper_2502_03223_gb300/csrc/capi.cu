@@ -33,10 +33,20 @@ void lagrange_weights(int n, const double *nodes, double t, double *w) {
 
 size_t round_up(size_t v, size_t m) { return (v + m - 1) / m * m; }
 
+// levels [0, G) share the coarse step; levels >= G take half their parent's step
+int lockstep_levels(const sacra_params *p) {
+  const int K = p->subcycle_from;
+  return (K <= 0 || K >= p->n_levels) ? p->n_levels : K;
+}
+
+// time slices a parent of a sub-cycled level keeps (Sec. II.D): the metric at
+// t^{n-1} and the interpolant, the primitives at t^{n-1}, t^n and the interpolant
+constexpr int kSubPlanes = 2 * NMET + 3 * NPRIM;
+
 // Device memory of one star (hierarchy): per level the state registers,
 // primitives, face fluxes, its own derivative and cartoon scratch (the levels
-// of a stage run concurrently), flux registers and status; then the
-// diagnostic partial sums.
+// of a stage run concurrently), the time slices when sub-cycling, flux
+// registers and status; then the diagnostic partial sums.
 struct Layout {
   size_t P;          // plane stride (doubles), multiple of 32
   int rw;            // flux register row width
@@ -51,7 +61,8 @@ Layout layout(const sacra_params *p) {
   o.P = round_up(px * pz, 32);
   o.rw = (p->nx > p->nz ? p->nx : p->nz) + 2;
   const size_t rwp = round_up((size_t)o.rw, 32);
-  const size_t planes = 4 * NST + NPRIM + 2 * NCONS + (size_t)z4c_scratch_planes() + 2 * NMET;
+  const size_t planes = 4 * NST + NPRIM + 2 * NCONS + (size_t)z4c_scratch_planes() + 2 * NMET +
+                        (lockstep_levels(p) < p->n_levels ? kSubPlanes : 0);
   o.per_level = round_up(planes * o.P * 8 + o.P * 4 /* status */ + 4 * NCONS * rwp * 8, 256);
   o.n_part = p->n_levels * ((p->nx * p->nz + 127) / 128);
   o.part_bytes = round_up((size_t)o.n_part * 9 * 8, 256);
@@ -80,6 +91,7 @@ bool valid(const sacra_params *p, std::string *why) {
   if (!(p->Gamma_th > 1.0) || (p->K != 0.0 && !(p->Gamma > 1.0))) { *why = "EOS indices must exceed 1"; return false; }
   if (!(p->rho_atm > 0) || !(p->w_max > 1) || !(p->c2p_tol > 0) || p->c2p_maxit < 1) { *why = "bad recovery parameters"; return false; }
   if (p->precision & ~SACRA_MIXED) { *why = "unknown precision bits"; return false; }
+  if (p->subcycle_from < 0) { *why = "subcycle_from must be >= 0"; return false; }
   return true;
 }
 
@@ -94,12 +106,12 @@ bool compatible(const sacra_params *a, const sacra_params *b) {
 // kernel kinds for launch counting and the optional per-kernel profile
 enum Kid {
   K_OUTFLOW, K_OUTER, K_PROLONG, K_PARITY_X, K_PARITY_Z, K_FLUX_X, K_FLUX_Z, K_HYDRO_DIV, K_CARTOON, K_Z4C_DERIVS,
-  K_Z4C_POINT, K_RK_UPDATE, K_RESTRICT, K_REFLUX, K_C2P, K_PRIM2CONS, K_DIAG, K_DIAG_FINAL, K_COUNT
+  K_Z4C_POINT, K_RK_UPDATE, K_RESTRICT, K_REFLUX, K_C2P, K_PRIM2CONS, K_DIAG, K_DIAG_FINAL, K_TIME_INTERP, K_COUNT
 };
 const char *kKidName[K_COUNT] = {"k_outflow", "k_outer", "k_prolong", "k_parity_x", "k_parity_z", "k_flux_x",
                                  "k_flux_z", "k_hydro_rhs", "k_cartoon", "k_z4c_derivs", "k_z4c_point",
                                  "k_rk_update", "k_restrict", "k_reflux", "k_c2p_region", "k_prim2cons_all",
-                                 "k_diag", "k_diag_final"};
+                                 "k_diag", "k_diag_final", "k_time_interp"};
 const Kid kKindKid[B_NKIND] = {K_FLUX_X, K_FLUX_Z, K_HYDRO_DIV, K_CARTOON, K_Z4C_DERIVS, K_Z4C_POINT, K_RK_UPDATE};
 
 struct ProfRec {
@@ -118,7 +130,16 @@ struct Star {
   double *part = nullptr;
   double dt_step = 0.0;
   bool have_data[kMaxLevels] = {};
+  int G = 1;                      // levels [0, G) share the coarse step
+  int lpar[kMaxLevels] = {};      // register swaps of each level mod 2
+  // time slices of a parent of a sub-cycled level (levels >= G - 1 with a child)
+  double *uold[kMaxLevels] = {}, *pold[kMaxLevels] = {}, *pnow[kMaxLevels] = {};
+  double *ut[kMaxLevels] = {}, *pt[kMaxLevels] = {};
+  bool have_old[kMaxLevels] = {};
 };
+
+// launch group of level l: 0 = the lockstep levels, then one per sub-cycled level
+int group_of(const Star &st, int l) { return l < st.G ? 0 : l - st.G + 1; }
 
 // ---- tile shapes and the autotuner's choice per kernel kind
 struct Shape {
@@ -177,11 +198,13 @@ struct Engine {
   int sms = 1;
   // plan of the batched launches
   std::vector<std::pair<int, int>> slots;   // (star, level)
+  std::vector<int> slot_group;    // launch group of each slot
+  std::vector<int> group_first;   // first slot of each group
+  int ngroups = 1;
   BL *bl_dev = nullptr;           // [2 parities][S][slots], then 2 x slots tuning copies
   Tile *tiles_dev = nullptr;
   size_t tiles_cap = 0, tune_cap = 0;
-  long long toff[4][B_NKIND] = {}, tcnt[4][B_NKIND] = {};
-  long long cells[4][B_NKIND] = {};
+  std::vector<long long> toff, tcnt, cells;   // [group][stage][kind]
   KindCfg cfg[B_NKIND];
   // bookkeeping
   long long launches = 0;
@@ -189,7 +212,7 @@ struct Engine {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   double gdt[2] = {0.0, 0.0};
   long long glaunch[2] = {0, 0};
-  int parity = 0;    // number of register swaps mod 2
+  int parity = 0;    // register swaps of group 0 mod 2 (the key of the step graphs)
   bool capturing = false;
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -278,7 +301,7 @@ BL make_bl(const Engine &e, int slot, int par, int s) {
   BL b;
   b.L = st.lv[l];
   b.P = st.dp;
-  if (par != e.parity) std::swap(b.L.un, b.L.us);   // st.lv holds the registers of the current parity
+  if (par != st.lpar[l]) std::swap(b.L.un, b.L.us);   // st.lv holds the registers of the current parity
   b.U = s == 0 ? b.L.un : b.L.us;
   b.DS = st.ds[l];
   const int ext = (l > 0 && s < e.S - 1) ? 4 : 0;
@@ -287,21 +310,34 @@ BL make_bl(const Engine &e, int slot, int par, int s) {
   b.has_child = l < st.prm.n_levels - 1;
   b.has_parent = l > 0;
   b.wb = stage_b(st.prm.rk, s);
+  b.wbp = l >= st.G ? 0.5 * b.wb : b.wb;             // a sub-cycled level registers two steps of dt / 2
   return b;
 }
 
-void build_tiles(const Engine &e, int s, int kind, Shape sh, std::vector<Tile> &out) {
+size_t plan_index(int g, int s, int kind) { return ((size_t)g * 4 + s) * B_NKIND + kind; }
+
+// register parity of launch group g (all its levels swap together)
+int group_parity(const Engine &e, int g) {
+  const auto &sl = e.slots[e.group_first[g]];
+  return e.stars[sl.first].lpar[sl.second];
+}
+
+// tiles of the slots of group g (every slot for g < 0)
+void build_tiles(const Engine &e, int g, int s, int kind, Shape sh, std::vector<Tile> &out) {
   out.clear();
   for (int i = 0; i < (int)e.slots.size(); ++i) {
+    if (g >= 0 && e.slot_group[i] != g) continue;
     const Region r = kind_region(e.stars[e.slots[i].first].prm, e.slots[i].second, s, e.S, kind);
     for (int k0 = r.k0; k0 <= r.k1; k0 += sh.y)
       for (int j0 = r.j0; j0 <= r.j1; j0 += sh.x) out.push_back(Tile{i, j0, k0, 0});
   }
 }
 
-long long region_cells(const Engine &e, int s, int kind) {
+long long region_cells(const Engine &e, int g, int s, int kind) {
   long long n = 0;
-  for (const auto &sl : e.slots) {
+  for (int i = 0; i < (int)e.slots.size(); ++i) {
+    if (e.slot_group[i] != g) continue;
+    const auto &sl = e.slots[i];
     const Region r = kind_region(e.stars[sl.first].prm, sl.second, s, e.S, kind);
     n += (long long)(r.j1 - r.j0 + 1) * (r.k1 - r.k0 + 1);
   }
@@ -324,7 +360,8 @@ long long max_tiles(const std::vector<sacra_params> &ps, int S, int s, int kind)
   return std::max(m, count_tiles(ps, S, s, kind, Shape{(int)f.x, (int)f.y}));
 }
 
-// tile capacity: every stage and kind at its largest count, then a tuning area
+// tile capacity: every stage and kind at its largest count (the groups
+// partition the slots, so their lists add up to the same), then a tuning area
 void plan_caps(const std::vector<sacra_params> &ps, size_t *cap, size_t *tune) {
   const int S = ps[0].rk == SACRA_RK4 ? 4 : 3;
   *cap = 0;
@@ -355,14 +392,20 @@ sacra_status upload_plan(Engine &e) {
       for (int i = 0; i < NL; ++i) bls[((size_t)par * e.S + s) * NL + i] = make_bl(e, i, par, s);
   cudaMemcpyAsync(e.bl_dev, bls.data(), bls.size() * sizeof(BL), cudaMemcpyHostToDevice, e.stream);
   std::vector<Tile> all, t;
-  for (int s = 0; s < e.S; ++s)
-    for (int kind = 0; kind < B_NKIND; ++kind) {
-      build_tiles(e, s, kind, kind_shape(e, kind), t);
-      e.toff[s][kind] = (long long)all.size();
-      e.tcnt[s][kind] = (long long)t.size();
-      e.cells[s][kind] = region_cells(e, s, kind);
-      all.insert(all.end(), t.begin(), t.end());
-    }
+  const size_t np = plan_index(e.ngroups, 0, 0);
+  e.toff.assign(np, 0);
+  e.tcnt.assign(np, 0);
+  e.cells.assign(np, 0);
+  for (int g = 0; g < e.ngroups; ++g)
+    for (int s = 0; s < e.S; ++s)
+      for (int kind = 0; kind < B_NKIND; ++kind) {
+        build_tiles(e, g, s, kind, kind_shape(e, kind), t);
+        const size_t i = plan_index(g, s, kind);
+        e.toff[i] = (long long)all.size();
+        e.tcnt[i] = (long long)t.size();
+        e.cells[i] = region_cells(e, g, s, kind);
+        all.insert(all.end(), t.begin(), t.end());
+      }
   if (all.size() > e.tiles_cap) return fail(e, SACRA_ERR_OOM, "tile capacity exceeded");
   cudaMemcpyAsync(e.tiles_dev, all.data(), all.size() * sizeof(Tile), cudaMemcpyHostToDevice, e.stream);
   // the host vectors must live until the copies are done
@@ -370,15 +413,15 @@ sacra_status upload_plan(Engine &e) {
   return cuda_check(e, "upload plan");
 }
 
-Batch batch_of(const Engine &e, int s, int kind) {
+Batch batch_of(const Engine &e, int g, int s, int kind) {
   Batch b;
-  b.bl = e.bl_dev + ((size_t)e.parity * e.S + s) * e.slots.size();
-  b.tiles = e.tiles_dev + e.toff[s][kind];
-  b.ntiles = (int)e.tcnt[s][kind];
+  b.bl = e.bl_dev + ((size_t)group_parity(e, g) * e.S + s) * e.slots.size();
+  b.tiles = e.tiles_dev + e.toff[plan_index(g, s, kind)];
+  b.ntiles = (int)e.tcnt[plan_index(g, s, kind)];
   const Shape sh = kind_shape(e, kind);
   b.block = dim3(sh.x, sh.y);
-  const long long g = (long long)e.sms * e.cfg[kind].blocks_per_sm;
-  b.grid = (int)std::max(1LL, std::min<long long>(g, b.ntiles));
+  const long long nb = (long long)e.sms * e.cfg[kind].blocks_per_sm;
+  b.grid = (int)std::max(1LL, std::min<long long>(nb, b.ntiles));
   return b;
 }
 
@@ -422,34 +465,58 @@ void enqueue_fill(Engine &e, Star &st, int s, double dt) {
   }
 }
 
-void swap_registers(Engine &e) {
-  for (Star &st : e.stars)
-    for (int l = 0; l < st.prm.n_levels; ++l) std::swap(st.lv[l].un, st.lv[l].us);
-  e.parity ^= 1;
+// swap the step and stage registers of the levels of group g
+void swap_group(Engine &e, int g) {
+  for (size_t i = 0; i < e.slots.size(); ++i) {
+    if (e.slot_group[i] != g) continue;
+    Star &st = e.stars[e.slots[i].first];
+    const int l = e.slots[i].second;
+    std::swap(st.lv[l].un, st.lv[l].us);
+    st.lpar[l] ^= 1;
+  }
+  if (g == 0) e.parity ^= 1;
 }
 
-// one RK stage of every level of every star: one batched launch per kernel kind
-void enqueue_stage(Engine &e, int s, double dt) {
+// One RK stage of the levels of group g with step dt: one batched launch per
+// kernel kind.  At stage 0 the flux registers at each level's child boundary
+// are cleared, those at its parent boundary when reset_parent is set (a
+// sub-cycled level sums them over both of its steps inside a parent step).
+// After the last stage: level 0's outer boundary, then the register swap.
+void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) {
   if (s == 0)
-    for (Star &st : e.stars) {
-      st.dt_step = dt;
-      for (int l = 0; l < st.prm.n_levels; ++l)
-        cudaMemsetAsync(st.lv[l].freg, 0, (size_t)4 * NCONS * st.lv[l].rw * sizeof(double), e.stream);
+    for (size_t i = 0; i < e.slots.size(); ++i) {
+      if (e.slot_group[i] != g) continue;
+      Star &st = e.stars[e.slots[i].first];
+      const Lev &L = st.lv[e.slots[i].second];
+      const size_t reg = (size_t)NCONS * L.rw;   // doubles per register
+      if (g == 0) st.dt_step = dt;
+      if (reset_parent) {
+        cudaMemsetAsync(L.freg, 0, 4 * reg * sizeof(double), e.stream);
+      } else {
+        cudaMemsetAsync(L.freg, 0, reg * sizeof(double), e.stream);
+        cudaMemsetAsync(L.freg + 2 * reg, 0, reg * sizeof(double), e.stream);
+      }
     }
   for (int kind = 0; kind < B_NKIND; ++kind) {
     if (!kind_used(e, kind)) continue;
-    const Batch b = batch_of(e, s, kind);
-    run(e, kKindKid[kind], e.cells[s][kind], [&] { launch_kind(e, kind, b, s, dt); });
+    const Batch b = batch_of(e, g, s, kind);
+    run(e, kKindKid[kind], e.cells[plan_index(g, s, kind)], [&] { launch_kind(e, kind, b, s, dt); });
   }
   if (s == e.S - 1) {
-    for (Star &st : e.stars)
-      if (st.prm.geometry == SACRA_CYLINDRICAL) {
-        const Lev &L0 = st.lv[0];
-        run(e, K_OUTER, (long long)(L0.nx + GH) * (L0.nz + GH) - (long long)L0.nx * L0.nz,
-            [&] { launch_outer(L0, L0.un, L0.us, dt, e.stream); });
-      }
-    swap_registers(e);
+    if (g == 0)
+      for (Star &st : e.stars)
+        if (st.prm.geometry == SACRA_CYLINDRICAL) {
+          const Lev &L0 = st.lv[0];
+          run(e, K_OUTER, (long long)(L0.nx + GH) * (L0.nz + GH) - (long long)L0.nx * L0.nz,
+              [&] { launch_outer(L0, L0.un, L0.us, dt, e.stream); });
+        }
+    swap_group(e, g);
   }
+}
+
+// one RK stage of every level of every star (all levels with the same dt)
+void enqueue_stage(Engine &e, int s, double dt) {
+  for (int g = 0; g < e.ngroups; ++g) enqueue_group_stage(e, g, s, dt, true);
 }
 
 void enqueue_restrict(Engine &e, Star &st) {
@@ -469,12 +536,119 @@ void enqueue_restrict(Engine &e, Star &st) {
   for (int l = 0; l < L - 1; ++l) enqueue_parity(e, st, l, st.lv[l].un);
 }
 
+// ---- Berger-Oliger sub-cycling (Sec. II.D)
+
+// restriction of level l onto its parent and reflux with the parent's step dt,
+// recovery there, and the parent's axis/equator ghosts
+void enqueue_restrict_pair(Engine &e, Star &st, int l, double dt) {
+  Lev &C = st.lv[l], &Pa = st.lv[l - 1];
+  enqueue_parity(e, st, l, C.un);
+  const int nh = Pa.nx / 2;
+  run(e, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, e.stream); });
+  run(e, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, dt, e.stream); });
+  run(e, K_C2P, (long long)(nh + 1) * (nh + 1) - 1,
+      [&] { launch_c2p_region(Pa, st.dp, Pa.un, 1, nh + 1, 1, nh + 1, e.stream, 1); });
+  enqueue_parity(e, st, l - 1, Pa.un);
+}
+
+// the primitives at t^n of a parent, taken at the start of its step
+void save_now(Engine &e, Star &st, int l) {
+  const Lev &L = st.lv[l];
+  cudaMemcpyAsync(st.pnow[l], L.prim, (size_t)NPRIM * L.P * sizeof(double), cudaMemcpyDeviceToDevice, e.stream);
+}
+
+// after a parent step and its children's: the t^n slice becomes t^{n-1}
+void rotate_slices(Engine &e, Star &st, int l) {
+  const Lev &L = st.lv[l];
+  cudaMemcpyAsync(st.uold[l], L.us, (size_t)NMET * L.P * sizeof(double), cudaMemcpyDeviceToDevice, e.stream);
+  cudaMemcpyAsync(st.pold[l], st.pnow[l], (size_t)NPRIM * L.P * sizeof(double), cudaMemcpyDeviceToDevice, e.stream);
+  st.have_old[l] = true;
+}
+
+// buffer zone of sub-cycled level l at stage s from its parent at t^n + theta dt_parent
+void enqueue_sub_fill(Engine &e, Star &st, int l, int s, double theta) {
+  const Lev &L = st.lv[l];
+  const Lev &Pa = st.lv[l - 1];
+  double *U = stage_state(st, l, s);
+  const long long np = (long long)Pa.px * Pa.pz;
+  run(e, K_TIME_INTERP, np * (NMET + NPRIM), [&] {
+    launch_time_interp(Pa, st.uold[l - 1], st.pold[l - 1], st.pnow[l - 1], st.ut[l - 1], st.pt[l - 1], theta,
+                       st.have_old[l - 1] ? 1 : 0, e.stream);
+  });
+  Lev Pt = Pa;
+  Pt.prim = st.pt[l - 1];
+  run(e, K_PROLONG, prolong_cells(L, s == 0), [&] { launch_prolong(L, Pt, st.dp, U, st.ut[l - 1], s == 0, e.stream); });
+  ++e.launches;   // the prolongation is two kernels
+  enqueue_parity(e, st, l, U);
+}
+
+// two steps of dtl of sub-cycled level l inside one step of its parent
+void advance_sub(Engine &e, Star &st, int l, double dtl) {
+  const int L = st.prm.n_levels, g = group_of(st, l);
+  for (int m = 0; m < 2; ++m) {
+    for (int s = 0; s < e.S; ++s) {
+      enqueue_sub_fill(e, st, l, s, 0.5 * (m + stage_c(st.prm.rk, s)));
+      if (s == 0 && l + 1 < L) save_now(e, st, l);
+      enqueue_group_stage(e, g, s, dtl, m == 0);
+    }
+    if (l + 1 < L) {
+      enqueue_parity(e, st, l, st.lv[l].un);
+      advance_sub(e, st, l + 1, 0.5 * dtl);
+      enqueue_restrict_pair(e, st, l + 1, dtl);
+      rotate_slices(e, st, l);
+    }
+  }
+}
+
+// one coarse step of a sub-cycled star: the lockstep levels [0, G) with dt,
+// each deeper level twice per step of its parent, restriction and reflux
+// whenever a child has caught up with its parent
+void enqueue_step_sub(Engine &e, Star &st, double dt) {
+  const int G = st.G;
+  for (int s = 0; s < e.S; ++s) {
+    for (int l = 0; l < G; ++l) {
+      double *U = stage_state(st, l, s);
+      const Lev &Lv = st.lv[l];
+      if (l == 0) {
+        run(e, K_OUTER, (long long)(Lv.nx + GH) * (Lv.nz + GH) - (long long)Lv.nx * Lv.nz,
+            [&] { launch_outer(Lv, Lv.un, U, stage_c(st.prm.rk, s) * dt, e.stream); });
+      } else {
+        double *Up = stage_state(st, l - 1, s);
+        run(e, K_PROLONG, prolong_cells(Lv, s == 0),
+            [&] { launch_prolong(Lv, st.lv[l - 1], st.dp, U, Up, s == 0, e.stream); });
+        ++e.launches;
+      }
+      enqueue_parity(e, st, l, U);
+    }
+    if (s == 0) save_now(e, st, G - 1);
+    enqueue_group_stage(e, 0, s, dt, true);
+  }
+  enqueue_parity(e, st, G - 1, st.lv[G - 1].un);
+  advance_sub(e, st, G, 0.5 * dt);
+  enqueue_restrict_pair(e, st, G, dt);
+  rotate_slices(e, st, G - 1);
+  for (int l = G - 1; l >= 1; --l) enqueue_restrict_pair(e, st, l, dt);
+}
+
 void enqueue_step(Engine &e, double dt) {
+  if (e.ngroups > 1) {           // a sub-cycled star (single contexts only)
+    enqueue_step_sub(e, e.stars[0], dt);
+    return;
+  }
   for (int s = 0; s < e.S; ++s) {
     for (Star &st : e.stars) enqueue_fill(e, st, s, dt);
     enqueue_stage(e, s, dt);
   }
   for (Star &st : e.stars) enqueue_restrict(e, st);
+}
+
+// every parent of a sub-cycled level holds a t^{n-1} slice (the time
+// interpolation's order is then fixed, and a captured step can be replayed)
+bool steady(const Engine &e) {
+  for (const Star &st : e.stars)
+    for (int l = st.G - 1; l < st.prm.n_levels - 1; ++l)
+      if (!st.have_old[l]) return false;
+  return true;
 }
 
 bool ready(const Engine &e) {
@@ -508,7 +682,7 @@ sacra_status tune(Engine &e, int reps) {
   const int NL = (int)e.slots.size();
   std::vector<BL> tv(2 * (size_t)NL);
   for (int i = 0; i < NL; ++i) {
-    BL b = make_bl(e, i, e.parity, 0);
+    BL b = make_bl(e, i, e.stars[e.slots[i].first].lpar[e.slots[i].second], 0);
     b.has_child = b.has_parent = 0;
     tv[i] = b;
     double *scr = reinterpret_cast<double *>(b.DS);
@@ -532,7 +706,7 @@ sacra_status tune(Engine &e, int reps) {
   sacra_status status = SACRA_OK;
   // coordinate descent per kind: the grid size at the current shape, then the shape at that grid size
   auto time_cfg = [&](int kind, Shape sh, int m, float *ms) -> sacra_status {
-    build_tiles(e, 0, kind, sh, t);
+    build_tiles(e, -1, 0, kind, sh, t);
     if (t.size() > e.tune_cap) { *ms = 1e30f; return SACRA_OK; }
     cudaMemcpyAsync(tune_tiles, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, e.stream);
     Batch bt;
@@ -605,6 +779,13 @@ void init_star_levels(Star &st, char *base) {
     st.ds[l] = dp; dp += (size_t)z4c_scratch_planes() * P;
     L.dy = dp; dp += NMET * P;
     L.dyy = dp; dp += NMET * P;
+    if (st.G < p->n_levels) {
+      st.uold[l] = dp; dp += NMET * P;
+      st.ut[l] = dp; dp += NMET * P;
+      st.pold[l] = dp; dp += NPRIM * P;
+      st.pnow[l] = dp; dp += NPRIM * P;
+      st.pt[l] = dp; dp += NPRIM * P;
+    }
     L.freg = dp; dp += 4 * NCONS * rwp;
     L.status = (int *)dp;
   }
@@ -683,11 +864,18 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
     st.prm = ps[i];
     fill_dev_params(&ps[i], &st.dp);
     st.lay = layout(&ps[i]);
+    st.G = lockstep_levels(&ps[i]);
     init_star_levels(st, p);
     p += star_bytes(&ps[i]);
     max_nx = std::max(max_nx, ps[i].nx);
-    for (int l = 0; l < ps[i].n_levels; ++l) e.slots.push_back({(int)i, l});
+    for (int l = 0; l < ps[i].n_levels; ++l) {
+      const int g = group_of(st, l);
+      if (g >= (int)e.group_first.size()) e.group_first.push_back((int)e.slots.size());
+      e.slots.push_back({(int)i, l});
+      e.slot_group.push_back(g);
+    }
   }
+  e.ngroups = (int)e.group_first.size();
   e.tab = (double *)p;
   p += round_up((size_t)(max_nx + 8) * 3 * kTabStride * 8, 256);
   e.dout = (double *)p;
@@ -741,6 +929,7 @@ sacra_status set_initial_data(Engine &e, int star, int level, int kind, const do
   cudaMemcpyAsync(L.us, L.un, (size_t)NST * L.P * 8, cudaMemcpyDeviceToDevice, e.stream);
   if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "set_initial_data");
   st.have_data[level] = true;
+  for (int l = 0; l < st.prm.n_levels; ++l) st.have_old[l] = false;   // no earlier time slice of the new data
   return cuda_check(e, "set_initial_data");
 }
 
@@ -748,7 +937,7 @@ sacra_status step(Engine &e, double dt, int n_steps, int use_graph) {
   if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
   if (!(dt > 0) || n_steps < 0) return fail(e, SACRA_ERR_ARG, "bad dt or n_steps");
   for (int it = 0; it < n_steps; ++it) {
-    if (!use_graph) {
+    if (!use_graph || !steady(e)) {
       enqueue_step(e, dt);
       continue;
     }
@@ -760,12 +949,12 @@ sacra_status step(Engine &e, double dt, int n_steps, int use_graph) {
       if (cudaStreamBeginCapture(e.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return cuda_check(e, "graph capture (the stream must be a non-default stream)");
       e.capturing = true;
-      enqueue_step(e, dt);       // swaps the registers on the host side
-      e.capturing = false;
+      enqueue_step(e, dt);       // swaps the registers on the host side (a sub-cycled
+      e.capturing = false;       // level swaps an even number of times per step)
       if (cudaStreamEndCapture(e.stream, &g) != cudaSuccess) return cuda_check(e, "graph capture");
       e.glaunch[par] = e.launches - before;
       e.launches = before;
-      swap_registers(e);         // undo: the graph has not run yet
+      swap_group(e, 0);          // undo: the graph has not run yet
       if (cudaGraphInstantiate(&e.gexec[par], g, 0) != cudaSuccess) {
         cudaGraphDestroy(g);
         return cuda_check(e, "graph instantiate");
@@ -776,7 +965,7 @@ sacra_status step(Engine &e, double dt, int n_steps, int use_graph) {
     if (cudaGraphLaunch(e.gexec[par], e.stream) != cudaSuccess) return cuda_check(e, "graph launch");
     e.launches += e.glaunch[par];
     for (Star &st : e.stars) st.dt_step = dt;
-    swap_registers(e);
+    swap_group(e, 0);
   }
   return cuda_check(e, "step");
 }
@@ -940,11 +1129,14 @@ sacra_status mlp_collect(Engine &e, float *dev_out, long long cap, long long *n)
   return cuda_check(e, "mlp_collect");
 }
 
+// a batch's stars share one launch group per stage, so none of them sub-cycles
 bool params_ok(const sacra_params *per_star, int n) {
   if (!per_star || n < 1) return false;
   std::string why;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!valid(&per_star[i], &why) || !compatible(&per_star[i], &per_star[0])) return false;
+    if (n > 1 && lockstep_levels(&per_star[i]) < per_star[i].n_levels) return false;
+  }
   return true;
 }
 
@@ -985,6 +1177,7 @@ sacra_status sacra_regrid_ghosts(sacra_ctx *c, int what, int stage, double dt) {
   if (!c) return SACRA_ERR_ARG;
   Engine &e = c->e;
   if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  if (e.ngroups > 1) return fail(e, SACRA_ERR_STATE, "stage-wise calls need a lockstep context");
   if (what == SACRA_FILL) {
     if (stage < 0 || stage >= e.S) return fail(e, SACRA_ERR_ARG, "bad stage");
     enqueue_fill(e, e.stars[0], stage, dt);
@@ -1000,6 +1193,7 @@ sacra_status sacra_rk_stage(sacra_ctx *c, int stage, double dt) {
   if (!c) return SACRA_ERR_ARG;
   Engine &e = c->e;
   if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  if (e.ngroups > 1) return fail(e, SACRA_ERR_STATE, "stage-wise calls need a lockstep context");
   if (stage < 0 || stage >= e.S || !(dt > 0)) return fail(e, SACRA_ERR_ARG, "bad stage or dt");
   enqueue_stage(e, stage, dt);
   return cuda_check(e, "rk_stage");

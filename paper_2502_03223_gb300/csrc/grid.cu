@@ -299,6 +299,37 @@ void launch_b_rk_update(const Batch &b, const DevParams &p, int stage, double dt
   else kb_rk_update<false><<<b.grid, b.block, 0, s>>>(b, p, stage, dt);
 }
 
+// Parent data of a sub-cycled child at time t^n + theta (t^{n+1} - t^n)
+// (Sec. II.D): second-order Lagrange through the parent's slices t^{n-1}
+// (uold, pold), t^n (us, pnow), t^{n+1} (un, prim) in difference form about
+// t^n; first order through t^n, t^{n+1} for a primitive where
+// (p^{n+1} - p^n)(p^n - p^{n-1}) < 0, and everywhere while have_old = 0.
+// One thread per padded cell and plane (25 metric planes, then 6 primitives).
+__global__ void k_time_interp(Lev P, const double *__restrict__ uold, const double *__restrict__ pold,
+                              const double *__restrict__ pnow, double *__restrict__ ut, double *__restrict__ pt,
+                              double theta, int have_old) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.px * P.pz) return;
+  const int f = blockIdx.y;
+  const double wm = 0.5 * theta * (theta - 1.0), wp = 0.5 * theta * (theta + 1.0);
+  if (f < NMET) {
+    const size_t o = (size_t)f * P.P + i;
+    const double q0 = P.us[o], q1 = P.un[o];
+    ut[o] = have_old ? q0 + wm * (uold[o] - q0) + wp * (q1 - q0) : q0 + theta * (q1 - q0);
+  } else {
+    const size_t o = (size_t)(f - NMET) * P.P + i;
+    const double q0 = pnow[o], q1 = P.prim[o];
+    const bool quad = have_old && !((q1 - q0) * (q0 - pold[o]) < 0.0);
+    pt[o] = quad ? q0 + wm * (pold[o] - q0) + wp * (q1 - q0) : q0 + theta * (q1 - q0);
+  }
+}
+
+void launch_time_interp(const Lev &P, const double *uold, const double *pold, const double *pnow, double *ut,
+                        double *pt, double theta, int have_old, cudaStream_t s) {
+  const int n = P.px * P.pz;
+  k_time_interp<<<dim3((n + 255) / 256, NMET + NPRIM), 256, 0, s>>>(P, uold, pold, pnow, ut, pt, theta, have_old);
+}
+
 // Restriction of child level C onto parent cells [1, N/2]^2 (Sec. II.D):
 // q as the volume-weighted average of the 2x2 children, the metric by 8th-
 // order Lagrange (nodes shifted inward so that none passes the child edge N).

@@ -175,7 +175,7 @@ __device__ inline void flux_face(const Lev &L, const DevParams &p, const double 
 // and accumulates the flux registers of the refinement boundaries.
 template <typename T>
 __device__ __forceinline__ void flux_x_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
-                                                 double wb, int has_child, int has_parent, int j, int k) {
+                                                 double wb, int has_child, int has_parent, int j, int k, double wbp) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
@@ -194,19 +194,19 @@ __device__ __forceinline__ void flux_x_cell(const Lev &L, const DevParams &p, co
     for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(0 * NCONS + v) * L.rw + k] += wb * f[v];
   if (has_parent && j == L.nx && k <= L.nz)
 #pragma unroll
-    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(1 * NCONS + v) * L.rw + k] += wb * f[v];
+    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(1 * NCONS + v) * L.rw + k] += wbp * f[v];
   if (fb) atomicAdd(L.nfb, 1ull);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent) {
-  flux_x_cell<T>(L, p, U, jmax, kmax, wb, has_child, has_parent, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1);
+  flux_x_cell<T>(L, p, U, jmax, kmax, wb, has_child, has_parent, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1, wb);
 }
 
 template <typename T>
 __device__ __forceinline__ void flux_z_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
-                                                 double wb, int has_child, int has_parent, int j, int k) {
+                                                 double wb, int has_child, int has_parent, int j, int k, double wbp) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
@@ -227,14 +227,14 @@ __device__ __forceinline__ void flux_z_cell(const Lev &L, const DevParams &p, co
     for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(2 * NCONS + v) * L.rw + j] += wb * f[v];
   if (has_parent && k == L.nz && j <= L.nx)
 #pragma unroll
-    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(3 * NCONS + v) * L.rw + j] += wb * f[v];
+    for (int v = 0; v < NCONS; ++v) L.freg[(size_t)(3 * NCONS + v) * L.rw + j] += wbp * f[v];
   if (fb) atomicAdd(L.nfb, 1ull);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_flux_z(Lev L, DevParams p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent) {
-  flux_z_cell<T>(L, p, U, jmax, kmax, wb, has_child, has_parent, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y);
+  flux_z_cell<T>(L, p, U, jmax, kmax, wb, has_child, has_parent, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y, wb);
 }
 
 // 6th-order central first derivative: exact differences (FP64, or FP32 from
@@ -400,14 +400,14 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
 template <typename T>
 __global__ void __launch_bounds__(256) kb_flux_x(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
-    flux_x_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+    flux_x_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y, q.wbp);
   });
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) kb_flux_z(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
-    flux_z_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+    flux_z_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y, q.wbp);
   });
 }
 

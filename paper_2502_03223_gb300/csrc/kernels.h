@@ -23,7 +23,8 @@ struct BL {                 // one level of one star as a stage sees it
   void *DS;                 // this level's derivative scratch (FP64 or FP32 planes)
   int jmax, kmax;           // update region [1, jmax] x [1, kmax]
   int has_child, has_parent;
-  double wb;                // RK weight of this stage's fluxes in the flux registers
+  double wb;                // RK weight of this stage's fluxes in the child-boundary flux registers
+  double wbp;               // ... in the parent-boundary registers (wb dt_level / dt_parent)
 };
 struct Tile {               // one block's worth of cells of one level
   int bl, j0, k0, pad;
@@ -91,6 +92,9 @@ int prolong_cells(const Lev &L, int full);
 void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, double dt, int jmax, int kmax,
                       cudaStream_t s);
 void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s);
+// parent data at time t^n + theta (t^{n+1} - t^n) for a sub-cycled child (Sec. II.D)
+void launch_time_interp(const Lev &P, const double *uold, const double *pold, const double *pnow, double *ut,
+                        double *pt, double theta, int have_old, cudaStream_t s);
 void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s);
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials,
                  int slot, cudaStream_t s);

@@ -43,7 +43,7 @@ class SacraParams(C.Structure):
     _fields_ = [
         ("n_levels", C.c_int), ("nx", C.c_int), ("nz", C.c_int), ("geometry", C.c_int),
         ("evolve_spacetime", C.c_int), ("solver", C.c_int), ("rk", C.c_int), ("c2p_maxit", C.c_int),
-        ("precision", C.c_int),
+        ("precision", C.c_int), ("subcycle_from", C.c_int),
         ("dx0", C.c_double), ("dz0", C.c_double),
         ("kappa", C.c_double), ("eta_B", C.c_double), ("eps_ko", C.c_double), ("r_z4", C.c_double),
         ("K", C.c_double), ("Gamma", C.c_double), ("Gamma_th", C.c_double),
@@ -144,6 +144,7 @@ def make_params(cfg) -> SacraParams:
     p.geometry = int(cfg.geometry); p.evolve_spacetime = int(cfg.evolve_spacetime)
     p.solver = int(cfg.solver); p.rk = int(cfg.rk); p.c2p_maxit = int(cfg.c2p_maxit)
     p.precision = int(getattr(cfg, "precision", 0))
+    p.subcycle_from = int(getattr(cfg, "subcycle_from", 0))
     p.dx0 = float(cfg.dx0); p.dz0 = float(cfg.dz0)
     p.kappa = float(cfg.kappa); p.eta_B = float(cfg.eta_B); p.eps_ko = float(cfg.eps_ko); p.r_z4 = float(cfg.r_z4)
     p.K = float(cfg.K); p.Gamma = float(cfg.Gamma); p.Gamma_th = float(cfg.Gamma_th)
