@@ -186,6 +186,13 @@ int orc_con2prim(const orc_params *p, double q[O_NCONS], double W, const double 
     orc_prim2cons(p, pr, W, h, x, q);
     return O_ST_ATM | O_ST_BAD;
   }
+  /* rho = D / w <= D for any root (w >= 1), so D < rho_atm always ends in the
+     atmosphere reset (Sec. II.C.4): the recovery's result would be discarded */
+  if (D < p->rho_atm) {
+    set_atmosphere(p, pr);
+    orc_prim2cons(p, pr, W, h, x, q);
+    return O_ST_ATM;
+  }
 
   double r = sqrt(up_norm2(gti, W, S)) / D;
   double qq = E / D - 1.0;

@@ -363,6 +363,13 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
     prim_to_cons(p, pr, W, gt, x, q);
     return ST_ATM | ST_BAD;
   }
+  // the recovery returns rho = D / w <= D (w >= 1, either branch), so D < rho_atm
+  // ends in the atmosphere reset of Sec. II.C.4 whatever the solve gives: skip it
+  if (D < p.rho_atm) {
+    atmosphere(p, pr);
+    prim_to_cons(p, pr, W, gt, x, q);
+    return ST_ATM;
+  }
   int st = 0;
   double r = sqrt(W * W * s3quad(gi, S, S)) / D;
   const double qq = E / D - 1.0;

@@ -133,3 +133,30 @@ def test_atmosphere_and_velocity_cap():
     assert st & 8
     w = math.sqrt(1.0 + pr[1] ** 2 + pr[2] ** 2 + pr[3] ** 2)
     assert w <= cfg2.w_max * (1 + 1e-9)
+
+
+def test_atmosphere_decided_by_D_alone():
+    """The recovery returns rho = D / w <= D on either branch (w >= 1), so a
+    cell with D = rho w < rho_atm always ends in the atmosphere: checked by
+    recovering random states (hot, cold-branch and fast ones) with no
+    atmosphere and comparing rho with D; with the atmosphere on, such a cell
+    returns the atmosphere primitives and the conserved state rebuilt from
+    them."""
+    cfg0 = _cfg(rho_atm=1e-300)
+    rng = np.random.default_rng(5)
+    rho, u, pfac = W.random_prims(rng, 200, w_max=30.0, log_rho=(-12.0, -3.0))
+    for i in range(len(rho)):
+        Wc, h = W.random_conformal_metric(rng)
+        P = cfg0.K * rho[i] ** cfg0.Gamma * (1.0 + pfac[i])
+        prim = np.array([rho[i], u[i, 0], u[i, 1], u[i, 2], P, O.eos_eps(cfg0, rho[i], P)])
+        x = rng.uniform(0.5, 3.0)
+        q = O.prim2cons(cfg0, prim, Wc, h, x)
+        if i % 3 == 0:
+            q[4] *= 0.5                                   # too little energy: cold branch
+        D = q[0] * (Wc * Wc * Wc)                        # as the recovery forms it
+        pr, _, st, _ = O.con2prim(cfg0, q.copy(), Wc, h, x)
+        assert not st & 4 and pr[0] <= D, (i, st, pr[0], D)
+        cfg = _cfg(rho_atm=D * 1.5)
+        pa, qa, sta, _ = O.con2prim(cfg, q.copy(), Wc, h, x)
+        assert sta == 4 and pa[0] == cfg.rho_atm and np.all(pa[1:4] == 0.0)
+        assert np.array_equal(qa, O.prim2cons(cfg, pa, Wc, h, x))
