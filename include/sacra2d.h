@@ -93,10 +93,16 @@ typedef struct {
                             calls (sacra_regrid_ghosts, sacra_rk_stage) return SACRA_ERR_STATE.  Each
                             parent of a sub-cycled level keeps 2 x 25 metric and 3 x 6 primitive
                             planes more (its t^{n-1} and t^n slices and their interpolant) */
+  int hydro_outer;       /* hydro at level 0's outer boundary: 0 = zero-gradient copy of the primitives,
+                            1 = held at the initial data given to sacra_set_initial_data (an inflow
+                            boundary with a known solution, e.g. Bondi accretion) */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;   /* cold polytrope P = K rho^Gamma plus thermal Gamma_th law (Sec. II.C.3) */
   double rho_atm, w_max, c2p_tol;
+  double r_hold;         /* > 0: the hydro of every cell with x^2 + z^2 < r_hold^2 is held at its state at the
+                            start of the step (an excised inner boundary, e.g. inside a black hole: the
+                            stage update keeps U^n and the recovery is skipped there); 0 = off */
 } sacra_params;
 
 /* Global diagnostics (Sec. II.F.1) over the cells not covered by a finer

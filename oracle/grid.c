@@ -127,7 +127,9 @@ static void outflow_fill(orc_ctx *c, int l, double **U) {
 /* Outer boundary of the coarsest level (Sec. II.B.3):
    Q(r) = Q_inf + (1 - tau/r) (Q^n - Q_inf)(r - tau), tau = c_s dt, with a
    2nd-order (3x3) Lagrange interpolation of the step-start state Q^n; the
-   hydro primitives are copied from the nearest interior cell. */
+   hydro primitives are copied from the nearest interior cell.  A frozen
+   metric (Cowling runs) keeps its ghosts as given; hydro_outer = 1 keeps the
+   hydro ghosts at the initial data (a known inflow solution). */
 static void outer_fill(orc_ctx *c, double **U, double tau) {
   orc_level *L = &c->lv[0];
   double **Un = L->un;
@@ -146,7 +148,7 @@ static void outer_fill(orc_ctx *c, double **U, double tau) {
       double wx[3], wz[3];
       orc_lagrange(3, n3, xi - i0, wx);
       orc_lagrange(3, n3, ze - k0, wz);
-      for (int f = 0; f < O_NMET; ++f) {
+      for (int f = 0; f < (c->p.evolve_spacetime ? O_NMET : 0); ++f) {
         double qinf = (f == O_W || f == O_AL) ? 1.0 : 0.0;
         /* interpolation in difference form about the central node (weights sum to 1) */
         double q0 = Un[f][oidx(L, i0, k0)] - qinf, s = 0.0;
@@ -154,6 +156,7 @@ static void outer_fill(orc_ctx *c, double **U, double tau) {
           for (int a = 0; a < 3; ++a) s += wx[a] * wz[b] * (Un[f][oidx(L, i0 - 1 + a, k0 - 1 + b)] - qinf - q0);
         U[f][d] = qinf + fac * (q0 + s);
       }
+      if (c->p.hydro_outer) continue;
       int jj = j > L->nx ? L->nx : j, kk = k > L->nz ? L->nz : k;
       int s = oidx(L, jj, kk);
       for (int f = 0; f < O_NPRIM; ++f) L->prim[f][d] = L->prim[f][s];
@@ -523,13 +526,22 @@ static void enforce(double **U, int id) {
   U[O_KH][id] += trA;
 }
 
+/* cell (j, k) of level l inside the excised inner boundary x^2 + z^2 < r_hold^2 */
+static int held(const orc_ctx *c, int l, int j, int k) {
+  if (!(c->p.r_hold > 0.0)) return 0;
+  double x = xc(&c->lv[l], j), z = zc(&c->lv[l], k);
+  return x * x + z * z < c->p.r_hold * c->p.r_hold;
+}
+
 /* ---------------- primitive recovery over a region ---------------- */
 
-static void c2p_region(orc_ctx *c, int l, double **U, int j0, int j1, int k0, int k1) {
+/* skip_held: leave the cells of the excised inner boundary alone (stage updates) */
+static void c2p_region_h(orc_ctx *c, int l, double **U, int j0, int j1, int k0, int k1, int skip_held) {
   orc_level *L = &c->lv[l];
 #pragma omp parallel for schedule(static)
   for (int k = k0; k <= k1; ++k)
     for (int j = j0; j <= j1; ++j) {
+      if (skip_held && held(c, l, j, k)) continue;
       int id = oidx(L, j, k);
       double q[O_NCONS], pr[O_NPRIM], h[6];
       for (int f = 0; f < O_NCONS; ++f) q[f] = U[O_NMET + f][id];
@@ -540,6 +552,10 @@ static void c2p_region(orc_ctx *c, int l, double **U, int j0, int j1, int k0, in
       for (int f = 0; f < O_NPRIM; ++f) L->prim[f][id] = pr[f];
       L->status[id] = (unsigned char)st;
     }
+}
+
+static void c2p_region(orc_ctx *c, int l, double **U, int j0, int j1, int k0, int k1) {
+  c2p_region_h(c, l, U, j0, j1, k0, k1, 0);
 }
 
 /* ---------------- one RK stage on all levels ---------------- */
@@ -568,8 +584,10 @@ static void stage_level(orc_ctx *c, int l, int s, double dt, int reset_parent) {
   for (int k = 1; k <= kmax; ++k)
     for (int j = 1; j <= jmax; ++j) {
       int id = oidx(L, j, k);
+      int hold = held(c, l, j, k);
       for (int f = 0; f < O_NSTATE; ++f) {
         if (f < O_NMET && !p->evolve_spacetime) continue;
+        if (f >= O_NMET && hold) { L->us[f][id] = L->un[f][id]; continue; }   /* excised: U^n kept */
         double un = L->un[f][id], us = U[f][id], kk = L->rhs[f][id];
         double out;
         if (p->rk == 0) {
@@ -589,7 +607,7 @@ static void stage_level(orc_ctx *c, int l, int s, double dt, int reset_parent) {
       }
       if (p->evolve_spacetime) enforce(L->us, id);
     }
-  c2p_region(c, l, L->us, 1, jmax, 1, kmax);
+  c2p_region_h(c, l, L->us, 1, jmax, 1, kmax, 1);
 }
 
 static void swap_level(orc_ctx *c, int l) {

@@ -49,10 +49,12 @@ typedef struct {
   int rk;                /* 0: classical RK4, 1: SSP-RK3 */
   int c2p_maxit;
   int subcycle_from;     /* 0: all levels share one dt (lockstep); K >= 1: levels >= K take dt / 2 of their parent */
+  int hydro_outer;       /* hydro at the outer boundary: 0 zero-gradient copy, 1 held at the initial data */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;
   double rho_atm, w_max, c2p_tol;
+  double r_hold;         /* > 0: hydro held at U^n inside x^2 + z^2 < r_hold^2 (excised inner boundary) */
 } orc_params;
 
 typedef struct {

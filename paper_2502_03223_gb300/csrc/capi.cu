@@ -92,6 +92,8 @@ bool valid(const sacra_params *p, std::string *why) {
   if (!(p->rho_atm > 0) || !(p->w_max > 1) || !(p->c2p_tol > 0) || p->c2p_maxit < 1) { *why = "bad recovery parameters"; return false; }
   if (p->precision & ~SACRA_MIXED) { *why = "unknown precision bits"; return false; }
   if (p->subcycle_from < 0) { *why = "subcycle_from must be >= 0"; return false; }
+  if (p->hydro_outer != 0 && p->hydro_outer != 1) { *why = "hydro_outer must be 0 or 1"; return false; }
+  if (!(p->r_hold >= 0.0)) { *why = "r_hold must be >= 0"; return false; }
   return true;
 }
 
@@ -455,7 +457,7 @@ void enqueue_fill(Engine &e, Star &st, int s, double dt) {
     }
     if (l == 0) {
       run(e, K_OUTER, (long long)(L.nx + GH) * (L.nz + GH) - (long long)L.nx * L.nz,
-          [&] { launch_outer(L, L.un, U, stage_c(st.prm.rk, s) * dt, e.stream); });
+          [&] { launch_outer(L, st.dp, L.un, U, stage_c(st.prm.rk, s) * dt, e.stream); });
     } else {
       double *Up = stage_state(st, l - 1, s);
       run(e, K_PROLONG, prolong_cells(L, s == 0), [&] { launch_prolong(L, st.lv[l - 1], st.dp, U, Up, s == 0, e.stream); });
@@ -508,7 +510,7 @@ void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) 
         if (st.prm.geometry == SACRA_CYLINDRICAL) {
           const Lev &L0 = st.lv[0];
           run(e, K_OUTER, (long long)(L0.nx + GH) * (L0.nz + GH) - (long long)L0.nx * L0.nz,
-              [&] { launch_outer(L0, L0.un, L0.us, dt, e.stream); });
+              [&] { launch_outer(L0, st.dp, L0.un, L0.us, dt, e.stream); });
         }
     swap_group(e, g);
   }
@@ -611,7 +613,7 @@ void enqueue_step_sub(Engine &e, Star &st, double dt) {
       const Lev &Lv = st.lv[l];
       if (l == 0) {
         run(e, K_OUTER, (long long)(Lv.nx + GH) * (Lv.nz + GH) - (long long)Lv.nx * Lv.nz,
-            [&] { launch_outer(Lv, Lv.un, U, stage_c(st.prm.rk, s) * dt, e.stream); });
+            [&] { launch_outer(Lv, st.dp, Lv.un, U, stage_c(st.prm.rk, s) * dt, e.stream); });
       } else {
         double *Up = stage_state(st, l - 1, s);
         run(e, K_PROLONG, prolong_cells(Lv, s == 0),

@@ -34,6 +34,8 @@ struct DevParams {
   int geometry, evolve, solver, rk, c2p_maxit, n_levels;
   int mixed;             // SACRA_MIXED_* bits: parts whose arithmetic runs in FP32 (FP64 differences and updates)
   int K_zero, gamma2;    // K == 0 (pure Gamma-law), Gamma == 2
+  int hydro_outer;       // 1: level 0's outer hydro ghosts stay at the initial data
+  double r_hold2;        // > 0: hydro held at U^n where x^2 + z^2 < r_hold2 (excised inner boundary)
   double K, Gamma, Gamma_th, rho_atm, w_max, c2p_tol;
   double kappa, eta_B, eps_ko, r_z4;
   double c2p_kmax;       // 2 v_max / (1 + v_max^2), v_max = sqrt(1 - 1 / w_max^2)
@@ -69,6 +71,8 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->ko = -p->eps_ko / 256.0;
   const double vmax = sqrt(1.0 - 1.0 / (p->w_max * p->w_max));
   d->c2p_kmax = 2.0 * vmax / (1.0 + vmax * vmax);
+  d->hydro_outer = p->hydro_outer != 0;
+  d->r_hold2 = p->r_hold > 0.0 ? p->r_hold * p->r_hold : 0.0;
 }
 
 // One refinement level as seen by a kernel: planes of P = px * pz doubles.

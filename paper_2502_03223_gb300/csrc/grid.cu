@@ -87,7 +87,8 @@ __global__ void k_outflow(Lev L, double *__restrict__ U) {
 // (blockIdx.y) that share the interpolation weights.
 constexpr int kOuterGroups = 5;
 
-__global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict__ U, double tau) {
+__global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict__ U, double tau, int metric,
+                        int prims) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int w = L.nx + GH, top = GH * w;
   int j, k;
@@ -110,7 +111,7 @@ __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict
   const double wx[3] = {0.5 * tx * (tx - 1.0), (1.0 - tx) * (1.0 + tx), 0.5 * tx * (tx + 1.0)};
   const double wz[3] = {0.5 * tz * (tz - 1.0), (1.0 - tz) * (1.0 + tz), 0.5 * tz * (tz + 1.0)};
   const int d = cid(L, j, k), c0 = cid(L, i0, k0);
-  for (int f = blockIdx.y; f < NMET; f += kOuterGroups) {
+  for (int f = blockIdx.y; metric && f < NMET; f += kOuterGroups) {
     const double qinf = (f == fW || f == fAL) ? 1.0 : 0.0;
     const double *u = Un + (size_t)f * P + c0;
     const double u0 = u[0] - qinf;
@@ -121,7 +122,7 @@ __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict
       for (int a = 0; a < 3; ++a) s += wx[a] * wz[b] * (u[(b - 1) * L.px + (a - 1)] - qinf - u0);
     U[(size_t)f * P + d] = qinf + fac * (u0 + s);
   }
-  if (blockIdx.y == 0) {
+  if (blockIdx.y == 0 && prims) {
     const int sc = cid(L, min(j, L.nx), min(k, L.nz));
 #pragma unroll
     for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = L.prim[(size_t)f * P + sc];
@@ -237,9 +238,15 @@ __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p,
   const int id = cid(L, j, k);
   double m[NST];
   const int f0 = p.evolve ? 0 : NMET;
+  bool held = false;   // excised inner boundary: the hydro keeps U^n and is not recovered
+  if (p.r_hold2 > 0.0) {
+    const double x = (j - 0.5) * L.dx, z = (k - 0.5) * L.dz;
+    held = x * x + z * z < p.r_hold2;
+  }
   for (int f = 0; f < NST; ++f) {
     const size_t o = (size_t)f * P + id;
     if (f < f0) { m[f] = L.us[o]; continue; }
+    if (f >= NMET && held) { m[f] = L.un[o]; continue; }
     const double un = L.un[o], kk = L.rhs[o];
     double out;
     if (p.rk == SACRA_RK4) {
@@ -258,6 +265,10 @@ __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p,
     m[f] = out;
   }
   if (p.evolve) enforce_algebraic(m);
+  if (held) {
+    for (int f = f0; f < NST; ++f) L.us[(size_t)f * P + id] = m[f];
+    return;
+  }
   Sym3 g;
   g.xx = 1.0 + m[fHXX]; g.xy = m[fHXY]; g.xz = m[fHXZ]; g.yy = 1.0 + m[fHYY]; g.yz = m[fHYZ]; g.zz = 1.0 + m[fHZZ];
   double pr[NPRIM];
@@ -552,9 +563,9 @@ void launch_outflow(const Lev &L, double *U, cudaStream_t s) {
   k_outflow<<<(unsigned)((L.P + 255) / 256), 256, 0, s>>>(L, U);
 }
 
-void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s) {
+void launch_outer(const Lev &L, const DevParams &p, const double *Un, double *U, double tau, cudaStream_t s) {
   const int n = GH * (L.nx + GH) + GH * L.nz;
-  k_outer<<<dim3((n + 127) / 128, kOuterGroups), 128, 0, s>>>(L, Un, U, tau);
+  k_outer<<<dim3((n + 127) / 128, kOuterGroups), 128, 0, s>>>(L, Un, U, tau, p.evolve, !p.hydro_outer);
 }
 
 int prolong_cells(const Lev &L, int full) {

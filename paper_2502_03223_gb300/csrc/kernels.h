@@ -84,7 +84,7 @@ int z4c_scratch_planes();
 void launch_parity_x(const Lev &L, double *U, cudaStream_t s);
 void launch_parity_z(const Lev &L, double *U, cudaStream_t s);
 void launch_outflow(const Lev &L, double *U, cudaStream_t s);
-void launch_outer(const Lev &L, const double *Un, double *U, double tau, cudaStream_t s);
+void launch_outer(const Lev &L, const DevParams &p, const double *Un, double *U, double tau, cudaStream_t s);
 // two launches: the metric (one thread per buffer cell and field), then the hydro
 void launch_prolong(const Lev &L, const Lev &Pa, const DevParams &p, double *U, const double *Up, int full,
                     cudaStream_t s);

@@ -40,6 +40,7 @@ class RunConfig:
     c2p_maxit: int = 100
     precision: int = 0         # 0 FP64, 1 mixed FP32/FP64 (GPU library only; the oracle is FP64)
     subcycle_from: int = 0     # 0 lockstep; K >= 1: levels >= K take half their parent's step
+    hydro_outer: int = 0       # outer hydro boundary: 0 zero-gradient copy, 1 held at the initial data
     dx0: float = 1.0
     dz0: float = 1.0
     kappa: float = 0.0
@@ -52,6 +53,7 @@ class RunConfig:
     rho_atm: float = 1e-13
     w_max: float = 100.0
     c2p_tol: float = 1e-12
+    r_hold: float = 0.0        # > 0: hydro held inside x^2 + z^2 < r_hold^2
     cfl: float = 0.5
     mass: float = 1.0          # total mass M used for kappa and eta_B
 
@@ -244,6 +246,172 @@ def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0, 
                          (1.0 - tov.M / (2.0 * rr)) / (1.0 + tov.M / (2.0 * rr)))
     d[25] = rho
     d[29] = P
+    return d
+
+
+# ------------------------------------------------------------------ Bondi accretion onto a trumpet black hole
+
+def trumpet_C(M=1.0):
+    """C of the maximal trumpet slice of Schwarzschild: alpha^2 = 1 - 2M/R + C^2/R^4."""
+    return 3.0 * math.sqrt(3.0) / 4.0 * M * M
+
+
+def trumpet_r_of_R(R, M=1.0):
+    """Coordinate radius r of the maximal trumpet slice at areal radius R >= 3M/2
+    (closed form of the paper's Sec. III vacuum test; r = 0 at R = 3M/2)."""
+    R = np.asarray(R, dtype=np.float64)
+    a = (2.0 * R + M + np.sqrt(4.0 * R * R + 4.0 * M * R + 3.0 * M * M)) / 4.0
+    b = (4.0 + 3.0 * math.sqrt(2.0)) * (2.0 * R - 3.0 * M) / (
+        8.0 * R + 6.0 * M + 3.0 * np.sqrt(8.0 * R * R + 8.0 * M * R + 6.0 * M * M))
+    return a * np.maximum(b, 0.0) ** (1.0 / math.sqrt(2.0))
+
+
+def trumpet_R_of_r(r, M=1.0):
+    """Areal radius R(r) by bisection of trumpet_r_of_R (monotone in R)."""
+    r = np.asarray(r, dtype=np.float64)
+    lo = np.full_like(r, 1.5 * M)
+    hi = r + 3.0 * M
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        below = trumpet_r_of_R(mid, M) < r
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return 0.5 * (lo + hi)
+
+
+@dataclasses.dataclass
+class BondiSolution:
+    M: float
+    K: float
+    Gamma: float
+    R_c: float
+    u_c: float          # |u^R| at the critical point
+    rho_c: float
+    Mdot: float         # accretion rate 4 pi R^2 rho |u^R|
+    bern: float         # h^2 (1 - 2M/R + (u^R)^2), constant along the flow
+
+
+def bondi_solve(M=1.0, K=1.0, Gamma=4.0 / 3.0, R_c=8.0):
+    """Transonic (Michel) accretion of a polytrope P = K rho^Gamma onto a
+    Schwarzschild black hole, fixed by its critical radius: (u^R)^2 = M / (2 R_c)
+    and c_s^2 = u^2 / (1 - 3 u^2) there."""
+    u2 = M / (2.0 * R_c)
+    cs2 = u2 / (1.0 - 3.0 * u2)
+    theta = cs2 / (Gamma * (1.0 - cs2 / (Gamma - 1.0)))       # P / rho with c_s^2 = Gamma P / (rho h)
+    rho_c = (theta / K) ** (1.0 / (Gamma - 1.0))
+    h_c = 1.0 + Gamma / (Gamma - 1.0) * theta
+    u_c = math.sqrt(u2)
+    return BondiSolution(M=M, K=K, Gamma=Gamma, R_c=R_c, u_c=u_c, rho_c=rho_c,
+                         Mdot=4.0 * math.pi * R_c * R_c * rho_c * u_c,
+                         bern=h_c * h_c * (1.0 - 2.0 * M / R_c + u2))
+
+
+def bondi_rho(sol: BondiSolution, R):
+    """Rest-mass density of the transonic solution at areal radius R: the root
+    of h^2 (1 - 2M/R + u^2) = const, u = Mdot / (4 pi R^2 rho), on the
+    subsonic side (larger rho) outside R_c and the supersonic side inside."""
+    R = np.asarray(R, dtype=np.float64)
+    g1 = sol.Gamma - 1.0
+
+    def F(y):                      # y = ln rho
+        rho = np.exp(y)
+        h = 1.0 + sol.Gamma / g1 * sol.K * rho ** g1
+        u = sol.Mdot / (4.0 * math.pi * R * R * rho)
+        return h * h * (1.0 - 2.0 * sol.M / R + u * u) - sol.bern
+
+    # minimum of F in ln rho (golden section), then bisection on the chosen side
+    a = np.full_like(R, math.log(1e-14))
+    b = np.full_like(R, math.log(10.0))
+    gr = (math.sqrt(5.0) - 1.0) / 2.0
+    for _ in range(200):
+        c = b - gr * (b - a)
+        d = a + gr * (b - a)
+        left = F(c) < F(d)
+        b = np.where(left, d, b)
+        a = np.where(left, a, c)
+    ymin = 0.5 * (a + b)
+    sub = R > sol.R_c
+    lo = np.where(sub, ymin, math.log(1e-14))
+    hi = np.where(sub, math.log(10.0), ymin)
+    flo = F(lo)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        fm = F(mid)
+        same = np.sign(fm) == np.sign(flo)
+        lo = np.where(same, mid, lo)
+        flo = np.where(same, fm, flo)
+        hi = np.where(same, hi, mid)
+    return np.exp(0.5 * (lo + hi))
+
+
+def bondi_trumpet_fields(sol: BondiSolution, x, z):
+    """Metric (25 fields) and primitives (rho, u_x, u_y, u_z, P, eps) of the
+    Bondi flow on the maximal trumpet slice at cartoon-plane points (x, z):
+    W = r/R, alpha^2 = 1 - 2M/R + C^2/R^4, beta^i = C x^i / R^3,
+    At_ij = (C / R^3)(delta_ij - 3 x^i x^j / r^2), h = Khat = Theta = Gt = B = 0.
+    The fluid's covariant velocity follows from the Schwarzschild solution
+    through ingoing Eddington-Finkelstein time v (regular at the horizon):
+    the slice is t = v + H(R), H' = -R^2 / (alpha (C + R^2 alpha)), so
+    u_R = 1/(s - u^R) + H' s with s = -u_v = sqrt((u^R)^2 + 1 - 2M/R), and
+    u_r = u_R dR/dr = u_R R alpha / r."""
+    M = sol.M
+    C = trumpet_C(M)
+    x = np.asarray(x, dtype=np.float64)
+    z = np.asarray(z, dtype=np.float64)
+    r = np.sqrt(x * x + z * z)
+    R = trumpet_R_of_r(r, M)
+    alpha = np.sqrt(1.0 - 2.0 * M / R + C * C / R ** 4)
+    met = np.zeros((NMET,) + x.shape)
+    met[0] = r / R
+    met[18] = alpha
+    cr3 = C / R ** 3
+    met[19] = cr3 * x
+    met[21] = cr3 * z
+    met[7] = cr3 * (1.0 - 3.0 * x * x / (r * r))
+    met[9] = cr3 * (-3.0 * x * z / (r * r))
+    met[10] = cr3
+    met[12] = cr3 * (1.0 - 3.0 * z * z / (r * r))
+    rho = bondi_rho(sol, R)
+    uR = -sol.Mdot / (4.0 * math.pi * R * R * rho)           # contravariant, inflow
+    s = np.sqrt(uR * uR + 1.0 - 2.0 * M / R)
+    Hp = -R * R / (alpha * (C + R * R * alpha))
+    u_R = 1.0 / (s - uR) + Hp * s
+    u_r = u_R * R * alpha / r
+    P = sol.K * rho ** sol.Gamma
+    prim = np.zeros((6,) + x.shape)
+    prim[0] = rho
+    prim[1] = u_r * x / r
+    prim[3] = u_r * z / r
+    prim[4] = P
+    prim[5] = P / ((sol.Gamma - 1.0) * rho)
+    return met, prim
+
+
+def bondi_config(N=64, n_levels=1, solver=0, rk=0, xmax=16.0, r_hold=0.4, cfl=0.5, sol=None):
+    """Bondi accretion in Cowling mode (metric frozen at the trumpet slice):
+    an ideal gas P = (Gamma - 1) rho eps with Gamma = 4/3 (no cold part, so no
+    cold-curve clamp), the flow on the adiabat K = 1 with critical radius 8M,
+    box x_max = z_max = 16M over n_levels levels of N^2 (the finest box
+    x_max / 2^(n_levels - 1)), hydro held inside r = 0.4M and at the outer
+    boundary."""
+    if sol is None:
+        sol = bondi_solve()
+    dx0 = xmax / N
+    cfg = RunConfig(name="bondi_%dx%d" % (n_levels, N), n_levels=n_levels, nx=N, nz=N, geometry=1,
+                    evolve_spacetime=0, solver=solver, rk=rk, dx0=dx0, dz0=dx0, K=0.0, Gamma=2.0,
+                    Gamma_th=sol.Gamma, rho_atm=1e-12 * sol.rho_c, cfl=cfl, mass=sol.M, hydro_outer=1,
+                    r_hold=r_hold)
+    return cfg, sol
+
+
+def bondi_level_data(cfg: RunConfig, sol: BondiSolution, level: int):
+    """Kind-0 level data (25 metric fields, then rho, u_x, u_y, u_z, P) of the
+    Bondi flow on the trumpet slice, ghosts included."""
+    X, Z = cell_centres(cfg, level)
+    met, prim = bondi_trumpet_fields(sol, X, Z)
+    d = np.zeros((30, cfg.pz, cfg.px))
+    d[:NMET] = met
+    d[25:30] = prim[:5]
     return d
 
 
