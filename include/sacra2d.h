@@ -96,6 +96,13 @@ typedef struct {
   int hydro_outer;       /* hydro at level 0's outer boundary: 0 = zero-gradient copy of the primitives,
                             1 = held at the initial data given to sacra_set_initial_data (an inflow
                             boundary with a known solution, e.g. Bondi accretion) */
+  int eos_adiabatic;     /* 0: cold part + thermal Gamma_th law (Sec. II.C.3); 1: the "adiabatic" EOS of the
+                            migration test (Sec. III): zero temperature, P = P_cold, eps = eps_cold everywhere,
+                            the energy equation discarded (the recovery uses D and S_i only and rebuilds E);
+                            needs K > 0 */
+  int n_pieces;          /* cold part: 0 or 1 = the single polytrope (K, Gamma); 2..8 = piecewise polytropic
+                            (Sec. II.C.3) with piece 1 = (K, Gamma) and the others from pwp_rho, pwp_Gamma.
+                            Not accepted by sacra_hydro_rhs_noalloc (SACRA_ERR_ARG) */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;   /* cold polytrope P = K rho^Gamma plus thermal Gamma_th law (Sec. II.C.3) */
@@ -103,6 +110,9 @@ typedef struct {
   double r_hold;         /* > 0: the hydro of every cell with x^2 + z^2 < r_hold^2 is held at its state at the
                             start of the step (an excised inner boundary, e.g. inside a black hole: the
                             stage update keeps U^n and the recovery is skipped there); 0 = off */
+  double pwp_rho[7];     /* transition densities rho_1 < rho_2 < ... < rho_(n_pieces-1), all > 0 */
+  double pwp_Gamma[7];   /* Gamma_2 .. Gamma_(n_pieces), each > 1; K_i and Delta eps_i follow from the
+                            continuity of P_cold and eps_cold at the transitions */
 } sacra_params;
 
 /* Global diagnostics (Sec. II.F.1) over the cells not covered by a finer

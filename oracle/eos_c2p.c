@@ -6,17 +6,45 @@
 #include <math.h>
 #include "orc.h"
 
-/* Hybrid EOS, Sec. II.C.3: one cold polytrope piece P_c = K rho^Gamma,
-   eps_c = K rho^(Gamma-1)/(Gamma-1) (Delta eps_1 = 0 for the first piece,
-   rho_0 = 0), plus the thermal Gamma-law P_th = rho (Gamma_th - 1) eps_th. */
+/* Hybrid EOS, Sec. II.C.3: a piecewise polytropic cold part,
+     P_c = K_i rho^Gamma_i,  eps_c = K_i rho^(Gamma_i - 1) / (Gamma_i - 1) + Delta eps_i
+   on rho_(i-1) <= rho < rho_i (rho_0 = 0), with K_1 = K, Gamma_1 = Gamma,
+   Delta eps_1 = 0 and, going up through the transitions, K_(i+1) from the
+   continuity of P_c and Delta eps_(i+1) from that of eps_c; plus the thermal
+   Gamma-law P_th = rho (Gamma_th - 1) eps_th. */
+static void cold_piece(const orc_params *p, double rho, double *K, double *G, double *de) {
+  double k = p->K, g = p->Gamma, d = 0.0;
+  for (int i = 0; i + 1 < p->n_pieces; ++i) {
+    double rt = p->pwp_rho[i];
+    if (rho < rt) break;
+    double g2 = p->pwp_Gamma[i];
+    double k2 = k * pow(rt, g - g2);                                   /* K_i rho_i^G_i = K_(i+1) rho_i^G_(i+1) */
+    d = d + k * pow(rt, g - 1.0) / (g - 1.0) - k2 * pow(rt, g2 - 1.0) / (g2 - 1.0);
+    k = k2;
+    g = g2;
+  }
+  *K = k; *G = g; *de = d;
+}
+
 double orc_eos_pcold(const orc_params *p, double rho) {
   if (p->K == 0.0) return 0.0;
-  return p->K * pow(rho, p->Gamma);
+  double K, G, de;
+  cold_piece(p, rho, &K, &G, &de);
+  return K * pow(rho, G);
 }
 
 double orc_eos_ecold(const orc_params *p, double rho) {
   if (p->K == 0.0) return 0.0;
-  return p->K * pow(rho, p->Gamma - 1.0) / (p->Gamma - 1.0);
+  double K, G, de;
+  cold_piece(p, rho, &K, &G, &de);
+  return K * pow(rho, G - 1.0) / (G - 1.0) + de;
+}
+
+/* Gamma_i of the piece holding rho (d ln P_c / d ln rho) */
+double orc_eos_gamma_cold(const orc_params *p, double rho) {
+  double K, G, de;
+  cold_piece(p, rho, &K, &G, &de);
+  return G;
 }
 
 /* P = P_cold + P_th with eps_th = eps - eps_cold (Sec. II.C.3). */
@@ -36,7 +64,7 @@ double orc_eos_eps(const orc_params *p, double rho, double press) {
 double orc_eos_cs2(const orc_params *p, double rho, double eps, double press) {
   double pc = orc_eos_pcold(p, rho);
   double h = 1.0 + eps + press / rho;
-  double cs2 = (p->Gamma * pc + p->Gamma_th * (press - pc)) / (rho * h);
+  double cs2 = (orc_eos_gamma_cold(p, rho) * pc + p->Gamma_th * (press - pc)) / (rho * h);
   if (!(cs2 > 0.0)) cs2 = 0.0;
   if (cs2 >= 1.0) cs2 = 1.0 - 1e-15;
   return cs2;
@@ -195,6 +223,39 @@ int orc_con2prim(const orc_params *p, double q[O_NCONS], double W, const double 
   }
 
   double r = sqrt(up_norm2(gti, W, S)) / D;
+  if (p->eos_adiabatic) {
+    /* "adiabatic" EOS (Sec. III): zero temperature, the energy equation is
+       discarded: the cold recovery from D and S_i alone, the Lorentz factor
+       capped at w_max through r (z = r / h_c <= r), then E rebuilt */
+    double zmax = sqrt(p->w_max * p->w_max - 1.0);
+    if (r > zmax) {
+      double s = zmax / r;
+      S[0] *= s; S[1] *= s; S[2] *= s;
+      r = zmax;
+      st |= O_ST_KRESCALE;
+    }
+    c2p_data dc = {p, D, 0.0, r};
+    int ok = 1;
+    double z = illinois(c2p_cold_master, &dc, 0.0, r, p->c2p_tol, p->c2p_maxit, iters, &ok);
+    if (!ok) st |= O_ST_NOCONV;
+    double w = sqrt(1.0 + z * z);
+    double rho = D / w;
+    double eps = orc_eos_ecold(p, rho);
+    double P = orc_eos_pcold(p, rho);
+    double hh = 1.0 + eps + P / rho;
+    pr[O_RHO] = rho;
+    pr[O_EPS] = eps;
+    pr[O_P] = P;
+    pr[O_UX] = S[0] / (D * hh);
+    pr[O_UY] = S[1] / (D * hh);
+    pr[O_UZ] = S[2] / (D * hh);
+    if (rho < p->rho_atm) {
+      set_atmosphere(p, pr);
+      st |= O_ST_ATM;
+    }
+    orc_prim2cons(p, pr, W, h, x, q);
+    return st;
+  }
   double qq = E / D - 1.0;
   double k = r / (1.0 + qq);
   double vmax = sqrt(1.0 - 1.0 / (p->w_max * p->w_max));

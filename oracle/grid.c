@@ -221,7 +221,7 @@ static void prolong_from(orc_ctx *c, int l, double **U, double **Up, double **Pp
         pr[f] = a0 + ox * sx + oz * sz;
       }
       double pc = orc_eos_pcold(&c->p, pr[O_RHO]);
-      if (pr[O_P] < pc) pr[O_P] = pc;
+      if (pr[O_P] < pc || c->p.eos_adiabatic) pr[O_P] = pc;
       pr[O_EPS] = orc_eos_eps(&c->p, pr[O_RHO], pr[O_P]);
       for (int f = 0; f < O_NPRIM; ++f) L->prim[f][d] = pr[f];
       double h[6], q[O_NCONS];
@@ -775,6 +775,7 @@ int orc_set_level(orc_ctx *c, int l, int kind, const double *data) {
         double pr[O_NPRIM];
         for (int v = 0; v < 4; ++v) pr[v] = data[(O_NMET + v) * n + id];
         pr[O_P] = data[(O_NMET + 4) * n + id];
+        if (c->p.eos_adiabatic) pr[O_P] = orc_eos_pcold(&c->p, pr[O_RHO]);   /* zero temperature */
         pr[O_EPS] = orc_eos_eps(&c->p, pr[O_RHO], pr[O_P]);
         for (int f = 0; f < O_NPRIM; ++f) L->prim[f][id] = pr[f];
         double h[6], q[O_NCONS];

@@ -50,11 +50,15 @@ typedef struct {
   int c2p_maxit;
   int subcycle_from;     /* 0: all levels share one dt (lockstep); K >= 1: levels >= K take dt / 2 of their parent */
   int hydro_outer;       /* hydro at the outer boundary: 0 zero-gradient copy, 1 held at the initial data */
+  int eos_adiabatic;     /* 1: zero temperature, P = P_cold, eps = eps_cold, energy equation discarded */
+  int n_pieces;          /* cold polytropic pieces (0 or 1: the single piece K, Gamma) */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;
   double rho_atm, w_max, c2p_tol;
   double r_hold;         /* > 0: hydro held at U^n inside x^2 + z^2 < r_hold^2 (excised inner boundary) */
+  double pwp_rho[7];     /* transition densities rho_1 < ... < rho_(n-1) */
+  double pwp_Gamma[7];   /* Gamma_2 .. Gamma_n (piece 1: K, Gamma) */
 } orc_params;
 
 typedef struct {
@@ -96,6 +100,7 @@ double orc_eos_ecold(const orc_params *p, double rho);
 double orc_eos_press(const orc_params *p, double rho, double eps);
 double orc_eos_eps(const orc_params *p, double rho, double press);
 double orc_eos_cs2(const orc_params *p, double rho, double eps, double press);
+double orc_eos_gamma_cold(const orc_params *p, double rho);
 void orc_inv3(const double g[6], double gi[6], double *det);
 void orc_prim2cons(const orc_params *p, const double pr[O_NPRIM], double W, const double h[6], double x, double q[O_NCONS]);
 int orc_con2prim(const orc_params *p, double q[O_NCONS], double W, const double h[6], double x, double pr[O_NPRIM], int *iters);

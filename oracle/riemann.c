@@ -54,6 +54,7 @@ typedef struct { double D, S[3], E, P, vx, lm, lp; } sr_state;
 
 /* tetrad-frame state from the tetrad 4-velocity components */
 static void sr_fill(const orc_params *p, double rho, double P, const double ut[3], sr_state *s) {
+  if (p->eos_adiabatic) P = orc_eos_pcold(p, rho);   /* zero temperature at the face too */
   double w = sqrt(1.0 + ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
   double v[3] = {ut[0] / w, ut[1] / w, ut[2] / w};
   double eps = orc_eos_eps(p, rho, P);

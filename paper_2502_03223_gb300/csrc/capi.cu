@@ -71,7 +71,7 @@ Layout layout(const sacra_params *p) {
 
 size_t star_bytes(const sacra_params *p) {
   const Layout o = layout(p);
-  return o.per_level * p->n_levels + o.part_bytes;
+  return o.per_level * p->n_levels + o.part_bytes + round_up(sizeof(PwpTable), 256);
 }
 
 bool valid(const sacra_params *p, std::string *why) {
@@ -94,6 +94,16 @@ bool valid(const sacra_params *p, std::string *why) {
   if (p->subcycle_from < 0) { *why = "subcycle_from must be >= 0"; return false; }
   if (p->hydro_outer != 0 && p->hydro_outer != 1) { *why = "hydro_outer must be 0 or 1"; return false; }
   if (!(p->r_hold >= 0.0)) { *why = "r_hold must be >= 0"; return false; }
+  if (p->eos_adiabatic != 0 && p->eos_adiabatic != 1) { *why = "eos_adiabatic must be 0 or 1"; return false; }
+  if (p->eos_adiabatic && !(p->K > 0.0)) { *why = "the adiabatic EOS needs a cold part (K > 0)"; return false; }
+  if (p->n_pieces < 0 || p->n_pieces > kMaxPieces) { *why = "n_pieces must be in [0, 8]"; return false; }
+  if (p->n_pieces > 1) {
+    if (!(p->K > 0.0)) { *why = "piecewise polytropes need K > 0"; return false; }
+    for (int i = 0; i + 1 < p->n_pieces; ++i) {
+      if (!(p->pwp_rho[i] > (i ? p->pwp_rho[i - 1] : 0.0))) { *why = "pwp_rho must increase from > 0"; return false; }
+      if (!(p->pwp_Gamma[i] > 1.0)) { *why = "pwp_Gamma must exceed 1"; return false; }
+    }
+  }
   return true;
 }
 
@@ -138,6 +148,7 @@ struct Star {
   double *uold[kMaxLevels] = {}, *pold[kMaxLevels] = {}, *pnow[kMaxLevels] = {};
   double *ut[kMaxLevels] = {}, *pt[kMaxLevels] = {};
   bool have_old[kMaxLevels] = {};
+  PwpTable *pwp = nullptr;        // device copy of the cold pieces
 };
 
 // launch group of level l: 0 = the lockstep levels, then one per sub-cycled level
@@ -792,6 +803,7 @@ void init_star_levels(Star &st, char *base) {
     L.status = (int *)dp;
   }
   st.part = (double *)(base + st.lay.per_level * p->n_levels);
+  st.pwp = (PwpTable *)(base + st.lay.per_level * p->n_levels + st.lay.part_bytes);
 }
 
 // shared tables: cartoon weights (for the largest nx) and the grid weights
@@ -868,6 +880,11 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
     st.lay = layout(&ps[i]);
     st.G = lockstep_levels(&ps[i]);
     init_star_levels(st, p);
+    PwpTable tab;
+    fill_pwp_table(&ps[i], &tab);
+    cudaMemcpyAsync(st.pwp, &tab, sizeof(tab), cudaMemcpyHostToDevice, e.stream);
+    if (cudaStreamSynchronize(e.stream) != cudaSuccess) return SACRA_ERR_CUDA;   // tab is on the stack
+    if (st.dp.n_pieces > 1) st.dp.pwp = st.pwp;
     p += star_bytes(&ps[i]);
     max_nx = std::max(max_nx, ps[i].nx);
     for (int l = 0; l < ps[i].n_levels; ++l) {
@@ -878,6 +895,7 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
     }
   }
   e.ngroups = (int)e.group_first.size();
+  e.dp.pwp = e.stars[0].dp.pwp;
   e.tab = (double *)p;
   p += round_up((size_t)(max_nx + 8) * 3 * kTabStride * 8, 256);
   e.dout = (double *)p;

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "sacra2d.h"
 
@@ -30,11 +31,23 @@ constexpr int ST_NOCONV = 1, ST_COLD = 2, ST_ATM = 4, ST_KRESCALE = 8, ST_BAD = 
 
 struct MlpNet;
 
+// Cold polytropic pieces of one star beyond the first (Sec. II.C.3), in
+// device memory: piece i (0-based) holds rho in [rho[i-1], rho[i]).
+constexpr int kMaxPieces = 8;
+struct PwpTable {
+  double rho[kMaxPieces - 1], K[kMaxPieces], G[kMaxPieces], gm1[kMaxPieces], de[kMaxPieces];
+  float frho[kMaxPieces - 1], fK[kMaxPieces], fG[kMaxPieces], fgm1[kMaxPieces], fde[kMaxPieces];
+};
+
 struct DevParams {
   int geometry, evolve, solver, rk, c2p_maxit, n_levels;
   int mixed;             // SACRA_MIXED_* bits: parts whose arithmetic runs in FP32 (FP64 differences and updates)
   int K_zero, gamma2;    // K == 0 (pure Gamma-law), Gamma == 2
   int hydro_outer;       // 1: level 0's outer hydro ghosts stay at the initial data
+  int adiabatic;         // 1: zero temperature, P = P_cold, eps = eps_cold, energy equation discarded
+  int n_pieces;          // cold pieces (1: K, Gamma; more: the table pwp)
+  const PwpTable *pwp;   // device copy of the pieces when n_pieces > 1
+  double c2p_zmax;       // sqrt(w_max^2 - 1): Lorentz-factor cap of the adiabatic recovery
   double r_hold2;        // > 0: hydro held at U^n where x^2 + z^2 < r_hold2 (excised inner boundary)
   double K, Gamma, Gamma_th, rho_atm, w_max, c2p_tol;
   double kappa, eta_B, eps_ko, r_z4;
@@ -73,6 +86,30 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->c2p_kmax = 2.0 * vmax / (1.0 + vmax * vmax);
   d->hydro_outer = p->hydro_outer != 0;
   d->r_hold2 = p->r_hold > 0.0 ? p->r_hold * p->r_hold : 0.0;
+  d->adiabatic = p->eos_adiabatic != 0;
+  d->n_pieces = p->n_pieces > 1 ? p->n_pieces : 1;
+  d->pwp = nullptr;      // set by the owner of the device copy
+  d->c2p_zmax = sqrt(p->w_max * p->w_max - 1.0);
+}
+
+// The pieces' constants (host): K_(i+1) from continuity of P_cold at rho_i,
+// Delta eps_(i+1) from continuity of eps_cold there, Delta eps_1 = 0.
+inline void fill_pwp_table(const sacra_params *p, PwpTable *t) {
+  memset(t, 0, sizeof(*t));
+  const int n = p->n_pieces > 1 ? p->n_pieces : 1;
+  t->K[0] = p->K; t->G[0] = p->Gamma; t->gm1[0] = p->Gamma - 1.0; t->de[0] = 0.0;
+  for (int i = 1; i < n; ++i) {
+    const double rt = p->pwp_rho[i - 1], g = t->G[i - 1], g2 = p->pwp_Gamma[i - 1], k = t->K[i - 1];
+    t->rho[i - 1] = rt;
+    t->G[i] = g2;
+    t->gm1[i] = g2 - 1.0;
+    t->K[i] = k * pow(rt, g - g2);
+    t->de[i] = t->de[i - 1] + k * pow(rt, g - 1.0) / (g - 1.0) - t->K[i] * pow(rt, g2 - 1.0) / (g2 - 1.0);
+  }
+  for (int i = 0; i < kMaxPieces; ++i) {
+    if (i < kMaxPieces - 1) t->frho[i] = (float)t->rho[i];
+    t->fK[i] = (float)t->K[i]; t->fG[i] = (float)t->G[i]; t->fgm1[i] = (float)t->gm1[i]; t->fde[i] = (float)t->de[i];
+  }
 }
 
 // One refinement level as seen by a kernel: planes of P = px * pz doubles.
@@ -226,18 +263,43 @@ __device__ inline Sym3 conf_metric(const double *U, size_t P, int id) {
 // the neutron-star workloads) takes the exact product instead, rounded the
 // same way as K * pow(rho, 2).  Templated on the arithmetic type T (double,
 // or float in the mixed-precision hydro); every constant goes through T(...).
+// More than one cold piece: the piece holding rho from the star's table.
+template <typename T>
+__device__ __forceinline__ int eos_piece(const DevParams &p, T rho) {
+  int i = 0;
+  while (i < p.n_pieces - 1 && rho >= pv<T>(p.pwp->rho[i], p.pwp->frho[i])) ++i;
+  return i;
+}
 template <typename T>
 __device__ inline T eos_pc(const DevParams &p, T rho) {
   if (p.K_zero) return T(0);
+  if (p.n_pieces > 1) {
+    const int i = eos_piece(p, rho);
+    return pv<T>(p.pwp->K[i], p.pwp->fK[i]) * pow(rho, pv<T>(p.pwp->G[i], p.pwp->fG[i]));
+  }
   const T K = pv<T>(p.K, p.fK);
   return p.gamma2 ? K * (rho * rho) : K * pow(rho, pv<T>(p.Gamma, p.fGamma));
 }
 template <typename T>
 __device__ inline T eos_ec(const DevParams &p, T rho) {
   if (p.K_zero) return T(0);
+  if (p.n_pieces > 1) {
+    const int i = eos_piece(p, rho);
+    const T gm1 = pv<T>(p.pwp->gm1[i], p.pwp->fgm1[i]);
+    return pv<T>(p.pwp->K[i], p.pwp->fK[i]) * pow(rho, gm1) / gm1 + pv<T>(p.pwp->de[i], p.pwp->fde[i]);
+  }
   const T K = pv<T>(p.K, p.fK);
   const T gm1 = pv<T>(p.Gamma - 1.0, p.fGm1);
   return p.gamma2 ? K * rho : K * pow(rho, gm1) / gm1;
+}
+// Gamma of the piece holding rho
+template <typename T>
+__device__ inline T eos_gc(const DevParams &p, T rho) {
+  if (p.n_pieces > 1) {
+    const int i = eos_piece(p, rho);
+    return pv<T>(p.pwp->G[i], p.pwp->fG[i]);
+  }
+  return pv<T>(p.Gamma, p.fGamma);
 }
 template <typename T>
 __device__ inline T eos_p(const DevParams &p, T rho, T eps) {
@@ -252,7 +314,7 @@ template <typename T>
 __device__ inline T eos_cs2(const DevParams &p, T rho, T eps, T P) {
   const T pc = eos_pc(p, rho);
   const T h = T(1) + eps + P / rho;
-  T c2 = (pv<T>(p.Gamma, p.fGamma) * pc + pv<T>(p.Gamma_th, p.fGamma_th) * (P - pc)) / (rho * h);
+  T c2 = (eos_gc(p, rho) * pc + pv<T>(p.Gamma_th, p.fGamma_th) * (P - pc)) / (rho * h);
   if (!(c2 > T(0))) c2 = T(0);
   const T cmax = sizeof(T) == 8 ? T(1.0 - 1e-15) : T(1.0f - 1e-6f);
   if (c2 >= T(1)) c2 = cmax;
@@ -376,6 +438,36 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
   }
   int st = 0;
   double r = sqrt(W * W * s3quad(gi, S, S)) / D;
+  if (p.adiabatic) {
+    // "adiabatic" EOS (Sec. III): zero temperature, the energy equation is
+    // discarded: the cold recovery from D and S_i alone, the Lorentz factor
+    // capped at w_max through r (z = r / h_c <= r), then E rebuilt
+    if (r > p.c2p_zmax) {
+      const double s = p.c2p_zmax / r;
+      S[0] *= s; S[1] *= s; S[2] *= s;
+      r = p.c2p_zmax;
+      st |= ST_KRESCALE;
+    }
+    int its, ok;
+    const double z = illinois<true>(p, 0.0, r, D, 0.0, r, &its, &ok);
+    if (!ok) st |= ST_NOCONV;
+    const double w = sqrt(1.0 + z * z);
+    const double rho = D / w;
+    const double eps = eos_ec(p, rho), P = eos_pc(p, rho);
+    const double Dh = D * (1.0 + eps + P / rho);
+    pr[pRHO] = rho;
+    pr[pEPS] = eps;
+    pr[pP] = P;
+    pr[pUX] = S[0] / Dh;
+    pr[pUY] = S[1] / Dh;
+    pr[pUZ] = S[2] / Dh;
+    if (rho < p.rho_atm) {
+      atmosphere(p, pr);
+      st |= ST_ATM;
+    }
+    prim_to_cons(p, pr, W, gt, x, q);
+    return st;
+  }
   const double qq = E / D - 1.0;
   double k = r / (1.0 + qq);
   const double kmax = p.c2p_kmax;
@@ -519,6 +611,11 @@ struct SRState {
 // the mixed-precision form (see face_flux).
 template <typename T>
 __device__ inline void sr_state(const DevParams &p, T rho, T P, T Poff, T u0, T u1, T u2, SRState<T> &s) {
+  if (p.adiabatic) {            // zero temperature at the face too
+    const T Pc = eos_pc(p, rho);
+    Poff += Pc - P;
+    P = Pc;
+  }
   const T w = sqrt(T(1) + u0 * u0 + u1 * u1 + u2 * u2);
   const T eps = eos_eps(p, rho, P);
   const T h = T(1) + eps + P / rho;

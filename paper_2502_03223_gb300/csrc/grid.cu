@@ -195,7 +195,7 @@ __global__ void k_prolong_hydro(Lev L, Lev Pa, DevParams p, double *__restrict__
     pr[f] = a0 + ox * minmod(a[1] - a0, a0 - a[-1]) + oz * minmod(a[Pa.px] - a0, a0 - a[-Pa.px]);
   }
   const double pc0 = eos_pc(p, pr[pRHO]);
-  if (pr[pP] < pc0) pr[pP] = pc0;
+  if (pr[pP] < pc0 || p.adiabatic) pr[pP] = pc0;
   pr[pEPS] = eos_eps(p, pr[pRHO], pr[pP]);
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = pr[f];

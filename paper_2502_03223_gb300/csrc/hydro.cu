@@ -361,6 +361,10 @@ __global__ void k_prim2cons_all(Lev L, DevParams p, double *__restrict__ U) {
   double pr[NPRIM];
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) pr[f] = L.prim[(size_t)f * P + i];
+  if (p.adiabatic) {                    // zero temperature
+    pr[pP] = eos_pc(p, pr[pRHO]);
+    L.prim[(size_t)pP * P + i] = pr[pP];
+  }
   pr[pEPS] = eos_eps(p, pr[pRHO], pr[pP]);
   L.prim[(size_t)pEPS * P + i] = pr[pEPS];
   const int j = i % L.px - GH + 1;
@@ -386,7 +390,7 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
   const int st = cons_to_prim(p, q, U[(size_t)fW * P + id], g, (j - 0.5) * L.dx, pr);
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + id] = pr[f];
-  if (st & (ST_ATM | ST_COLD | ST_KRESCALE))
+  if ((st & (ST_ATM | ST_COLD | ST_KRESCALE)) || p.adiabatic)   // the adiabatic recovery always rebuilds E
 #pragma unroll
     for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + id] = q[v];
   L.status[id] = st;

@@ -35,6 +35,8 @@ extern "C" sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level
   if (p->geometry != SACRA_PLANAR && p->geometry != SACRA_CYLINDRICAL) return SACRA_ERR_ARG;
   if (p->solver != SACRA_HLLC && p->solver != SACRA_TVDLF) return SACRA_ERR_ARG;
   if (!(p->dx0 > 0) || !(p->dz0 > 0) || !(p->Gamma_th > 1.0)) return SACRA_ERR_ARG;
+  if (p->n_pieces > 1) return SACRA_ERR_ARG;          // the piece table needs the context's device memory
+  if (p->eos_adiabatic && !(p->K > 0.0)) return SACRA_ERR_ARG;
   const size_t px = (size_t)p->nx + 2 * GH, pz = (size_t)p->nz + 2 * GH;
   if (px * pz > kMaxPlane) return SACRA_ERR_ARG;    // beyond the static scratch
 

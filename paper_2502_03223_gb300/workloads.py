@@ -41,6 +41,8 @@ class RunConfig:
     precision: int = 0         # 0 FP64, 1 mixed FP32/FP64 (GPU library only; the oracle is FP64)
     subcycle_from: int = 0     # 0 lockstep; K >= 1: levels >= K take half their parent's step
     hydro_outer: int = 0       # outer hydro boundary: 0 zero-gradient copy, 1 held at the initial data
+    eos_adiabatic: int = 0     # 1: zero temperature (P = P_cold, eps = eps_cold), energy equation discarded
+    pwp: tuple = ()            # further cold pieces: ((rho_1, Gamma_2), (rho_2, Gamma_3), ...)
     dx0: float = 1.0
     dz0: float = 1.0
     kappa: float = 0.0
@@ -149,15 +151,62 @@ class TOVSolution:
     alpha: np.ndarray   # equilibrium lapse on the table (exterior: isotropic Schwarzschild)
 
 
-def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
-    """Tolman-Oppenheimer-Volkoff equilibrium of P = K rho^Gamma by classical
-    RK4 in the areal radius R, with the isotropic radius r(R) integrated
-    alongside and matched to exterior Schwarzschild at the surface."""
+def cold_pieces(K, Gamma, pwp=()):
+    """Piecewise polytropic cold curve for the initial data: one entry
+    (rho_lo, K_i, Gamma_i, Delta eps_i) per piece, K_(i+1) and Delta eps_(i+1)
+    from continuity of P and eps at rho_i."""
+    out = [(0.0, K, Gamma, 0.0)]
+    for rt, g2 in pwp:
+        _, k, g, d = out[-1]
+        k2 = k * rt ** (g - g2)
+        out.append((rt, k2, g2, d + k * rt ** (g - 1.0) / (g - 1.0) - k2 * rt ** (g2 - 1.0) / (g2 - 1.0)))
+    return out
+
+
+def _piece_of_rho(pieces, rho):
+    i = 0
+    while i + 1 < len(pieces) and rho >= pieces[i + 1][0]:
+        i += 1
+    return pieces[i]
+
+
+def cold_P(pieces, rho):
+    rho = np.asarray(rho, dtype=np.float64)
+    if len(pieces) == 1:
+        return pieces[0][1] * rho ** pieces[0][2]
+    out = np.zeros_like(rho)
+    for i, (rlo, k, g, _) in enumerate(pieces):
+        rhi = pieces[i + 1][0] if i + 1 < len(pieces) else np.inf
+        m = (rho >= rlo) & (rho < rhi)
+        out[m] = k * rho[m] ** g
+    return out
+
+
+def cold_rho_of_P(pieces, P):
+    """Inverse of cold_P (scalar)."""
+    i = 0
+    while i + 1 < len(pieces) and P >= pieces[i + 1][1] * pieces[i + 1][0] ** pieces[i + 1][2]:
+        i += 1
+    _, k, g, _ = pieces[i]
+    return (P / k) ** (1.0 / g)
+
+
+def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3, pwp=()) -> TOVSolution:
+    """Tolman-Oppenheimer-Volkoff equilibrium of the cold curve (one
+    polytrope P = K rho^Gamma, or the pieces of cold_pieces) by classical RK4
+    in the areal radius R, with the isotropic radius r(R) integrated alongside
+    and matched to exterior Schwarzschild at the surface."""
+    pieces = cold_pieces(K, Gamma, pwp)
+
     def eos_e(P):
         if P <= 0.0:
             return 0.0, 0.0
-        rho = (P / K) ** (1.0 / Gamma)
-        return rho, rho + P / (Gamma - 1.0)
+        if not pwp:
+            rho = (P / K) ** (1.0 / Gamma)
+            return rho, rho + P / (Gamma - 1.0)
+        rho = cold_rho_of_P(pieces, P)
+        _, k, g, d = _piece_of_rho(pieces, rho)
+        return rho, rho * (1.0 + k * rho ** (g - 1.0) / (g - 1.0) + d)
 
     def rhs(R, y):
         m, P, lnr, mb, nu = y
@@ -171,8 +220,12 @@ def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
         dmb = 4.0 * math.pi * R * R * rho / math.sqrt(1.0 - 2.0 * m / R)
         return np.array([dm, dP, dlnr, dmb, dnu])
 
-    Pc = K * rho_c ** Gamma
-    ec = rho_c + Pc / (Gamma - 1.0)
+    if not pwp:
+        Pc = K * rho_c ** Gamma
+        ec = rho_c + Pc / (Gamma - 1.0)
+    else:
+        Pc = float(cold_P(pieces, np.array([rho_c]))[0])
+        ec = eos_e(Pc)[1]
     R = dR * 1e-3
     y = np.array([4.0 / 3.0 * math.pi * R ** 3 * ec, Pc, math.log(R), 4.0 / 3.0 * math.pi * R ** 3 * rho_c, 0.0])
     Rs, Ys = [R], [y.copy()]
@@ -202,7 +255,7 @@ def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
     lnr = Ys[:, 2] - Ys[-1, 2] + math.log(rsurf)
     r = np.exp(lnr)
     P = np.maximum(Ys[:, 1], 0.0)
-    rho = (P / K) ** (1.0 / Gamma)
+    rho = (P / K) ** (1.0 / Gamma) if not pwp else np.array([cold_rho_of_P(pieces, x) if x > 0 else 0.0 for x in P])
     psi = np.sqrt(Rs / r)
     # lapse e^nu matched to sqrt(1 - 2M/R) at the surface
     alpha = np.exp(Ys[:, 4] - Ys[-1, 4]) * math.sqrt(1.0 - 2.0 * M / Rsurf)
@@ -211,14 +264,16 @@ def tov_solve(K=100.0, Gamma=2.0, rho_c=1.28e-3, dR=2e-3) -> TOVSolution:
 
 
 def tov_config(name, rho_c=1.28e-3, n_levels=3, N=256, dx_fine=0.25, rk=1, solver=0, f_atm=1e-10,
-               K=100.0, Gamma=2.0, Gamma_th=2.0, tov: TOVSolution | None = None) -> tuple[RunConfig, TOVSolution]:
+               K=100.0, Gamma=2.0, Gamma_th=2.0, tov: TOVSolution | None = None, pwp=(),
+               eos_adiabatic=0) -> tuple[RunConfig, TOVSolution]:
     if tov is None:
-        tov = tov_solve(K, Gamma, rho_c)
+        tov = tov_solve(K, Gamma, rho_c, pwp=pwp)
     dx0 = dx_fine * (1 << (n_levels - 1))
     xmax = dx0 * N
     cfg = RunConfig(name=name, n_levels=n_levels, nx=N, nz=N, geometry=1, evolve_spacetime=1, solver=solver,
                     rk=rk, dx0=dx0, dz0=dx0, kappa=5e-3 / tov.M, eta_B=1.0 / tov.M, eps_ko=0.5, r_z4=xmax / 6.0,
-                    K=K, Gamma=Gamma, Gamma_th=Gamma_th, rho_atm=f_atm * rho_c, cfl=0.5, mass=tov.M)
+                    K=K, Gamma=Gamma, Gamma_th=Gamma_th, rho_atm=f_atm * rho_c, cfl=0.5, mass=tov.M,
+                    pwp=tuple(pwp), eos_adiabatic=eos_adiabatic)
     return cfg, tov
 
 
@@ -227,6 +282,8 @@ def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0, 
     Khat = Theta = Gt = beta = B = 0, fluid at rest; atmosphere outside.  A
     pressure depletion factor lowers P on the cold curve (rho scaled so that
     P = K rho^Gamma still holds)."""
+    if cfg.pwp and p_deplete != 1.0:
+        raise ValueError("pressure depletion is implemented for single-polytrope stars")
     X, Z = cell_centres(cfg, level)
     r = np.sqrt(X * X + Z * Z)
     inside = r < tov.r_iso
@@ -236,7 +293,10 @@ def tov_level_data(cfg: RunConfig, tov: TOVSolution, level: int, p_deplete=1.0, 
     if p_deplete != 1.0:
         rho = rho * p_deplete ** (1.0 / cfg.Gamma)
     rho = np.maximum(rho, rho_atm)
-    P = cfg.K * rho ** cfg.Gamma
+    if cfg.pwp:
+        P = cold_P(cold_pieces(cfg.K, cfg.Gamma, cfg.pwp), rho)
+    else:
+        P = cfg.K * rho ** cfg.Gamma
     d = np.zeros((30, cfg.pz, cfg.px))
     d[0] = psi ** -2
     d[18] = psi ** -2
