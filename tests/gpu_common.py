@@ -7,6 +7,7 @@ from paper_2502_03223_gb300 import sacra2d as S
 from paper_2502_03223_gb300 import workloads as W
 
 G = 8
+ST_COLD, ST_ATM = 2, 4
 
 
 def both(cfg, datas):
@@ -44,11 +45,31 @@ def group_scale(planes, groups, f, xmax=1.0):
     raise KeyError(f)
 
 
-def compare_level(gpu, orc, level, tol=1e-11, which=(0, 1, 2), max_frac=1e-3, report=None):
+def atmosphere_threshold_cells(gpu, orc, level, rho_atm, rel=1e-9):
+    """Cells where one side reset to the atmosphere and the other did not,
+    with the density at the threshold on both sides (|rho / rho_atm - 1| <=
+    rel): the decision rho < rho_atm taken on values that differ by rounding.
+    Both outcomes are valid; the velocities of such a cell (S / (D h) with S
+    at round-off, against 0) are not comparable."""
+    sa = gpu.read(level, S.STATUS, 0).astype(np.int64)
+    sb = orc.read(level, 4, 0).astype(np.int64)
+    ra = gpu.read(level, S.PRIMS, 0)
+    rb = orc.read(level, 2, 0)
+    flip = (sa & ST_ATM) != (sb & ST_ATM)
+    at = (np.abs(ra / rho_atm - 1.0) <= rel) & (np.abs(rb / rho_atm - 1.0) <= rel)
+    return flip & at
+
+
+def compare_level(gpu, orc, level, tol=1e-11, which=(0, 1, 2), max_frac=1e-3, report=None, excuse=None,
+                  floors=None):
     """Compare the state / primitive / rhs planes of a level cell by cell:
     |a - b| <= tol * max(|b|, S_group).  Returns the worst ratio; asserts that
     at most max_frac of the cells exceed tol (cells where a discrete branch,
-    e.g. a limiter or the recovery's iteration count, flipped)."""
+    e.g. a limiter or the recovery's iteration count, flipped).  Cells in the
+    boolean mask `excuse` (a flip checked separately to be valid on both
+    sides) are left out.  floors = {state field: S}: a lower bound on S_group
+    for fields whose own maximum understates the size of the terms they are
+    computed from (see the caller)."""
     worst = 0.0
     for w in which:
         prim = w == S.PRIMS
@@ -61,21 +82,22 @@ def compare_level(gpu, orc, level, tol=1e-11, which=(0, 1, 2), max_frac=1e-3, re
         for f in range(nf):
             a, b = A[f], B[f]
             sg = group_scale(B, groups, f, xmax)
+            if floors and not prim and f in floors:
+                sg = max(sg, floors[f])
             if prim and f in (1, 2, 3):
                 sg = max(sg, 1.0)          # velocities: units of c
             scale = np.maximum(np.abs(b), sg)
             with np.errstate(divide="ignore", invalid="ignore"):
                 r = np.where(scale > 0, np.abs(a - b) / scale, np.where(a == b, 0.0, np.inf))
             bad = ~(r <= tol)
+            if excuse is not None:
+                bad &= ~excuse
             frac = float(bad.mean())
             worst = max(worst, float(np.max(r[~bad])) if np.any(~bad) else 0.0)
             if report is not None and frac > 0:
                 report.append((level, w, f, frac, float(np.max(r))))
             assert frac <= max_frac, (level, w, f, frac, float(np.nanmax(r)))
     return worst
-
-
-ST_COLD, ST_ATM = 2, 4
 
 
 def _observable_status(st):
