@@ -48,6 +48,8 @@ struct DevParams {
   int n_pieces;          // cold pieces (1: K, Gamma; more: the table pwp)
   const PwpTable *pwp;   // device copy of the pieces when n_pieces > 1
   double c2p_zmax;       // sqrt(w_max^2 - 1): Lorentz-factor cap of the adiabatic recovery
+  double ith1;           // 1 / (Gamma_th - 1)
+  float fith1;
   double r_hold2;        // > 0: hydro held at U^n where x^2 + z^2 < r_hold2 (excised inner boundary)
   double K, Gamma, Gamma_th, rho_atm, w_max, c2p_tol;
   double kappa, eta_B, eps_ko, r_z4;
@@ -90,6 +92,8 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->n_pieces = p->n_pieces > 1 ? p->n_pieces : 1;
   d->pwp = nullptr;      // set by the owner of the device copy
   d->c2p_zmax = sqrt(p->w_max * p->w_max - 1.0);
+  d->ith1 = 1.0 / (p->Gamma_th - 1.0);
+  d->fith1 = (float)d->ith1;
 }
 
 // The pieces' constants (host): K_(i+1) from continuity of P_cold at rho_i,
@@ -343,28 +347,33 @@ __device__ inline void prim_to_cons(const DevParams &p, const double pr[NPRIM], 
   q[4] = psi6 * (rhw * w - P);
 }
 
+// D and its reciprocal (1 / rho = w / D inside the master function)
+struct C2pD {
+  double v, inv;
+};
+
 // Master functions of the recovery (Sec. II.C.4, Eq. c2p_fn); COLD selects
 // z - r / h_cold(rho(z)).  The thermal EOS sees eps clamped to the cold curve.
+// h = (1 + eps)(1 + a), a = P / (rho (1 + eps)), is formed as 1 + eps + P / rho.
 template <bool COLD>
-__device__ inline double c2p_fun(const DevParams &p, double z, double D, double qq, double r) {
+__device__ inline double c2p_fun(const DevParams &p, double z, C2pD D, double qq, double r) {
   const double w = sqrt(1.0 + z * z);
-  const double rho = D / w;
+  const double rho = D.v / w, irho = w * D.inv;
   if (COLD) {
-    const double hc = 1.0 + eos_ec(p, rho) + eos_pc(p, rho) / rho;
+    const double hc = 1.0 + eos_ec(p, rho) + eos_pc(p, rho) * irho;
     return z - r / hc;
   }
   double eps = w * qq - z * r + z * z / (1.0 + w);
   const double emin = eos_ec(p, rho);
   if (eps < emin) eps = emin;
   const double P = eos_p(p, rho, eps);
-  const double a = P / (rho * (1.0 + eps));
-  return z - r / ((1.0 + eps) * (1.0 + a));
+  return z - r / (1.0 + eps + P * irho);
 }
 
 // Illinois bracketing iteration from the bracket [a, b] with the master
 // function's values fa, fb there; *ok = 0 on no sign change or at the cap
 template <bool COLD>
-__device__ double illinois_from(const DevParams &p, double a, double fa, double b, double fb, double D, double qq,
+__device__ double illinois_from(const DevParams &p, double a, double fa, double b, double fb, C2pD D, double qq,
                                 double r, int *its, int *ok) {
   *its = 0;
   *ok = 1;
@@ -398,7 +407,7 @@ __device__ double illinois_from(const DevParams &p, double a, double fa, double 
 
 // Illinois bracketing iteration on [a, b]
 template <bool COLD>
-__device__ double illinois(const DevParams &p, double a, double b, double D, double qq, double r, int *its, int *ok) {
+__device__ double illinois(const DevParams &p, double a, double b, C2pD D, double qq, double r, int *its, int *ok) {
   const double fa = c2p_fun<COLD>(p, a, D, qq, r), fb = c2p_fun<COLD>(p, b, D, qq, r);
   return illinois_from<COLD>(p, a, fa, b, fb, D, qq, r, its, ok);
 }
@@ -449,7 +458,7 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
       st |= ST_KRESCALE;
     }
     int its, ok;
-    const double z = illinois<true>(p, 0.0, r, D, 0.0, r, &its, &ok);
+    const double z = illinois<true>(p, 0.0, r, C2pD{D, 1.0 / D}, 0.0, r, &its, &ok);
     if (!ok) st |= ST_NOCONV;
     const double w = sqrt(1.0 + z * z);
     const double rho = D / w;
@@ -468,6 +477,7 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
     prim_to_cons(p, pr, W, gt, x, q);
     return st;
   }
+  const C2pD Dd{D, 1.0 / D};
   const double qq = E / D - 1.0;
   double k = r / (1.0 + qq);
   const double kmax = p.c2p_kmax;
@@ -496,20 +506,20 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
     if (v > 0.0f && v < 1.0f) {
       const float z0 = v * rsqrtf(1.0f - v * v), dl = net->delta;
       const double zs = fmin(fmax(f64_of(z0), zlo), zhi);
-      const double f0 = c2p_fun<false>(p, zs, D, qq, r);
+      const double f0 = c2p_fun<false>(p, zs, Dd, qq, r);
       double a, fa, b, fb;
       if (f0 < 0.0) {
         a = zs; fa = f0;
         b = fmin(zhi, f64_of(z0 * (1.0f + dl)));
-        fb = c2p_fun<false>(p, b, D, qq, r);
+        fb = c2p_fun<false>(p, b, Dd, qq, r);
       } else {
         b = zs; fb = f0;
         a = fmax(zlo, f64_of(z0 * (1.0f - dl)));
-        fa = c2p_fun<false>(p, a, D, qq, r);
+        fa = c2p_fun<false>(p, a, Dd, qq, r);
       }
       ev += 2;
       if (a <= b) {
-        z = illinois_from<false>(p, a, fa, b, fb, D, qq, r, &its, &ok);
+        z = illinois_from<false>(p, a, fa, b, fb, Dd, qq, r, &its, &ok);
         ev += its;
         solved = ok != 0;
         held = solved ? 1 : 0;
@@ -517,7 +527,7 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
     }
   }
   if (!solved) {
-    z = illinois<false>(p, zlo, zhi, D, qq, r, &its, &ok);
+    z = illinois<false>(p, zlo, zhi, Dd, qq, r, &its, &ok);
     ev += its + 2;
   }
   if (p.c2p_stats) {
@@ -532,7 +542,7 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
   double eps = w * qq - z * r + z * z / (1.0 + w);
   double P;
   if (eps < eos_ec(p, rho)) {
-    z = illinois<true>(p, 0.0, r, D, qq, r, &its, &ok);
+    z = illinois<true>(p, 0.0, r, Dd, qq, r, &its, &ok);
     if (!ok) st |= ST_NOCONV;
     w = sqrt(1.0 + z * z);
     rho = D / w;
@@ -588,9 +598,9 @@ __device__ inline void ppm_pair(const T c[6], T &left, T &right) {
   const T s2 = mc_slope(c[1], c[2], c[3]);
   const T s3 = mc_slope(c[2], c[3], c[4]);
   const T s4 = mc_slope(c[3], c[4], c[5]);
-  const T im = c[1] + T(0.5) * (c[2] - c[1]) - (s2 - s1) / T(6);   // face j-1/2
-  const T i0 = c[2] + T(0.5) * (c[3] - c[2]) - (s3 - s2) / T(6);   // face j+1/2
-  const T ip = c[3] + T(0.5) * (c[4] - c[3]) - (s4 - s3) / T(6);   // face j+3/2
+  const T im = c[1] + T(0.5) * (c[2] - c[1]) - (s2 - s1) * T(1.0 / 6.0);   // face j-1/2
+  const T i0 = c[2] + T(0.5) * (c[3] - c[2]) - (s3 - s2) * T(1.0 / 6.0);   // face j+1/2
+  const T ip = c[3] + T(0.5) * (c[4] - c[3]) - (s4 - s3) * T(1.0 / 6.0);   // face j+3/2
   T aL = im, aR = i0;
   ppm_limit(c[2], aL, aR);
   left = aR;
@@ -616,16 +626,21 @@ __device__ inline void sr_state(const DevParams &p, T rho, T P, T Poff, T u0, T 
     Poff += Pc - P;
     P = Pc;
   }
+  // the EOS quantities of eos_eps and eos_cs2 with one reciprocal of rho and of w
   const T w = sqrt(T(1) + u0 * u0 + u1 * u1 + u2 * u2);
-  const T eps = eos_eps(p, rho, P);
-  const T h = T(1) + eps + P / rho;
-  const T c2 = eos_cs2(p, rho, eps, P);
+  const T iw = T(1) / w, irho = T(1) / rho;
+  const T pc = eos_pc(p, rho);
+  const T eps = eos_ec(p, rho) + (P - pc) * irho * pv<T>(p.ith1, p.fith1);
+  const T h = T(1) + eps + P * irho;
+  T c2 = (eos_gc(p, rho) * pc + pv<T>(p.Gamma_th, p.fGamma_th) * (P - pc)) * irho / h;
+  if (!(c2 > T(0))) c2 = T(0);
+  if (c2 >= T(1)) c2 = sizeof(T) == 8 ? T(1.0 - 1e-15) : T(1.0f - 1e-6f);
   const T rhw = rho * h * w;          // rho h w^2 v = rho h w u
   s.D = rho * w;
   s.S0 = rhw * u0; s.S1 = rhw * u1; s.S2 = rhw * u2;
   s.E = rhw * w - P;
   s.P = Poff;
-  const T v0 = u0 / w, v1 = u1 / w, v2 = u2 / w;
+  const T v0 = u0 * iw, v1 = u1 * iw, v2 = u2 * iw;
   s.vx = v0;
   const T vv = v0 * v0 + v1 * v1 + v2 * v2;
   T disc = c2 * (T(1) - vv) * (T(1) - vv * c2 - v0 * v0 * (T(1) - c2));

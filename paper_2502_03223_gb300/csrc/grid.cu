@@ -215,11 +215,11 @@ __device__ inline void enforce_algebraic(double m[NST]) {
   const Sym3 gi = s3inv(g, &det);
   const double tr = gi.xx * m[fAXX] + gi.yy * m[fAYY] + gi.zz * m[fAZZ]
                   + 2.0 * (gi.xy * m[fAXY] + gi.xz * m[fAXZ] + gi.yz * m[fAYZ]);
-  const double c13 = rcbrt(det), c16 = sqrt(c13);
+  const double c13 = rcbrt(det), c16 = sqrt(c13), tr3 = tr / 3.0;
   const double gv[6] = {g.xx, g.xy, g.xz, g.yy, g.yz, g.zz};
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    m[fAXX + a] = c13 * (m[fAXX + a] - gv[a] * tr / 3.0);
+    m[fAXX + a] = c13 * (m[fAXX + a] - gv[a] * tr3);
     const double gn = c13 * gv[a];
     m[fHXX + a] = (a == 0 || a == 3 || a == 5) ? gn - 1.0 : gn;
   }
@@ -255,12 +255,12 @@ __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p,
         L.ka[o] = (stage == 0 ? 0.0 : L.ka[o]) + bw * kk;
         out = un + (stage == 2 ? 1.0 : 0.5) * dt * kk;
       } else {
-        out = un + dt * (L.ka[o] + kk / 6.0);
+        out = un + dt * (L.ka[o] + kk * (1.0 / 6.0));
       }
     } else {
       if (stage == 0) out = un + dt * kk;
       else if (stage == 1) out = 0.75 * un + 0.25 * Ust[o] + 0.25 * dt * kk;
-      else out = un / 3.0 + (2.0 / 3.0) * Ust[o] + (2.0 / 3.0) * dt * kk;
+      else out = un * (1.0 / 3.0) + (2.0 / 3.0) * Ust[o] + (2.0 / 3.0) * dt * kk;
     }
     m[f] = out;
   }
