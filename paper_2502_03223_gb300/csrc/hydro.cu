@@ -290,8 +290,9 @@ __device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p,
   const T rho = pr[pRHO], Pp = pr[pP];
   const T u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
   const T w = sqrt(T(1) + W * W * s3quad(gi, u, u));
+  const T iw = T(1) / w;
   const T rhw2 = rho * (T(1) + pr[pEPS] + Pp / rho) * w * w;
-  const T vd[3] = {u[0] / w, u[1] / w, u[2] / w};
+  const T vd[3] = {u[0] * iw, u[1] * iw, u[2] * iw};
   T vu[3];
   s3vec(gi, vd, vu);
   vu[0] *= W * W; vu[1] *= W * W; vu[2] *= W * W;
@@ -330,12 +331,13 @@ __device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p,
   if constexpr (sizeof(T) == 4) K = ld(fKH) + 2.0f * ld(fTH);
   else K = U[(size_t)fKH * P + id] + 2.0 * U[(size_t)fTH * P + id];
   Sym3T<T> Kd;
-  Kd.xx = (ld(fAXX) + g.xx * K / T(3)) * iW * iW;
-  Kd.xy = (ld(fAXY) + g.xy * K / T(3)) * iW * iW;
-  Kd.xz = (ld(fAXZ) + g.xz * K / T(3)) * iW * iW;
-  Kd.yy = (ld(fAYY) + g.yy * K / T(3)) * iW * iW;
-  Kd.yz = (ld(fAYZ) + g.yz * K / T(3)) * iW * iW;
-  Kd.zz = (ld(fAZZ) + g.zz * K / T(3)) * iW * iW;
+  const T K3 = K * T(1.0 / 3.0), iW2 = iW * iW;
+  Kd.xx = (ld(fAXX) + g.xx * K3) * iW2;
+  Kd.xy = (ld(fAXY) + g.xy * K3) * iW2;
+  Kd.xz = (ld(fAXZ) + g.xz * K3) * iW2;
+  Kd.yy = (ld(fAYY) + g.yy * K3) * iW2;
+  Kd.yz = (ld(fAYZ) + g.yz * K3) * iW2;
+  Kd.zz = (ld(fAZZ) + g.zz * K3) * iW2;
   // gamma^ij K_ij = W^2 gt^ij K_ij (equal to K when At is trace-free)
   const T trK = W * W * (gi.xx * Kd.xx + gi.yy * Kd.yy + gi.zz * Kd.zz
                          + T(2) * (gi.xy * Kd.xy + gi.xz * Kd.xz + gi.yz * Kd.yz));

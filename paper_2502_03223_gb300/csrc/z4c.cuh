@@ -180,7 +180,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
   const T Str = W * W * (gi.xx * Sij[0] + gi.yy * Sij[3] + gi.zz * Sij[5]
                               + T(2.0) * (gi.xy * Sij[1] + gi.xz * Sij[2] + gi.yz * Sij[4]));
 
-  out[fW] = W * (al * K - divb) / T(3.0);
+  out[fW] = W * (al * K - divb) * T(1.0 / 3.0);
 
   // X_ij = alpha R_ij - D_i D_j alpha - 8 pi alpha S_ij and its gt-trace
   T X[6];
@@ -193,7 +193,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
     for (int j = i; j < 3; ++j) {
       const int ij = sp(i, j);
       T sh = -T(2.0) * al * z.A[ij] - (T(2.0) / T(3.0)) * gm[i][j] * divb;
-      T sa = W * W * (X[ij] - gm[i][j] * trX / T(3.0))
+      T sa = W * W * (X[ij] - gm[i][j] * (trX * T(1.0 / 3.0)))
                 + al * (K * z.A[ij] - T(2.0) * (Am[i][0] * z.A[sp(0, j)] + Am[i][1] * z.A[sp(1, j)] + Am[i][2] * z.A[sp(2, j)]))
                 - (T(2.0) / T(3.0)) * z.A[ij] * divb;
 #pragma unroll
@@ -205,7 +205,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
       out[fAXX + ij] = sa;
     }
 
-  out[fKH] = -D2a + al * (AA + K * K / T(3.0)) + T(4.0) * PI * al * (Str + E) + al * kap * z.Th;
+  out[fKH] = -D2a + al * (AA + K * K * T(1.0 / 3.0)) + T(4.0) * PI * al * (Str + E) + al * kap * z.Th;
 
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -213,7 +213,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       s -= T(2.0) * Au[sp(i, j)] * z.dal[j];
-      in -= gim[i][j] * (T(2.0) * z.dKh[j] + z.dTh[j]) / T(3.0) + T(3.0) * iW * Au[sp(i, j)] * z.dW[j]
+      in -= gim[i][j] * (T(2.0) * z.dKh[j] + z.dTh[j]) * T(1.0 / 3.0) + T(3.0) * iW * Au[sp(i, j)] * z.dW[j]
           + T(8.0) * PI * gim[i][j] * Si[j];
       grad += gim[i][j] * (z.ddb[0][sp(j, 0)] + z.ddb[1][sp(j, 1)] + z.ddb[2][sp(j, 2)]);
       s -= G.Gd[j] * z.db[i][j];
@@ -222,7 +222,7 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
     for (int a = 0; a < 6; ++a) in += (a == 0 || a == 3 || a == 5 ? T(1.0) : T(2.0)) * G.G2[i][a] * Au[a];
     lap = gi.xx * z.ddb[i][0] + gi.yy * z.ddb[i][3] + gi.zz * z.ddb[i][5]
         + T(2.0) * (gi.xy * z.ddb[i][1] + gi.xz * z.ddb[i][2] + gi.yz * z.ddb[i][4]);
-    s += T(2.0) * al * in + (T(2.0) / T(3.0)) * G.Gd[i] * divb + lap + grad / T(3.0) - T(2.0) * al * kap * (z.Gt[i] - G.Gd[i]);
+    s += T(2.0) * al * in + (T(2.0) / T(3.0)) * G.Gd[i] * divb + lap + grad * T(1.0 / 3.0) - T(2.0) * al * kap * (z.Gt[i] - G.Gd[i]);
     out[fGX + i] = s;
     out[fBBX + i] = s - pv<T>(p.eta_B, p.feta_B) * z.B[i];
   }
