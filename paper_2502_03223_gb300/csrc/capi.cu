@@ -540,6 +540,7 @@ void enqueue_restrict(Engine &e, Star &st) {
     enqueue_parity(e, st, l, C.un);
     const int nh = Pa.nx / 2;
     run(e, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, e.stream); });
+    ++e.launches;   // the restriction is two kernels
     run(e, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, st.dt_step, e.stream); });
     // the restricted cells [1, N/2]^2 and the refluxed strips next to them (not the corner)
     run(e, K_C2P, (long long)(nh + 1) * (nh + 1) - 1,
@@ -558,6 +559,7 @@ void enqueue_restrict_pair(Engine &e, Star &st, int l, double dt) {
   enqueue_parity(e, st, l, C.un);
   const int nh = Pa.nx / 2;
   run(e, K_RESTRICT, (long long)nh * nh, [&] { launch_restrict(C, Pa, e.stream); });
+  ++e.launches;   // the restriction is two kernels
   run(e, K_REFLUX, 2LL * nh, [&] { launch_reflux(C, Pa, dt, e.stream); });
   run(e, K_C2P, (long long)(nh + 1) * (nh + 1) - 1,
       [&] { launch_c2p_region(Pa, st.dp, Pa.un, 1, nh + 1, 1, nh + 1, e.stream, 1); });

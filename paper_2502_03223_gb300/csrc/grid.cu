@@ -344,13 +344,13 @@ void launch_time_interp(const Lev &P, const double *uold, const double *pold, co
 // Restriction of child level C onto parent cells [1, N/2]^2 (Sec. II.D):
 // q as the volume-weighted average of the 2x2 children, the metric by 8th-
 // order Lagrange (nodes shifted inward so that none passes the child edge N).
-// blockIdx.z: the field (metric 0..24, conserved 25..29).
-__global__ void k_restrict(Lev C, Lev Pa) {
+// blockIdx.z + f0: the field (metric 0..24, conserved 25..29).
+__global__ void k_restrict(Lev C, Lev Pa, int f0) {
   const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
   const int nh = Pa.nx / 2;
   if (j > nh || k > nh) return;
-  const int f = blockIdx.z;
+  const int f = f0 + (int)blockIdx.z;
   const size_t P = C.P, PP = Pa.P;
   const int d = cid(Pa, j, k);
   const int c00 = cid(C, 2 * j - 1, 2 * k - 1);
@@ -379,6 +379,49 @@ __global__ void k_restrict(Lev C, Lev Pa) {
     s += wz[b] * r;
   }
   Pa.un[(size_t)f * PP + d] = u0 + s;
+}
+
+// The metric part of the restriction as two passes through shared memory: the
+// x-interpolation of every child row a tile of parent cells needs (each row
+// serves four parent rows), then the z-interpolation of those row values;
+// the same 8 x 8 weights as k_restrict, applied as separable sums.  Block:
+// RX x RZ parent cells of one field (blockIdx.z).
+constexpr int RX = 32, RZ = 8, RROWS = 2 * RZ + 6;
+__global__ void __launch_bounds__(RX * RZ) k_restrict_metric(Lev C, Lev Pa) {
+  __shared__ double row[RROWS][RX];
+  const int nh = Pa.nx / 2, N = C.nx;
+  const int j0 = 1 + (int)blockIdx.x * RX, k0 = 1 + (int)blockIdx.y * RZ;
+  const double *u = C.un + (size_t)blockIdx.z * C.P;
+  // pass 1: child rows rs .. rs + RROWS - 1 interpolated in x at each parent
+  // column; rs = 2 k0 - 4, or N - 7 when the tile holds only the last two rows
+  const int rs = min(2 * k0 - 4, N - 7);
+  const int tid = threadIdx.y * RX + threadIdx.x;
+  for (int e = tid; e < RROWS * RX; e += RX * RZ) {
+    const int rr = e / RX, jj = e % RX;
+    const int j = j0 + jj, kc = rs + rr;
+    double v = 0.0;
+    if (j <= nh && kc <= N) {
+      const double *wx;
+      int bx;
+      if (j <= nh - 2) { wx = cW.rest_c; bx = 2 * j - 4; } else { wx = (j == nh) ? cW.rest_s0 : cW.rest_s1; bx = N - 7; }
+      const double *q = u + cid(C, bx, kc);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) v += wx[a] * q[a];
+    }
+    row[rr][jj] = v;
+  }
+  __syncthreads();
+  // pass 2: z-interpolation of the rows
+  const int j = j0 + (int)threadIdx.x, k = k0 + (int)threadIdx.y;
+  if (j > nh || k > nh) return;
+  const double *wz;
+  int bz;
+  if (k <= nh - 2) { wz = cW.rest_c; bz = 2 * k - 4; } else { wz = (k == nh) ? cW.rest_s0 : cW.rest_s1; bz = N - 7; }
+  const int r0 = bz - rs;
+  double s = 0.0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) s += wz[b] * row[r0 + b][threadIdx.x];
+  Pa.un[(size_t)blockIdx.z * Pa.P + cid(Pa, j, k)] = s;
 }
 
 // Reflux (Sec. II.D): parent cells next to the child's outer faces get the
@@ -590,8 +633,9 @@ void launch_rk_update(const Lev &L, const DevParams &p, double *Ust, int stage, 
 
 void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s) {
   const int nh = Pa.nx / 2;
-  dim3 b(32, 4), g((nh + 31) / 32, (nh + 3) / 4, NST);
-  k_restrict<<<g, b, 0, s>>>(C, Pa);
+  k_restrict_metric<<<dim3((nh + RX - 1) / RX, (nh + RZ - 1) / RZ, NMET), dim3(RX, RZ), 0, s>>>(C, Pa);
+  dim3 b(32, 4), g((nh + 31) / 32, (nh + 3) / 4, NCONS);
+  k_restrict<<<g, b, 0, s>>>(C, Pa, NMET);
 }
 
 void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s) {
