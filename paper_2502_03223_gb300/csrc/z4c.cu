@@ -496,9 +496,18 @@ __constant__ signed char kD2Of[NMET] = {0, 1, 2, 3, 4, 5, 6, -1, -1, -1, -1, -1,
 
 template <typename T>
 __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
-                                                double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k) {
+                                                double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k,
+                                                double *sdz = nullptr, int j0 = 0) {
   static_assert(sizeof(T) == 8, "the FP32 form is z4c_derivs_f32_tile");
-  if (j > jmax || k > kmax) return;
+  // XCH (sdz given): the mixed derivative d_xz is the x-difference of the
+  // z-differences of the neighbouring columns, which the block exchanges
+  // through shared memory (row of blockDim.x + 6 columns per thread row);
+  // every thread of the block then runs the field loop (it has barriers)
+  const bool xch = sdz != nullptr;
+  const bool active = j <= jmax && k <= kmax;
+  if (!xch && !active) return;
+  const int bw = (int)blockDim.x + 6;
+  double *srow = xch ? sdz + (size_t)threadIdx.y * bw : nullptr;
   const size_t P = L.P;
   const int id = cid(L, j, k);
   const int sz = L.px;
@@ -508,6 +517,20 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
   const double ko = p.ko, ikx = L.idx, ikz = L.idz;
 #pragma unroll 1
   for (int f = 0; f < NMET; ++f) {
+    if (xch && kD2Of[f] >= 0) {
+      __syncthreads();                                   // the previous field's row is read
+      for (int e = threadIdx.x; e < bw; e += blockDim.x) {
+        const int jc = j0 - 3 + e;
+        double v = 0.0;
+        if (k <= kmax && jc <= jmax + 3) {
+          const double *c = U + (size_t)f * P + cid(L, jc, k);
+          v = 45.0 * (c[sz] - c[-sz]) - 9.0 * (c[2 * sz] - c[-2 * sz]) + (c[3 * sz] - c[-3 * sz]);
+        }
+        srow[e] = v;
+      }
+      __syncthreads();
+    }
+    if (!active) continue;
     const double *u = U + (size_t)f * P + id;
     const double u0 = u[0];
     double Dx[9], Dz[9];
@@ -525,13 +548,18 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
     }
     if (a2 >= 0) {
       double dxz = 0.0;
+      if (xch) {
+        const double *r = srow + threadIdx.x + 3;        // r[n]: z-difference at column j + n
+        dxz = 45.0 * (r[1] - r[-1]) - 9.0 * (r[2] - r[-2]) + (r[3] - r[-3]);
+      } else {
 #pragma unroll
-      for (int n = 1; n <= 3; ++n) {
-        const double w = n == 1 ? 45.0 : (n == 2 ? -9.0 : 1.0);
-        // d_z at j+n minus d_z at j-n (pair form in both directions)
-        const double zp = 45.0 * (u[n + sz] - u[n - sz]) - 9.0 * (u[n + 2 * sz] - u[n - 2 * sz]) + (u[n + 3 * sz] - u[n - 3 * sz]);
-        const double zm = 45.0 * (u[-n + sz] - u[-n - sz]) - 9.0 * (u[-n + 2 * sz] - u[-n - 2 * sz]) + (u[-n + 3 * sz] - u[-n - 3 * sz]);
-        dxz += w * (zp - zm);
+        for (int n = 1; n <= 3; ++n) {
+          const double w = n == 1 ? 45.0 : (n == 2 ? -9.0 : 1.0);
+          // d_z at j+n minus d_z at j-n (pair form in both directions)
+          const double zp = 45.0 * (u[n + sz] - u[n - sz]) - 9.0 * (u[n + 2 * sz] - u[n - 2 * sz]) + (u[n + 3 * sz] - u[n - 3 * sz]);
+          const double zm = 45.0 * (u[-n + sz] - u[-n - sz]) - 9.0 * (u[-n + 2 * sz] - u[-n - 2 * sz]) + (u[-n + 3 * sz] - u[-n - 3 * sz]);
+          dxz += w * (zp - zm);
+        }
       }
       double dxy = 0.0, dyz = 0.0, dyy = 0.0;
       if (cyl) {
@@ -563,6 +591,7 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
     adv += ko * (kx * ikx + kz * ikz);
     DS[(size_t)(DS_AK + f) * P + id] = adv;
   }
+  if (!active) return;
   if (edge) {
     // Eq. cartoon_bnd for cells beyond the level edge: d_xy from d_x and values
     const double x = (j - 0.5) * L.dx;
@@ -725,11 +754,14 @@ __global__ void __launch_bounds__(128) kb_cartoon_f32(Batch b, const double *__r
   });
 }
 
+constexpr int kDxzRow = 304;   // (blockDim.x + 6) * blockDim.y for every tuned shape up to 256 threads
 __global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
+  __shared__ double sdz[kDxzRow];
   const int cyl = p.geometry == SACRA_CYLINDRICAL;
+  const bool xch = ((int)blockDim.x + 6) * (int)blockDim.y <= kDxzRow;
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     z4c_derivs_cell<double>(q.L, q.P, q.U, reinterpret_cast<double *>(q.DS), q.jmax, q.kmax, cyl, tl.j0 + threadIdx.x,
-                            tl.k0 + threadIdx.y);
+                            tl.k0 + threadIdx.y, xch ? sdz : nullptr, tl.j0);
   });
 }
 
