@@ -711,7 +711,7 @@ __device__ inline int face_flux(const DevParams &p, int dir, const T pl[5], cons
   sr_qf(R, qR, fR);
   const T lamL = fmin(L.lm, R.lm);
   const T lamR = fmax(L.lp, R.lp);
-  const T sgxx = W * sqrt(mi.xx);
+  const T sgxx = W * (mi.xx * Bh);           // W sqrt(gt^xx)
   const T vint = bn / (alpha * sgxx);
 
   T F[5];
@@ -784,8 +784,8 @@ __device__ inline int face_flux(const DevParams &p, int dir, const T pl[5], cons
   }
   // back to the Eulerian frame with the covariant legs e_(a)_i:
   //   e_x = (B/W)(1,0,0), e_y = (D/W)(-gt^xy, gt^xx, 0), e_z = (C/W)(gt_xz, gt_yz, gt_zz)
-  const T pre = alpha / (W * W * W) * sgxx;
   const T iW = T(1) / W;
+  const T pre = alpha * (iW * iW * iW) * sgxx;
   const T S0 = iW * (Bh * F[1] - Dh * mi.xy * F[2] + Ch * m.xz * F[3]);
   const T S1 = iW * (Dh * mi.xx * F[2] + Ch * m.yz * F[3]);
   const T S2 = iW * (Ch * m.zz * F[3]);
