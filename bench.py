@@ -496,6 +496,13 @@ def run_native(args, dist, rank, ws, local):
                 "units_per_launch": units_per_launch,
                 "kernel_share": {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in
                                  sorted(kern.items(), key=lambda kv: -kv[1][0])[:8]}}
+    # the whole step: the algorithmic FP64 work of every counted kernel over the device time of
+    # every kernel of the profiled steps (ghost fill, restriction and diagnostics count as time only)
+    path_flops = sum(ALG_FLOPS[k] * v[2] for k, v in kern.items() if k in ALG_FLOPS)
+    path_s = sum(v[0] for v in kern.values()) * 1e-3
+    roofline["path"] = {"achieved": path_flops / path_s / 1e12, "unit": "TFLOP/s",
+                        "frac": (path_flops / path_s / 1e12 / peak) if peak else None,
+                        "kernels": sorted(k for k in kern if k in ALG_FLOPS)}
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None

@@ -404,21 +404,21 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
 // block walks the tile list with a grid stride; a tile is one block's worth of
 // cells of one level (origin j0, k0; extent = the block shape).
 template <typename T>
-__global__ void __launch_bounds__(256) kb_flux_x(Batch b, DevParams p) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_flux_x(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     flux_x_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y, q.wbp);
   });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) kb_flux_z(Batch b, DevParams p) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_flux_z(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     flux_z_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y, q.wbp);
   });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) kb_hydro_rhs(Batch b, DevParams p) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_hydro_rhs(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     hydro_rhs_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
   });

@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(128) kb_cartoon_f64(Batch b, const double *__r
   });
 }
 
-__global__ void __launch_bounds__(128) kb_cartoon_f32(Batch b, const double *__restrict__ tab, int tab_stride) {
+__global__ void __launch_bounds__(128, 3) kb_cartoon_f32(Batch b, const double *__restrict__ tab, int tab_stride) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     cartoon_f32_cell(q.L, q.U, tab, tab_stride, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
   });
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) kb_z4c_point(Batch b, DevParams p) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 0) kb_z4c_point(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     z4c_point_cell<T>(q.L, q.P, q.U, reinterpret_cast<const T *>(q.DS), q.jmax, q.kmax, tl.j0 + threadIdx.x,
                       tl.k0 + threadIdx.y);
