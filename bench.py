@@ -408,7 +408,7 @@ def run_native(args, dist, rank, ws, local):
     for _ in range(args.warmup):
         one_step()
     sim.sync()
-    tuning = sim.tune(reps=2) if not args.no_tune else None   # autotuner, outside the timed region
+    tuning = sim.tune(reps=4) if not args.no_tune else None   # autotuner, outside the timed region
     for _ in range(2):
         one_step()
     sim.sync()
@@ -428,7 +428,7 @@ def run_native(args, dist, rank, ws, local):
         msim.step(dt, 1, use_graph=True)
         msim.constraints()
     msim.sync()
-    mtuning = msim.tune(reps=2) if not args.no_tune else None
+    mtuning = msim.tune(reps=4) if not args.no_tune else None
     for _ in range(2):
         msim.step(dt, 1, use_graph=True)
         msim.constraints()

@@ -425,8 +425,8 @@ __device__ inline void atmosphere(const DevParams &p, double pr[NPRIM]) {
 // SEED: the learned seed is compiled in (and used when net is not null)
 template <bool SEED = false>
 __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W, const Sym3 &gt, double x,
-                                   double pr[NPRIM], const MlpNet *net = nullptr) {
-  const Sym3 gi = s3inv(gt, (double *)nullptr);
+                                   double pr[NPRIM], const MlpNet *net = nullptr, const Sym3 *gi_known = nullptr) {
+  const Sym3 gi = gi_known ? *gi_known : s3inv(gt, (double *)nullptr);   // the caller may hold gt^-1
   const double W3 = W * W * W;
   const double D = q[0] * W3;
   double S[3] = {q[1] * W3, q[2] * W3, q[3] * W3};
@@ -463,13 +463,13 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
     const double w = sqrt(1.0 + z * z);
     const double rho = D / w;
     const double eps = eos_ec(p, rho), P = eos_pc(p, rho);
-    const double Dh = D * (1.0 + eps + P / rho);
+    const double iDh = 1.0 / (D * (1.0 + eps + P / rho));
     pr[pRHO] = rho;
     pr[pEPS] = eps;
     pr[pP] = P;
-    pr[pUX] = S[0] / Dh;
-    pr[pUY] = S[1] / Dh;
-    pr[pUZ] = S[2] / Dh;
+    pr[pUX] = S[0] * iDh;
+    pr[pUY] = S[1] * iDh;
+    pr[pUZ] = S[2] * iDh;
     if (rho < p.rho_atm) {
       atmosphere(p, pr);
       st |= ST_ATM;
@@ -488,8 +488,8 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
     k = kmax;
     st |= ST_KRESCALE;
   }
-  const double zlo = 0.5 * k / sqrt(1.0 - 0.25 * k * k);
-  const double zhi = k / sqrt(1.0 - k * k);
+  const double zlo = 0.5 * k * rsqrt(1.0 - 0.25 * k * k);
+  const double zhi = k * rsqrt(1.0 - k * k);
   int its, ok;
   double z = 0.0;
   bool solved = false;
@@ -552,13 +552,13 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
   } else {
     P = eos_p(p, rho, eps);
   }
-  const double Dh = D * (1.0 + eps + P / rho);
+  const double iDh = 1.0 / (D * (1.0 + eps + P / rho));
   pr[pRHO] = rho;
   pr[pEPS] = eps;
   pr[pP] = P;
-  pr[pUX] = S[0] / Dh;
-  pr[pUY] = S[1] / Dh;
-  pr[pUZ] = S[2] / Dh;
+  pr[pUX] = S[0] * iDh;
+  pr[pUY] = S[1] * iDh;
+  pr[pUZ] = S[2] * iDh;
   if (rho < p.rho_atm) {
     atmosphere(p, pr);
     st |= ST_ATM;

@@ -208,7 +208,9 @@ __global__ void k_prolong_hydro(Lev L, Lev Pa, DevParams p, double *__restrict__
 
 // det gt = 1 and tr At = 0 after every stage (Sec. II.B.1):
 // gt <- d^(-1/3) gt, W <- d^(-1/6) W, At <- d^(-1/3)(At - gt tr/3), Khat += tr
-__device__ inline void enforce_algebraic(double m[NST]) {
+// gi_out: the inverse of the normalised conformal metric, gt^-1 / c13 with
+// 1 / c13 = det c13^2
+__device__ inline void enforce_algebraic(double m[NST], Sym3 *gi_out) {
   Sym3 g;
   g.xx = 1.0 + m[fHXX]; g.xy = m[fHXY]; g.xz = m[fHXZ]; g.yy = 1.0 + m[fHYY]; g.yz = m[fHYZ]; g.zz = 1.0 + m[fHZZ];
   double det;
@@ -225,6 +227,9 @@ __device__ inline void enforce_algebraic(double m[NST]) {
   }
   m[fW] *= c16;
   m[fKH] += tr;
+  const double s = det * c13 * c13;
+  gi_out->xx = gi.xx * s; gi_out->xy = gi.xy * s; gi_out->xz = gi.xz * s;
+  gi_out->yy = gi.yy * s; gi_out->yz = gi.yz * s; gi_out->zz = gi.zz * s;
 }
 
 // RK stage combination on [1, jmax] x [1, kmax], then algebraic constraints
@@ -264,7 +269,8 @@ __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p,
     }
     m[f] = out;
   }
-  if (p.evolve) enforce_algebraic(m);
+  Sym3 gin;
+  if (p.evolve) enforce_algebraic(m, &gin);
   if (held) {
     for (int f = f0; f < NST; ++f) L.us[(size_t)f * P + id] = m[f];
     return;
@@ -272,7 +278,7 @@ __device__ __forceinline__ void rk_update_cell(const Lev &L, const DevParams &p,
   Sym3 g;
   g.xx = 1.0 + m[fHXX]; g.xy = m[fHXY]; g.xz = m[fHXZ]; g.yy = 1.0 + m[fHYY]; g.yz = m[fHYZ]; g.zz = 1.0 + m[fHZZ];
   double pr[NPRIM];
-  const int st = cons_to_prim<SEED>(p, m + fQD, m[fW], g, (j - 0.5) * L.dx, pr, net);
+  const int st = cons_to_prim<SEED>(p, m + fQD, m[fW], g, (j - 0.5) * L.dx, pr, net, p.evolve ? &gin : nullptr);
   for (int f = f0; f < NST; ++f) L.us[(size_t)f * P + id] = m[f];
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + id] = pr[f];
