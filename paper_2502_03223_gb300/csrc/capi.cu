@@ -934,16 +934,13 @@ sacra_status set_initial_data(Engine &e, int star, int level, int kind, const do
   if (n_fields != 30) return fail(e, SACRA_ERR_ARG, "n_fields must be 30");
   Lev &L = st.lv[level];
   const size_t np = (size_t)L.px * L.pz;
+  // one pitched copy per group of planes (host planes are packed, device planes have stride P)
   if (kind == SACRA_PRIM_METRIC) {
-    for (int f = 0; f < NMET; ++f)
-      cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, e.stream);
-    for (int v = 0; v < 5; ++v)
-      cudaMemcpyAsync(L.prim + (size_t)v * L.P, host + (size_t)(NMET + v) * np, np * 8, cudaMemcpyHostToDevice,
-                      e.stream);
+    cudaMemcpy2DAsync(L.un, L.P * 8, host, np * 8, np * 8, NMET, cudaMemcpyHostToDevice, e.stream);
+    cudaMemcpy2DAsync(L.prim, L.P * 8, host + (size_t)NMET * np, np * 8, np * 8, 5, cudaMemcpyHostToDevice, e.stream);
     run(e, K_PRIM2CONS, (long long)np, [&] { launch_prim2cons_all(L, st.dp, L.un, e.stream); });
   } else if (kind == SACRA_RAW) {
-    for (int f = 0; f < NST; ++f)
-      cudaMemcpyAsync(L.un + (size_t)f * L.P, host + (size_t)f * np, np * 8, cudaMemcpyHostToDevice, e.stream);
+    cudaMemcpy2DAsync(L.un, L.P * 8, host, np * 8, np * 8, NST, cudaMemcpyHostToDevice, e.stream);
     run(e, K_C2P, (long long)np, [&] { launch_c2p_region(L, st.dp, L.un, 1 - GH, L.nx + GH, 1 - GH, L.nz + GH, e.stream); });
   } else {
     return fail(e, SACRA_ERR_ARG, "unknown kind");
