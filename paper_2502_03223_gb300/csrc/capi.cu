@@ -1140,7 +1140,8 @@ sacra_status mlp_collect(Engine &e, float *dev_out, long long cap, long long *n)
   if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
   cudaMemsetAsync(collect_counter(e), 0, sizeof(unsigned long long), e.stream);
   for (Star &st : e.stars)
-    for (int l = 0; l < st.prm.n_levels; ++l) launch_mlp_collect(st.lv[l], st.dp, dev_out, cap, collect_counter(e), e.stream);
+    for (int l = 0; l < st.prm.n_levels; ++l)   // the level's derivative scratch holds the block counts
+      launch_mlp_collect(st.lv[l], st.dp, dev_out, cap, collect_counter(e), st.ds[l], e.stream);
   unsigned long long h = 0;
   cudaMemcpyAsync(&h, collect_counter(e), sizeof(h), cudaMemcpyDeviceToHost, e.stream);
   if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "mlp_collect");

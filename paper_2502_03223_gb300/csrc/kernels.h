@@ -103,8 +103,10 @@ void launch_diag_final(const double *partials, int n, double *out, cudaStream_t 
 
 // learned seed of the primitive recovery (mlp.cu): tuples from a level's state,
 // training (forward, backward, Adam) and the full-batch gradient
+size_t mlp_collect_scratch_bytes(const Lev &L);
+// tuples of one level appended in cell order at *count; scratch: mlp_collect_scratch_bytes(L) device bytes
 void launch_mlp_collect(const Lev &L, const DevParams &p, float *out, long long cap, unsigned long long *count,
-                        cudaStream_t s);
+                        void *scratch, cudaStream_t s);
 int mlp_train(const float *samples, long long n, int steps, int batch_blocks, float lr, unsigned long long seed,
               float kmin, MlpNet *dev_net, float *host_loss, float *host_report, cudaStream_t s);
 int mlp_grad(const float *samples, long long n, const MlpNet *dev_net, float *host_grad, float *host_loss,

@@ -18,17 +18,16 @@ constexpr int MLP_S = 128;              // samples per block in training
 
 // One tuple per interior cell of the level whose recovery is non-trivial (moving
 // fluid, above the atmosphere, no cold or atmosphere branch): the inputs the
-// recovery computes from (q, W, gt) and the converged log10(P / D).
-__global__ void k_mlp_collect(Lev L, DevParams p, float *__restrict__ out, long long cap,
-                              unsigned long long *__restrict__ count) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.nx * L.nz) return;
+// recovery computes from (q, W, gt) and the converged log10(P / D).  Cell i of
+// the level (row-major over the interior) gives the tuple; false if none.
+__device__ inline bool collect_cell(const Lev &L, const DevParams &p, int i, float x[MLP_IN], float *y) {
+  if (i >= L.nx * L.nz) return false;
   const int j = 1 + i % L.nx, k = 1 + i / L.nx;
   const size_t P = L.P;
   const int id = cid(L, j, k);
-  if (L.status[id] & (ST_ATM | ST_COLD | ST_BAD | ST_NOCONV)) return;
+  if (L.status[id] & (ST_ATM | ST_COLD | ST_BAD | ST_NOCONV)) return false;
   const double rho = L.prim[(size_t)pRHO * P + id], Pr = L.prim[(size_t)pP * P + id];
-  if (!(rho > 10.0 * p.rho_atm) || !(Pr > 0.0)) return;
+  if (!(rho > 10.0 * p.rho_atm) || !(Pr > 0.0)) return false;
   const Sym3 gt = conf_metric(L.un, P, id);
   const Sym3 gi = s3inv(gt, (double *)nullptr);
   const double W = L.un[(size_t)fW * P + id];
@@ -38,13 +37,52 @@ __global__ void k_mlp_collect(Lev L, DevParams p, float *__restrict__ out, long 
   if (p.geometry == SACRA_CYLINDRICAL) S[1] /= (j - 0.5) * L.dx;
   const double E = L.un[(size_t)fQE * P + id] * W3;
   const double r = sqrt(W * W * s3quad(gi, S, S)) / D;
-  if (!(r > 0.0) || !(D > 0.0)) return;
+  if (!(r > 0.0) || !(D > 0.0)) return false;
   const double qq = E / D - 1.0;
   const double kk = fmin(r / (1.0 + qq), p.c2p_kmax);
-  float x[MLP_IN];
   c2p_features(p, D, qq, r, kk, W, gt, gi, x);
-  const float y = log10f(f32_of(Pr / D));
-  const unsigned long long slot = atomicAdd(count, 1ull);
+  *y = log10f(f32_of(Pr / D));
+  return true;
+}
+
+// The tuples are written in cell order (levels in call order), so that the
+// training set, its held-out split and the trained network do not depend on
+// the order in which threads ran: a count per block of MC_B cells, a scan of
+// those counts (from the running total of earlier calls), then each cell's
+// slot = its block's offset + its rank among the block's tuples.
+constexpr int MC_B = 256;
+
+__global__ void __launch_bounds__(MC_B) k_mlp_count(Lev L, DevParams p, int *__restrict__ bcount) {
+  float x[MLP_IN], y;
+  const bool v = collect_cell(L, p, blockIdx.x * MC_B + threadIdx.x, x, &y);
+  const int c = __syncthreads_count(v);
+  if (threadIdx.x == 0) bcount[blockIdx.x] = c;
+}
+
+__global__ void k_mlp_scan(const int *__restrict__ bcount, int nb, unsigned long long *__restrict__ count,
+                           unsigned long long *__restrict__ boff) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned long long base = *count;
+  for (int b = 0; b < nb; ++b) {
+    boff[b] = base;
+    base += (unsigned long long)bcount[b];
+  }
+  *count = base;
+}
+
+__global__ void __launch_bounds__(MC_B) k_mlp_write(Lev L, DevParams p, const unsigned long long *__restrict__ boff,
+                                                    float *__restrict__ out, long long cap) {
+  __shared__ int wsum[MC_B / 32];
+  float x[MLP_IN], y = 0.0f;
+  const bool v = collect_cell(L, p, blockIdx.x * MC_B + threadIdx.x, x, &y);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, v);
+  if (lane == 0) wsum[w] = __popc(m);
+  __syncthreads();
+  int before = __popc(m & ((1u << lane) - 1u));
+  for (int q = 0; q < w; ++q) before += wsum[q];
+  if (!v) return;
+  const unsigned long long slot = boff[blockIdx.x] + (unsigned long long)before;
   if ((long long)slot >= cap) return;
   float *o = out + slot * MLP_TUPLE;
 #pragma unroll
@@ -249,10 +287,19 @@ size_t mlp_grad_smem() {
 
 // ---------------------------------------------------------------- host side
 
+size_t mlp_collect_scratch_bytes(const Lev &L) {
+  const size_t nb = (size_t)(L.nx * L.nz + MC_B - 1) / MC_B;
+  return nb * sizeof(unsigned long long) + nb * sizeof(int);
+}
+
 void launch_mlp_collect(const Lev &L, const DevParams &p, float *out, long long cap, unsigned long long *count,
-                        cudaStream_t s) {
-  const int n = L.nx * L.nz;
-  k_mlp_collect<<<(n + 127) / 128, 128, 0, s>>>(L, p, out, cap, count);
+                        void *scratch, cudaStream_t s) {
+  const int nb = (L.nx * L.nz + MC_B - 1) / MC_B;
+  unsigned long long *boff = reinterpret_cast<unsigned long long *>(scratch);
+  int *bcount = reinterpret_cast<int *>(boff + nb);
+  k_mlp_count<<<nb, MC_B, 0, s>>>(L, p, bcount);
+  k_mlp_scan<<<1, 32, 0, s>>>(bcount, nb, count, boff);
+  k_mlp_write<<<nb, MC_B, 0, s>>>(L, p, boff, out, cap);
 }
 
 namespace {
@@ -366,7 +413,7 @@ int mlp_train(const float *samples, long long n, int steps, int batch_blocks, fl
   const size_t q = std::min<size_t>(sz.size() - 1, (size_t)(0.999 * sz.size()));
   std::nth_element(sz.begin(), sz.begin() + q, sz.end());
   const float zq = sz[q];
-  const float delta = std::min(0.05f, std::max(1e-5f, 4.0f * zq));
+  const float delta = std::min(0.05f, std::max(1e-5f, 2.0f * zq));   // twice the 99.9th percentile
   cudaMemcpyAsync(&dev_net->delta, &delta, sizeof(float), cudaMemcpyHostToDevice, s);
   if (host_report) {
     double sy = 0.0;

@@ -613,7 +613,11 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
 template <typename T>
 __global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const double *__restrict__ U,
                                                      double *__restrict__ DS, int jmax, int kmax, int cyl) {
-  z4c_derivs_cell<T>(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * blockDim.x + threadIdx.x + 1, blockIdx.y * blockDim.y + threadIdx.y + 1);
+  __shared__ double sdz[(32 + 6) * 4];   // the launch shape is 32 x 4
+  const int j0 = blockIdx.x * blockDim.x + 1;
+  const bool xch = blockDim.x == 32 && blockDim.y == 4;
+  z4c_derivs_cell<T>(L, p, U, DS, jmax, kmax, cyl, j0 + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
+                     xch ? sdz : nullptr, j0);
 }
 
 __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,

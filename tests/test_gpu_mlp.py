@@ -130,8 +130,9 @@ def test_seeded_recovery_equals_plain_and_gains(trained):
 def test_seed_gain_in_a_relativistic_flow():
     """A relativistic shock tube (left state v = 0.9, w = 2.3, hitting a dense
     counter-flow): the plain bracket needs ~9 master-function evaluations per
-    recovery; the trained seed cuts that by more than 15 % with the same
-    primitives (the Illinois iteration judges every seeded solve)."""
+    recovery; the trained seed cuts that by more than 20 % (measured 33 %;
+    tuples, split and training are deterministic) with the same primitives
+    (the Illinois iteration judges every seeded solve)."""
     import torch
     cfg = W.shock_tube_config(400, 4, solver=0, rk=0, cfl=0.4)
     d = W.shock_tube_data(cfg, left=(1.0, 1.0, 0.9), right=(10.0, 0.01, -0.5))
@@ -163,4 +164,4 @@ def test_seed_gain_in_a_relativistic_flow():
     print("relativistic tube: Illinois evaluations per recovery plain %.3f, seeded %.3f; held-out RMS of "
           "log10(P/D) %.4f, delta %.3g" % (ep[0] / ep[3], es[0] / es[3], rep["val_rms_log10"], rep["delta"]))
     assert es[2] >= 0.99 * es[1]
-    assert es[0] / es[3] < 0.85 * ep[0] / ep[3]
+    assert es[0] / es[3] < 0.8 * ep[0] / ep[3]
