@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParam
   z4c_derivs_f32_tile(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * DTX + 1, blockIdx.y * DTZ + 1, tile);
 }
 
-__global__ void __launch_bounds__(DTX * DTZ, 3) kb_z4c_derivs_f32(Batch b, DevParams p) {
+__global__ void __launch_bounds__(DTX * DTZ, 4) kb_z4c_derivs_f32(Batch b, DevParams p) {
   __shared__ float2 tile[DHZ][DHX];
   const int cyl = p.geometry == SACRA_CYLINDRICAL;
   for_tiles(b, [&](const BL &q, const Tile &tl) {
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 0) kb_z4c_point(Batch b, DevParams p) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 0) kb_z4c_point(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     z4c_point_cell<T>(q.L, q.P, q.U, reinterpret_cast<const T *>(q.DS), q.jmax, q.kmax, tl.j0 + threadIdx.x,
                       tl.k0 + threadIdx.y);
