@@ -454,12 +454,43 @@ __global__ void k_reflux(Lev C, Lev Pa, double dt) {
 constexpr int DIAG_Q = 9;   // H^2 dV, Mx^2 dV, My^2 dV, Mz^2 dV, dV, qD dV, qSphi dV, rho_max, n_fail
 constexpr int DIAG_T = 128;
 
+// Block reduction of the diagnostic sums (slot 7: maximum) in a fixed order, so
+// the result is the same on every run: a shuffle tree inside each warp, then
+// warp 0 combines the per-warp values the same way.  The block total ends in
+// acc of thread 0.
+__device__ __forceinline__ void diag_block_reduce(double acc[DIAG_Q], double (*sh)[DIAG_T / 32], int t) {
+  const int lane = t & 31, w = t >> 5;
+#pragma unroll
+  for (int q = 0; q < DIAG_Q; ++q) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_down_sync(0xffffffffu, v, o);
+      v = (q == 7) ? fmax(v, u) : v + u;
+    }
+    if (lane == 0) sh[q][w] = v;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < DIAG_Q; ++q) {
+      double v = lane < DIAG_T / 32 ? sh[q][lane] : (q == 7 ? -1e300 : 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_down_sync(0xffffffffu, v, o);
+        v = (q == 7) ? fmax(v, u) : v + u;
+      }
+      acc[q] = v;
+    }
+  }
+}
+
 // S: storage type of the derivative scratch and the cartoon planes (FP32 in
 // the mixed-precision Z4c form); the constraint algebra is FP64 either way.
 template <typename S>
 __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__restrict__ DS, int covered,
                                                  int evolve, double *__restrict__ partials) {
-  __shared__ double sh[DIAG_Q][DIAG_T];
+  __shared__ double sh[DIAG_Q][DIAG_T / 32];
   const int t = threadIdx.x;
   const int n = L.nx * L.nz;
   const int i = blockIdx.x * DIAG_T + t;
@@ -559,23 +590,15 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__
       }
     }
   }
-#pragma unroll
-  for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = acc[q];
-  __syncthreads();
-  for (int w = DIAG_T / 2; w > 0; w >>= 1) {
-    if (t < w)
-#pragma unroll
-      for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = (q == 7) ? fmax(sh[q][t], sh[q][t + w]) : sh[q][t] + sh[q][t + w];
-    __syncthreads();
-  }
+  diag_block_reduce(acc, sh, t);
   if (t == 0)
 #pragma unroll
-    for (int q = 0; q < DIAG_Q; ++q) partials[(size_t)blockIdx.x * DIAG_Q + q] = sh[q][0];
+    for (int q = 0; q < DIAG_Q; ++q) partials[(size_t)blockIdx.x * DIAG_Q + q] = acc[q];
 }
 
 // fixed-order sum of the block partials (deterministic)
 __global__ void k_diag_final(const double *__restrict__ partials, int n, double *__restrict__ out) {
-  __shared__ double sh[DIAG_Q][DIAG_T];
+  __shared__ double sh[DIAG_Q][DIAG_T / 32];
   const int t = threadIdx.x;
   double acc[DIAG_Q];
 #pragma unroll
@@ -584,18 +607,10 @@ __global__ void k_diag_final(const double *__restrict__ partials, int n, double 
 #pragma unroll
     for (int q = 0; q < DIAG_Q; ++q)
       acc[q] = (q == 7) ? fmax(acc[q], partials[(size_t)b * DIAG_Q + q]) : acc[q] + partials[(size_t)b * DIAG_Q + q];
-#pragma unroll
-  for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = acc[q];
-  __syncthreads();
-  for (int w = DIAG_T / 2; w > 0; w >>= 1) {
-    if (t < w)
-#pragma unroll
-      for (int q = 0; q < DIAG_Q; ++q) sh[q][t] = (q == 7) ? fmax(sh[q][t], sh[q][t + w]) : sh[q][t] + sh[q][t + w];
-    __syncthreads();
-  }
+  diag_block_reduce(acc, sh, t);
   if (t == 0)
 #pragma unroll
-    for (int q = 0; q < DIAG_Q; ++q) out[q] = sh[q][0];
+    for (int q = 0; q < DIAG_Q; ++q) out[q] = acc[q];
 }
 
 // ---------------------------------------------------------------- host launchers
