@@ -26,9 +26,11 @@ def built():
     assert torch.cuda.is_available()
 
 
-def _drift(N, T=100.0):
+def _drift(N, T=100.0, precision=0):
     """N cells per level over the same domain (x_max = 256): finest dx = 64 / N."""
+    import dataclasses
     cfg, tov = W.tov_config("tov_conv", rho_c=1.28e-3, n_levels=3, N=N, dx_fine=64.0 / N, rk=1)
+    cfg = dataclasses.replace(cfg, precision=precision)
     s = S.Sacra(cfg)
     for l in range(cfg.n_levels):
         s.set_initial_data(l, S.PRIM_METRIC, W.tov_level_data(cfg, tov, l))
@@ -53,3 +55,12 @@ def test_stable_star_equilibrium_converges():
     # measured: drift 7.5e-2, 9.6e-3, 2.0e-3 (orders 3.0, 2.3); ||H|| 3.3e-7, 7.4e-8, 3.8e-8
     assert d[0] > d[1] > d[2] and h[0] > h[1] > h[2]
     assert min(od) > 1.8, (d, od)
+
+
+def test_mixed_precision_holds_the_same_equilibrium():
+    """The mixed form over the same 100M at N = 128: its central-density drift
+    and constraint norm stay within a few per cent of the FP64 run's."""
+    d64, _, h64 = _drift(128)
+    dmx, _, hmx = _drift(128, precision=S.MIXED)
+    print("TOV N = 128, t = 100: drift FP64 %.4e mixed %.4e; ||H|| FP64 %.4e mixed %.4e" % (d64, dmx, h64, hmx))
+    assert abs(dmx - d64) <= 0.05 * d64 and abs(hmx - h64) <= 0.05 * h64
