@@ -357,8 +357,9 @@ struct C2pD {
 // h = (1 + eps)(1 + a), a = P / (rho (1 + eps)), is formed as 1 + eps + P / rho.
 template <bool COLD>
 __device__ inline double c2p_fun(const DevParams &p, double z, C2pD D, double qq, double r) {
-  const double w = sqrt(1.0 + z * z);
-  const double rho = D.v / w, irho = w * D.inv;
+  const double w2 = 1.0 + z * z, iw = rsqrt(w2);   // 1 / w: rho = D / w without a division
+  const double w = w2 * iw;
+  const double rho = D.v * iw, irho = w * D.inv;
   if (COLD) {
     const double hc = 1.0 + eos_ec(p, rho) + eos_pc(p, rho) * irho;
     return z - r / hc;
