@@ -103,6 +103,9 @@ typedef struct {
   int n_pieces;          /* cold part: 0 or 1 = the single polytrope (K, Gamma); 2..8 = piecewise polytropic
                             (Sec. II.C.3) with piece 1 = (K, Gamma) and the others from pwp_rho, pwp_Gamma.
                             Not accepted by sacra_hydro_rhs_noalloc (SACRA_ERR_ARG) */
+  int bssn;              /* 0: Z4c (Sec. II.B.1); 1: the BSSN formulation the paper switches to for a cleaner
+                            waveform (Sec. III): Theta held at zero (its right-hand side is zero; give Theta = 0
+                            in the initial data) and no constraint damping (kappa taken as 0) */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;   /* cold polytrope P = K rho^Gamma plus thermal Gamma_th law (Sec. II.C.3) */
@@ -275,8 +278,10 @@ const char *sacra_last_error(const sacra_ctx *c);
 
 /* ---- Batches of independent stars (no counterpart in the paper: many
    hierarchies advanced together).  Each star has its own sacra_params; the
-   stars may differ in n_levels, nx = nz and dx0 = dz0 and must agree in
-   everything else (else SACRA_ERR_ARG).  All stars take the same dt.  Every
+   stars must agree in the choices that select kernels (geometry,
+   evolve_spacetime, solver, rk, precision; else SACRA_ERR_ARG) and may differ
+   in everything else (grid, EOS, gauge, atmosphere, recovery, bssn), which
+   each launch reads per star.  All stars take the same dt.  Every
    RK stage is one persistent launch per kernel kind over the tiles of every
    level of every star (ghost fill, restriction and reflux stay per level);
    sacra_batch_step with use_graph != 0 replays whole steps of all stars as

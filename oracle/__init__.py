@@ -84,6 +84,7 @@ class Params(C.Structure):
         ("n_levels", C.c_int), ("nx", C.c_int), ("nz", C.c_int), ("geometry", C.c_int),
         ("evolve_spacetime", C.c_int), ("solver", C.c_int), ("rk", C.c_int), ("c2p_maxit", C.c_int),
         ("subcycle_from", C.c_int), ("hydro_outer", C.c_int), ("eos_adiabatic", C.c_int), ("n_pieces", C.c_int),
+        ("bssn", C.c_int),
         ("dx0", C.c_double), ("dz0", C.c_double),
         ("kappa", C.c_double), ("eta_B", C.c_double), ("eps_ko", C.c_double), ("r_z4", C.c_double),
         ("K", C.c_double), ("Gamma", C.c_double), ("Gamma_th", C.c_double),
@@ -106,6 +107,7 @@ def make_params(cfg) -> Params:
     p.rho_atm = float(cfg.rho_atm); p.w_max = float(cfg.w_max); p.c2p_tol = float(cfg.c2p_tol)
     p.hydro_outer = int(getattr(cfg, "hydro_outer", 0)); p.r_hold = float(getattr(cfg, "r_hold", 0.0))
     p.eos_adiabatic = int(getattr(cfg, "eos_adiabatic", 0))
+    p.bssn = int(getattr(cfg, "bssn", 0))
     pieces = list(getattr(cfg, "pwp", ()) or ())       # [(rho_i, Gamma_(i+1)), ...]
     p.n_pieces = 1 + len(pieces)
     for i, (rt, gi) in enumerate(pieces):

@@ -52,6 +52,7 @@ typedef struct {
   int hydro_outer;       /* hydro at the outer boundary: 0 zero-gradient copy, 1 held at the initial data */
   int eos_adiabatic;     /* 1: zero temperature, P = P_cold, eps = eps_cold, energy equation discarded */
   int n_pieces;          /* cold polytropic pieces (0 or 1: the single piece K, Gamma) */
+  int bssn;              /* 1: BSSN (Theta held at zero, kappa = 0) instead of Z4c */
   double dx0, dz0;       /* spacing of level 0 */
   double kappa, eta_B, eps_ko, r_z4;
   double K, Gamma, Gamma_th;

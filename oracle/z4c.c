@@ -422,7 +422,7 @@ void orc_z4c_point(const orc_params *p, const double Q[O_NMET], const double dQ[
   const double PI = 3.14159265358979323846;
   double W = G.W, al = G.al, Kh = G.Kh, Th = G.Th;
   double K = Kh + 2.0 * Th;
-  double kap = p->kappa * fz;   /* Z4 damping radius factor exp(-r^2/r_Z4^2) on kappa */
+  double kap = p->bssn ? 0.0 : p->kappa * fz;   /* Z4 damping radius factor exp(-r^2/r_Z4^2) on kappa; none in BSSN */
 
   double beta[3] = {Q[O_BX], Q[O_BY], Q[O_BZ]};
   double Bv[3] = {Q[O_BBX], Q[O_BBY], Q[O_BBZ]};
@@ -531,9 +531,10 @@ void orc_z4c_point(const orc_params *p, const double Q[O_NMET], const double dQ[
     gsrc[i] = s;
     rhs[O_GX + i] = adv[O_GX + i] + s;
   }
-  /* Theta */
-  rhs[O_TH] = adv[O_TH] + fz * (0.5 * al * (G.Rs - AA + 2.0 / 3.0 * K * K) - 8.0 * PI * al * E)
-              - 2.0 * al * kap * Th;
+  /* Theta (held at zero in BSSN) */
+  rhs[O_TH] = p->bssn ? 0.0
+                      : adv[O_TH] + fz * (0.5 * al * (G.Rs - AA + 2.0 / 3.0 * K * K) - 8.0 * PI * al * E)
+                            - 2.0 * al * kap * Th;
   /* gauge: 1+log with Khat, Gamma-driver */
   rhs[O_AL] = adv[O_AL] - 2.0 * al * Kh;
   for (int i = 0; i < 3; ++i) {

@@ -95,6 +95,7 @@ bool valid(const sacra_params *p, std::string *why) {
   if (p->hydro_outer != 0 && p->hydro_outer != 1) { *why = "hydro_outer must be 0 or 1"; return false; }
   if (!(p->r_hold >= 0.0)) { *why = "r_hold must be >= 0"; return false; }
   if (p->eos_adiabatic != 0 && p->eos_adiabatic != 1) { *why = "eos_adiabatic must be 0 or 1"; return false; }
+  if (p->bssn != 0 && p->bssn != 1) { *why = "bssn must be 0 or 1"; return false; }
   if (p->eos_adiabatic && !(p->K > 0.0)) { *why = "the adiabatic EOS needs a cold part (K > 0)"; return false; }
   if (p->n_pieces < 0 || p->n_pieces > kMaxPieces) { *why = "n_pieces must be in [0, 8]"; return false; }
   if (p->n_pieces > 1) {

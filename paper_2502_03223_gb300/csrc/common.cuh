@@ -46,6 +46,7 @@ struct DevParams {
   int hydro_outer;       // 1: level 0's outer hydro ghosts stay at the initial data
   int adiabatic;         // 1: zero temperature, P = P_cold, eps = eps_cold, energy equation discarded
   int n_pieces;          // cold pieces (1: K, Gamma; more: the table pwp)
+  int bssn;              // 1: BSSN (Theta held at zero, kappa = 0)
   const PwpTable *pwp;   // device copy of the pieces when n_pieces > 1
   double c2p_zmax;       // sqrt(w_max^2 - 1): Lorentz-factor cap of the adiabatic recovery
   double ith1;           // 1 / (Gamma_th - 1)
@@ -89,6 +90,8 @@ inline void fill_dev_params(const sacra_params *p, DevParams *d) {
   d->hydro_outer = p->hydro_outer != 0;
   d->r_hold2 = p->r_hold > 0.0 ? p->r_hold * p->r_hold : 0.0;
   d->adiabatic = p->eos_adiabatic != 0;
+  d->bssn = p->bssn != 0;
+  if (d->bssn) { d->kappa = 0.0; d->fkappa = 0.0f; }
   d->n_pieces = p->n_pieces > 1 ? p->n_pieces : 1;
   d->pwp = nullptr;      // set by the owner of the device copy
   d->c2p_zmax = sqrt(p->w_max * p->w_max - 1.0);

@@ -227,7 +227,8 @@ __device__ inline void z4c_source(const DevParams &p, const Z4cIn<T> &z, const G
     out[fBBX + i] = s - pv<T>(p.eta_B, p.feta_B) * z.B[i];
   }
 
-  out[fTH] = fz * (T(0.5) * al * (G.Rs - AA + (T(2.0) / T(3.0)) * K * K) - T(8.0) * PI * al * E) - T(2.0) * al * kap * z.Th;
+  out[fTH] = p.bssn ? T(0)
+                    : fz * (T(0.5) * al * (G.Rs - AA + (T(2.0) / T(3.0)) * K * K) - T(8.0) * PI * al * E) - T(2.0) * al * kap * z.Th;
   out[fAL] = -T(2.0) * al * z.Kh;
 #pragma unroll
   for (int i = 0; i < 3; ++i) out[fBX + i] = T(0.75) * z.B[i];

@@ -43,6 +43,7 @@ class RunConfig:
     hydro_outer: int = 0       # outer hydro boundary: 0 zero-gradient copy, 1 held at the initial data
     eos_adiabatic: int = 0     # 1: zero temperature (P = P_cold, eps = eps_cold), energy equation discarded
     pwp: tuple = ()            # further cold pieces: ((rho_1, Gamma_2), (rho_2, Gamma_3), ...)
+    bssn: int = 0              # 1: BSSN (Theta held at zero, no constraint damping) instead of Z4c
     dx0: float = 1.0
     dz0: float = 1.0
     kappa: float = 0.0

@@ -3,6 +3,8 @@ same seeded inputs: per cell and per RK stage within 1e-11 relative, with the
 floor S_group of gpu_common.compare_level for values formed by cancellation,
 and the rest-mass density L1 norm within 1e-9 after 100 steps.  Status flags of
 the primitive recovery agree except where a branch flipped (< 0.1% of cells)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -81,6 +83,21 @@ def test_tov_fmr_stagewise(rk):
     cfg, datas = _tov_small(rk=rk)
     _, _, worst = _stagewise(cfg, datas, steps=2)
     assert worst < 1e-11
+
+
+@pytest.mark.parametrize("rk", [0, 1])
+def test_tov_fmr_stagewise_bssn(rk):
+    """The BSSN formulation of Sec. III.C (Theta frozen at zero, no constraint
+    damping): per-stage parity, and Theta stays exactly zero through the RK
+    stages, ghost fill, prolongation and restriction."""
+    cfg, datas = _tov_small(rk=rk)
+    cfg = dataclasses.replace(cfg, bssn=1)
+    for d in datas:
+        d[17] = 0.0
+    gpu, _, worst = _stagewise(cfg, datas, steps=2)
+    assert worst < 1e-11
+    for l in range(cfg.n_levels):
+        assert not np.any(gpu.read(l, S.STATE_STEP, 17))
 
 
 def test_tov_fmr_tvdlf_and_ragged():

@@ -221,9 +221,10 @@ def _adm(s):
     return dict(R=R, dtg=dtg, dtK=dtK, H=H, M=M, gi=gi)
 
 
-def _oracle_rhs(s, kappa=0.3, eta=0.7):
-    cfg = W.RunConfig(kappa=kappa, eta_B=eta)
-    Q, dQ, ddQ = s["Q"], s["dQ"], s["ddQ"]
+def _oracle_rhs(s, kappa=0.3, eta=0.7, bssn=0, Q=None):
+    cfg = W.RunConfig(kappa=kappa, eta_B=eta, bssn=bssn)
+    Q = s["Q"] if Q is None else Q
+    dQ, ddQ = s["dQ"], s["ddQ"]
     adv = dQ @ Q[19:22]
     Sij6 = np.array([s["Sij"][i, j] for i, j in PAIRS])
     return O.z4c_point(cfg, Q, dQ, ddQ, adv, s["E"], s["Si"], Sij6, 1.0), adv
@@ -236,9 +237,16 @@ def test_ricci_matches_christoffel_definition(setup):
         assert abs(R[a] - ref[i, j]) < 1e-11 * (1 + abs(ref[i, j])), (i, j, R[a], ref[i, j])
 
 
-def test_metric_and_curvature_evolution_match_adm(setup):
+@pytest.mark.parametrize("bssn", [0, 1])
+def test_metric_and_curvature_evolution_match_adm(setup, bssn):
+    """Z4c, and the BSSN formulation (Theta frozen at zero, no damping) used
+    for the cleaner waveform of Sec. III.C.  With Theta = 0 Z4c reproduces the
+    ADM equations for gamma_ij and K_ij (its Theta equation carries the alpha H
+    that ADM's d_t K has); BSSN's d_t K is ADM's with the Hamiltonian
+    constraint substituted, so its d_t K_ij is ADM's minus gamma_ij alpha H / 3,
+    whatever kappa is set to."""
     s = setup
-    r, adv = _oracle_rhs(s)
+    r, adv = _oracle_rhs(s, bssn=bssn)
     ref = _adm(s)
     Q = s["Q"]
     Wc = Q[0]
@@ -252,14 +260,19 @@ def test_metric_and_curvature_evolution_match_adm(setup):
     dtg = dgt / Wc ** 2 - 2 * gt * dW / Wc ** 3
     dtK = (dAt + dgt * K / 3 + gt * dKt / 3) / Wc ** 2 - 2 * (At + gt * K / 3) * dW / Wc ** 3
     assert np.allclose(dtg, ref["dtg"], rtol=0, atol=1e-12)
-    assert np.allclose(dtK, ref["dtK"], rtol=0, atol=1e-11)
-    # Theta: alpha H / 2 (damping factor 1, Theta = 0)
-    assert abs(r[17] - 0.5 * s["a"] * ref["H"]) < 1e-11
+    expect_K = ref["dtK"] - (s["g"] * s["a"] * ref["H"] / 3 if bssn else 0.0)
+    assert np.allclose(dtK, expect_K, rtol=0, atol=1e-11)
+    if bssn:
+        assert r[17] == 0.0
+    else:
+        # Theta: alpha H / 2 (damping factor 1, Theta = 0)
+        assert abs(r[17] - 0.5 * s["a"] * ref["H"]) < 1e-11
 
 
-def test_gamma_tilde_evolution_matches_constraint_identity(setup):
+@pytest.mark.parametrize("bssn", [0, 1])
+def test_gamma_tilde_evolution_matches_constraint_identity(setup, bssn):
     s = setup
-    r, adv = _oracle_rhs(s)
+    r, adv = _oracle_rhs(s, bssn=bssn)
     ref = _adm(s)
     Q = s["Q"]
     gt = np.eye(3) + np.array([[Q[1 + S6[i][j]] for j in range(3)] for i in range(3)])
@@ -292,3 +305,34 @@ def test_minkowski_rhs_vanishes_exactly():
     r = O.z4c_point(W.RunConfig(kappa=0.1), Q, np.zeros((25, 3)), np.zeros((25, 6)), np.zeros(25), 0.0,
                     np.zeros(3), np.zeros(6), 1.0)
     assert np.all(r == 0.0)
+
+
+def test_damping_terms_and_their_absence_in_bssn(setup):
+    """The kappa terms of Eq. bssn are linear in kappa: with Gt^i = Gd^i + delta^i
+    (delta constant near the point) and Theta = th, Z4c(kappa) - Z4c(0) is
+    alpha kappa th in K-hat, -2 alpha kappa delta^i in Gt^i and in B^i (the
+    Gamma-driver's source is d_t Gt^i, Eq. moving_puncture) and -2 alpha kappa th
+    in Theta, nothing elsewhere.  The BSSN setting drops exactly those terms and
+    freezes Theta: it equals Z4c at kappa = 0 except Theta's right-hand side,
+    which is zero."""
+    s = setup
+    Q = s["Q"].copy()
+    delta = np.array([0.013, -0.021, 0.008])
+    th = 0.017
+    Q[14:17] += delta
+    Q[17] = th
+    kap = 0.3
+    a = Q[18]
+    r_k, _ = _oracle_rhs(s, kappa=kap, Q=Q)
+    r_0, _ = _oracle_rhs(s, kappa=0.0, Q=Q)
+    r_b, _ = _oracle_rhs(s, kappa=kap, bssn=1, Q=Q)
+    d = r_k - r_0
+    expect = np.zeros(25)
+    expect[13] = a * kap * th
+    expect[14:17] = -2 * a * kap * delta
+    expect[22:25] = -2 * a * kap * delta
+    expect[17] = -2 * a * kap * th
+    assert np.allclose(d, expect, rtol=0, atol=1e-13), (d, expect)
+    assert r_b[17] == 0.0
+    keep = np.arange(25) != 17
+    assert np.array_equal(r_b[keep], r_0[keep])
