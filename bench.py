@@ -7,7 +7,9 @@ Gamma_th=2, atmosphere 1e-10 of rho_c), equatorial symmetry, 3 FMR levels of
 256^2 cells, finest dx = 0.25, SSP-RK3, FP64.  One step = the whole hot path:
 ghost fill / prolongation, hydro and Z4c right-hand sides, RK combination with
 algebraic constraints and primitive recovery for every stage, then
-restriction + reflux and the constraint diagnostics.  The working set (about
+restriction + reflux; the constraint and conservation diagnostics of the state
+at the start of each step are formed inside its first stage (from that stage's
+derivative pass) and read back to the host every step.  The working set (about
 0.7 GB of FP64 state per step) exceeds the 129 MB L2, so no flush is needed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -246,9 +248,10 @@ def run_reference(args, dist, rank, ws):
 
 
 def timed_steps(sim, dt, steps, dist):
-    """K graph-replayed steps (plus the constraint diagnostics) bracketed by a
-    barrier and a device synchronize, timed by CUDA events on the library's
-    stream.  Returns (ms, launches, last diagnostics, clocks)."""
+    """K graph-replayed steps, each with the diagnostics of its starting state
+    read back, bracketed by a barrier and a device synchronize, timed by CUDA
+    events on the library's stream.  Returns (ms, launches, last diagnostics,
+    clocks)."""
     import torch
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -260,8 +263,7 @@ def timed_steps(sim, dt, steps, dist):
     ev0.record(sim.stream)
     diag = None
     for _ in range(steps):
-        sim.step(dt, 1, use_graph=True)
-        diag = sim.constraints()
+        diag = sim.step_constraints(dt, 1, use_graph=True)[0]
     ev1.record(sim.stream)
     ev1.synchronize()
     torch.cuda.synchronize()
@@ -402,8 +404,7 @@ def run_native(args, dist, rank, ws, local):
     cells_per_step = cfg.interior_cells * cfg.n_stages
 
     def one_step(graph=True):
-        sim.step(dt, 1, use_graph=graph)
-        return sim.constraints()
+        return sim.step_constraints(dt, 1, use_graph=graph)[0]
 
     for _ in range(args.warmup):
         one_step()
@@ -416,6 +417,7 @@ def run_native(args, dist, rank, ws, local):
 
     # ---- timed region (device time, CUDA events on the library's stream)
     ms, launches, diag, clocks = timed_steps(sim, dt, args.steps, dist)
+    diag = sim.constraints()          # the state after the last step (untimed)
     ms_max = max_over_ranks(dist, ms)
     value = ws * cells_per_step * args.steps / (ms_max * 1e-3)
 
@@ -425,13 +427,11 @@ def run_native(args, dist, rank, ws, local):
     for l, d in enumerate(datas):
         msim.set_initial_data(l, S.PRIM_METRIC, d)
     for _ in range(args.warmup):
-        msim.step(dt, 1, use_graph=True)
-        msim.constraints()
+        msim.step_constraints(dt, 1, use_graph=True)
     msim.sync()
     mtuning = msim.tune(reps=4) if not args.no_tune else None
     for _ in range(2):
-        msim.step(dt, 1, use_graph=True)
-        msim.constraints()
+        msim.step_constraints(dt, 1, use_graph=True)
     msim.sync()
     mms, mlaunches, _, mclocks = timed_steps(msim, dt, args.steps, dist)
     mms_max = max_over_ranks(dist, mms)

@@ -169,6 +169,17 @@ sacra_status sacra_rk_stage(sacra_ctx *c, int stage, double dt);
    use_graph != 0 captures one step in a CUDA graph on first use and replays it. */
 sacra_status sacra_step(sacra_ctx *c, double dt, int n_steps, int use_graph);
 
+/* n_steps steps as sacra_step, with the diagnostics (Sec. II.F.1) of the
+   state at the START of step i written to out[i], i < n_steps.  They are
+   formed inside the step's first RK stage from the derivatives its Z4c pass
+   has just computed, after the same ghost fill sacra_constraints does, so
+   out[i] equals sacra_constraints called just before step i, without a second
+   cartoon and derivative pass (n_fallback: the counter after step i).  The
+   host waits for the stream after each step.  out: host array of n_steps
+   entries (NULL with n_steps > 0: SACRA_ERR_ARG).  Lockstep contexts only
+   (sub-cycled: SACRA_ERR_STATE). */
+sacra_status sacra_step_constraints(sacra_ctx *c, double dt, int n_steps, int use_graph, sacra_diag *out);
+
 /* Copy one plane to HOST memory.  which: SACRA_STATE_STEP (state at the start
    of the step, i.e. the current state between steps), SACRA_STATE_STAGE,
    SACRA_PRIMS, SACRA_RHS or SACRA_STATUS (per-cell recovery flags as

@@ -223,9 +223,11 @@ struct Engine {
   // bookkeeping
   long long launches = 0;
   std::string err;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  double gdt[2] = {0.0, 0.0};
-  long long glaunch[2] = {0, 0};
+  // step graphs, keyed by 2 * parity + (diagnostics in the first stage)
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  double gdt[4] = {0.0, 0.0, 0.0, 0.0};
+  long long glaunch[4] = {0, 0, 0, 0};
+  bool stage0_diag = false;       // enqueue the diagnostics inside the first stage of each step
   int parity = 0;    // register swaps of group 0 mod 2 (the key of the step graphs)
   bool capturing = false;
   bool prof = false;
@@ -496,6 +498,8 @@ void swap_group(Engine &e, int g) {
 // are cleared, those at its parent boundary when reset_parent is set (a
 // sub-cycled level sums them over both of its steps inside a parent step).
 // After the last stage: level 0's outer boundary, then the register swap.
+void enqueue_diag(Engine &e, Star &st, bool own_derivs);
+
 void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) {
   if (s == 0)
     for (size_t i = 0; i < e.slots.size(); ++i) {
@@ -512,6 +516,11 @@ void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) 
       }
     }
   for (int kind = 0; kind < B_NKIND; ++kind) {
+    // the diagnostics of the state at the start of the step read the
+    // derivative scratch the stage has just formed, before the stage update
+    // overwrites the primitives
+    if (kind == B_POINT && s == 0 && g == 0 && e.stage0_diag)
+      for (Star &st : e.stars) enqueue_diag(e, st, false);
     if (!kind_used(e, kind)) continue;
     const Batch b = batch_of(e, g, s, kind);
     run(e, kKindKid[kind], e.cells[plan_index(g, s, kind)], [&] { launch_kind(e, kind, b, s, dt); });
@@ -675,7 +684,7 @@ bool ready(const Engine &e) {
 }
 
 void drop_graphs(Engine &e) {
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 4; ++i)
     if (e.gexec[i]) {
       cudaGraphExecDestroy(e.gexec[i]);
       e.gexec[i] = nullptr;
@@ -953,39 +962,56 @@ sacra_status set_initial_data(Engine &e, int star, int level, int kind, const do
   return cuda_check(e, "set_initial_data");
 }
 
-sacra_status step(Engine &e, double dt, int n_steps, int use_graph) {
+sacra_status read_diag(Engine &e, sacra_diag *out);
+
+// n_steps steps; with `diag` the first stage of each step also forms the
+// diagnostics of the state at the start of the step, copied to diag[it]
+sacra_status step(Engine &e, double dt, int n_steps, int use_graph, sacra_diag *diag = nullptr) {
   if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
   if (!(dt > 0) || n_steps < 0) return fail(e, SACRA_ERR_ARG, "bad dt or n_steps");
+  if (diag && e.ngroups > 1) return fail(e, SACRA_ERR_STATE, "diagnostics inside the step need a lockstep context");
   for (int it = 0; it < n_steps; ++it) {
+    e.stage0_diag = diag != nullptr;
     if (!use_graph || !steady(e)) {
       enqueue_step(e, dt);
-      continue;
-    }
-    const int par = e.parity;
-    if (!e.gexec[par] || e.gdt[par] != dt) {
-      if (e.gexec[par]) { cudaGraphExecDestroy(e.gexec[par]); e.gexec[par] = nullptr; }
-      cudaGraph_t g;
-      const long long before = e.launches;
-      if (cudaStreamBeginCapture(e.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-        return cuda_check(e, "graph capture (the stream must be a non-default stream)");
-      e.capturing = true;
-      enqueue_step(e, dt);       // swaps the registers on the host side (a sub-cycled
-      e.capturing = false;       // level swaps an even number of times per step)
-      if (cudaStreamEndCapture(e.stream, &g) != cudaSuccess) return cuda_check(e, "graph capture");
-      e.glaunch[par] = e.launches - before;
-      e.launches = before;
-      swap_group(e, 0);          // undo: the graph has not run yet
-      if (cudaGraphInstantiate(&e.gexec[par], g, 0) != cudaSuccess) {
+    } else {
+      const int gi = 2 * e.parity + (diag ? 1 : 0);
+      if (!e.gexec[gi] || e.gdt[gi] != dt) {
+        if (e.gexec[gi]) { cudaGraphExecDestroy(e.gexec[gi]); e.gexec[gi] = nullptr; }
+        cudaGraph_t g;
+        const long long before = e.launches;
+        if (cudaStreamBeginCapture(e.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          e.stage0_diag = false;
+          return cuda_check(e, "graph capture (the stream must be a non-default stream)");
+        }
+        e.capturing = true;
+        enqueue_step(e, dt);       // swaps the registers on the host side (a sub-cycled
+        e.capturing = false;       // level swaps an even number of times per step)
+        e.stage0_diag = false;
+        if (cudaStreamEndCapture(e.stream, &g) != cudaSuccess) return cuda_check(e, "graph capture");
+        e.glaunch[gi] = e.launches - before;
+        e.launches = before;
+        swap_group(e, 0);          // undo: the graph has not run yet
+        if (cudaGraphInstantiate(&e.gexec[gi], g, 0) != cudaSuccess) {
+          cudaGraphDestroy(g);
+          return cuda_check(e, "graph instantiate");
+        }
         cudaGraphDestroy(g);
-        return cuda_check(e, "graph instantiate");
+        e.gdt[gi] = dt;
       }
-      cudaGraphDestroy(g);
-      e.gdt[par] = dt;
+      if (cudaGraphLaunch(e.gexec[gi], e.stream) != cudaSuccess) {
+        e.stage0_diag = false;
+        return cuda_check(e, "graph launch");
+      }
+      e.launches += e.glaunch[gi];
+      for (Star &st : e.stars) st.dt_step = dt;
+      swap_group(e, 0);
     }
-    if (cudaGraphLaunch(e.gexec[par], e.stream) != cudaSuccess) return cuda_check(e, "graph launch");
-    e.launches += e.glaunch[par];
-    for (Star &st : e.stars) st.dt_step = dt;
-    swap_group(e, 0);
+    e.stage0_diag = false;
+    if (diag) {
+      const sacra_status r = read_diag(e, &diag[it]);
+      if (r != SACRA_OK) return r;
+    }
   }
   return cuda_check(e, "step");
 }
@@ -1028,18 +1054,19 @@ sacra_status read_state(Engine &e, int star, int level, int which, int field, do
   return cuda_check(e, "read_state");
 }
 
-sacra_status constraints(Engine &e, int star, sacra_diag *out) {
-  if (star < 0 || star >= (int)e.stars.size() || !out) return fail(e, SACRA_ERR_ARG, "bad star or output");
-  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
-  Star &st = e.stars[star];
-  enqueue_fill(e, st, 0, 0.0);
+// the constraint and conservation diagnostics of the star's current state
+// (Sec. II.F.1): per-level partial sums, then one fixed-order final sum into
+// e.dout.  own_derivs: run the cartoon and derivative passes first; without
+// it the level scratch must already hold the derivatives of this state (the
+// first stage of a step has just formed them).
+void enqueue_diag(Engine &e, Star &st, bool own_derivs) {
   const int L = st.prm.n_levels;
   int slot = 0;
   for (int l = 0; l < L; ++l) {
     Lev &lv = st.lv[l];
     const long long cells = (long long)lv.nx * lv.nz;
     double *ds = reinterpret_cast<double *>(st.ds[l]);
-    if (st.prm.evolve_spacetime) {
+    if (own_derivs && st.prm.evolve_spacetime) {
       run(e, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, st.dp, lv.un, e.tab, kTabStride, e.stream); });
       run(e, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, st.dp, lv.un, ds, lv.nx, lv.nz, e.stream); });
     }
@@ -1048,6 +1075,10 @@ sacra_status constraints(Engine &e, int star, sacra_diag *out) {
     slot += diag_blocks(lv);
   }
   run(e, K_DIAG_FINAL, slot, [&] { launch_diag_final(st.part, slot, e.dout, e.stream); });
+}
+
+// copy the final sums and the fallback counter to the host (waits for the stream)
+sacra_status read_diag(Engine &e, sacra_diag *out) {
   double h[9];
   unsigned long long nfb = 0;
   cudaMemcpyAsync(h, e.dout, sizeof(h), cudaMemcpyDeviceToHost, e.stream);
@@ -1061,6 +1092,15 @@ sacra_status constraints(Engine &e, int star, sacra_diag *out) {
   out->n_c2p_fail = h[8];
   out->n_fallback = (double)nfb;
   return cuda_check(e, "constraints");
+}
+
+sacra_status constraints(Engine &e, int star, sacra_diag *out) {
+  if (star < 0 || star >= (int)e.stars.size() || !out) return fail(e, SACRA_ERR_ARG, "bad star or output");
+  if (!ready(e)) return fail(e, SACRA_ERR_STATE, "initial data missing on some level");
+  Star &st = e.stars[star];
+  enqueue_fill(e, st, 0, 0.0);
+  enqueue_diag(e, st, true);
+  return read_diag(e, out);
 }
 
 sacra_status profile_get(Engine &e, int idx, char *name, size_t name_len, double *total_ms, long long *launches,
@@ -1223,6 +1263,12 @@ sacra_status sacra_rk_stage(sacra_ctx *c, int stage, double dt) {
 sacra_status sacra_step(sacra_ctx *c, double dt, int n_steps, int use_graph) {
   if (!c) return SACRA_ERR_ARG;
   return step(c->e, dt, n_steps, use_graph);
+}
+
+sacra_status sacra_step_constraints(sacra_ctx *c, double dt, int n_steps, int use_graph, sacra_diag *out) {
+  if (!c) return SACRA_ERR_ARG;
+  if (!out && n_steps > 0) return fail(c->e, SACRA_ERR_ARG, "out must hold n_steps diagnostics");
+  return step(c->e, dt, n_steps, use_graph, out);
 }
 
 sacra_status sacra_read_state(sacra_ctx *c, int level, int which, int field, double *host, size_t n) {

@@ -25,8 +25,8 @@ FILL, RESTRICT_REFLUX = 0, 1
 STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
 
 EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
-           "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync",
-           "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_tune",
+           "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_constraints",
+           "sacra_sync", "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_tune",
            "sacra_get_tuning", "sacra_destroy", "sacra_last_error",
            "sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
            "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH):
     L.sacra_regrid_ghosts.argtypes = [vp, C.c_int, C.c_int, C.c_double]
     L.sacra_rk_stage.argtypes = [vp, C.c_int, C.c_double]
     L.sacra_step.argtypes = [vp, C.c_double, C.c_int, C.c_int]
+    L.sacra_step_constraints.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.POINTER(SacraDiag)]
     L.sacra_read_state.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, C.c_size_t]
     L.sacra_constraints.argtypes = [vp, C.POINTER(SacraDiag)]
     L.sacra_sync.argtypes = [vp]
@@ -134,7 +135,8 @@ def load(path: str = LIB_PATH):
                  "sacra_batch_sync", "sacra_batch_profile", "sacra_batch_profile_get"):
         getattr(L, name).restype = C.c_int
     for name in ("sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
-                 "sacra_rk_stage", "sacra_step", "sacra_read_state", "sacra_constraints", "sacra_sync"):
+                 "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_constraints",
+                 "sacra_sync"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -234,6 +236,14 @@ class Sacra:
 
     def step(self, dt, n=1, use_graph=False):
         self._chk(self._L.sacra_step(self._c, dt, n, 1 if use_graph else 0), "step")
+
+    def step_constraints(self, dt, n=1, use_graph=False):
+        """n steps; row i holds the diagnostics of the state at the start of
+        step i (formed inside its first stage), in the order of constraints()."""
+        d = (SacraDiag * max(n, 1))()
+        self._chk(self._L.sacra_step_constraints(self._c, dt, n, 1 if use_graph else 0, d), "step_constraints")
+        return np.array([[x.H_L2, x.M_L2[0], x.M_L2[1], x.M_L2[2], x.Mb, x.J, x.rho_max, x.n_c2p_fail, x.n_fallback]
+                         for x in d[:n]])
 
     def sync(self):
         self._chk(self._L.sacra_sync(self._c), "sync")
