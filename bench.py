@@ -416,7 +416,7 @@ def run_native(args, dist, rank, ws, local):
     diag0 = sim.constraints()
 
     # ---- timed region (device time, CUDA events on the library's stream)
-    ms, launches, diag, clocks = timed_steps(sim, dt, args.steps, dist)
+    ms, launches, diag_in, clocks = timed_steps(sim, dt, args.steps, dist)
     diag = sim.constraints()          # the state after the last step (untimed)
     ms_max = max_over_ranks(dist, ms)
     value = ws * cells_per_step * args.steps / (ms_max * 1e-3)
@@ -433,11 +433,15 @@ def run_native(args, dist, rank, ws, local):
     for _ in range(2):
         msim.step_constraints(dt, 1, use_graph=True)
     msim.sync()
-    mms, mlaunches, _, mclocks = timed_steps(msim, dt, args.steps, dist)
+    mms, mlaunches, mdiag_in, mclocks = timed_steps(msim, dt, args.steps, dist)
     mms_max = max_over_ranks(dist, mms)
     mvalue = ws * cells_per_step * args.steps / (mms_max * 1e-3)
     mixed = {"value": mvalue, "unit": UNIT, "ms_per_step": mms_max / args.steps, "speedup_vs_fp64": mvalue / value,
              "gpu_launches": mlaunches, "clocks": mclocks, "tuning": mtuning,
+             # ||H|| of the same starting state of the last timed step, formed in the step
+             # (mixed: from the FP32 Ricci scalar of its pointwise pass)
+             "H_L2_in_step": {"mixed": mdiag_in[0], "fp64": diag_in[0],
+                              "rel_diff": abs(mdiag_in[0] - diag_in[0]) / diag_in[0]},
              "arith": "FP32 reconstruction, Riemann solver, hydro sources and Z4c algebra; FP64 finite "
                       "differences, primitive recovery, algebraic constraints, RK and flux accumulation"}
 

@@ -448,7 +448,7 @@ void launch_kind(Engine &e, int kind, const Batch &b, int s, double dt) {
     case B_HYDRO: launch_b_hydro_div(b, e.dp, e.stream); break;
     case B_CARTOON: launch_b_cartoon(b, e.dp, e.tab, kTabStride, e.stream); break;
     case B_DERIVS: launch_b_z4c_derivs(b, e.dp, e.stream); break;
-    case B_POINT: launch_b_z4c_point(b, e.dp, e.stream); break;
+    case B_POINT: launch_b_z4c_point(b, e.dp, e.stream, s == 0 && e.stage0_diag ? 1 : 0); break;
     case B_RK: launch_b_rk_update(b, e.dp, s, dt, e.stream); break;
   }
 }
@@ -517,9 +517,9 @@ void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) 
     }
   for (int kind = 0; kind < B_NKIND; ++kind) {
     // the diagnostics of the state at the start of the step read the
-    // derivative scratch the stage has just formed, before the stage update
-    // overwrites the primitives
-    if (kind == B_POINT && s == 0 && g == 0 && e.stage0_diag)
+    // derivative scratch and the Ricci scalar the stage has just formed,
+    // before the stage update overwrites the primitives
+    if (kind == B_RK && s == 0 && g == 0 && e.stage0_diag)
       for (Star &st : e.stars) enqueue_diag(e, st, false);
     if (!kind_used(e, kind)) continue;
     const Batch b = batch_of(e, g, s, kind);
@@ -1071,7 +1071,10 @@ void enqueue_diag(Engine &e, Star &st, bool own_derivs) {
       run(e, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, st.dp, lv.un, ds, lv.nx, lv.nz, e.stream); });
     }
     const int sl = slot;
-    run(e, K_DIAG, cells, [&] { launch_diag(lv, st.dp, ds, l < L - 1, st.prm.evolve_spacetime, st.part, sl, e.stream); });
+    // in a step, the pointwise pass has also stored the Ricci scalar (in the
+    // mixed form the FP32 value its own algebra used)
+    const double *rs = (!own_derivs && st.prm.evolve_spacetime) ? ds + (size_t)z4c_ricci_plane() * lv.P : nullptr;
+    run(e, K_DIAG, cells, [&] { launch_diag(lv, st.dp, ds, l < L - 1, st.prm.evolve_spacetime, st.part, sl, e.stream, rs); });
     slot += diag_blocks(lv);
   }
   run(e, K_DIAG_FINAL, slot, [&] { launch_diag_final(st.part, slot, e.dout, e.stream); });

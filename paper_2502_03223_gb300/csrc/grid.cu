@@ -488,8 +488,9 @@ __device__ __forceinline__ void diag_block_reduce(double acc[DIAG_Q], double (*s
 // S: storage type of the derivative scratch and the cartoon planes (FP32 in
 // the mixed-precision Z4c form); the constraint algebra is FP64 either way.
 template <typename S>
-__global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__restrict__ DS, int covered,
-                                                 int evolve, double *__restrict__ partials) {
+__global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__restrict__ DS,
+                                                 const double *__restrict__ RS, int covered, int evolve,
+                                                 double *__restrict__ partials) {
   __shared__ double sh[DIAG_Q][DIAG_T / 32];
   const int t = threadIdx.x;
   const int n = L.nx * L.nz;
@@ -519,30 +520,47 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__
         Z4cIn<double> z;
         z.W = U[(size_t)fW * P + id]; z.al = U[(size_t)fAL * P + id];
         z.Kh = U[(size_t)fKH * P + id]; z.Th = U[(size_t)fTH * P + id];
+        // every loop below is unrolled so that all indices are compile-time
+        // constants and the arrays stay in registers
+#pragma unroll
         for (int a = 0; a < 6; ++a) { z.h[a] = U[(size_t)(fHXX + a) * P + id]; z.A[a] = U[(size_t)(fAXX + a) * P + id]; }
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           z.Gt[c] = U[(size_t)(fGX + c) * P + id]; z.beta[c] = U[(size_t)(fBX + c) * P + id];
           z.B[c] = U[(size_t)(fBBX + c) * P + id];
         }
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
           z.dW[c] = DS[(size_t)(D1 + c) * P + id];
+#pragma unroll
           for (int a = 0; a < 6; ++a) z.dh[a][c] = DS[(size_t)(D1 + 3 * (1 + a) + c) * P + id];
           z.dKh[c] = DS[(size_t)(D1 + 21 + c) * P + id];
+#pragma unroll
           for (int a = 0; a < 3; ++a) z.dGt[a][c] = DS[(size_t)(D1 + 3 * (8 + a) + c) * P + id];
           z.dTh[c] = DS[(size_t)(D1 + 33 + c) * P + id];
           z.dal[c] = DS[(size_t)(D1 + 36 + c) * P + id];
+#pragma unroll
           for (int a = 0; a < 3; ++a) z.db[a][c] = DS[(size_t)(D1 + 3 * (13 + a) + c) * P + id];
-        }
-        for (int q = 0; q < 6; ++q) {
-          z.ddW[q] = DS[(size_t)(D2 + q) * P + id];
-          for (int a = 0; a < 6; ++a) z.ddh[a][q] = DS[(size_t)(D2 + 6 * (1 + a) + q) * P + id];
-          z.ddal[q] = DS[(size_t)(D2 + 42 + q) * P + id];
-          for (int a = 0; a < 3; ++a) z.ddb[a][q] = DS[(size_t)(D2 + 6 * (8 + a) + q) * P + id];
         }
         Geo<double> G;
         geo_fill(z, G);
-        geo_ricci(z, G);
+        if (RS) {
+          // the pointwise pass of the same stage has formed the Ricci scalar
+          G.Rs = RS[id];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) {
+            z.ddW[q] = DS[(size_t)(D2 + q) * P + id];
+#pragma unroll
+            for (int a = 0; a < 6; ++a) z.ddh[a][q] = DS[(size_t)(D2 + 6 * (1 + a) + q) * P + id];
+            z.ddal[q] = DS[(size_t)(D2 + 42 + q) * P + id];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) z.ddb[a][q] = DS[(size_t)(D2 + 6 * (8 + a) + q) * P + id];
+          }
+          geo_ricci(z, G);
+        }
         double pr[NPRIM];
+#pragma unroll
         for (int f = 0; f < NPRIM; ++f) pr[f] = L.prim[(size_t)f * P + id];
         double E, Si[3], Sij[6];
         matter(pr, z.W, G.g, G.gi, E, Si, Sij);
@@ -550,38 +568,61 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__
         const Sym3 &gi = G.gi;
         const double gim[3][3] = {{gi.xx, gi.xy, gi.xz}, {gi.xy, gi.yy, gi.yz}, {gi.xz, gi.yz, gi.zz}};
         double Am[3][3];   // At^j_i -> Am[j][i]
+#pragma unroll
         for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
           for (int ii = 0; ii < 3; ++ii)
             Am[jj][ii] = gim[jj][0] * z.A[sp(0, ii)] + gim[jj][1] * z.A[sp(1, ii)] + gim[jj][2] * z.A[sp(2, ii)];
         double AA = 0.0, trA = 0.0;
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
           trA += Am[a][a];
+#pragma unroll
           for (int b = 0; b < 3; ++b) AA += Am[a][b] * Am[b][a];
         }
         const double H = G.Rs + K * K - (AA + (2.0 / 3.0) * K * trA + K * K / 3.0) - 16.0 * PI * E;
         // d_k At_ij: x, z by central differences, y from the cartoon planes
         double dA[6][3];
         const double i60x = 1.0 / (60.0 * L.dx), i60z = 1.0 / (60.0 * L.dz);
+#pragma unroll
         for (int a = 0; a < 6; ++a) {
           const double *u = U + (size_t)(fAXX + a) * P + id;
           dA[a][0] = (45.0 * (u[1] - u[-1]) - 9.0 * (u[2] - u[-2]) + (u[3] - u[-3])) * i60x;
           dA[a][2] = (45.0 * (u[L.px] - u[-L.px]) - 9.0 * (u[2 * L.px] - u[-2 * L.px]) + (u[3 * L.px] - u[-3 * L.px])) * i60z;
           dA[a][1] = (cyl && a != 5) ? (double)reinterpret_cast<const S *>(L.dy)[(size_t)(fAXX + a) * P + id] : 0.0;
         }
+        // v^k = d_j gt^jk = -gt^ja gt^kb d_j gt_ab (summed over j)
+        double v[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          double t = 0.0;
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const double ga = gim[jj][a];
+#pragma unroll
+              for (int b = 0; b < 3; ++b) t -= ga * gim[kk][b] * z.dh[sp(a, b)][jj];
+            }
+          v[kk] = t;
+        }
+        const double i3W = 3.0 / z.W;
         double M[3];
+#pragma unroll
         for (int ii = 0; ii < 3; ++ii) {
           double s = 0.0;
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            s += v[kk] * z.A[sp(kk, ii)];
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj) s += gim[jj][kk] * dA[sp(kk, ii)][jj];
+          }
+#pragma unroll
           for (int jj = 0; jj < 3; ++jj)
-            for (int kk = 0; kk < 3; ++kk) {
-              // d_j gt^jk = -gt^ja gt^kb d_j gt_ab
-              double dgi = 0.0;
-              for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) dgi -= gim[jj][a] * gim[kk][b] * z.dh[sp(a, b)][jj];
-              s += dgi * z.A[sp(kk, ii)] + gim[jj][kk] * dA[sp(kk, ii)][jj];
-            }
-          for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
             for (int l = 0; l < 3; ++l) s -= G.G2[l][sp(jj, ii)] * Am[jj][l];
-          for (int l = 0; l < 3; ++l) s -= 3.0 / z.W * Am[l][ii] * z.dW[l];
+#pragma unroll
+          for (int l = 0; l < 3; ++l) s -= i3W * Am[l][ii] * z.dW[l];
           s -= (2.0 / 3.0) * (z.dKh[ii] + 2.0 * z.dTh[ii]) + 8.0 * PI * Si[ii];
           M[ii] = s;
         }
@@ -667,12 +708,12 @@ void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s) {
 int diag_blocks(const Lev &L) { return (L.nx * L.nz + DIAG_T - 1) / DIAG_T; }
 
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials, int slot,
-                 cudaStream_t s) {
+                 cudaStream_t s, const double *RS) {
   if (p.mixed & SACRA_MIXED_Z4C)
-    k_diag<float><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, reinterpret_cast<const float *>(DS), covered, evolve,
+    k_diag<float><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, reinterpret_cast<const float *>(DS), RS, covered, evolve,
                                                     partials + (size_t)slot * DIAG_Q);
   else
-    k_diag<double><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, covered, evolve, partials + (size_t)slot * DIAG_Q);
+    k_diag<double><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, RS, covered, evolve, partials + (size_t)slot * DIAG_Q);
 }
 
 void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s) {

@@ -61,7 +61,9 @@ void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s);
 void launch_b_hydro_div(const Batch &b, const DevParams &p, cudaStream_t s);
 void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, cudaStream_t s);
 void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s);
-void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s);
+// store_rs: the pass also writes the Ricci scalar it forms (FP64, or the FP32
+// value widened) into the FP64 scratch plane z4c_ricci_plane()
+void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s, int store_rs = 0);
 void launch_b_rk_update(const Batch &b, const DevParams &p, int stage, double dt, cudaStream_t s);
 // the FP32 derivative pass has a fixed tile shape
 dim3 z4c_derivs_f32_block();
@@ -80,6 +82,7 @@ void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double
 void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const double *DS, int jmax, int kmax,
                       cudaStream_t s);
 int z4c_scratch_planes();
+int z4c_ricci_plane();
 
 void launch_parity_x(const Lev &L, double *U, cudaStream_t s);
 void launch_parity_z(const Lev &L, double *U, cudaStream_t s);
@@ -96,8 +99,10 @@ void launch_restrict(const Lev &C, const Lev &Pa, cudaStream_t s);
 void launch_time_interp(const Lev &P, const double *uold, const double *pold, const double *pnow, double *ut,
                         double *pt, double theta, int have_old, cudaStream_t s);
 void launch_reflux(const Lev &C, const Lev &Pa, double dt, cudaStream_t s);
+// RS: NULL, or the Ricci scalar of this state per cell, which then replaces
+// the second derivatives and the Ricci tensor
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials,
-                 int slot, cudaStream_t s);
+                 int slot, cudaStream_t s, const double *RS = nullptr);
 int diag_blocks(const Lev &L);
 void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s);
 

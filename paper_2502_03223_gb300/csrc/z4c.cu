@@ -301,7 +301,11 @@ __global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__rest
 // AK advection + KO of all 25 fields.
 __constant__ int kD1Fields[16] = {fW, fHXX, fHXY, fHXZ, fHYY, fHYZ, fHZZ, fKH, fGX, fGY, fGZ, fTH, fAL, fBX, fBY, fBZ};
 __constant__ int kD2Fields[11] = {fW, fHXX, fHXY, fHXZ, fHYY, fHYZ, fHZZ, fAL, fBX, fBY, fBZ};
-constexpr int DS_D1 = 0, DS_D2 = 48, DS_AK = 114, DS_N = 139;
+// DS_RS: the Ricci scalar of the pointwise pass, written when the diagnostics
+// of the step's starting state are formed in the same stage.  The plane index
+// counts FP64 planes in both forms: in the FP32 form it lies past the FP32
+// planes of the same allocation (DS_N FP64 planes).
+constexpr int DS_D1 = 0, DS_D2 = 48, DS_AK = 114, DS_RS = 139, DS_N = 140;
 
 __device__ __forceinline__ bool y_zero(int f) {
   return f == fW || f == fKH || f == fTH || f == fAL || f == fGZ || f == fBZ || f == fBBZ || f == fHZZ || f == fAZZ;
@@ -683,7 +687,8 @@ __device__ inline void load_z4c_in(const Lev &L, const double *__restrict__ U, c
 
 template <typename T>
 __device__ __forceinline__ void z4c_point_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
-                                                    const T *__restrict__ DS, int jmax, int kmax, int j, int k) {
+                                                    const T *__restrict__ DS, int jmax, int kmax, int j, int k,
+                                                    double *__restrict__ rs_out = nullptr) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -692,6 +697,7 @@ __device__ __forceinline__ void z4c_point_cell(const Lev &L, const DevParams &p,
   Geo<T> G;
   geo_fill(z, G);
   geo_ricci(z, G);
+  if (rs_out) rs_out[id] = to_f64<T>(G.Rs);
   T pr[NPRIM];
 #pragma unroll
   for (int f = 0; f < NPRIM; ++f) pr[f] = ld_as<T>(L.prim[(size_t)f * P + id]);
@@ -770,10 +776,11 @@ __global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 0) kb_z4c_point(Batch b, DevParams p) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 0) kb_z4c_point(Batch b, DevParams p, int store_rs) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
+    double *rs = store_rs ? reinterpret_cast<double *>(q.DS) + (size_t)DS_RS * q.L.P : nullptr;
     z4c_point_cell<T>(q.L, q.P, q.U, reinterpret_cast<const T *>(q.DS), q.jmax, q.kmax, tl.j0 + threadIdx.x,
-                      tl.k0 + threadIdx.y);
+                      tl.k0 + threadIdx.y, rs);
   });
 }
 
@@ -789,14 +796,15 @@ void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s) {
   else kb_z4c_derivs<<<b.grid, b.block, 0, s>>>(b, p);
 }
 
-void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s) {
+void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s, int store_rs) {
   if (b.ntiles <= 0) return;
-  if (p.mixed & SACRA_MIXED_Z4C) kb_z4c_point<float><<<b.grid, b.block, 0, s>>>(b, p);
-  else kb_z4c_point<double><<<b.grid, b.block, 0, s>>>(b, p);
+  if (p.mixed & SACRA_MIXED_Z4C) kb_z4c_point<float><<<b.grid, b.block, 0, s>>>(b, p, store_rs);
+  else kb_z4c_point<double><<<b.grid, b.block, 0, s>>>(b, p, store_rs);
 }
 
 dim3 z4c_derivs_f32_block() { return dim3(DTX, DTZ); }
 
 int z4c_scratch_planes() { return DS_N; }
+int z4c_ricci_plane() { return DS_RS; }
 
 }  // namespace sacra
