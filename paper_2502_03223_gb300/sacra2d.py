@@ -243,7 +243,7 @@ class Sacra:
         d = (SacraDiag * max(n, 1))()
         self._chk(self._L.sacra_step_constraints(self._c, dt, n, 1 if use_graph else 0, d), "step_constraints")
         return np.array([[x.H_L2, x.M_L2[0], x.M_L2[1], x.M_L2[2], x.Mb, x.J, x.rho_max, x.n_c2p_fail, x.n_fallback]
-                         for x in d[:n]])
+                         for x in d[:n]]).reshape(n, 9)
 
     def sync(self):
         self._chk(self._L.sacra_sync(self._c), "sync")
