@@ -336,3 +336,31 @@ def test_damping_terms_and_their_absence_in_bssn(setup):
     assert r_b[17] == 0.0
     keep = np.arange(25) != 17
     assert np.array_equal(r_b[keep], r_0[keep])
+
+
+def test_bssn_keeps_theta_zero_on_the_grid():
+    """The BSSN switch on a whole two-level hierarchy of the stable star (with
+    a random metric perturbation so that the constraints do not vanish): Theta
+    stays exactly zero through the stages, the ghost fill, the prolongation and
+    the restriction, and the Z4c run from the same data does grow a Theta."""
+    import dataclasses
+    cfg, tov = W.tov_config("bssn", rho_c=1.28e-3, n_levels=2, N=16, dx_fine=1.0, rk=1)
+    datas = []
+    for l in range(2):
+        d = W.tov_level_data(cfg, tov, l)
+        d[:25] += W.random_metric_perturbation(cfg, l, np.random.default_rng(5), amp=1e-3)
+        d[17] = 0.0
+        datas.append(d)
+    runs = {}
+    for bssn in (0, 1):
+        c = dataclasses.replace(cfg, bssn=bssn)
+        o = O.Oracle(c)
+        for l, d in enumerate(datas):
+            o.set_level(l, 0, d)
+        o.step(c.dt, 3)
+        runs[bssn] = [o.read(l, 0, 17) for l in range(2)]
+        for l in range(2):
+            assert np.all(np.isfinite(o.read(l, 0, 0)))
+    for l in range(2):
+        assert not np.any(runs[1][l]), l
+        assert np.max(np.abs(runs[0][l])) > 1e-8, l
