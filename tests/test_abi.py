@@ -66,6 +66,7 @@ def test_parameter_checks_of_the_eos_variants_and_boundaries(lib_path):
     assert L.sacra_arena_bytes(ctypes.byref(p), ctypes.byref(n)) == -1
     assert ok(eos_adiabatic=1) and not ok(eos_adiabatic=1, K=0.0) and not ok(eos_adiabatic=2)
     assert not ok(r_hold=-1.0) and not ok(hydro_outer=2) and not ok(subcycle_from=-1)
+    assert ok(bssn=1) and not ok(bssn=2) and not ok(bssn=-1)
     # the allocation-free entry point has no device memory for a piece table
     p = S.make_params(dataclasses_replace(cfg, n_levels=1, pwp=((1e-4, 2.5),)))
     null = ctypes.c_void_p(1)
