@@ -107,3 +107,27 @@ def test_incompatible_stars_are_rejected():
     b, _ = W.tov_config("b", n_levels=1, N=32, dx_fine=0.5, rk=0)      # another integrator
     with pytest.raises(S.SacraError):
         S.SacraBatch([a, b])
+
+
+def test_batch_mixes_bssn_and_z4c_stars():
+    """The formulation is a per-star parameter: a batch holding BSSN and Z4c
+    stars advances each exactly as its own context does (Theta stays zero in
+    the BSSN stars only)."""
+    stars = [(dataclasses.replace(c, bssn=i % 2), ds) for i, (c, ds) in enumerate(_stars(0))]
+    dt = min(c.dt for c, _ in stars)
+    batch = S.SacraBatch([c for c, _ in stars])
+    for i, (c, ds) in enumerate(stars):
+        for l, d in enumerate(ds):
+            batch.set_initial_data(i, l, S.PRIM_METRIC, d)
+    batch.step(dt, 3, use_graph=True)
+    for i, (c, ds) in enumerate(stars):
+        alone = S.Sacra(c)
+        for l, d in enumerate(ds):
+            alone.set_initial_data(l, S.PRIM_METRIC, d)
+        alone.step(dt, 3, use_graph=True)
+        for l in range(c.n_levels):
+            for f in range(30):
+                assert _same(batch.read(i, l, S.STATE_STEP, f), alone.read(l, S.STATE_STEP, f)), (i, l, f)
+        theta = batch.read(i, 0, S.STATE_STEP, 17)
+        assert (not np.any(theta)) if c.bssn else np.any(theta), i
+        alone.close()
