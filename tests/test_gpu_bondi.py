@@ -68,9 +68,11 @@ def test_bondi_convergence_on_the_gpu(solver, levels, K):
     """eps_L1(rho) at t = 20M for N = 32 .. 256 (the paper's study; with three
     levels N is per level and the finest box is 4M) falls at every doubling.
     The measured order is about 1 at this time (the paper reports about 2):
-    the error is dominated by grid-scale noise that starts at the staircase
-    edge of the held region r < 0.4M and spreads upstream through the
-    reconstruction stencils, see test_bondi_smooth_error_is_second_order."""
+    the error is dominated by an odd-even mode that starts at the staircase
+    edge of the held region r < 0.4M and spreads upstream; PPM in
+    method-of-lines form does not damp it in smooth monotone flow (see the
+    oracle's test_smooth_monotone_flow_has_no_numerical_dissipation and
+    test_bondi_smooth_error_is_second_order)."""
     Ns = (32, 64, 128, 256)
     errs = [_l1_at(N, 20.0, solver, levels, K) for N in Ns]
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(Ns) - 1)]
