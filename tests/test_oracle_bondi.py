@@ -11,11 +11,12 @@ import oracle as O
 from paper_2502_03223_gb300 import workloads as W
 
 from bondi_common import G, bondi_l1
+from golden_values import PAPER
 
 
 def test_bondi_solution_matches_the_paper_and_is_transonic():
-    sol = W.bondi_solve()
-    assert round(sol.Mdot, 4) == 0.0848                       # the paper's accretion rate for R_c = 8M
+    sol = W.bondi_solve(K=PAPER["bondi_K"], Gamma=PAPER["bondi_Gamma"], R_c=PAPER["bondi_r_c"])
+    assert round(sol.Mdot, 4) == PAPER["bondi_mdot"]          # the paper's accretion rate for R_c = 8M
     R = np.array([1.6, 2.0, 4.0, 7.0, 8.0, 9.0, 16.0, 40.0])
     rho = W.bondi_rho(sol, R)
     g1 = sol.Gamma - 1.0
@@ -32,8 +33,8 @@ def test_bondi_solution_matches_the_paper_and_is_transonic():
 
 def test_trumpet_slice_closed_forms():
     C = W.trumpet_C()
-    assert W.trumpet_r_of_R(1.5) == 0.0                        # r = 0 at R = 3M/2
-    assert W.trumpet_r_of_R(2.0) == pytest.approx(0.78, abs=5e-3)   # horizon at r ~ 0.78M
+    assert W.trumpet_r_of_R(PAPER["trumpet_R_at_r0"]) == 0.0   # r = 0 at R = 3M/2
+    assert W.trumpet_r_of_R(2.0) == pytest.approx(PAPER["trumpet_r_horizon"], abs=5e-3)   # horizon at r ~ 0.78M
     R = np.array([1.6, 2.0, 3.0, 8.0, 30.0])
     alpha = np.sqrt(1.0 - 2.0 / R + C * C / R ** 4)
     h = 1e-6

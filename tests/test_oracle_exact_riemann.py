@@ -8,11 +8,13 @@ from scipy.integrate import solve_ivp
 
 from oracle.exact_riemann import ExactRiemann, IdealGas
 
+from golden_values import PAPER
+
 
 def test_contact_position_of_the_paper():
     # (rho, P, v) = (10, 40/3, 0) | (1, 0, 0), Gamma = 5/3: contact at x = 0.786 for t = 0.4
     e = ExactRiemann(5.0 / 3.0, (10.0, 40.0 / 3.0, 0.0), (1.0, 0.0, 0.0))
-    assert abs(0.5 + 0.4 * e.vstar - 0.786) < 5e-4
+    assert abs(0.5 + PAPER["shock_tube_t"] * e.vstar - PAPER["shock_tube_contact_x"]) < 5e-4
 
 
 def _cons(g, rho, p, v):

@@ -8,17 +8,20 @@ from scipy.optimize import brentq
 import oracle as O
 from paper_2502_03223_gb300 import workloads as W
 
+from golden_values import PAPER
+
 G = 8
 MSUN_KM = 1.4767
 
 
 def test_migration_star_radius_and_stable_partner():
-    unstable = W.tov_solve(100.0, 2.0, 8e-3)
+    K, Gam = PAPER["migration_K"], PAPER["migration_Gamma"]
+    unstable = W.tov_solve(K, Gam, PAPER["migration_rho_c"])
     # initial (isotropic coordinate) radius quoted as 6.31 km
-    assert abs(unstable.r_iso * MSUN_KM - 6.31) < 0.03
+    assert abs(unstable.r_iso * MSUN_KM - PAPER["migration_radius_km"]) < 0.03
     # stable-branch model with the same baryon mass: rho_s = 1.346e-3
-    rho_s = brentq(lambda r: W.tov_solve(100.0, 2.0, r, dR=4e-3).Mb - unstable.Mb, 1.0e-3, 2.0e-3, xtol=1e-8)
-    assert abs(rho_s - 1.346e-3) < 0.005 * 1.346e-3
+    rho_s = brentq(lambda r: W.tov_solve(K, Gam, r, dR=4e-3).Mb - unstable.Mb, 1.0e-3, 2.0e-3, xtol=1e-8)
+    assert abs(rho_s - PAPER["migration_rho_s"]) < 0.005 * PAPER["migration_rho_s"]
 
 
 def _cowling_residual(N, dx):
