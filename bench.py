@@ -2,24 +2,33 @@
 """Throughput of the SACRA-2D hot path on GB300: cell-updates per second per
 RK stage of Z4c + HLLC GRHD on the fixed-mesh-refinement cartoon grid.
 
-Workload (default): the stable TOV star (K=100, Gamma=2, rho_c=1.28e-3,
-Gamma_th=2, atmosphere 1e-10 of rho_c), equatorial symmetry, 3 FMR levels of
-256^2 cells, finest dx = 0.25, SSP-RK3, FP64.  One step = the whole hot path:
-ghost fill / prolongation, hydro and Z4c right-hand sides, RK combination with
-algebraic constraints and primitive recovery for every stage, then
-restriction + reflux; the constraint and conservation diagnostics of the state
-at the start of each step are formed inside its first stage (from that stage's
-derivative pass) and read back to the host every step.  The working set (about
-0.7 GB of FP64 state per step) exceeds the 129 MB L2, so no flush is needed.
+Headline workload (default): the unstable-branch migration star (K=100,
+Gamma=2, rho_c=7.993e-3 with a 1% pressure depletion, Gamma_th=2, atmosphere
+1e-10 of rho_c), equatorial symmetry, 5 FMR levels of 512^2 cells, finest
+dx = 0.1, classical RK4, FP64.  One step = the whole hot path: ghost fill /
+prolongation, hydro and Z4c right-hand sides, RK combination with algebraic
+constraints and primitive recovery for every stage, then restriction +
+reflux; the constraint and conservation diagnostics of the state at the start
+of each step are formed inside its first stage and read back to the host
+every step.  The working set (about 2.5 GB of FP64 state per step) exceeds the
+129 MB L2, so no flush is needed.
+
+Beside it on the same line: the mixed-precision form of the same workload;
+the stable star (3 levels of 256^2, SSP-RK3) in both forms; the large run
+(the migration star at 7 levels of 1024^2, levels 5 and 6 sub-cycled) in
+both forms; the batched sweep of 64 stars; the end-to-end rate through the C
+ABI with the state copied both ways every step; the roofline of the dominant
+kernel and of the whole step against the method's own operation count.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun every rank advances its own replica (the path has no exchange
-step on one level set; weak scaling, no collective on the data path).
+Under torchrun every rank advances its own replica (independent problems, no
+exchange step; weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
 import argparse
 import ctypes
+import dataclasses
 import json
 import os
 import subprocess
@@ -35,13 +44,21 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per RK stage (Z4c+HLLC), FP64 vs mixed/batched, % of roofline"
 UNIT = "cell-updates/s"
 
-# Algorithmic FLOPs per unit of work, counted on the oracle's plain
-# restatement with its op-counting build (oracle/opcount.cpp), benchmark
-# workload, one RK stage.  Unit: a cell of the update region, a face for the
-# flux kernels, a cell of the plane patch for the cartoon kernel.
-ALG_FLOPS = {
-    "k_flux_x": 1071.2, "k_flux_z": 1071.2, "k_hydro_rhs": 1383.2, "k_cartoon": 3481.0,
-    "k_z4c_derivs": 5296.0, "k_z4c_point": 4197.0, "k_rk_update": 576.7,
+# FP64 operations per unit of work of the method itself (add, sub, mul = 1; an
+# FMA = 2; div, sqrt, exp = 1), counted by hand on the minimal form of each
+# kernel's arithmetic.  Stencils: symmetric pair form (u_n - u_-n, u_n + u_-n)
+# with the weights and 1/dx factors hoisted and zero taps skipped, pair sums
+# shared between the derivative kinds, the mixed x-z derivative separable (the
+# z-difference numerator of a column serves the cell's own d_z and its
+# neighbours' d_xz), the lopsided advection at beta != 0.  Cartoon: the nine-
+# point interpolation and the +-phi rotations folded into per-column weights
+# of each d_y / d_yy output.  Pointwise algebra, fluxes, sources and the stage
+# update: the plain evaluation (the oracle's operation count), which has no
+# stencil redundancy.  Units: a cell of the update region; a face for the flux
+# kernels; a cell of the plane patch for the cartoon kernel.
+METHOD_FLOPS = {
+    "k_z4c_derivs": 2139.0, "k_cartoon": 878.0, "k_z4c_point": 4197.0, "k_flux_x": 1071.2,
+    "k_flux_z": 1071.2, "k_hydro_rhs": 1383.2, "k_rk_update": 576.7,
 }
 NOMINAL_FP64_TFLOPS = 1.25
 
@@ -146,7 +163,11 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- workloads
 
+WORKLOADS = ("migration_5x512", "tov_stable_3x256", "large_7x1024", "shock_tube_400x4")
+
+
 def workload(name):
+    """(RunConfig, per-level initial data) of a named workload."""
     from paper_2502_03223_gb300 import workloads as W
     if name == "tov_stable_3x256":
         cfg, tov = W.config_tov_stable()
@@ -154,10 +175,33 @@ def workload(name):
     if name == "migration_5x512":
         cfg, tov = W.config_migration()
         return cfg, [W.tov_level_data(cfg, tov, l, p_deplete=0.99) for l in range(cfg.n_levels)]
+    if name == "large_7x1024":
+        # the migration star at 7 levels of 1024^2; the paper's l_fix = 4: levels >= 5 sub-cycle
+        cfg, tov = W.config_migration(N=1024, n_levels=7)
+        cfg = dataclasses.replace(cfg, name="large_7x1024", subcycle_from=5)
+        return cfg, [W.tov_level_data(cfg, tov, l, p_deplete=0.99) for l in range(cfg.n_levels)]
     if name == "shock_tube_400x4":
         cfg = W.config_shock_tube()
         return cfg, [W.shock_tube_data(cfg)]
     raise SystemExit("unknown workload " + name)
+
+
+def cell_updates_per_step(cfg):
+    """Interior cells x RK stages of one (coarse) step; a sub-cycled level
+    takes 2^(l - K + 1) steps per coarse step."""
+    K = cfg.subcycle_from
+    n = 0
+    for l in range(cfg.n_levels):
+        reps = (1 << (l - K + 1)) if (0 < K < cfg.n_levels and l >= K) else 1
+        n += cfg.nx * cfg.nz * reps
+    return n * cfg.n_stages
+
+
+def describe(cfg):
+    return {"workload": cfg.name, "levels": cfg.n_levels, "cells_per_level": [cfg.nx, cfg.nz],
+            "finest_dx": cfg.dx(cfg.n_levels - 1), "integrator": "SSP-RK3" if cfg.rk else "RK4",
+            "stages_per_step": cfg.n_stages, "cell_updates_per_step": cell_updates_per_step(cfg),
+            "subcycled_from_level": cfg.subcycle_from if 0 < cfg.subcycle_from < cfg.n_levels else None}
 
 
 def fp64_peak():
@@ -173,12 +217,12 @@ def fp64_peak():
     return tf.value if rc == 0 else None
 
 
-def read_traffic():
-    """DRAM bytes per launch of a kernel from the committed ncu summary
-    (profiles/traffic_tov_stable_3x256.txt), kept only if the kernel's sources
-    still hash to the recorded value (else the counters are stale)."""
+def read_traffic(workload_name):
+    """DRAM bytes per launch of a kernel from the committed ncu summary of
+    this workload (profiles/traffic_<workload>.txt), kept only if the kernel's
+    sources still hash to the recorded value (else the counters are stale)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic_tov_stable_3x256.txt")
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % workload_name)
     out = {}
     if not os.path.exists(path):
         return out
@@ -198,22 +242,28 @@ def read_traffic():
     return out
 
 
-# ---------------------------------------------------------------- arms
+# ---------------------------------------------------------------- the reference arm (CPU oracle)
 
-def oracle_sample(cfg, datas, stages=1):
+def oracle_sample(cfg, datas, stages=1, full_step=False):
     """Time `stages` RK stages (ghost fill + stage) of the whole hierarchy on
-    the CPU oracle (single thread).  Returns (cell-updates, seconds)."""
+    the CPU oracle, or one whole step (every stage, restriction and reflux)
+    with full_step.  Returns (cell-updates, seconds)."""
     import oracle as O
     o = O.Oracle(cfg)
     for l, d in enumerate(datas):
         o.set_level(l, 0, d)
     t0 = time.perf_counter()
-    for s in range(stages):
-        o.fill(s % cfg.n_stages, cfg.dt)
-        o.stage(s % cfg.n_stages, cfg.dt)
+    if full_step:
+        o.step(cfg.dt, 1)
+        n = cell_updates_per_step(cfg)
+    else:
+        for s in range(stages):
+            o.fill(s % cfg.n_stages, cfg.dt)
+            o.stage(s % cfg.n_stages, cfg.dt)
+        n = cfg.interior_cells * stages
     el = time.perf_counter() - t0
     o.close()
-    return cfg.interior_cells * stages, el
+    return n, el
 
 
 def run_reference(args, dist, rank, ws):
@@ -235,11 +285,12 @@ def run_reference(args, dist, rank, ws):
         cells += c
         el += t
     value = cells / el
+    conf = describe(cfg)
+    conf["reference"] = "CPU oracle (plain FP64 C)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "levels": cfg.n_levels, "cells_per_level": [cfg.nx, cfg.nz],
-                       "integrator": "SSP-RK3" if cfg.rk else "RK4", "reference": "CPU oracle (plain FP64 C)"},
+            "config": conf,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "each step: one RK stage (ghost fill + stage) of the whole %s hierarchy, "
                                        "OpenMP over %d threads" % (cfg.name, cores)},
@@ -247,11 +298,13 @@ def run_reference(args, dist, rank, ws):
     print(json.dumps(line), flush=True)
 
 
-def timed_steps(sim, dt, steps, dist):
-    """K graph-replayed steps, each with the diagnostics of its starting state
-    read back, bracketed by a barrier and a device synchronize, timed by CUDA
-    events on the library's stream.  Returns (ms, launches, last diagnostics,
-    clocks)."""
+# ---------------------------------------------------------------- timing helpers
+
+def timed_region(sim, nsteps, dt, dist, with_diag):
+    """nsteps graph-replayed steps bracketed by a barrier and a device
+    synchronize, timed by CUDA events on the library's stream.  with_diag:
+    each step forms the diagnostics of its starting state and reads them
+    back.  Returns (ms, launches, last diagnostics or None, clocks)."""
     import torch
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
@@ -262,14 +315,57 @@ def timed_steps(sim, dt, steps, dist):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(sim.stream)
     diag = None
-    for _ in range(steps):
-        diag = sim.step_constraints(dt, 1, use_graph=True)[0]
+    if with_diag:
+        for _ in range(nsteps):
+            diag = sim.step_constraints(dt, 1, use_graph=True)[0]
+    else:
+        sim.step(dt, nsteps, use_graph=True)
     ev1.record(sim.stream)
     ev1.synchronize()
     torch.cuda.synchronize()
     barrier(dist)
     clocks = sampler.stop()
     return ev0.elapsed_time(ev1), sim.launch_count - n0, diag, clocks
+
+
+def bench_context(cfg, datas, args, dist, ws, repeats, repeat_steps, steps=None, tune=True):
+    """Build a context of cfg, warm it up, autotune it (outside the timed
+    regions), then time `steps` steps (the line's region) and `repeats` more
+    regions of `repeat_steps` steps each.  Returns (sim, result dict)."""
+    from paper_2502_03223_gb300 import sacra2d as S
+    steps = args.steps if steps is None else steps
+    sim = S.Sacra(cfg)
+    for l, d in enumerate(datas):
+        sim.set_initial_data(l, S.PRIM_METRIC, d)
+    lockstep = not (0 < cfg.subcycle_from < cfg.n_levels)
+    dt = cfg.dt
+    for _ in range(args.warmup):
+        sim.step(dt, 1, use_graph=True)
+    sim.sync()
+    tuning = sim.tune(reps=4) if (tune and not args.no_tune) else None
+    for _ in range(2):
+        sim.step(dt, 1, use_graph=True)
+    sim.sync()
+    diag0 = sim.constraints() if lockstep else None
+    cps = cell_updates_per_step(cfg)
+    ms, launches, diag_in, clocks = timed_region(sim, steps, dt, dist, lockstep)
+    ms = max_over_ranks(dist, ms)
+    res = {"value": ws * cps * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "gpu_launches": launches, "clocks": clocks, "tuning": tuning,
+           "diagnostics_in_step": lockstep}
+    if repeats > 0:
+        vals, rclk = [], []
+        for _ in range(repeats):
+            rms, _, _, rc = timed_region(sim, repeat_steps, dt, dist, lockstep)
+            rms = max_over_ranks(dist, rms)
+            vals.append(ws * cps * repeat_steps / (rms * 1e-3))
+            rclk.append(rc.get("sm_mhz"))
+        res["repeats"] = {"n": repeats, "steps_each": repeat_steps, "median_value": float(np.median(vals)),
+                          "values": vals, "median_ms_per_step": ws * cps / float(np.median(vals)) * 1e3,
+                          "sm_mhz": rclk}
+    res["_diag_in"] = diag_in
+    res["_diag0"] = diag0
+    return sim, res
 
 
 def errors_vs_oracle(cfg, datas, sims, steps=1):
@@ -376,7 +472,7 @@ def run_batch(args, dist, ws):
             lms, _, lclocks = timed(steps)
             learned = {"ms_per_step": lms / steps, "tuples": n, "train": rep, "clocks": lclocks}
             b.set_mlp(None)
-    cells = sum(c.interior_cells * c.n_stages for c in cfgs)
+    cells = sum(cell_updates_per_step(c) for c in cfgs)
     if learned is not None:
         learned["value"] = ws * cells * steps / (learned["ms_per_step"] * steps * 1e-3)
         learned["unit"] = UNIT
@@ -385,130 +481,146 @@ def run_batch(args, dist, ws):
     return {"workload": "batch_sweep_%d" % len(cfgs), "value": ws * cells * steps / (ms * 1e-3), "unit": UNIT,
             "ms_per_step": ms / steps, "steps": steps, "n_stars": len(cfgs),
             "cell_updates_per_step": cells, "precision": "mixed", "cuda_graph": True, "tuning": tuning,
-            "gpu_launches": launches, "clocks": clocks, "init_s": t_init, "learned_seed": learned,
-            "star0_H_L2": diag[0], "sizes": sorted(set((c.nx, c.n_levels) for c in cfgs))[:40]}
+            "gpu_launches": launches, "launches_per_step": launches / steps, "clocks": clocks, "init_s": t_init,
+            "learned_seed": learned, "star0_H_L2": diag[0],
+            "sizes": sorted(set((c.nx, c.n_levels) for c in cfgs))[:40]}
+
+
+MIXED_ARITH = ("FP32: reconstruction, Riemann solver, hydro sources, the weighted sums of the Z4c finite "
+               "differences (of FP64-exact differences, as FP32 hi/lo splits), the cartoon planes and the Z4c "
+               "pointwise algebra; FP64: primitive recovery, algebraic constraints, RK combination, flux "
+               "divergence and registers, restriction, prolongation, diagnostics")
+
+
+def pair_forms(cfg, datas, args, dist, ws, repeats, repeat_steps, steps):
+    """FP64 and mixed contexts of one workload, each timed; returns
+    (fp64 sim, fp64 result, mixed sim, mixed result)."""
+    from paper_2502_03223_gb300 import sacra2d as S
+    sim, r64 = bench_context(cfg, datas, args, dist, ws, repeats, repeat_steps, steps=steps)
+    mcfg = dataclasses.replace(cfg, precision=S.MIXED)
+    msim, rmx = bench_context(mcfg, datas, args, dist, ws, repeats, repeat_steps, steps=steps)
+    rmx["speedup_vs_fp64"] = rmx["value"] / r64["value"]
+    rmx["arith"] = MIXED_ARITH
+    return sim, r64, msim, rmx
+
+
+def strip(d):
+    return {k: v for k, v in d.items() if not k.startswith("_")}
 
 
 def run_native(args, dist, rank, ws, local):
-    import dataclasses
     import torch
     from paper_2502_03223_gb300 import build as B
     B.build()
     from paper_2502_03223_gb300 import sacra2d as S
     torch.cuda.set_device(local)
     cfg, datas = workload(args.workload)
-    sim = S.Sacra(cfg)
-    for l, d in enumerate(datas):
-        sim.set_initial_data(l, S.PRIM_METRIC, d)
-    dt = cfg.dt
-    cells_per_step = cfg.interior_cells * cfg.n_stages
+    cps = cell_updates_per_step(cfg)
+    reps, rsteps = args.repeats, max(args.steps, args.repeat_steps)
 
-    def one_step(graph=True):
-        return sim.step_constraints(dt, 1, use_graph=graph)[0]
-
-    for _ in range(args.warmup):
-        one_step()
-    sim.sync()
-    tuning = sim.tune(reps=4) if not args.no_tune else None   # autotuner, outside the timed region
-    for _ in range(2):
-        one_step()
-    sim.sync()
-    diag0 = sim.constraints()
-
-    # ---- timed region (device time, CUDA events on the library's stream)
-    ms, launches, diag_in, clocks = timed_steps(sim, dt, args.steps, dist)
-    diag = sim.constraints()          # the state after the last step (untimed)
-    ms_max = max_over_ranks(dist, ms)
-    value = ws * cells_per_step * args.steps / (ms_max * 1e-3)
-
-    # ---- the mixed-precision form of the same step, timed the same way
-    mcfg = dataclasses.replace(cfg, precision=S.MIXED)
-    msim = S.Sacra(mcfg)
-    for l, d in enumerate(datas):
-        msim.set_initial_data(l, S.PRIM_METRIC, d)
-    for _ in range(args.warmup):
-        msim.step_constraints(dt, 1, use_graph=True)
-    msim.sync()
-    mtuning = msim.tune(reps=4) if not args.no_tune else None
-    for _ in range(2):
-        msim.step_constraints(dt, 1, use_graph=True)
-    msim.sync()
-    mms, mlaunches, mdiag_in, mclocks = timed_steps(msim, dt, args.steps, dist)
-    mms_max = max_over_ranks(dist, mms)
-    mvalue = ws * cells_per_step * args.steps / (mms_max * 1e-3)
-    mixed = {"value": mvalue, "unit": UNIT, "ms_per_step": mms_max / args.steps, "speedup_vs_fp64": mvalue / value,
-             "gpu_launches": mlaunches, "clocks": mclocks, "tuning": mtuning,
-             # ||H|| of the same starting state of the last timed step, formed in the step
-             # (mixed: from the FP32 Ricci scalar of its pointwise pass)
-             "H_L2_in_step": {"mixed": mdiag_in[0], "fp64": diag_in[0],
-                              "rel_diff": abs(mdiag_in[0] - diag_in[0]) / diag_in[0]},
-             "arith": "FP32 reconstruction, Riemann solver, hydro sources and Z4c algebra; FP64 finite "
-                      "differences, primitive recovery, algebraic constraints, RK and flux accumulation"}
-
-    # ---- the batched sweep (independent stars of mixed sizes in one set of
-    # persistent launches per stage), mixed precision, one graph per step
-    batch = None
-    if not args.no_batch:
-        batch = run_batch(args, dist, ws)
+    # ---- the headline workload: FP64 (the line's value) and the mixed form
+    sim, r64, msim, rmx = pair_forms(cfg, datas, args, dist, ws, reps, rsteps, args.steps)
+    value, ms_step = r64["value"], r64["ms_per_step"]
+    diag = sim.constraints() if r64["diagnostics_in_step"] else None
+    mixed = strip(rmx)
+    if r64["_diag_in"] is not None and rmx["_diag_in"] is not None:
+        # ||H|| of the same starting state of the last timed step, formed in the step
+        # (mixed: from the FP32 Ricci scalar of its pointwise pass)
+        h64, hmx = r64["_diag_in"][0], rmx["_diag_in"][0]
+        mixed["H_L2_in_step"] = {"mixed": hmx, "fp64": h64, "rel_diff": abs(hmx - h64) / h64 if h64 else None}
 
     # ---- end to end through the C ABI with host buffers: every step the state
-    # of all levels goes host -> device from pinned memory (set_initial_data, RAW),
-    # one step runs, and the diagnostics come back to the host
-    host = []
+    # of all levels goes host -> device from pinned memory (set_initial_data,
+    # RAW), one step runs with its diagnostics read back, and the evolved state
+    # of all levels comes back device -> host into pinned memory (read_level)
+    host_in, host_out = [], []
     for l in range(cfg.n_levels):
-        buf = torch.empty(30 * sim.px * sim.pz, dtype=torch.float64, pin_memory=True)
-        a = buf.numpy()
-        for f in range(30):
-            a[f * sim.px * sim.pz:(f + 1) * sim.px * sim.pz] = sim.read(l, S.STATE_STEP, f).ravel()
-        host.append(a)
+        a = torch.empty(30 * sim.px * sim.pz, dtype=torch.float64, pin_memory=True).numpy()
+        sim.read_level(l, a)
+        host_in.append(a)
+        host_out.append(torch.empty(30 * sim.px * sim.pz, dtype=torch.float64, pin_memory=True).numpy())
     e2e_steps = max(3, min(args.steps, 20))
-    h2d = sum(a.nbytes for a in host)
-    d2h = ctypes.sizeof(S.SacraDiag)
+    h2d = sum(a.nbytes for a in host_in)
+    d2h = sum(a.nbytes for a in host_out) + ctypes.sizeof(S.SacraDiag)
     sim.sync()
     barrier(dist)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for l in range(cfg.n_levels):
-            sim.set_initial_data(l, S.RAW, host[l])
-        one_step()
+            sim.set_initial_data(l, S.RAW, host_in[l])
+        sim.step_constraints(cfg.dt, 1, use_graph=True)
+        for l in range(cfg.n_levels):
+            sim.read_level(l, host_out[l])
     el = time.perf_counter() - t0
     el = max_over_ranks(dist, el)
-    e2e = ws * cells_per_step * e2e_steps / el
+    e2e = {"value": ws * cps * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "steps": e2e_steps, "what": "per step: all levels' state host->device (pinned), one step with its "
+                                       "diagnostics read back, all levels' evolved state device->host (pinned)"}
 
     # ---- per-kernel device time (eager launches bracketed by CUDA events)
     sim.profile(True)
-    prof_steps = max(2, min(args.steps, 10))
+    prof_steps = max(2, min(args.steps, 5))
     for _ in range(prof_steps):
-        one_step(graph=False)
+        sim.step_constraints(cfg.dt, 1, use_graph=False)
     rep = sim.profile_report()
     sim.profile(False)
     kern = {k: v for k, v in rep.items()}
-    dom = max((k for k in kern if k in ALG_FLOPS), key=lambda k: kern[k][0])
+    dom = max((k for k in kern if k in METHOD_FLOPS), key=lambda k: kern[k][0])
     tot_ms, n_launch, n_cells = kern[dom]
     avg_s = tot_ms * 1e-3 / n_launch
     units_per_launch = n_cells / n_launch
-    if dom == "k_flux_x":
-        units_per_launch = n_cells / n_launch * 1.0   # faces ~ cells of the region
-    achieved = ALG_FLOPS[dom] * units_per_launch / avg_s / 1e12
+    achieved = METHOD_FLOPS[dom] * units_per_launch / avg_s / 1e12
     peak = fp64_peak()
-    traffic = read_traffic().get(dom)
+    traffic = read_traffic(cfg.name).get(dom)
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if peak else None,
                 "traffic": (traffic[0] / traffic[1] * units_per_launch) if traffic else None,
-                "peak_source": "FP64 FMA probe measured in this run (nominal %.2f TFLOP/s)" % NOMINAL_FP64_TFLOPS,
-                "alg_flops_per_unit": ALG_FLOPS[dom], "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "FP64 FMA probe measured in this run (nominal %.2f TFLOP/s); of measured"
+                               % NOMINAL_FP64_TFLOPS,
+                "method_flops_per_unit": METHOD_FLOPS[dom], "avg_launch_ms": avg_s * 1e3,
                 "units_per_launch": units_per_launch,
                 "kernel_share": {k: round(v[0] / sum(x[0] for x in kern.values()), 4) for k, v in
-                                 sorted(kern.items(), key=lambda kv: -kv[1][0])[:8]}}
-    # the whole step: the algorithmic FP64 work of every counted kernel over the device time of
+                                 sorted(kern.items(), key=lambda kv: -kv[1][0])[:10]},
+                "kernel_frac": {k: round(METHOD_FLOPS[k] * v[2] / (v[0] * 1e-3) / 1e12 / peak, 3)
+                                for k, v in kern.items() if k in METHOD_FLOPS and peak}}
+    # the whole step: the method's FP64 work of every counted kernel over the device time of
     # every kernel of the profiled steps (ghost fill, restriction and diagnostics count as time only)
-    path_flops = sum(ALG_FLOPS[k] * v[2] for k, v in kern.items() if k in ALG_FLOPS)
+    path_flops = sum(METHOD_FLOPS[k] * v[2] for k, v in kern.items() if k in METHOD_FLOPS)
     path_s = sum(v[0] for v in kern.values()) * 1e-3
     roofline["path"] = {"achieved": path_flops / path_s / 1e12, "unit": "TFLOP/s",
                         "frac": (path_flops / path_s / 1e12 / peak) if peak else None,
-                        "kernels": sorted(k for k in kern if k in ALG_FLOPS)}
+                        "kernels": sorted(k for k in kern if k in METHOD_FLOPS)}
 
-    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
+    # ---- each output's error against the FP64 oracle after one step from the initial data
+    if rank == 0 and ws == 1 and not args.no_errors:
+        e64, emx = errors_vs_oracle(cfg, datas, [sim, msim], steps=1)
+        mixed["err_vs_oracle"] = emx
+        mixed["fp64_err_vs_oracle"] = {"rho_l1_rel": e64["rho_l1_rel"],
+                                       "max_group_rel": max(e64["max_group_rel"].values())}
+    sim.close()
+    msim.close()
+
+    # ---- the other workloads, beside the headline
+    extra = {}
+    if not args.no_extra:
+        c2, d2 = workload("tov_stable_3x256")
+        s2, a2, m2, b2 = pair_forms(c2, d2, args, dist, ws, 0, 0, args.steps)
+        extra["tov_stable_3x256"] = {"config": describe(c2), "fp64": strip(a2), "mixed": strip(b2)}
+        s2.close()
+        m2.close()
+        del d2
+    if not args.no_large:
+        c5, d5 = workload("large_7x1024")
+        s5, a5, m5, b5 = pair_forms(c5, d5, args, dist, ws, 0, 0, args.large_steps)
+        s5.close()
+        m5.close()
+        del d5
+        extra["large_7x1024"] = {"config": describe(c5), "fp64": strip(a5), "mixed": strip(b5)}
+    batch = None
+    if not args.no_batch:
+        batch = run_batch(args, dist, ws)
+
+    # ---- CPU oracle on a bounded sample of the headline workload (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle as O
@@ -518,31 +630,26 @@ def run_native(args, dist, rank, ws, local):
         O.set_threads(0)
         cores = O.get_threads()
         oracle_sample(cfg, datas, 1)              # warm the thread pool
-        c, t = oracle_sample(cfg, datas, 3)
+        c, t = oracle_sample(cfg, datas, full_step=True)
         cpu = {"value": c / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "one SSP-RK3 step (3 x ghost fill + stage) of the whole %s hierarchy, OpenMP over %d "
-                         "threads" % (cfg.name, cores),
-               "single_thread_value": c1 / t1}
-        if not args.no_errors:
-            # each output's error against the FP64 oracle after one step from the initial data
-            e64, emx = errors_vs_oracle(cfg, datas, [sim, msim], steps=1)
-            mixed["err_vs_oracle"] = emx
-            mixed["fp64_err_vs_oracle"] = {"rho_l1_rel": e64["rho_l1_rel"],
-                                           "max_group_rel": max(e64["max_group_rel"].values())}
+               "sample": "one whole %s step (%d stages with ghost fill, restriction and reflux) of the %s "
+                         "hierarchy, OpenMP over %d threads" % ("RK4" if cfg.rk == 0 else "SSP-RK3", cfg.n_stages,
+                                                                 cfg.name, cores),
+               "single_thread_value": c1 / t1, "single_thread_sample": "one RK stage of the whole hierarchy"}
 
     if rank == 0:
+        conf = describe(cfg)
+        conf.update({"parallelism": "replicas" if ws > 1 else "single", "l2": "working set > L2 (no flush)",
+                     "cuda_graph": True, "diagnostics_every_step": r64["diagnostics_in_step"]})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": cfg.name, "levels": cfg.n_levels, "cells_per_level": [cfg.nx, cfg.nz],
-                           "finest_dx": cfg.dx(cfg.n_levels - 1), "integrator": "SSP-RK3" if cfg.rk else "RK4",
-                           "stages_per_step": cfg.n_stages, "cell_updates_per_step": cells_per_step,
-                           "parallelism": "replicas" if ws > 1 else "single",
-                           "l2": "working set > L2 (no flush)", "cuda_graph": True},
-                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "mixed": mixed, "batch": batch, "tuning": tuning,
-                "diag": {"H_L2": diag[0], "Mb": diag[4], "rho_max": diag[6], "Mb_drift": (diag[4] - diag0[4]) / diag0[4]}}
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": conf,
+                "e2e": e2e, "gpu_launches": r64["gpu_launches"], "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": r64["clocks"], "repeats": r64.get("repeats"), "tuning": r64["tuning"], "mixed": mixed,
+                "extra": extra, "batch": batch}
+        if diag is not None and r64["_diag0"] is not None:
+            d0 = r64["_diag0"]
+            line["diag"] = {"H_L2": diag[0], "Mb": diag[4], "rho_max": diag[6], "Mb_drift": (diag[4] - d0[4]) / d0[4]}
         print(json.dumps(line), flush=True)
 
 
@@ -552,11 +659,16 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="tov_stable_3x256")
+    ap.add_argument("--workload", default="migration_5x512", choices=WORKLOADS)
+    ap.add_argument("--repeats", type=int, default=5, help="further timed regions of the headline (median)")
+    ap.add_argument("--repeat-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-errors", action="store_true", help="skip the per-output error report against the oracle")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default launch shapes)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
+    ap.add_argument("--no-extra", action="store_true", help="skip the stable-star workload")
+    ap.add_argument("--no-large", action="store_true", help="skip the 7 x 1024^2 workload")
+    ap.add_argument("--large-steps", type=int, default=6)
     ap.add_argument("--batch-stars", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned recovery seed")
     ap.add_argument("--batch-steps", type=int, default=5)

@@ -187,6 +187,16 @@ sacra_status sacra_step_constraints(sacra_ctx *c, double dt, int n_steps, int us
    the padded plane. */
 sacra_status sacra_read_state(sacra_ctx *c, int level, int which, int field, double *host_out, size_t n);
 
+/* Copy all n_fields = 30 padded planes of one level (metric + conserved,
+   which = SACRA_STATE_STEP, SACRA_STATE_STAGE or SACRA_RHS) to HOST memory:
+   host_planes holds n_fields * pz * px doubles, packed plane after plane in
+   field order, the layout sacra_set_initial_data(kind = SACRA_RAW) takes, so
+   the pair saves and restores a level (e.g. a checkpoint).  One pitched
+   device-to-host copy on the context's stream; waits for it.  Pinned host
+   memory lets the copy run at the link's rate.  Errors: SACRA_ERR_ARG for a
+   bad level, which, n_fields or a NULL buffer. */
+sacra_status sacra_read_level(sacra_ctx *c, int level, int which, double *host_planes, int n_fields);
+
 /* Diagnostics of the current state (a stage-0 ghost fill is done first). */
 sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out);
 
@@ -220,9 +230,15 @@ sacra_status sacra_profile_get(sacra_ctx *c, int idx, char *name, size_t name_le
    cuda_stream.  px*pz must not exceed SACRA_NOALLOC_MAX_PLANE (up to 256 x 256
    interior cells), else SACRA_ERR_ARG.  The face-flux scratch is one
    file-scope device array per GPU (about 5.9 MB, held until the process
-   exits); its device address is looked up on the first call on each device,
-   so that first call should come before any stream capture.  Every call
-   shares the array: calls that overlap on the GPU race (serialize them). */
+   exits); its device address is looked up on every call (no allocation),
+   and the first call on a device loads the library's device code, so make
+   that first call before any stream capture.  Every call shares the array:
+   calls that overlap on the GPU race (serialize them).  precision may carry
+   SACRA_MIXED_FLUX / SACRA_MIXED_SOURCES (the FP32 flux and source kernels).
+   The HLLC -> TVDLF fallback count is not reported by this entry point.
+   Returns SACRA_ERR_CUDA without launching anything if the calling thread
+   already holds an unread CUDA error (left by earlier work), and
+   SACRA_ERR_CUDA if a launch fails. */
 #define SACRA_NOALLOC_MAX_PLANE 73984
 sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level, const double *state, const double *prims,
                                      double *rhs_out, void *cuda_stream);

@@ -798,6 +798,7 @@ void init_star_levels(Star &st, char *base) {
     L.us = dp; dp += NST * P;
     L.ka = dp; dp += NST * P;
     L.rhs = dp; dp += NST * P;
+    L.rhsq = L.rhs + (size_t)fQD * P;
     L.prim = dp; dp += NPRIM * P;
     L.fx = dp; dp += NCONS * P;
     L.fz = dp; dp += NCONS * P;
@@ -960,6 +961,22 @@ sacra_status set_initial_data(Engine &e, int star, int level, int kind, const do
   st.have_data[level] = true;
   for (int l = 0; l < st.prm.n_levels; ++l) st.have_old[l] = false;   // no earlier time slice of the new data
   return cuda_check(e, "set_initial_data");
+}
+
+// all 30 padded state planes of one level to packed host planes (one pitched copy)
+sacra_status read_level(Engine &e, int star, int level, int which, double *host, int n_fields) {
+  if (star < 0 || star >= (int)e.stars.size()) return fail(e, SACRA_ERR_ARG, "bad star");
+  Star &st = e.stars[star];
+  if (level < 0 || level >= st.prm.n_levels || !host) return fail(e, SACRA_ERR_ARG, "bad level or buffer");
+  if (n_fields != NST) return fail(e, SACRA_ERR_ARG, "n_fields must be 30");
+  if (which != SACRA_STATE_STEP && which != SACRA_STATE_STAGE && which != SACRA_RHS)
+    return fail(e, SACRA_ERR_ARG, "which must be a state or right-hand-side set");
+  const Lev &L = st.lv[level];
+  const size_t np = (size_t)L.px * L.pz;
+  const double *src = which == SACRA_STATE_STEP ? L.un : (which == SACRA_STATE_STAGE ? L.us : L.rhs);
+  cudaMemcpy2DAsync(host, np * 8, src, L.P * 8, np * 8, NST, cudaMemcpyDeviceToHost, e.stream);
+  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "read_level");
+  return cuda_check(e, "read_level");
 }
 
 sacra_status read_diag(Engine &e, sacra_diag *out);
@@ -1277,6 +1294,11 @@ sacra_status sacra_step_constraints(sacra_ctx *c, double dt, int n_steps, int us
 sacra_status sacra_read_state(sacra_ctx *c, int level, int which, int field, double *host, size_t n) {
   if (!c) return SACRA_ERR_ARG;
   return read_state(c->e, 0, level, which, field, host, n);
+}
+
+sacra_status sacra_read_level(sacra_ctx *c, int level, int which, double *host_planes, int n_fields) {
+  if (!c) return SACRA_ERR_ARG;
+  return read_level(c->e, 0, level, which, host_planes, n_fields);
 }
 
 sacra_status sacra_constraints(sacra_ctx *c, sacra_diag *out) {

@@ -132,6 +132,7 @@ struct Lev {
   LevF f;
   size_t P;
   double *un, *us, *ka, *rhs;   // NST planes each
+  double *rhsq;                 // NCONS planes of the hydro right-hand side (d_t q_D .. d_t q_E)
   double *prim;                 // NPRIM planes
   int *status;
   double *fx, *fz;              // NCONS planes of face fluxes (area-weighted)

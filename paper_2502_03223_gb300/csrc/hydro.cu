@@ -343,11 +343,12 @@ __device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p,
                          + T(2) * (gi.xy * Kd.xy + gi.xz * Kd.xz + gi.yz * Kd.yz));
   const T KS = rhw2 * s3quad(Kd, vu, vu) + Pp * trK;
   const T sE = iW3 * (al * KS - rhw2 * (vu[0] * dal[0] + vu[2] * dal[1]));
-  L.rhs[(size_t)fQD * P + id] = -div[0];
-  L.rhs[(size_t)fQSX * P + id] = to_f64<T>(src[0] + geo) - div[1];
-  L.rhs[(size_t)fQSY * P + id] = -div[2];
-  L.rhs[(size_t)fQSZ * P + id] = to_f64<T>(src[1]) - div[3];
-  L.rhs[(size_t)fQE * P + id] = to_f64<T>(sE) - div[4];
+  double *rq = L.rhsq + id;     // planes d_t q_D, q_Sx, q_Sy, q_Sz, q_E
+  rq[0] = -div[0];
+  rq[P] = to_f64<T>(src[0] + geo) - div[1];
+  rq[2 * P] = -div[2];
+  rq[3 * P] = to_f64<T>(src[1]) - div[3];
+  rq[4 * P] = to_f64<T>(sE) - div[4];
 }
 
 template <typename T>

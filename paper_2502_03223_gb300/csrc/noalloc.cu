@@ -20,11 +20,10 @@ constexpr size_t kMaxPlane = SACRA_NOALLOC_MAX_PLANE;   // padded plane of at mo
 constexpr size_t kScratchDoubles = 2 * NCONS * kMaxPlane + 32;   // x and z face fluxes + a counter
 
 // Shared by every call on a device and kept between calls; every GPU that
-// loads the library holds it (about 5.9 MB) until the process exits.
+// loads the library holds it (about 5.9 MB) until the process exits.  The
+// last word counts HLLC -> TVDLF fallbacks; this entry point does not report
+// it (the kernels need somewhere to count).
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
-
-constexpr int kMaxDevices = 64;
-double *g_scratch_addr[kMaxDevices] = {nullptr};
 
 }  // namespace
 
@@ -37,27 +36,26 @@ extern "C" sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level
   if (!(p->dx0 > 0) || !(p->dz0 > 0) || !(p->Gamma_th > 1.0)) return SACRA_ERR_ARG;
   if (p->n_pieces > 1) return SACRA_ERR_ARG;          // the piece table needs the context's device memory
   if (p->eos_adiabatic && !(p->K > 0.0)) return SACRA_ERR_ARG;
+  if (p->precision & ~SACRA_MIXED) return SACRA_ERR_ARG;
   const size_t px = (size_t)p->nx + 2 * GH, pz = (size_t)p->nz + 2 * GH;
   if (px * pz > kMaxPlane) return SACRA_ERR_ARG;    // beyond the static scratch
 
-  // set-up, once per device and with that device current: the device address
-  // of the static array (its host-side name is only a stand-in)
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  // An error the calling thread left unread belongs to earlier work: report
+  // it without clearing it or launching anything, so that the check after
+  // the launches below sees this call's launches only.
+  if (cudaPeekAtLastError() != cudaSuccess) return SACRA_ERR_CUDA;
+
+  // The device address of the static array on the current device (its
+  // host-side name is only a stand-in).  Looked up on every call: the lookup
+  // allocates nothing, and a context torn down and created again (after
+  // cudaDeviceReset, say) reloads the module at another address.  The first
+  // call on a device loads the module, so make it before any stream capture.
+  double *scratch = nullptr;
+  if (cudaGetSymbolAddress((void **)&scratch, g_scratch) != cudaSuccess || !scratch) {
     cudaGetLastError();
     return SACRA_ERR_CUDA;
   }
-  if (!g_scratch_addr[dev]) {
-    double *addr = nullptr;
-    if (cudaGetSymbolAddress((void **)&addr, g_scratch) != cudaSuccess || !addr) {
-      cudaGetLastError();
-      return SACRA_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = addr;
-  }
-  double *scratch = g_scratch_addr[dev];
 
-  if (p->precision & ~SACRA_MIXED) return SACRA_ERR_ARG;
   DevParams d;
   fill_dev_params(p, &d);
 
@@ -71,7 +69,7 @@ extern "C" sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level
   L.prim = const_cast<double *>(prims);
   L.fx = scratch;
   L.fz = scratch + NCONS * P;
-  L.rhs = rhs_out - (size_t)fQD * P;       // the kernels write planes fQD..fQE of rhs
+  L.rhsq = rhs_out;                        // the hydro kernels write planes d_t q_D .. d_t q_E here
   L.nfb = reinterpret_cast<unsigned long long *>(scratch + 2 * NCONS * kMaxPlane);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // every face a divergence reads is written first, so the scratch needs no clearing

@@ -25,8 +25,8 @@ FILL, RESTRICT_REFLUX = 0, 1
 STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
 
 EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
-           "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_constraints",
-           "sacra_sync", "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_tune",
+           "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_read_level",
+           "sacra_constraints", "sacra_sync", "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_tune",
            "sacra_get_tuning", "sacra_destroy", "sacra_last_error",
            "sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
            "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.sacra_step.argtypes = [vp, C.c_double, C.c_int, C.c_int]
     L.sacra_step_constraints.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.POINTER(SacraDiag)]
     L.sacra_read_state.argtypes = [vp, C.c_int, C.c_int, C.c_int, dp, C.c_size_t]
+    L.sacra_read_level.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int]
     L.sacra_constraints.argtypes = [vp, C.POINTER(SacraDiag)]
     L.sacra_sync.argtypes = [vp]
     L.sacra_launch_count.argtypes = [vp]
@@ -135,8 +136,8 @@ def load(path: str = LIB_PATH):
                  "sacra_batch_sync", "sacra_batch_profile", "sacra_batch_profile_get"):
         getattr(L, name).restype = C.c_int
     for name in ("sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
-                 "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_constraints",
-                 "sacra_sync"):
+                 "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_read_level",
+                 "sacra_constraints", "sacra_sync"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -254,6 +255,14 @@ class Sacra:
         self._chk(self._L.sacra_read_state(self._c, level, which, field, out.ctypes.data_as(C.POINTER(C.c_double)), n),
                   "read_state")
         return out.reshape((self.pz, self.px) if padded else (self.cfg.nz, self.cfg.nx))
+
+    def read_level(self, level, out, which=STATE_STEP):
+        """All 30 padded state planes of `level` into `out` (a contiguous
+        float64 array of 30 * pz * px elements, e.g. pinned torch memory as
+        numpy), the layout set_initial_data(RAW) takes."""
+        assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"] and out.size == 30 * self.px * self.pz
+        self._chk(self._L.sacra_read_level(self._c, level, which, out.ctypes.data, 30), "read_level")
+        return out
 
     def constraints(self):
         d = SacraDiag()

@@ -18,9 +18,14 @@ def built():
     B.build()
 
 
-def test_noalloc_hydro_rhs_matches_rk_stage():
+@pytest.mark.parametrize("precision", [S.FP64, S.MIXED_FLUX | S.MIXED_SOURCES], ids=["fp64", "mixed_hydro"])
+def test_noalloc_hydro_rhs_matches_rk_stage(precision):
+    """Same rates as the hydro part of sacra_rk_stage run with the same
+    precision bits (the FP32 flux and source kernels in the mixed case)."""
+    import dataclasses
     import torch
     cfg, tov = W.tov_config("noalloc", rho_c=1.28e-3, n_levels=1, N=64, dx_fine=0.5, rk=0)
+    cfg = dataclasses.replace(cfg, precision=precision)
     d = W.tov_level_data(cfg, tov, 0)
     X, Z = W.cell_centres(cfg, 0)
     bump = np.exp(-((X - 4.0) ** 2 + (Z - 3.0) ** 2) / 4.0)
@@ -50,7 +55,7 @@ def test_noalloc_hydro_rhs_matches_rk_stage():
             scale = max(float(np.max(np.abs(ref[[0, 1, 3, 4]][:, G:G + cfg.nz, G:G + cfg.nx]))), 1e-300)
             if v == 2:
                 scale *= cfg.nx * cfg.dx0
-            assert np.all(np.abs(a - b) <= 1e-11 * np.maximum(np.abs(b), scale)), (call, v)
+            assert np.all(np.abs(a - b) <= 1e-11 * np.maximum(np.abs(b), scale)), (precision, call, v)
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
