@@ -596,7 +596,8 @@ def run_native(args, dist, rank, ws, local):
         e64, emx = errors_vs_oracle(cfg, datas, [sim, msim], steps=1)
         mixed["err_vs_oracle"] = emx
         mixed["fp64_err_vs_oracle"] = {"rho_l1_rel": e64["rho_l1_rel"],
-                                       "max_group_rel": max(e64["max_group_rel"].values())}
+                                       "max_group_rel": max(e64["max_group_rel"].values()),
+                                       "per_field": e64["max_group_rel"]}
     sim.close()
     msim.close()
 

@@ -145,6 +145,7 @@ def lib():
             L.orc_fallbacks.argtypes = [C.c_void_p]
             L.orc_derivs_batch.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                            _dp, _dp, _dp]
+            L.orc_time_interp_probe.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, _dp, _dp]
             L.orc_stencil_init.argtypes = []
             L.orc_fd_weights.argtypes = [C.c_int, _dp, C.c_double, C.c_int, _dp]
             L.orc_lagrange.argtypes = [C.c_int, _dp, C.c_double, _dp]
@@ -394,6 +395,19 @@ class Oracle:
 
     def fallbacks(self):
         return self._L.orc_fallbacks(self._c)
+
+    def time_interp(self, level, theta, have_old, old, now, new, p_old, p_now, p_new):
+        """The parent data a sub-cycled child sees at t^n + theta (t^{n+1} - t^n)
+        from the level's time slices (metric planes [25, pz, px] and primitive
+        planes [6, pz, px] at t^{n-1}, t^n, t^{n+1}).  Returns (metric, prims)."""
+        n = self.px * self.pz
+        s = np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64).ravel()
+                                                 for a in (old, now, new, p_old, p_now, p_new)]))
+        assert s.size == 3 * (NMET + 6) * n
+        out = np.zeros((NMET + 6) * n)
+        self._L.orc_time_interp_probe(self._c, level, float(theta), int(have_old), _ptr(s), _ptr(out))
+        out = out.reshape(NMET + 6, self.pz, self.px)
+        return out[:NMET], out[NMET:]
 
     @property
     def n_stages(self):

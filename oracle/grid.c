@@ -927,3 +927,29 @@ void orc_derivs_batch(orc_ctx *c, int l, int n, const int *js, const int *ks, do
   if (cyl)
     for (int f = 0; f < O_NMET; ++f) { free(dy[f]); free(dyy[f]); }
 }
+
+/* The parent data a sub-cycled child sees at time t^n + theta (t^{n+1} - t^n)
+   (time_interp), for tests: slices packs the level's padded planes in the
+   order 25 metric at t^{n-1}, t^n, t^{n+1}, then 6 primitives at t^{n-1},
+   t^n, t^{n+1}; out receives the 25 interpolated metric planes and the 6
+   interpolated primitive planes.  have_old = 0: no t^{n-1} slice yet. */
+void orc_time_interp_probe(orc_ctx *c, int l, double theta, int have_old, const double *slices, double *out) {
+  orc_level *P = &c->lv[l];
+  size_t n = (size_t)P->px * P->pz;
+  const double *s = slices;
+  for (int f = 0; f < O_NMET; ++f) memcpy(P->uold[f], s + (size_t)f * n, n * sizeof(double));
+  s += (size_t)O_NMET * n;
+  for (int f = 0; f < O_NMET; ++f) memcpy(P->us[f], s + (size_t)f * n, n * sizeof(double));
+  s += (size_t)O_NMET * n;
+  for (int f = 0; f < O_NMET; ++f) memcpy(P->un[f], s + (size_t)f * n, n * sizeof(double));
+  s += (size_t)O_NMET * n;
+  for (int f = 0; f < O_NPRIM; ++f) memcpy(P->pold[f], s + (size_t)f * n, n * sizeof(double));
+  s += (size_t)O_NPRIM * n;
+  for (int f = 0; f < O_NPRIM; ++f) memcpy(P->pnow[f], s + (size_t)f * n, n * sizeof(double));
+  s += (size_t)O_NPRIM * n;
+  for (int f = 0; f < O_NPRIM; ++f) memcpy(P->prim[f], s + (size_t)f * n, n * sizeof(double));
+  P->have_old = have_old;
+  time_interp(c, l, theta);
+  for (int f = 0; f < O_NMET; ++f) memcpy(out + (size_t)f * n, P->ut[f], n * sizeof(double));
+  for (int f = 0; f < O_NPRIM; ++f) memcpy(out + (size_t)(O_NMET + f) * n, P->pt[f], n * sizeof(double));
+}
