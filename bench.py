@@ -497,6 +497,8 @@ def pair_forms(cfg, datas, args, dist, ws, repeats, repeat_steps, steps):
     (fp64 sim, fp64 result, mixed sim, mixed result)."""
     from paper_2502_03223_gb300 import sacra2d as S
     sim, r64 = bench_context(cfg, datas, args, dist, ws, repeats, repeat_steps, steps=steps)
+    if args.fp64_only:
+        return sim, r64, None, None
     mcfg = dataclasses.replace(cfg, precision=S.MIXED)
     msim, rmx = bench_context(mcfg, datas, args, dist, ws, repeats, repeat_steps, steps=steps)
     rmx["speedup_vs_fp64"] = rmx["value"] / r64["value"]
@@ -522,8 +524,8 @@ def run_native(args, dist, rank, ws, local):
     sim, r64, msim, rmx = pair_forms(cfg, datas, args, dist, ws, reps, rsteps, args.steps)
     value, ms_step = r64["value"], r64["ms_per_step"]
     diag = sim.constraints() if r64["diagnostics_in_step"] else None
-    mixed = strip(rmx)
-    if r64["_diag_in"] is not None and rmx["_diag_in"] is not None:
+    mixed = strip(rmx) if rmx is not None else None
+    if rmx is not None and r64["_diag_in"] is not None and rmx["_diag_in"] is not None:
         # ||H|| of the same starting state of the last timed step, formed in the step
         # (mixed: from the FP32 Ricci scalar of its pointwise pass)
         h64, hmx = r64["_diag_in"][0], rmx["_diag_in"][0]
@@ -592,31 +594,34 @@ def run_native(args, dist, rank, ws, local):
                         "kernels": sorted(k for k in kern if k in METHOD_FLOPS)}
 
     # ---- each output's error against the FP64 oracle after one step from the initial data
-    if rank == 0 and ws == 1 and not args.no_errors:
+    if rank == 0 and ws == 1 and not args.no_errors and msim is not None:
         e64, emx = errors_vs_oracle(cfg, datas, [sim, msim], steps=1)
         mixed["err_vs_oracle"] = emx
         mixed["fp64_err_vs_oracle"] = {"rho_l1_rel": e64["rho_l1_rel"],
                                        "max_group_rel": max(e64["max_group_rel"].values()),
                                        "per_field": e64["max_group_rel"]}
     sim.close()
-    msim.close()
+    if msim is not None:
+        msim.close()
 
     # ---- the other workloads, beside the headline
     extra = {}
     if not args.no_extra:
         c2, d2 = workload("tov_stable_3x256")
         s2, a2, m2, b2 = pair_forms(c2, d2, args, dist, ws, 0, 0, args.steps)
-        extra["tov_stable_3x256"] = {"config": describe(c2), "fp64": strip(a2), "mixed": strip(b2)}
+        extra["tov_stable_3x256"] = {"config": describe(c2), "fp64": strip(a2), "mixed": strip(b2) if b2 else None}
         s2.close()
-        m2.close()
+        if m2 is not None:
+            m2.close()
         del d2
     if not args.no_large:
         c5, d5 = workload("large_7x1024")
         s5, a5, m5, b5 = pair_forms(c5, d5, args, dist, ws, 0, 0, args.large_steps)
         s5.close()
-        m5.close()
+        if m5 is not None:
+            m5.close()
         del d5
-        extra["large_7x1024"] = {"config": describe(c5), "fp64": strip(a5), "mixed": strip(b5)}
+        extra["large_7x1024"] = {"config": describe(c5), "fp64": strip(a5), "mixed": strip(b5) if b5 else None}
     batch = None
     if not args.no_batch:
         batch = run_batch(args, dist, ws)
@@ -669,6 +674,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
     ap.add_argument("--no-extra", action="store_true", help="skip the stable-star workload")
     ap.add_argument("--no-large", action="store_true", help="skip the 7 x 1024^2 workload")
+    ap.add_argument("--fp64-only", action="store_true", help="time the FP64 form only (no mixed contexts)")
     ap.add_argument("--large-steps", type=int, default=6)
     ap.add_argument("--batch-stars", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned recovery seed")

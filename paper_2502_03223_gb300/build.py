@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["hydro.cu", "z4c.cu", "grid.cu", "capi.cu", "noalloc.cu", "mlp.cu"]
-HEADERS = ["common.cuh", "z4c.cuh", "kernels.h"]
+HEADERS = ["common.cuh", "z4c.cuh", "kernels.h", "fixed.cuh"]
 LIB = os.path.join(BUILD, "libsacra2d.so")
 PROBE = os.path.join(BUILD, "libsacra_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

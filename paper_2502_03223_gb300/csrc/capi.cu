@@ -207,7 +207,7 @@ struct Engine {
   cudaStream_t stream = nullptr;
   char *arena = nullptr;
   bool own_arena = false;
-  double *tab = nullptr, *dout = nullptr;
+  double *tab = nullptr, *tabw = nullptr, *dout = nullptr;
   unsigned long long *nfb = nullptr;
   int sms = 1;
   // plan of the batched launches
@@ -446,7 +446,7 @@ void launch_kind(Engine &e, int kind, const Batch &b, int s, double dt) {
     case B_FLUX_X: launch_b_flux_x(b, e.dp, e.stream); break;
     case B_FLUX_Z: launch_b_flux_z(b, e.dp, e.stream); break;
     case B_HYDRO: launch_b_hydro_div(b, e.dp, e.stream); break;
-    case B_CARTOON: launch_b_cartoon(b, e.dp, e.tab, kTabStride, e.stream); break;
+    case B_CARTOON: launch_b_cartoon(b, e.dp, e.tab, kTabStride, e.tabw, e.stream); break;
     case B_DERIVS: launch_b_z4c_derivs(b, e.dp, e.stream); break;
     case B_POINT: launch_b_z4c_point(b, e.dp, e.stream, s == 0 && e.stage0_diag ? 1 : 0); break;
     case B_RK: launch_b_rk_update(b, e.dp, s, dt, e.stream); break;
@@ -836,7 +836,36 @@ void upload_tables(Engine &e, int max_nx) {
       t[10] = m / vp;
       t[11] = -(double)(m * m) / (vp * (x + vp));   // cos phi - 1 without cancellation
     }
+  // combined weights of the FP64 kernel (kernels.h): with t_m the weights above, c_m = cos,
+  // s_m = sin, w1 = (45, -9, 1), w2 = (270, -27, 2):
+  //   Sd = sum_m 2 w2 t_m      (d_yy of a scalar, on u_n - u_0)
+  //   D1 = -2 sum_m w1 s_m t_m (d_y of v_x from v_y; d_y v_y = -(D1 . v_x))
+  //   E1 = -4 sum_m w1 c_m s_m t_m (d_y T_xx from T_xy; d_y T_xy = -E1 . (T_xx - T_yy) / 2)
+  //   C2 = sum_m 2 w2 c_m t_m, K2 = sum_m 2 w2 (c_m - 1) (d_yy of a vector component, T_xz, T_yz)
+  //   F = sum_m 2 w2 c_m^2 t_m, G = sum_m 2 w2 s_m^2 t_m, H = sum_m 2 w2 (c_m^2 - s_m^2) t_m,
+  //   Kb = sum_m 2 w2 s_m^2    (d_yy of T_xx, T_yy, T_xy)
+  std::vector<double> tw((size_t)nj * kCartoonW, 0.0);
+  const double w1[3] = {45.0, -9.0, 1.0}, w2[3] = {270.0, -27.0, 2.0};
+  for (int j = 1; j < nj; ++j) {
+    double *W = &tw[(size_t)j * kCartoonW];
+    for (int m = 0; m < 3; ++m) {
+      const double *t = &tab[(size_t)(j * 3 + m) * kTabStride];
+      const double c = t[9], sn = t[10], cm1 = t[11];
+      for (int n = 0; n < 9; ++n) {
+        W[n] += 2.0 * w2[m] * t[n];
+        W[9 + n] += -2.0 * w1[m] * sn * t[n];
+        W[18 + n] += -4.0 * w1[m] * c * sn * t[n];
+        W[27 + n] += 2.0 * w2[m] * c * t[n];
+        W[36 + n] += 2.0 * w2[m] * c * c * t[n];
+        W[45 + n] += 2.0 * w2[m] * sn * sn * t[n];
+        W[54 + n] += 2.0 * w2[m] * (c * c - sn * sn) * t[n];
+      }
+      W[63] += 2.0 * w2[m] * cm1;
+      W[64] += 2.0 * w2[m] * sn * sn;
+    }
+  }
   cudaMemcpyAsync(e.tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, e.stream);
+  cudaMemcpyAsync(e.tabw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, e.stream);
   GridWeights w;
   double n8[8];
   for (int n = 0; n < 8; ++n) n8[n] = n - 3;
@@ -856,7 +885,7 @@ size_t engine_bytes(const std::vector<sacra_params> &ps) {
     n += star_bytes(&p);
     max_nx = std::max(max_nx, p.nx);
   }
-  return n + round_up((size_t)(max_nx + 8) * 3 * kTabStride * 8, 256) + 256 /* dout */ + 256 /* nfb */ +
+  return n + round_up((size_t)(max_nx + 8) * (3 * kTabStride + kCartoonW) * 8, 256) + 256 /* dout */ + 256 /* nfb */ +
          plan_bytes(ps);
 }
 
@@ -910,7 +939,8 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
   e.ngroups = (int)e.group_first.size();
   e.dp.pwp = e.stars[0].dp.pwp;
   e.tab = (double *)p;
-  p += round_up((size_t)(max_nx + 8) * 3 * kTabStride * 8, 256);
+  e.tabw = e.tab + (size_t)(max_nx + 8) * 3 * kTabStride;
+  p += round_up((size_t)(max_nx + 8) * (3 * kTabStride + kCartoonW) * 8, 256);
   e.dout = (double *)p;
   p += 256;
   e.nfb = (unsigned long long *)p;
@@ -1084,7 +1114,7 @@ void enqueue_diag(Engine &e, Star &st, bool own_derivs) {
     const long long cells = (long long)lv.nx * lv.nz;
     double *ds = reinterpret_cast<double *>(st.ds[l]);
     if (own_derivs && st.prm.evolve_spacetime) {
-      run(e, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, st.dp, lv.un, e.tab, kTabStride, e.stream); });
+      run(e, K_CARTOON, (long long)(lv.nx + 7) * (lv.nz + 10), [&] { launch_cartoon(lv, st.dp, lv.un, e.tab, kTabStride, e.tabw, e.stream); });
       run(e, K_Z4C_DERIVS, cells, [&] { launch_z4c_derivs(lv, st.dp, lv.un, ds, lv.nx, lv.nz, e.stream); });
     }
     const int sl = slot;

@@ -59,7 +59,13 @@ enum BKind { B_FLUX_X = 0, B_FLUX_Z, B_HYDRO, B_CARTOON, B_DERIVS, B_POINT, B_RK
 void launch_b_flux_x(const Batch &b, const DevParams &p, cudaStream_t s);
 void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s);
 void launch_b_hydro_div(const Batch &b, const DevParams &p, cudaStream_t s);
-void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, cudaStream_t s);
+// FP64 cartoon kernel: per column j, the weights of each d_y / d_yy output on the nine
+// values x_{j-4..j+4} (interpolation at varpi_m, rotation by +-phi_m and the 6th-order
+// differences over the planes m = -3..3 folded together), dimensionless:
+//   [0, 9) Sd, [9, 18) D1, [18, 27) E1, [27, 36) C2, [36, 45) F, [45, 54) G, [54, 63) H, 63 K2, 64 Kb
+constexpr int kCartoonW = 68;
+void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, const double *tabw,
+                      cudaStream_t s);
 void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s);
 // store_rs: the pass also writes the Ricci scalar it forms (FP64, or the FP32
 // value widened) into the FP64 scratch plane z4c_ricci_plane()
@@ -77,7 +83,8 @@ void launch_prim2cons_all(const Lev &L, const DevParams &p, double *U, cudaStrea
 void launch_c2p_region(const Lev &L, const DevParams &p, double *U, int j0, int j1, int k0, int k1, cudaStream_t s,
                        int skip_corner = 0);
 
-void launch_cartoon(const Lev &L, const DevParams &p, const double *U, const double *tab, int tab_stride, cudaStream_t s);
+void launch_cartoon(const Lev &L, const DevParams &p, const double *U, const double *tab, int tab_stride,
+                    const double *tabw, cudaStream_t s);
 void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s);
 void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const double *DS, int jmax, int kmax,
                       cudaStream_t s);

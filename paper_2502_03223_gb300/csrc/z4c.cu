@@ -9,6 +9,7 @@
 
 #include "kernels.h"
 #include "z4c.cuh"
+#include "fixed.cuh"
 
 namespace sacra {
 
@@ -26,161 +27,116 @@ __device__ __forceinline__ double par_x(int f) {
   }
 }
 
-// field of cartoon slot a (kCartoonFields, compile-time form)
-__host__ __device__ constexpr int cartoon_field(int a) {
-  constexpr int f[20] = {fW, fAL, fHXX, fHXY, fHXZ, fHYY, fHYZ, fHZZ, fAXX, fAXY,
-                         fAXZ, fAYY, fAYZ, fBX, fBY, fBZ, fGX, fGY, fBBX, fBBY};
-  return f[a];
-}
-
 // x-parity of the cartoon fields in kCartoonFields order (compile-time form)
 __host__ __device__ constexpr float par_x_slot(int a) {
   return (a == 4 || a == 6 || a == 10 || a == 12 || a == 13 || a == 14 || a == 16 || a == 17 || a == 18 || a == 19)
              ? -1.0f : 1.0f;
 }
 
-// rotate interpolated base values v[20] (ordered as kCartoonFields) by phi
-__device__ __forceinline__ void rotate20(const double v[20], double c, double s, double o[20]) {
-  o[0] = v[0]; o[1] = v[1];
-  // tensor h: xx,xy,xz,yy,yz,zz at 2..7
-  o[2] = c * c * v[2] - 2.0 * c * s * v[3] + s * s * v[5];
-  o[3] = c * s * (v[2] - v[5]) + (c * c - s * s) * v[3];
-  o[4] = c * v[4] - s * v[6];
-  o[5] = s * s * v[2] + 2.0 * c * s * v[3] + c * c * v[5];
-  o[6] = s * v[4] + c * v[6];
-  o[7] = v[7];
-  // tensor At: xx,xy,xz,yy,yz at 8..12
-  o[8] = c * c * v[8] - 2.0 * c * s * v[9] + s * s * v[11];
-  o[9] = c * s * (v[8] - v[11]) + (c * c - s * s) * v[9];
-  o[10] = c * v[10] - s * v[12];
-  o[11] = s * s * v[8] + 2.0 * c * s * v[9] + c * c * v[11];
-  o[12] = s * v[10] + c * v[12];
-  // vectors beta (13..15), Gt (16,17), B (18,19)
-  o[13] = c * v[13] - s * v[14];
-  o[14] = s * v[13] + c * v[14];
-  o[15] = v[15];
-  o[16] = c * v[16] - s * v[17];
-  o[17] = s * v[16] + c * v[17];
-  o[18] = c * v[18] - s * v[19];
-  o[19] = s * v[18] + c * v[19];
-}
-
-// Planes y = +-m dy at (x_j, z_k): 9-point Lagrange in x at varpi, rotated by
-// +-phi (Sec. II.B.2); j <= 0 from the rotation by pi of (x_{1-j}, -+m dy).
-// d_y and d_yy by 6th-order central differences over m = -3..3 (dy = dx).
-// The fields are taken group by group (scalars, the h and At tensors, the
-// beta, Gt and B vectors): each group's three planes come from one pass over
-// its 9-point stencils, and only the group's components are live at a time.
-struct CartoonOut {
-  double *dy, *dyy;
-  size_t P;
-  int o;
-  double i1, i2;
-};
-
-// accumulate the d_y / d_yy sums of slot a from its +m / -m plane values
-__device__ __forceinline__ void cartoon_acc(int a, bool flip, double w1, double w2, double pp, double pm, double base,
-                                            double &d1, double &d2) {
-  const double pr = par_x_slot(a);
-  const double plus = flip ? pr * pm : pp;
-  const double minus = flip ? pr * pp : pm;
-  const double centre = flip ? pr * base : base;
-  d1 += w1 * (plus - minus);
-  d2 += w2 * ((plus - centre) + (minus - centre));
-}
-
-__device__ __forceinline__ void cartoon_store(const CartoonOut &c, int a, double d1, double d2) {
-  const int f = cartoon_field(a);
-  if (f != fHZZ && f != fBZ && a >= 2) c.dy[(size_t)f * c.P + c.o] = d1 * c.i1;
-  if (a <= 7 || (a >= 13 && a <= 15)) c.dyy[(size_t)f * c.P + c.o] = d2 * c.i2;
-}
-
-__device__ __forceinline__ void cartoon_f64_cell(const Lev &L, const double *__restrict__ U, const double *__restrict__ tab,
-                                                     int tab_stride, int j, int k) {
+// d_y and d_yy at (x_j, z_k) by the cartoon method (Sec. II.B.2): the planes
+// y = +-m dy (m = 1..3, dy = dx) hold the 9-point Lagrange interpolant in x at
+// varpi_m = sqrt(x_j^2 + (m dy)^2), rotated by +-phi_m, and d_y, d_yy are the
+// 6th-order central differences over the seven planes.  All three steps are
+// linear in the nine values u(x_{j-4..j+4}), so each output is one 9-point
+// sum with per-column weights (kernels.h, built on the host from the same
+// interpolation weights): a scalar's d_yy; a vector's d_y from its other
+// component and its d_yy; a symmetric tensor's d_y from the rotated
+// components and its d_yy from the pairs (xx, yy), xy, xz, yz.  Second
+// derivatives are taken on u_n - u_0 (exact zero on constants).  Columns
+// j <= 0 are the rotation by pi of column 1 - j: d_y there is -parity times
+// the value at 1 - j, d_yy parity times it.
+__device__ __forceinline__ void cartoon_f64_cell(const Lev &L, const double *__restrict__ U,
+                                                 const double *__restrict__ tabw, int j, int k) {
   if (j > L.nx + 4 || k > L.nz + 7) return;
   const bool flip = j <= 0;
   const int jj = flip ? 1 - j : j;
   const size_t P = L.P;
-  const int c0 = cid(L, jj, k);
-  const double *t0 = tab + (size_t)(jj * 3) * tab_stride;   // per m: 9 weights, cos, sin
-  CartoonOut co{L.dy, L.dyy, P, cid(L, j, k), L.i60x, L.i180x};
-  const double c1w[3] = {45.0, -9.0, 1.0}, c2w[3] = {270.0, -27.0, 2.0};
-  // the three planes of slot a: v[m] = base + sum_n t_m[n] (u[n] - base)
-  auto planes = [&](int a, double &base, double v[3]) {
-    const double *u = U + (size_t)cartoon_field(a) * P + c0 - 4;
-    base = u[4];
-    double s[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int n = 0; n < 9; ++n) {
-      const double d = u[n] - base;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) s[m] += t0[m * tab_stride + n] * d;
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) v[m] = base + s[m];
-  };
-  // scalars under the rotation: W, alpha, h_zz, beta^z
+  const int c0 = cid(L, jj, k) - 4;
+  const int o = cid(L, j, k);
+  const double *Wt = tabw + (size_t)jj * kCartoonW;
+  const double *Sd = Wt, *D1 = Wt + 9, *E1 = Wt + 18, *C2 = Wt + 27, *F = Wt + 36, *G = Wt + 45, *H = Wt + 54;
+  const double K2 = Wt[63], Kb = Wt[64];
+  const double i1 = L.i60x, i2 = L.i180x;
+  auto ld = [&](int f, int n) { return U[(size_t)f * P + c0 + n]; };
+  auto st1 = [&](int f, double v) { L.dy[(size_t)f * P + o] = (flip ? -par_x(f) * v : v) * i1; };
+  auto st2 = [&](int f, double v) { L.dyy[(size_t)f * P + o] = (flip ? par_x(f) * v : v) * i2; };
+  // scalars under the rotation: W, alpha, h_zz, beta^z (d_y = 0)
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int a = q == 0 ? 0 : (q == 1 ? 1 : (q == 2 ? 7 : 15));
-    double base, v[3], d1 = 0.0, d2 = 0.0;
-    planes(a, base, v);
+    const int f = q == 0 ? fW : (q == 1 ? fAL : (q == 2 ? fHZZ : fBZ));
+    const double u0 = ld(f, 4);
+    double s = 0.0;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) cartoon_acc(a, flip, c1w[m], c2w[m], v[m], v[m], base, d1, d2);
-    cartoon_store(co, a, d1, d2);
+    for (int n = 0; n < 9; ++n)
+      if (n != 4) s += Sd[n] * (ld(f, n) - u0);
+    st2(f, s);
   }
-  // vectors (x, y components): beta, Gt, B
+  // vectors (x, y components): beta (d_y, d_yy), Gt and B (d_y)
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const int a = q == 0 ? 13 : (q == 1 ? 16 : 18);
-    double bx, by, vx[3], vy[3];
-    planes(a, bx, vx);
-    planes(a + 1, by, vy);
-    double d1x = 0.0, d2x = 0.0, d1y = 0.0, d2y = 0.0;
+    const int fx_ = q == 0 ? fBX : (q == 1 ? fGX : fBBX), fy_ = fx_ + 1;
+    double sx = 0.0, sy = 0.0;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const double c = t0[m * tab_stride + 9], sn = t0[m * tab_stride + 10];
-      const double px = c * vx[m] - sn * vy[m], py = sn * vx[m] + c * vy[m];
-      const double mx = c * vx[m] - (-sn) * vy[m], my = (-sn) * vx[m] + c * vy[m];
-      cartoon_acc(a, flip, c1w[m], c2w[m], px, mx, bx, d1x, d2x);
-      cartoon_acc(a + 1, flip, c1w[m], c2w[m], py, my, by, d1y, d2y);
+    for (int n = 0; n < 9; ++n) {
+      sx += D1[n] * ld(fy_, n);
+      sy += D1[n] * ld(fx_, n);
     }
-    cartoon_store(co, a, d1x, d2x);
-    cartoon_store(co, a + 1, d1y, d2y);
+    st1(fx_, sx);
+    st1(fy_, -sy);
+    if (q == 0) {
+      const double x0 = ld(fx_, 4), y0 = ld(fy_, 4);
+      double ax = K2 * x0, ay = K2 * y0;
+#pragma unroll
+      for (int n = 0; n < 9; ++n)
+        if (n != 4) {
+          ax += C2[n] * (ld(fx_, n) - x0);
+          ay += C2[n] * (ld(fy_, n) - y0);
+        }
+      st2(fx_, ax);
+      st2(fy_, ay);
+    }
   }
-  // symmetric tensors h_ij (slots 2..6) and At_ij (8..12): xx, xy, xz, yy, yz
+  // symmetric tensors h_ij (d_y, d_yy) and At_ij (d_y): components xx, xy, xz, yy, yz
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const int a0 = q == 0 ? 2 : 8;
-    double b[5], v[5][3];
+    const int f0 = q == 0 ? fHXX : fAXX;
+    double exy = 0.0, exxyy = 0.0, dxz = 0.0, dyz = 0.0;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) planes(a0 + i, b[i], v[i]);
-    double d1[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, d2[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const double c = t0[m * tab_stride + 9];
-      double pp[5], pm[5];
-#pragma unroll
-      for (int sg = 0; sg < 2; ++sg) {
-        const double sn = sg == 0 ? t0[m * tab_stride + 10] : -t0[m * tab_stride + 10];
-        double *r = sg == 0 ? pp : pm;
-        r[0] = c * c * v[0][m] - 2.0 * c * sn * v[1][m] + sn * sn * v[3][m];
-        r[1] = c * sn * (v[0][m] - v[3][m]) + (c * c - sn * sn) * v[1][m];
-        r[2] = c * v[2][m] - sn * v[4][m];
-        r[3] = sn * sn * v[0][m] + 2.0 * c * sn * v[1][m] + c * c * v[3][m];
-        r[4] = sn * v[2][m] + c * v[4][m];
-      }
-#pragma unroll
-      for (int i = 0; i < 5; ++i) cartoon_acc(a0 + i, flip, c1w[m], c2w[m], pp[i], pm[i], b[i], d1[i], d2[i]);
+    for (int n = 0; n < 9; ++n) {
+      exy += E1[n] * ld(f0 + 1, n);
+      exxyy += E1[n] * (ld(f0, n) - ld(f0 + 3, n));
+      dxz += D1[n] * ld(f0 + 4, n);
+      dyz += D1[n] * ld(f0 + 2, n);
     }
+    st1(f0, exy);
+    st1(f0 + 3, -exy);
+    st1(f0 + 1, -0.5 * exxyy);
+    st1(f0 + 2, dxz);
+    st1(f0 + 4, -dyz);
+    if (q == 0) {
+      const double xx0 = ld(f0, 4), xy0 = ld(f0 + 1, 4), xz0 = ld(f0 + 2, 4), yy0 = ld(f0 + 3, 4), yz0 = ld(f0 + 4, 4);
+      double axx = Kb * (yy0 - xx0), ayy = Kb * (xx0 - yy0), axy = -2.0 * Kb * xy0, axz = K2 * xz0, ayz = K2 * yz0;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) cartoon_store(co, a0 + i, d1[i], d2[i]);
+      for (int n = 0; n < 9; ++n)
+        if (n != 4) {
+          const double dxx = ld(f0, n) - xx0, dyy = ld(f0 + 3, n) - yy0;
+          axx += F[n] * dxx + G[n] * dyy;
+          ayy += G[n] * dxx + F[n] * dyy;
+          axy += H[n] * (ld(f0 + 1, n) - xy0);
+          axz += C2[n] * (ld(f0 + 2, n) - xz0);
+          ayz += C2[n] * (ld(f0 + 4, n) - yz0);
+        }
+      st2(f0, axx);
+      st2(f0 + 1, axy);
+      st2(f0 + 2, axz);
+      st2(f0 + 3, ayy);
+      st2(f0 + 4, ayz);
+    }
   }
 }
 
-__global__ void __launch_bounds__(128) k_cartoon_f64(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
-                                                     int tab_stride) {
-  cartoon_f64_cell(L, U, tab, tab_stride, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
+__global__ void __launch_bounds__(128) k_cartoon_f64(Lev L, const double *__restrict__ U, const double *__restrict__ tabw) {
+  cartoon_f64_cell(L, U, tabw, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
 }
 
 // Mixed precision: the same planes in FP32, formed as differences from the
@@ -491,12 +447,24 @@ __device__ __forceinline__ void z4c_derivs_f32_tile(const Lev &L, const DevParam
   }
 }
 
-// FP64 derivative pass, one thread per cell: per field the differences
-// u(n) - u(0), n = -4..4, along x and z are formed once and shared by the
-// first and second derivatives, the lopsided advection and the Kreiss-Oliger
-// term (difference form: exact zero on constants).
+// FP64 derivative pass, one thread per cell.  Per field the seventeen stencil
+// values (nine along x, nine along z) go onto one fixed-point grid (fixed.cuh)
+// and every integer-weight sum is formed exactly in 64-bit integers: the
+// central first and second derivatives, the lopsided advection stencil (as
+// its odd and even parts A + sign(beta) B, both from the symmetric pairs), the
+// Kreiss-Oliger sum and the z-difference numerator that the neighbouring
+// columns use for d_xz.  Each result is converted and scaled once in FP64.
+// A field falls back to the FP64 difference form (u(n) - u(0), exact zero on
+// constants) where the fixed-point form does not apply: non-finite values,
+// values below 2^-895 (grid below the normal range), or a second-derivative
+// sum that could pass 2^63.
 __constant__ signed char kD1Of[NMET] = {0, 1, 2, 3, 4, 5, 6, -1, -1, -1, -1, -1, -1, 7, 8, 9, 10, 11, 12, 13, 14, 15, -1, -1, -1};
 __constant__ signed char kD2Of[NMET] = {0, 1, 2, 3, 4, 5, 6, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, 7, 8, 9, 10, -1, -1, -1};
+
+// the (unscaled) 6th-order z-difference numerator at column c in FP64
+__device__ __forceinline__ double zdiff_num(const double *c, int sz) {
+  return 45.0 * (c[sz] - c[-sz]) - 9.0 * (c[2 * sz] - c[-2 * sz]) + (c[3 * sz] - c[-3 * sz]);
+}
 
 template <typename T>
 __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
@@ -504,69 +472,89 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
                                                 double *sdz = nullptr, int j0 = 0) {
   static_assert(sizeof(T) == 8, "the FP32 form is z4c_derivs_f32_tile");
   // XCH (sdz given): the mixed derivative d_xz is the x-difference of the
-  // z-differences of the neighbouring columns, which the block exchanges
-  // through shared memory (row of blockDim.x + 6 columns per thread row);
-  // every thread of the block then runs the field loop (it has barriers)
+  // z-difference numerators of the neighbouring columns, which the block
+  // exchanges through shared memory (row of blockDim.x + 6 columns per thread
+  // row: each thread its own column, the three threads at either end of a
+  // row one halo column each); every thread of the block runs the field loop
+  // (it has barriers)
   const bool xch = sdz != nullptr;
   const bool active = j <= jmax && k <= kmax;
   if (!xch && !active) return;
-  const int bw = (int)blockDim.x + 6;
+  const int bw = (int)blockDim.x + 6, tx = (int)threadIdx.x;
   double *srow = xch ? sdz + (size_t)threadIdx.y * bw : nullptr;
   const size_t P = L.P;
   const int id = cid(L, j, k);
   const int sz = L.px;
   const double i60x = L.i60x, i60z = L.i60z, i180x = L.i180x, i180z = L.i180z, ixz = L.ixz;
   const bool edge = cyl && j > L.nx;
-  const double bx = U[(size_t)fBX * P + id], by = U[(size_t)fBY * P + id], bz = U[(size_t)fBZ * P + id];
+  const bool own_col = k <= kmax && j <= jmax + 3;          // a column some cell of the row differentiates
+  double bx = 0.0, by = 0.0, bz = 0.0;
+  if (active) {
+    bx = U[(size_t)fBX * P + id]; by = U[(size_t)fBY * P + id]; bz = U[(size_t)fBZ * P + id];
+  }
+  // per-cell factors: the integer lopsided sums are doubled, the KO sums share one grid
+  const double ax = bx * (0.5 * i60x), az = bz * (0.5 * i60z);
+  const bool bxpos = fx::bits(bx) > 0, bzpos = fx::bits(bz) > 0;   // beta > 0 (a zero beta has ax = 0)
   const double ko = p.ko, ikx = L.idx, ikz = L.idz;
+  const double kfx = ko * ikx, kfz = ko * ikz;
+  const bool same_d = ikx == ikz;
 #pragma unroll 1
   for (int f = 0; f < NMET; ++f) {
-    if (xch && kD2Of[f] >= 0) {
-      __syncthreads();                                   // the previous field's row is read
-      for (int e = threadIdx.x; e < bw; e += blockDim.x) {
-        const int jc = j0 - 3 + e;
-        double v = 0.0;
-        if (k <= kmax && jc <= jmax + 3) {
-          const double *c = U + (size_t)f * P + cid(L, jc, k);
-          v = 45.0 * (c[sz] - c[-sz]) - 9.0 * (c[2 * sz] - c[-2 * sz]) + (c[3 * sz] - c[-3 * sz]);
-        }
-        srow[e] = v;
-      }
-      __syncthreads();
-    }
-    if (!active) continue;
-    const double *u = U + (size_t)f * P + id;
-    const double u0 = u[0];
-    double Dx[9], Dz[9];
-#pragma unroll
-    for (int n = -4; n <= 4; ++n) {
-      Dx[n + 4] = n == 0 ? 0.0 : u[n] - u0;
-      Dz[n + 4] = n == 0 ? 0.0 : u[n * sz] - u0;
-    }
     const int a1 = kD1Of[f], a2 = kD2Of[f];
     const bool yz = y_zero(f);
-    if (a1 >= 0) {
-      DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (45.0 * (Dx[5] - Dx[3]) - 9.0 * (Dx[6] - Dx[2]) + (Dx[7] - Dx[1])) * i60x;
-      DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (45.0 * (Dz[5] - Dz[3]) - 9.0 * (Dz[6] - Dz[2]) + (Dz[7] - Dz[1])) * i60z;
-      DS[(size_t)(DS_D1 + 3 * a1 + 1) * P + id] = (cyl && !yz) ? L.dy[(size_t)f * P + id] : 0.0;
-    }
-    if (a2 >= 0) {
-      double dxz = 0.0;
-      if (xch) {
-        const double *r = srow + threadIdx.x + 3;        // r[n]: z-difference at column j + n
-        dxz = 45.0 * (r[1] - r[-1]) - 9.0 * (r[2] - r[-2]) + (r[3] - r[-3]);
-      } else {
+    const double *u = U + (size_t)f * P + id;
+    double cown = 0.0;                 // z-difference numerator of this thread's column
+    if (active) {
+      long long X[9], Z[9];
 #pragma unroll
-        for (int n = 1; n <= 3; ++n) {
-          const double w = n == 1 ? 45.0 : (n == 2 ? -9.0 : 1.0);
-          // d_z at j+n minus d_z at j-n (pair form in both directions)
-          const double zp = 45.0 * (u[n + sz] - u[n - sz]) - 9.0 * (u[n + 2 * sz] - u[n - 2 * sz]) + (u[n + 3 * sz] - u[n - 3 * sz]);
-          const double zm = 45.0 * (u[-n + sz] - u[-n - sz]) - 9.0 * (u[-n + 2 * sz] - u[-n - 2 * sz]) + (u[-n + 3 * sz] - u[-n - 3 * sz]);
-          dxz += w * (zp - zm);
-        }
+      for (int n = 0; n < 9; ++n) {
+        X[n] = fx::bits(u[n - 4]);
+        Z[n] = n == 4 ? X[4] : fx::bits(u[(n - 4) * sz]);
       }
-      double dxy = 0.0, dyz = 0.0, dyy = 0.0;
-      if (cyl) {
+      int E = 0;
+#pragma unroll
+      for (int n = 0; n < 9; ++n) E = max(E, max(fx::expo(X[n]), fx::expo(Z[n])));
+      bool fast = E >= 128 && E < 2047, zero = false;
+      long long d1xn = 0, d1zn = 0, d2xn = 0, d2zn = 0, kxn = 0, kzn = 0, lxn = 0, lzn = 0;
+      if (E == 0) {                                   // zeros (or subnormals: FP64 form)
+        long long o = 0;
+#pragma unroll
+        for (int n = 0; n < 9; ++n) o |= (X[n] | Z[n]) & ~(1ll << 63);
+        zero = o == 0;
+      } else if (fast) {
+#pragma unroll
+        for (int n = 0; n < 9; ++n) {
+          X[n] = fx::fix(X[n], E);
+          Z[n] = n == 4 ? X[4] : fx::fix(Z[n], E);
+        }
+        const long long c2 = 2 * X[4];
+        const long long ox1 = X[5] - X[3], ox2 = X[6] - X[2], ox3 = X[7] - X[1], ox4 = X[8] - X[0];
+        const long long ex1 = X[5] + X[3] - c2, ex2 = X[6] + X[2] - c2, ex3 = X[7] + X[1] - c2, ex4 = X[8] + X[0] - c2;
+        const long long oz1 = Z[5] - Z[3], oz2 = Z[6] - Z[2], oz3 = Z[7] - Z[1], oz4 = Z[8] - Z[0];
+        const long long ez1 = Z[5] + Z[3] - c2, ez2 = Z[6] + Z[2] - c2, ez3 = Z[7] + Z[1] - c2, ez4 = Z[8] + Z[0] - c2;
+        // |values| < 2^54 on the grid: the first-derivative, lopsided (doubled) and KO sums stay
+        // below 2^63 by their weight sums (110, 360, 256); the second derivative (weight sum 1088
+        // on the values) is checked on its pair sums
+        d1xn = 45 * ox1 - 9 * ox2 + ox3;
+        d1zn = 45 * oz1 - 9 * oz2 + oz3;
+        if (a2 >= 0) {
+          // the sums wrap (unsigned) where the check fails; the FP64 form then replaces them
+          typedef unsigned long long u64;
+          const long long m = fx::mag(ex1) | fx::mag(ex2) | fx::mag(ex3) | fx::mag(ez1) | fx::mag(ez2) | fx::mag(ez3);
+          fast = (m >> 54) == 0;
+          d2xn = (long long)(270ull * (u64)ex1 - 27ull * (u64)ex2 + 2ull * (u64)ex3);
+          d2zn = (long long)(270ull * (u64)ez1 - 27ull * (u64)ez2 + 2ull * (u64)ez3);
+        }
+        kxn = ex4 - 8 * ex3 + 28 * ex2 - 56 * ex1;      // each below 2^62, so their sum fits as well
+        kzn = ez4 - 8 * ez3 + 28 * ez2 - 56 * ez1;
+        const long long Ax = 104 * ox1 - 32 * ox2 + 8 * ox3 - ox4, Bx = 56 * ex1 - 28 * ex2 + 8 * ex3 - ex4;
+        const long long Az = 104 * oz1 - 32 * oz2 + 8 * oz3 - oz4, Bz = 56 * ez1 - 28 * ez2 + 8 * ez3 - ez4;
+        lxn = bxpos ? Ax + Bx : Ax - Bx;
+        lzn = bzpos ? Az + Bz : Az - Bz;
+      }
+      double dxy = 0.0, dyz = 0.0, dyy = 0.0, dy1 = 0.0;
+      if (cyl && !yz) dy1 = L.dy[(size_t)f * P + id];
+      if (a2 >= 0 && cyl) {
         dyy = L.dyy[(size_t)f * P + id];
         if (!yz) {
           const double *q = L.dy + (size_t)f * P + id;
@@ -574,26 +562,95 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
           if (!edge) dxy = (45.0 * (q[1] - q[-1]) - 9.0 * (q[2] - q[-2]) + (q[3] - q[-3])) * i60x;
         }
       }
-      double *o = DS + (size_t)(DS_D2 + 6 * a2) * P + id;
-      o[0] = (270.0 * (Dx[5] + Dx[3]) - 27.0 * (Dx[6] + Dx[2]) + 2.0 * (Dx[7] + Dx[1])) * i180x;
-      o[P] = dxy;
-      o[2 * P] = dxz * ixz;
-      o[3 * P] = dyy;
-      o[4 * P] = dyz;
-      o[5 * P] = (270.0 * (Dz[5] + Dz[3]) - 27.0 * (Dz[6] + Dz[2]) + 2.0 * (Dz[7] + Dz[1])) * i180z;
+      double adv = by * dy1;
+      if (fast || zero) {
+        if (fast) {
+          if (a1 >= 0) {
+            DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (double)d1xn * fx::unit(i60x, E);
+            DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (double)d1zn * fx::unit(i60z, E);
+            cown = (double)d1zn * fx::unit(1.0, E);
+          }
+          if (a2 >= 0) {
+            DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = (double)d2xn * fx::unit(i180x, E);
+            DS[(size_t)(DS_D2 + 6 * a2 + 5) * P + id] = (double)d2zn * fx::unit(i180z, E);
+          }
+          adv += (double)lxn * fx::unit(ax, E);
+          adv += (double)lzn * fx::unit(az, E);
+          if (same_d) adv += (double)(kxn + kzn) * fx::unit(kfx, E);
+          else adv += (double)kxn * fx::unit(kfx, E) + (double)kzn * fx::unit(kfz, E);
+        } else {
+          if (a1 >= 0) {
+            DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = 0.0;
+            DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = 0.0;
+          }
+          if (a2 >= 0) {
+            DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = 0.0;
+            DS[(size_t)(DS_D2 + 6 * a2 + 5) * P + id] = 0.0;
+          }
+        }
+      } else {
+        // FP64 difference form
+        const double u0 = u[0];
+        double Dx[9], Dz[9];
+#pragma unroll
+        for (int n = -4; n <= 4; ++n) {
+          Dx[n + 4] = n == 0 ? 0.0 : u[n] - u0;
+          Dz[n + 4] = n == 0 ? 0.0 : u[n * sz] - u0;
+        }
+        if (a1 >= 0) {
+          DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (45.0 * (Dx[5] - Dx[3]) - 9.0 * (Dx[6] - Dx[2]) + (Dx[7] - Dx[1])) * i60x;
+          DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (45.0 * (Dz[5] - Dz[3]) - 9.0 * (Dz[6] - Dz[2]) + (Dz[7] - Dz[1])) * i60z;
+          cown = zdiff_num(u, sz);
+        }
+        if (a2 >= 0) {
+          DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = (270.0 * (Dx[5] + Dx[3]) - 27.0 * (Dx[6] + Dx[2]) + 2.0 * (Dx[7] + Dx[1])) * i180x;
+          DS[(size_t)(DS_D2 + 6 * a2 + 5) * P + id] = (270.0 * (Dz[5] + Dz[3]) - 27.0 * (Dz[6] + Dz[2]) + 2.0 * (Dz[7] + Dz[1])) * i180z;
+        }
+        auto lop = [](const double *D, double v) {
+          if (v > 0.0) return 2.0 * D[2] - 24.0 * D[3] + 80.0 * D[5] - 30.0 * D[6] + 8.0 * D[7] - D[8];
+          if (v < 0.0) return -(2.0 * D[6] - 24.0 * D[5] + 80.0 * D[3] - 30.0 * D[2] + 8.0 * D[1] - D[0]);
+          return 0.0;
+        };
+        adv += bx * (lop(Dx, bx) * i60x) + bz * (lop(Dz, bz) * i60z);
+        const double kx = (Dx[8] + Dx[0]) - 8.0 * (Dx[7] + Dx[1]) + 28.0 * (Dx[6] + Dx[2]) - 56.0 * (Dx[5] + Dx[3]);
+        const double kz = (Dz[8] + Dz[0]) - 8.0 * (Dz[7] + Dz[1]) + 28.0 * (Dz[6] + Dz[2]) - 56.0 * (Dz[5] + Dz[3]);
+        adv += ko * (kx * ikx + kz * ikz);
+      }
+      if (a1 >= 0) DS[(size_t)(DS_D1 + 3 * a1 + 1) * P + id] = dy1;
+      if (a2 >= 0) {
+        double *o = DS + (size_t)(DS_D2 + 6 * a2) * P + id;
+        o[P] = dxy;
+        o[3 * P] = dyy;
+        o[4 * P] = dyz;
+      }
+      DS[(size_t)(DS_AK + f) * P + id] = adv;
+    } else if (xch && a2 >= 0 && own_col) {
+      cown = zdiff_num(u, sz);          // a column right of the region that cells of the region use
     }
-    // advection: lopsided in x and z (upwind side of the shift), central in y; KO
-    auto lop = [](const double *D, double v) {
-      if (v > 0.0) return 2.0 * D[2] - 24.0 * D[3] + 80.0 * D[5] - 30.0 * D[6] + 8.0 * D[7] - D[8];
-      if (v < 0.0) return -(2.0 * D[6] - 24.0 * D[5] + 80.0 * D[3] - 30.0 * D[2] + 8.0 * D[1] - D[0]);
-      return 0.0;
-    };
-    double adv = bx * (lop(Dx, bx) * i60x) + bz * (lop(Dz, bz) * i60z);
-    if (cyl && !yz) adv += by * L.dy[(size_t)f * P + id];
-    const double kx = (Dx[8] + Dx[0]) - 8.0 * (Dx[7] + Dx[1]) + 28.0 * (Dx[6] + Dx[2]) - 56.0 * (Dx[5] + Dx[3]);
-    const double kz = (Dz[8] + Dz[0]) - 8.0 * (Dz[7] + Dz[1]) + 28.0 * (Dz[6] + Dz[2]) - 56.0 * (Dz[5] + Dz[3]);
-    adv += ko * (kx * ikx + kz * ikz);
-    DS[(size_t)(DS_AK + f) * P + id] = adv;
+    if (a2 >= 0) {
+      double dxz = 0.0;
+      if (xch) {
+        __syncthreads();                                 // the previous field's row is read
+        srow[tx + 3] = own_col ? cown : 0.0;
+        if (tx < 3 || tx >= (int)blockDim.x - 3) {
+          const int e = tx < 3 ? tx : tx + 6;            // halo slot: columns j0 - 3 .. j0 - 1, j0 + bx .. + 2
+          const int jc = j0 - 3 + e;
+          srow[e] = (k <= kmax && jc <= jmax + 3) ? zdiff_num(U + (size_t)f * P + cid(L, jc, k), sz) : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+          const double *r = srow + tx + 3;                 // r[n]: z-difference numerator at column j + n
+          dxz = 45.0 * (r[1] - r[-1]) - 9.0 * (r[2] - r[-2]) + (r[3] - r[-3]);
+        }
+      } else if (active) {
+#pragma unroll
+        for (int n = 1; n <= 3; ++n) {
+          const double w = n == 1 ? 45.0 : (n == 2 ? -9.0 : 1.0);
+          dxz += w * (zdiff_num(u + n, sz) - zdiff_num(u - n, sz));
+        }
+      }
+      if (active) DS[(size_t)(DS_D2 + 6 * a2 + 2) * P + id] = dxz * ixz;
+    }
   }
   if (!active) return;
   if (edge) {
@@ -734,10 +791,11 @@ void launch_z4c_point(const Lev &L, const DevParams &p, const double *U, const d
   else k_z4c_point<double><<<g, b, 0, s>>>(L, p, U, DS, jmax, kmax);
 }
 
-void launch_cartoon(const Lev &L, const DevParams &p, const double *U, const double *tab, int tab_stride, cudaStream_t s) {
+void launch_cartoon(const Lev &L, const DevParams &p, const double *U, const double *tab, int tab_stride,
+                    const double *tabw, cudaStream_t s) {
   dim3 b(32, 4), g((L.nx + 7 + 31) / 32, (L.nz + 10 + 3) / 4);
   if (p.mixed & SACRA_MIXED_Z4C) k_cartoon_f32<<<g, b, 0, s>>>(L, U, tab, tab_stride);
-  else k_cartoon_f64<<<g, b, 0, s>>>(L, U, tab, tab_stride);
+  else k_cartoon_f64<<<g, b, 0, s>>>(L, U, tabw);
 }
 
 void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double *DS, int jmax, int kmax, cudaStream_t s) {
@@ -752,9 +810,9 @@ void launch_z4c_derivs(const Lev &L, const DevParams &p, const double *U, double
 
 // ---------------------------------------------------------------- batched persistent kernels
 
-__global__ void __launch_bounds__(128) kb_cartoon_f64(Batch b, const double *__restrict__ tab, int tab_stride) {
+__global__ void __launch_bounds__(128) kb_cartoon_f64(Batch b, const double *__restrict__ tabw) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
-    cartoon_f64_cell(q.L, q.U, tab, tab_stride, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+    cartoon_f64_cell(q.L, q.U, tabw, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
   });
 }
 
@@ -784,10 +842,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 0) kb_z4c_point(Batc
   });
 }
 
-void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, cudaStream_t s) {
+void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, const double *tabw,
+                      cudaStream_t s) {
   if (b.ntiles <= 0) return;
   if (p.mixed & SACRA_MIXED_Z4C) kb_cartoon_f32<<<b.grid, b.block, 0, s>>>(b, tab, tab_stride);
-  else kb_cartoon_f64<<<b.grid, b.block, 0, s>>>(b, tab, tab_stride);
+  else kb_cartoon_f64<<<b.grid, b.block, 0, s>>>(b, tabw);
 }
 
 void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s) {

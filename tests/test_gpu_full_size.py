@@ -13,7 +13,7 @@ import oracle as O
 from paper_2502_03223_gb300 import sacra2d as S
 from paper_2502_03223_gb300 import workloads as W
 
-from gpu_common import G, atmosphere_threshold_cells, both, compare_level
+from gpu_common import G, ZERO_BORN, atmosphere_threshold_cells, both, compare_level
 
 pytestmark = pytest.mark.gpu
 
@@ -40,15 +40,6 @@ def _rho_l1(gpu_read, orc, cfg):
 def _migration():
     cfg, tov = W.config_migration()
     return cfg, [W.tov_level_data(cfg, tov, l, p_deplete=0.99) for l in range(cfg.n_levels)]
-
-
-# Gt^i, beta^i and B^i vanish in the conformally flat initial data, so after
-# one step they are dt times right-hand sides formed by cancelling terms of
-# order unity (matter, lapse-gradient and Ricci-driven terms near the centre
-# of a compact star, cartoon terms near the axis).  Their rounding is then
-# ~1e-16 x dt x O(1) x (number of terms) ~ 1e-15 absolute, measured up to
-# 1.5e-15, while their own maximum is ~3e-5: the floor 1e-3 allows 1e-14.
-ZERO_BORN = {f: 1e-3 for f in (14, 15, 16, 19, 20, 21, 22, 23, 24)}
 
 
 def _compare_all(gpu, orc, cfg):
