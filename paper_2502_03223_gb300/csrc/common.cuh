@@ -574,26 +574,43 @@ __device__ inline int cons_to_prim(const DevParams &p, double q[NCONS], double W
 
 // ------------------------------------------------------------------ PPM (Colella & Woodward 1984)
 
+// The reconstruction is written with explicitly rounded operations (no fused
+// multiply-add chosen by the compiler), so that the per-face form and the
+// shared-memory staged form of the flux kernels give the same values.
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+
 template <typename T>
 __device__ inline T mc_slope(T am, T a0, T ap) {
-  const T dl = a0 - am, dr = ap - a0;
-  if (dl * dr <= T(0)) return T(0);
-  const T dc = T(0.5) * (ap - am);
+  const T dl = rn_sub(a0, am), dr = rn_sub(ap, a0);
+  if (rn_mul(dl, dr) <= T(0)) return T(0);
+  const T dc = rn_mul(T(0.5), rn_sub(ap, am));
   const T lim = fmin(fabs(dc), fmin(T(2) * fabs(dl), T(2) * fabs(dr)));
   return dc > T(0) ? lim : -lim;
 }
 
 template <typename T>
 __device__ inline void ppm_limit(T a0, T &aL, T &aR) {
-  if ((aR - a0) * (a0 - aL) <= T(0)) {
+  if (rn_mul(rn_sub(aR, a0), rn_sub(a0, aL)) <= T(0)) {
     aL = a0;
     aR = a0;
     return;
   }
-  const T d = aR - aL;
-  const T a6 = T(6) * (a0 - T(0.5) * (aL + aR));
-  if (d * a6 > d * d) aL = T(3) * a0 - T(2) * aR;
-  else if (-d * d > d * a6) aR = T(3) * a0 - T(2) * aL;
+  const T d = rn_sub(aR, aL);
+  const T a6 = rn_mul(T(6), rn_sub(a0, rn_mul(T(0.5), rn_add(aL, aR))));
+  const T dd = rn_mul(d, d), da6 = rn_mul(d, a6);
+  if (da6 > dd) aL = rn_sub(rn_mul(T(3), a0), T(2) * aR);
+  else if (-dd > da6) aR = rn_sub(rn_mul(T(3), a0), T(2) * aL);
+}
+
+// interface value between cells a (slope sa) and b (slope sb), 4th order
+template <typename T>
+__device__ __forceinline__ T ppm_iface(T a, T b, T sa, T sb) {
+  return rn_sub(rn_add(a, rn_mul(T(0.5), rn_sub(b, a))), rn_mul(rn_sub(sb, sa), T(1.0 / 6.0)));
 }
 
 // face between c[2] and c[3] of the six cells c[0..5]
@@ -603,9 +620,9 @@ __device__ inline void ppm_pair(const T c[6], T &left, T &right) {
   const T s2 = mc_slope(c[1], c[2], c[3]);
   const T s3 = mc_slope(c[2], c[3], c[4]);
   const T s4 = mc_slope(c[3], c[4], c[5]);
-  const T im = c[1] + T(0.5) * (c[2] - c[1]) - (s2 - s1) * T(1.0 / 6.0);   // face j-1/2
-  const T i0 = c[2] + T(0.5) * (c[3] - c[2]) - (s3 - s2) * T(1.0 / 6.0);   // face j+1/2
-  const T ip = c[3] + T(0.5) * (c[4] - c[3]) - (s4 - s3) * T(1.0 / 6.0);   // face j+3/2
+  const T im = ppm_iface(c[1], c[2], s1, s2);   // face j-1/2
+  const T i0 = ppm_iface(c[2], c[3], s2, s3);   // face j+1/2
+  const T ip = ppm_iface(c[3], c[4], s3, s4);   // face j+3/2
   T aL = im, aR = i0;
   ppm_limit(c[2], aL, aR);
   left = aR;

@@ -16,20 +16,16 @@ __device__ __forceinline__ double face6(const double *u, int s) {
 
 // Face j+1/2 (dir 0, stride 1) or k+1/2 (dir 1, stride px) of cell (j, k):
 // reconstruction, metric at the face and the flux, FP64.
+// The flux of the face from its reconstructed states pl (cell side), pr
+// (neighbour side): a side whose density or pressure is not positive drops
+// to first order, then the metric at the face and the Riemann solver.
 template <int DIR>
-__device__ inline void flux_at_f64(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
-                                   double out[NCONS], int *fb) {
+__device__ inline void flux_states_f64(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                       double pl[5], double pr[5], double out[NCONS], int *fb) {
   const size_t P = L.P;
   const int s = DIR == 0 ? 1 : L.px;
   const int id = cid(L, j, k);
   const int pf[5] = {pRHO, pUX, pUY, pUZ, pP};
-  double pl[5], pr[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) {
-    const double *a = L.prim + (size_t)pf[v] * P + id;
-    const double c[6] = {a[-2 * s], a[-s], a[0], a[s], a[2 * s], a[3 * s]};
-    ppm_pair(c, pl[v], pr[v]);
-  }
   if (!(pl[0] > 0.0) || !(pl[4] > 0.0))
 #pragma unroll
     for (int v = 0; v < 5; ++v) pl[v] = L.prim[(size_t)pf[v] * P + id];
@@ -49,6 +45,89 @@ __device__ inline void flux_at_f64(const Lev &L, const DevParams &p, const doubl
   g.yz = face6(U + (size_t)fHYZ * P + id, s);
   g.zz = 1.0 + face6(U + (size_t)fHZZ * P + id, s);
   *fb = face_flux<double>(p, DIR, pl, pr, alpha, beta, W, g, out);
+}
+
+template <int DIR>
+__device__ inline void flux_at_f64(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                   double out[NCONS], int *fb) {
+  const size_t P = L.P;
+  const int s = DIR == 0 ? 1 : L.px;
+  const int id = cid(L, j, k);
+  const int pf[5] = {pRHO, pUX, pUY, pUZ, pP};
+  double pl[5], pr[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double *a = L.prim + (size_t)pf[v] * P + id;
+    const double c[6] = {a[-2 * s], a[-s], a[0], a[s], a[2 * s], a[3 * s]};
+    ppm_pair(c, pl[v], pr[v]);
+  }
+  flux_states_f64<DIR>(L, p, U, j, k, pl, pr, out, fb);
+}
+
+// PPM of the lines of a tile through shared memory (FP64).  The per-face form
+// forms each MC slope for four faces and each interface value for three; here
+// a block forms every slope, interface value and limited parabola of its
+// tile's lines once, with the same formulas (the same values), and each face
+// reads its two states.  Lines run along the face normal: rows for x-faces
+// (DIR 0), columns for z-faces (DIR 1); a tile holds nli lines of nal faces
+// starting at along-index a0 and line l0.  Shared memory (kernels' dynamic
+// buffer): per variable and line, the slopes of cells a0-1 .. a0+nal+1 (then
+// the left parabola values of cells a0 .. a0+nal), the interfaces between
+// cells a0-1+t and a0+t, t < nal+2, and the right parabola values of cells
+// a0 .. a0+nal.  Only cells that faces of the region use are formed.
+__host__ __device__ constexpr int ppm_tile_doubles(int nal, int nli) { return 5 * nli * ((nal + 3) + (nal + 2) + (nal + 1)); }
+
+template <int DIR>
+__device__ __forceinline__ void ppm_tile(const Lev &L, int j0, int k0, int jmax, int kmax, double *sm) {
+  const int nal = DIR == 0 ? (int)blockDim.x : (int)blockDim.y, nli = DIR == 0 ? (int)blockDim.y : (int)blockDim.x;
+  const int nth = (int)(blockDim.x * blockDim.y), tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+  const int sS = nal + 3, sI = nal + 2, sR = nal + 1;
+  double *S = sm, *I = S + 5 * nli * sS, *RR = I + 5 * nli * sI;
+  const int s = DIR == 0 ? 1 : L.px;
+  const int a0 = DIR == 0 ? j0 : k0, l0 = DIR == 0 ? k0 : j0;
+  const int amax = DIR == 0 ? jmax : kmax, lmax = DIR == 0 ? kmax : jmax;
+  auto at = [&](int v, int line, int along) {
+    const int pf = v == 0 ? pRHO : (v == 1 ? pUX : (v == 2 ? pUY : (v == 3 ? pUZ : pP)));
+    const int j = DIR == 0 ? along : line, k = DIR == 0 ? line : along;
+    return L.prim + (size_t)pf * L.P + cid(L, j, k);
+  };
+  for (int it = tid; it < 5 * nli * sS; it += nth) {          // slopes of cells a0 - 1 + t
+    const int t = it % sS, r = it / sS, line = r % nli, v = r / nli, c = a0 - 1 + t;
+    if (l0 + line > lmax || c > amax + 2) continue;
+    const double *a = at(v, l0 + line, c);
+    S[it] = mc_slope(a[-s], a[0], a[s]);
+  }
+  __syncthreads();
+  for (int it = tid; it < 5 * nli * sI; it += nth) {          // interface between cells c and c + 1
+    const int t = it % sI, r = it / sI, line = r % nli, v = r / nli, c = a0 - 1 + t;
+    if (l0 + line > lmax || c > amax + 1) continue;
+    const double *a = at(v, l0 + line, c);
+    const double *sl = S + (size_t)r * sS + t;
+    I[it] = ppm_iface(a[0], a[s], sl[0], sl[1]);
+  }
+  __syncthreads();
+  for (int it = tid; it < 5 * nli * sR; it += nth) {          // limited parabola of cell a0 + t
+    const int t = it % sR, r = it / sR, line = r % nli, v = r / nli, c = a0 + t;
+    if (l0 + line > lmax || c > amax + 1) continue;
+    double aL = I[(size_t)r * sI + t], aR = I[(size_t)r * sI + t + 1];
+    ppm_limit(*at(v, l0 + line, c), aL, aR);
+    S[(size_t)r * sS + t] = aL;
+    RR[it] = aR;
+  }
+  __syncthreads();
+}
+
+// the two states of face (a0 + t) of line `line` of the staged tile
+template <int DIR>
+__device__ __forceinline__ void ppm_tile_states(const double *sm, int t, int line, double pl[5], double pr[5]) {
+  const int nal = DIR == 0 ? (int)blockDim.x : (int)blockDim.y, nli = DIR == 0 ? (int)blockDim.y : (int)blockDim.x;
+  const int sS = nal + 3, sI = nal + 2, sR = nal + 1;
+  const double *S = sm, *RR = sm + 5 * nli * (sS + sI);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    pl[v] = RR[(size_t)(v * nli + line) * sR + t];
+    pr[v] = S[(size_t)(v * nli + line) * sS + t + 1];
+  }
 }
 
 // The FP32 face interpolation as an increment over the cell value u[0],
@@ -175,11 +254,18 @@ __device__ inline void flux_face(const Lev &L, const DevParams &p, const double 
 // and accumulates the flux registers of the refinement boundaries.
 template <typename T>
 __device__ __forceinline__ void flux_x_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
-                                                 double wb, int has_child, int has_parent, int j, int k, double wbp) {
+                                                 double wb, int has_child, int has_parent, int j, int k, double wbp,
+                                                 const double *stage_sm = nullptr) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
-  flux_face<T, 0>(L, p, U, j, k, f, &fb);
+  if (stage_sm) {
+    double pl[5], pr[5];
+    ppm_tile_states<0>(stage_sm, threadIdx.x, threadIdx.y, pl, pr);
+    flux_states_f64<0>(L, p, U, j, k, pl, pr, f, &fb);
+  } else {
+    flux_face<T, 0>(L, p, U, j, k, f, &fb);
+  }
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
   const double xf = j * L.dx;
   const double area = cyl ? xf * L.dz : L.dz;
@@ -206,11 +292,18 @@ __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double
 
 template <typename T>
 __device__ __forceinline__ void flux_z_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
-                                                 double wb, int has_child, int has_parent, int j, int k, double wbp) {
+                                                 double wb, int has_child, int has_parent, int j, int k, double wbp,
+                                                 const double *stage_sm = nullptr) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
-  flux_face<T, 1>(L, p, U, j, k, f, &fb);
+  if (stage_sm) {
+    double pl[5], pr[5];
+    ppm_tile_states<1>(stage_sm, threadIdx.y, threadIdx.x, pl, pr);
+    flux_states_f64<1>(L, p, U, j, k, pl, pr, f, &fb);
+  } else {
+    flux_face<T, 1>(L, p, U, j, k, f, &fb);
+  }
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
   // equatorial mirror plane: D, S_x, S_phi, E are even in z, their z-fluxes vanish there
   if (cyl && k == 0) f[0] = f[1] = f[2] = f[4] = 0.0;
@@ -418,6 +511,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_flux_z(Batch b
   });
 }
 
+// FP64 faces with the PPM staged through shared memory (dynamic buffer of
+// ppm_tile_doubles(...) doubles)
+__global__ void __launch_bounds__(256, 2) kb_flux_x_st(Batch b, DevParams p) {
+  extern __shared__ double ppm_sm[];
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    ppm_tile<0>(q.L, tl.j0, tl.k0, q.jmax, q.kmax, ppm_sm);
+    flux_x_cell<double>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x,
+                        tl.k0 + threadIdx.y, q.wbp, ppm_sm);
+  });
+}
+
+__global__ void __launch_bounds__(256, 2) kb_flux_z_st(Batch b, DevParams p) {
+  extern __shared__ double ppm_sm[];
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    ppm_tile<1>(q.L, tl.j0, tl.k0, q.jmax, q.kmax, ppm_sm);
+    flux_z_cell<double>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x,
+                        tl.k0 + threadIdx.y, q.wbp, ppm_sm);
+  });
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_hydro_rhs(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
@@ -425,15 +538,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_hydro_rhs(Batc
   });
 }
 
+// The FP64 faces always stage their PPM (one kernel per direction, so every
+// tile shape gives the same values); the buffer of every candidate shape
+// stays within the 48 KB a launch may take without opting in, and a shape
+// beyond it would keep the per-face form.
+constexpr size_t kPpmSmemMax = 48 * 1024;
+
 void launch_b_flux_x(const Batch &b, const DevParams &p, cudaStream_t s) {
   if (b.ntiles <= 0) return;
+  const size_t sm = ppm_tile_doubles(b.block.x, b.block.y) * sizeof(double);
   if (p.mixed & SACRA_MIXED_FLUX) kb_flux_x<float><<<b.grid, b.block, 0, s>>>(b, p);
+  else if (sm <= kPpmSmemMax) kb_flux_x_st<<<b.grid, b.block, sm, s>>>(b, p);
   else kb_flux_x<double><<<b.grid, b.block, 0, s>>>(b, p);
 }
 
 void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s) {
   if (b.ntiles <= 0) return;
+  const size_t sm = ppm_tile_doubles(b.block.y, b.block.x) * sizeof(double);
   if (p.mixed & SACRA_MIXED_FLUX) kb_flux_z<float><<<b.grid, b.block, 0, s>>>(b, p);
+  else if (sm <= kPpmSmemMax) kb_flux_z_st<<<b.grid, b.block, sm, s>>>(b, p);
   else kb_flux_z<double><<<b.grid, b.block, 0, s>>>(b, p);
 }
 

@@ -78,6 +78,29 @@ __device__ inline void geo_ricci(const Z4cIn<T> &z, Geo<T> &G) {
   const T trDDW = gi.xx * DDW[0] + gi.yy * DDW[3] + gi.zz * DDW[5] + T(2.0) * (gi.xy * DDW[1] + gi.xz * DDW[2] + gi.yz * DDW[4]);
   const T dW2 = s3quad(gi, z.dW, z.dW);
   const T iW = T(1.0) / z.W;
+  // gt^lm (Gt^k_li Gt_{j,km} + Gt^k_lj Gt_{i,km} + Gt^k_im Gt_{k,lj}) with the last
+  // index of Gt_{j,km} raised once, M[j][k][l] = gt^lm Gt_{j,km}: the first two
+  // terms are Q_ij + Q_ji with Q_ij = Gt^k_li M[j][k][l], the third Gt^k_im M[k][j][m]
+  T M[3][3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        M[j][k][l] = gim[l][0] * G.Gl[j][sp(k, 0)] + gim[l][1] * G.Gl[j][sp(k, 1)] + gim[l][2] * G.Gl[j][sp(k, 2)];
+  T Q[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T q = T(0.0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) q += G.G2[k][sp(l, i)] * M[j][k][l];
+      Q[i][j] = q;
+    }
   T Rsum = T(0.0);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -94,18 +117,13 @@ __device__ inline void geo_ricci(const Z4cIn<T> &z, Geo<T> &G) {
       // Gt_d^k Gt_(ij)k
 #pragma unroll
       for (int k = 0; k < 3; ++k) r += T(0.5) * G.Gd[k] * (G.Gl[i][sp(j, k)] + G.Gl[j][sp(i, k)]);
-      // gt^lm (Gt^k_li Gt_{j,km} + Gt^k_lj Gt_{i,km} + Gt^k_im Gt_{k,lj})
+      // the quadratic Christoffel terms (above)
+      T s3 = Q[i][j] + Q[j][i];
 #pragma unroll
-      for (int l = 0; l < 3; ++l)
+      for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          T s = T(0.0);
-#pragma unroll
-          for (int k = 0; k < 3; ++k)
-            s += G.G2[k][sp(l, i)] * G.Gl[j][sp(k, m)] + G.G2[k][sp(l, j)] * G.Gl[i][sp(k, m)]
-               + G.G2[k][sp(i, m)] * G.Gl[k][sp(l, j)];
-          r += gim[l][m] * s;
-        }
+        for (int m = 0; m < 3; ++m) s3 += G.G2[k][sp(i, m)] * M[k][j][m];
+      r += s3;
       r += (DDW[ij] + gm[i][j] * trDDW) * iW - T(2.0) * gm[i][j] * dW2 * iW * iW;
       G.R[ij] = r;
       Rsum += (i == j ? T(1.0) : T(2.0)) * gim[i][j] * r;
