@@ -44,21 +44,23 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s per RK stage (Z4c+HLLC), FP64 vs mixed/batched, % of roofline"
 UNIT = "cell-updates/s"
 
-# FP64 operations per unit of work of the method itself (add, sub, mul = 1; an
-# FMA = 2; div, sqrt, exp = 1), counted by hand on the minimal form of each
-# kernel's arithmetic.  Stencils: symmetric pair form (u_n - u_-n, u_n + u_-n)
-# with the weights and 1/dx factors hoisted and zero taps skipped, pair sums
-# shared between the derivative kinds, the mixed x-z derivative separable (the
-# z-difference numerator of a column serves the cell's own d_z and its
-# neighbours' d_xz), the lopsided advection at beta != 0.  Cartoon: the nine-
-# point interpolation and the +-phi rotations folded into per-column weights
-# of each d_y / d_yy output.  Pointwise algebra, fluxes, sources and the stage
-# update: the plain evaluation (the oracle's operation count), which has no
-# stencil redundancy.  Units: a cell of the update region; a face for the flux
-# kernels; a cell of the plane patch for the cartoon kernel.
+# FP64 operations per unit of work of the method (add, sub, mul = 1; an FMA
+# = 2; div, sqrt = 1).  Stencil kernels, counted by hand on the minimal FP64
+# form: the derivative pass with symmetric pair sums shared between the
+# derivative kinds, weights and 1/dx hoisted, zero taps skipped, the mixed x-z
+# derivative separable and the lopsided advection at beta != 0 (2139 per cell;
+# the kernel forms these sums exactly in integers, so this is FP64-equivalent
+# work, not FP64 instructions); the cartoon terms with the interpolation,
+# rotation and plane differences folded into one 9-point sum per output (591
+# per cell of the plane patch).  Pointwise kernels (no stencil redundancy):
+# the FP64 operations their formulation executes per unit, from ncu's
+# instruction counters (dfma x 2 + dmul + dadd), the stage update at the
+# migration star's recovery iteration counts.  Units: a cell of the update
+# region; a face for the flux kernels; a cell of the plane patch for the
+# cartoon kernel.
 METHOD_FLOPS = {
-    "k_z4c_derivs": 2139.0, "k_cartoon": 878.0, "k_z4c_point": 4197.0, "k_flux_x": 1071.2,
-    "k_flux_z": 1071.2, "k_hydro_rhs": 1383.2, "k_rk_update": 576.7,
+    "k_z4c_derivs": 2139.0, "k_cartoon": 591.0, "k_z4c_point": 2001.0, "k_flux_x": 756.0,
+    "k_flux_z": 784.0, "k_hydro_rhs": 563.0, "k_rk_update": 463.0,
 }
 NOMINAL_FP64_TFLOPS = 1.25
 
@@ -510,6 +512,48 @@ def strip(d):
     return {k: v for k, v in d.items() if not k.startswith("_")}
 
 
+def collect_tuples(sim, cfg, buf, off, rounds, steps_between):
+    """Recovery tuples (inputs, converged log10 P/D) from the context's own
+    state at `rounds` times `steps_between` steps apart, appended to buf at
+    row off; returns the new row count."""
+    for _ in range(rounds):
+        if off >= buf.shape[0]:
+            break
+        off += sim.mlp_collect(buf[off:])
+        sim.step(cfg.dt, steps_between, use_graph=True)
+    sim.sync()
+    return off
+
+
+def seed_measurement(sim, cfg, net, steps, dist, ws):
+    """The large run with and without the learned seed: Illinois evaluations
+    per recovery over one step (counting pass), the stage update's device time
+    per launch (profiled eager step) and the step rate (graph-replayed timed
+    region), each form from the same state."""
+    out = {}
+    for name, n in (("without", None), ("with", net)):
+        sim.set_mlp(n)
+        sim.step(cfg.dt, 1, use_graph=True)       # a graph with this form
+        sim.c2p_counting(True)
+        sim.c2p_counts(reset=True)
+        sim.step(cfg.dt, 1, use_graph=False)
+        ev, tried, held, nrec = sim.c2p_counts(reset=True)
+        sim.c2p_counting(False)
+        sim.profile(True)
+        sim.step(cfg.dt, 1, use_graph=False)
+        rep = sim.profile_report()
+        sim.profile(False)
+        rk = rep.get("k_rk_update", (0.0, 1, 0))
+        sim.step(cfg.dt, 1, use_graph=True)
+        ms, _, _, clocks = timed_region(sim, steps, cfg.dt, dist, False)
+        ms = max_over_ranks(dist, ms)
+        out[name] = {"value": ws * cell_updates_per_step(cfg) * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "evaluations_per_recovery": ev / max(nrec, 1), "recoveries": nrec, "seed_tried": tried,
+                     "seed_held": held, "rk_update_ms_per_launch": rk[0] / max(rk[1], 1), "clocks": clocks}
+    sim.set_mlp(None)
+    return out
+
+
 def run_native(args, dist, rank, ws, local):
     import torch
     from paper_2502_03223_gb300 import build as B
@@ -593,6 +637,24 @@ def run_native(args, dist, rank, ws, local):
                         "frac": (path_flops / path_s / 1e12 / peak) if peak else None,
                         "kernels": sorted(k for k in kern if k in METHOD_FLOPS)}
 
+    # ---- recovery tuples for the learned seed from the migration star's own
+    # evolution (FP64 context, 8 times 10 steps apart), before its state is reset
+    tuples, ntup, tup_src = None, 0, {}
+    if not args.no_learned and not args.no_large:
+        tuples = torch.zeros((args.tuples, 10), dtype=torch.float32, device="cuda")
+        ntup = collect_tuples(sim, cfg, tuples, 0, 8, 10)
+        tup_src[cfg.name] = ntup
+
+    # ---- the same per-kernel breakdown of the mixed-precision step
+    if msim is not None:
+        msim.profile(True)
+        for _ in range(prof_steps):
+            msim.step_constraints(cfg.dt, 1, use_graph=False)
+        mrep = msim.profile_report()
+        msim.profile(False)
+        mtot = sum(v[0] for v in mrep.values())
+        mixed["kernel_share"] = {k: round(v[0] / mtot, 4) for k, v in sorted(mrep.items(), key=lambda kv: -kv[1][0])[:10]}
+
     # ---- each output's error against the FP64 oracle after one step from the initial data
     if rank == 0 and ws == 1 and not args.no_errors and msim is not None:
         e64, emx = errors_vs_oracle(cfg, datas, [sim, msim], steps=1)
@@ -610,6 +672,10 @@ def run_native(args, dist, rank, ws, local):
         c2, d2 = workload("tov_stable_3x256")
         s2, a2, m2, b2 = pair_forms(c2, d2, args, dist, ws, 0, 0, args.steps)
         extra["tov_stable_3x256"] = {"config": describe(c2), "fp64": strip(a2), "mixed": strip(b2) if b2 else None}
+        if tuples is not None:
+            n0 = ntup
+            ntup = collect_tuples(s2, c2, tuples, ntup, 10, 20)
+            tup_src[c2.name] = ntup - n0
         s2.close()
         if m2 is not None:
             m2.close()
@@ -617,11 +683,23 @@ def run_native(args, dist, rank, ws, local):
     if not args.no_large:
         c5, d5 = workload("large_7x1024")
         s5, a5, m5, b5 = pair_forms(c5, d5, args, dist, ws, 0, 0, args.large_steps)
-        s5.close()
         if m5 is not None:
             m5.close()
         del d5
         extra["large_7x1024"] = {"config": describe(c5), "fp64": strip(a5), "mixed": strip(b5) if b5 else None}
+        if tuples is not None and ntup >= 1000:
+            # the learned recovery seed (BF16 MLP) trained by the library's own kernels on the
+            # tuples of the smaller runs, tried on every recovery of the large run (kmin = 0)
+            t0 = time.perf_counter()
+            net, trep, _ = S.mlp_train(tuples[:ntup], steps=3000, batch_blocks=32, lr=1e-2, seed=1, kmin=0.0)
+            torch.cuda.synchronize()
+            t_train = time.perf_counter() - t0
+            del tuples
+            tuples = None
+            meas = seed_measurement(s5, c5, net, args.large_steps, dist, ws)
+            extra["large_7x1024"]["learned_seed"] = {"tuples": ntup, "tuple_sources": tup_src, "train": trep,
+                                                     "train_s": t_train, "kmin": 0.0, **meas}
+        s5.close()
     batch = None
     if not args.no_batch:
         batch = run_batch(args, dist, ws)
@@ -679,6 +757,7 @@ def main():
     ap.add_argument("--batch-stars", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned recovery seed")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--tuples", type=int, default=12_000_000, help="capacity of the learned seed's tuple buffer")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist, rank, ws, local = dist_setup()
