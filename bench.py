@@ -461,6 +461,18 @@ def run_batch(args, dist, ws):
         return max_over_ranks(dist, ev0.elapsed_time(ev1)), b.launch_count - n0, sampler.stop()
 
     ms, launches, clocks = timed(steps)
+    # per-kernel device time of one eager step (events around each launch): the
+    # batched kinds against the per-level ghost fill, prolongation, restriction,
+    # reflux and recovery launches
+    b.profile(True)
+    b.step(dt, 1, use_graph=False)
+    brep = b.profile_report()
+    b.profile(False)
+    btot = sum(v[0] for v in brep.values())
+    per_level = ("k_parity_x", "k_parity_z", "k_outer", "k_prolong", "k_restrict", "k_reflux", "k_c2p_region",
+                 "k_outflow", "k_time_interp")
+    kshare = {k: round(v[0] / btot, 4) for k, v in sorted(brep.items(), key=lambda kv: -kv[1][0])}
+    klaunch = {k: int(v[1]) for k, v in brep.items()}
     # the learned recovery seed, trained on tuples of this batch's own state
     learned = None
     if not args.no_learned:
@@ -484,6 +496,9 @@ def run_batch(args, dist, ws):
             "ms_per_step": ms / steps, "steps": steps, "n_stars": len(cfgs),
             "cell_updates_per_step": cells, "precision": "mixed", "cuda_graph": True, "tuning": tuning,
             "gpu_launches": launches, "launches_per_step": launches / steps, "clocks": clocks, "init_s": t_init,
+            "kernel_share": kshare, "launches_per_kernel_eager_step": klaunch,
+            "per_level_share": round(sum(v for k, v in kshare.items() if k in per_level), 4),
+            "eager_step_device_ms": btot,
             "learned_seed": learned, "star0_H_L2": diag[0],
             "sizes": sorted(set((c.nx, c.n_levels) for c in cfgs))[:40]}
 
