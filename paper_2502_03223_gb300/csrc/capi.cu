@@ -220,6 +220,20 @@ struct Engine {
   size_t tiles_cap = 0, tune_cap = 0;
   std::vector<long long> toff, tcnt, cells;   // [group][stage][kind]
   KindCfg cfg[B_NKIND];
+  // level lists of the lockstep step (kernels.h, LItem): the ghost fill and the
+  // restriction as one launch per operation and level depth over every star
+  struct LList {
+    long long off = 0;       // first item in litems_dev
+    int n = 0, max_nx = 0;   // items, the largest nx among them
+    long long cells = 0;     // units of work (profiling)
+  };
+  LItem *litems_dev = nullptr;
+  size_t litems_cap = 0;
+  int lmax = 0;                        // the largest level count of the stars
+  bool lists = false;                  // the lockstep step runs on the level lists
+  std::vector<LList> l_fill, l_fpar;   // [parity][stage][depth]: outer (depth 0) / prolongation; parity
+  std::vector<LList> l_restr, l_rpar;  // [parity][depth]: restriction of depth onto depth - 1; child parity
+  LList l_oend[2], l_ppar[2];          // [parity]: outer boundary after the last stage; parents' parity
   // bookkeeping
   long long launches = 0;
   std::string err;
@@ -399,9 +413,127 @@ size_t plan_bytes(const std::vector<sacra_params> &ps) {
   return round_up((2 * (size_t)S + 2) * nl * sizeof(BL), 256) + round_up((cap + tune) * sizeof(Tile), 256);
 }
 
-// upload the level views and the tile lists of the current choice of shapes
+// level l of star st as parity par sees it (st.lv holds the current registers)
+Lev level_view(const Star &st, int l, int par) {
+  Lev L = st.lv[l];
+  if (par != st.lpar[l]) std::swap(L.un, L.us);
+  return L;
+}
+
+// items of the level lists (counted by litem_count); each list contiguous
+void build_lists(Engine &e, std::vector<LItem> &items) {
+  items.clear();
+  e.lmax = 0;
+  bool same = true;
+  const sacra_params &p0 = e.stars[0].prm;
+  for (const Star &st : e.stars) {
+    e.lmax = std::max(e.lmax, st.prm.n_levels);
+    same = same && st.prm.geometry == SACRA_CYLINDRICAL && st.prm.evolve_spacetime == p0.evolve_spacetime &&
+           st.prm.hydro_outer == p0.hydro_outer && st.prm.rk == p0.rk;
+  }
+  e.lists = e.ngroups == 1 && same;
+  const int D = e.lmax;
+  e.l_fill.assign((size_t)2 * e.S * D, Engine::LList());
+  e.l_fpar.assign((size_t)2 * e.S * D, Engine::LList());
+  e.l_restr.assign((size_t)2 * D, Engine::LList());
+  e.l_rpar.assign((size_t)2 * D, Engine::LList());
+  auto open = [&](Engine::LList &ll) { ll = Engine::LList(); ll.off = (long long)items.size(); };
+  // max_nx: the largest extent in x or z (the launches are sized for it)
+  auto add = [&](Engine::LList &ll, const LItem &it, int nx, long long cells) {
+    items.push_back(it);
+    ++ll.n;
+    ll.max_nx = std::max(ll.max_nx, std::max(nx, it.L.nz));
+    ll.cells += cells;
+  };
+  for (int par = 0; par < 2; ++par) {
+    for (int s = 0; s < e.S; ++s)
+      for (int d = 0; d < D; ++d) {
+        Engine::LList &F = e.l_fill[((size_t)par * e.S + s) * D + d];
+        open(F);
+        for (const Star &st : e.stars) {
+          if (st.prm.n_levels <= d) continue;
+          LItem it;
+          memset(&it, 0, sizeof(it));
+          it.L = level_view(st, d, par);
+          it.P = st.dp;
+          it.B = s == 0 ? it.L.un : it.L.us;
+          if (d == 0) {
+            it.A = it.L.un;
+            add(F, it, st.prm.nx, (long long)(it.L.nx + GH) * (it.L.nz + GH) - (long long)it.L.nx * it.L.nz);
+          } else {
+            it.Pa = level_view(st, d - 1, par);
+            it.A = s == 0 ? it.Pa.un : it.Pa.us;
+            add(F, it, st.prm.nx, prolong_cells(it.L, s == 0));
+          }
+        }
+        Engine::LList &Q = e.l_fpar[((size_t)par * e.S + s) * D + d];
+        open(Q);
+        for (const Star &st : e.stars) {
+          if (st.prm.n_levels <= d) continue;
+          LItem it;
+          memset(&it, 0, sizeof(it));
+          it.L = level_view(st, d, par);
+          it.P = st.dp;
+          it.B = s == 0 ? it.L.un : it.L.us;
+          add(Q, it, st.prm.nx, 8LL * (it.L.nz + GH));
+        }
+      }
+    open(e.l_oend[par]);
+    for (const Star &st : e.stars) {
+      LItem it;
+      memset(&it, 0, sizeof(it));
+      it.L = level_view(st, 0, par);
+      it.P = st.dp;
+      it.A = it.L.un;
+      it.B = it.L.us;
+      add(e.l_oend[par], it, st.prm.nx, (long long)(it.L.nx + GH) * (it.L.nz + GH) - (long long)it.L.nx * it.L.nz);
+    }
+    for (int d = 1; d < D; ++d) {
+      Engine::LList &Q = e.l_rpar[(size_t)par * D + d];
+      open(Q);
+      for (const Star &st : e.stars) {
+        if (st.prm.n_levels <= d) continue;
+        LItem it;
+        memset(&it, 0, sizeof(it));
+        it.L = level_view(st, d, par);
+        it.P = st.dp;
+        it.B = it.L.un;
+        add(Q, it, st.prm.nx, 8LL * (it.L.nz + GH));
+      }
+      Engine::LList &R = e.l_restr[(size_t)par * D + d];
+      open(R);
+      for (const Star &st : e.stars) {
+        if (st.prm.n_levels <= d) continue;
+        LItem it;
+        memset(&it, 0, sizeof(it));
+        it.L = level_view(st, d, par);
+        it.Pa = level_view(st, d - 1, par);
+        it.P = st.dp;
+        add(R, it, st.prm.nx, (long long)(st.prm.nx / 2) * (st.prm.nx / 2));
+      }
+    }
+    open(e.l_ppar[par]);
+    for (const Star &st : e.stars)
+      for (int l = 0; l < st.prm.n_levels - 1; ++l) {
+        LItem it;
+        memset(&it, 0, sizeof(it));
+        it.L = level_view(st, l, par);
+        it.P = st.dp;
+        it.B = it.L.un;
+        add(e.l_ppar[par], it, st.prm.nx, 8LL * (it.L.nz + GH));
+      }
+  }
+}
+
+// upload the level views, the tile lists of the current choice of shapes and
+// the level lists
 sacra_status upload_plan(Engine &e) {
   const int NL = (int)e.slots.size();
+  std::vector<LItem> litems;
+  build_lists(e, litems);
+  if (litems.size() > e.litems_cap) return fail(e, SACRA_ERR_OOM, "level-list capacity exceeded");
+  if (!litems.empty())
+    cudaMemcpyAsync(e.litems_dev, litems.data(), litems.size() * sizeof(LItem), cudaMemcpyHostToDevice, e.stream);
   std::vector<BL> bls((size_t)2 * e.S * NL);
   for (int par = 0; par < 2; ++par)
     for (int s = 0; s < e.S; ++s)
@@ -481,6 +613,55 @@ void enqueue_fill(Engine &e, Star &st, int s, double dt) {
   }
 }
 
+// ---- the lockstep step on the level lists: one launch per operation and
+// level depth over every star (the order within a star is that of
+// enqueue_fill / enqueue_restrict: a level's ghost fill reads its parent's
+// filled ghosts, a restriction reads its child's restricted interior)
+
+void enqueue_parity_list(Engine &e, const Engine::LList &Q) {
+  if (Q.n <= 0) return;
+  const LItem *it = e.litems_dev + Q.off;
+  run(e, K_PARITY_X, Q.cells, [&] { launch_l_parity_x(it, Q.n, Q.max_nx, e.stream); });
+  run(e, K_PARITY_Z, Q.cells, [&] { launch_l_parity_z(it, Q.n, Q.max_nx, e.stream); });
+}
+
+void enqueue_fill_lists(Engine &e, int s, double dt) {
+  const sacra_params &p0 = e.stars[0].prm;
+  const size_t base = ((size_t)e.parity * e.S + s) * e.lmax;
+  for (int d = 0; d < e.lmax; ++d) {
+    const Engine::LList &F = e.l_fill[base + d];
+    const LItem *it = e.litems_dev + F.off;
+    if (F.n > 0) {
+      if (d == 0) {
+        run(e, K_OUTER, F.cells, [&] {
+          launch_l_outer(it, F.n, F.max_nx, stage_c(p0.rk, s) * dt, p0.evolve_spacetime, !p0.hydro_outer, e.stream);
+        });
+      } else {
+        run(e, K_PROLONG, F.cells, [&] { launch_l_prolong(it, F.n, F.max_nx, s == 0, e.stream); });
+        ++e.launches;   // the prolongation is two kernels
+      }
+    }
+    enqueue_parity_list(e, e.l_fpar[base + d]);
+  }
+}
+
+void enqueue_restrict_lists(Engine &e, double dt) {
+  const size_t base = (size_t)e.parity * e.lmax;
+  for (int d = e.lmax - 1; d >= 1; --d) {
+    enqueue_parity_list(e, e.l_rpar[base + d]);
+    const Engine::LList &R = e.l_restr[base + d];
+    if (R.n <= 0) continue;
+    const LItem *it = e.litems_dev + R.off;
+    run(e, K_RESTRICT, R.cells, [&] { launch_l_restrict(it, R.n, R.max_nx, e.stream); });
+    ++e.launches;   // the restriction is two kernels
+    run(e, K_REFLUX, (long long)R.n * R.max_nx, [&] { launch_l_reflux(it, R.n, R.max_nx, dt, e.stream); });
+    // the restricted cells [1, N/2]^2 and the refluxed strips next to them (not the corner)
+    run(e, K_C2P, R.cells, [&] { launch_l_c2p_restricted(it, R.n, R.max_nx, e.stream); });
+  }
+  // the parents' axis/equator ghosts mirror their restricted interiors
+  enqueue_parity_list(e, e.l_ppar[e.parity]);
+}
+
 // swap the step and stage registers of the levels of group g
 void swap_group(Engine &e, int g) {
   for (size_t i = 0; i < e.slots.size(); ++i) {
@@ -526,7 +707,13 @@ void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) 
     run(e, kKindKid[kind], e.cells[plan_index(g, s, kind)], [&] { launch_kind(e, kind, b, s, dt); });
   }
   if (s == e.S - 1) {
-    if (g == 0)
+    if (g == 0 && e.lists) {
+      const Engine::LList &O = e.l_oend[e.parity];
+      const sacra_params &p0 = e.stars[0].prm;
+      run(e, K_OUTER, O.cells, [&] {
+        launch_l_outer(e.litems_dev + O.off, O.n, O.max_nx, dt, p0.evolve_spacetime, !p0.hydro_outer, e.stream);
+      });
+    } else if (g == 0)
       for (Star &st : e.stars)
         if (st.prm.geometry == SACRA_CYLINDRICAL) {
           const Lev &L0 = st.lv[0];
@@ -658,6 +845,14 @@ void enqueue_step_sub(Engine &e, Star &st, double dt) {
 void enqueue_step(Engine &e, double dt) {
   if (e.ngroups > 1) {           // a sub-cycled star (single contexts only)
     enqueue_step_sub(e, e.stars[0], dt);
+    return;
+  }
+  if (e.lists) {
+    for (int s = 0; s < e.S; ++s) {
+      enqueue_fill_lists(e, s, dt);
+      enqueue_stage(e, s, dt);
+    }
+    enqueue_restrict_lists(e, dt);
     return;
   }
   for (int s = 0; s < e.S; ++s) {
@@ -878,6 +1073,16 @@ void upload_tables(Engine &e, int max_nx) {
   cudaStreamSynchronize(e.stream);                 // tab lives on the host stack
 }
 
+// items of the level lists (build_lists): per star, at both register parities,
+// ghost fill (2 per level and stage), the outer boundary after the last stage
+// (1), restriction, child parity and parents' parity (1 each per level pair)
+size_t litem_count(const std::vector<sacra_params> &ps) {
+  const size_t S = ps.empty() ? 4 : (ps[0].rk == SACRA_RK4 ? 4 : 3);
+  size_t n = 0;
+  for (const sacra_params &p : ps) n += 2 * (2 * S * (size_t)p.n_levels + 1 + 3 * (size_t)(p.n_levels - 1));
+  return n;
+}
+
 size_t engine_bytes(const std::vector<sacra_params> &ps) {
   size_t n = 0;
   int max_nx = 0;
@@ -886,7 +1091,7 @@ size_t engine_bytes(const std::vector<sacra_params> &ps) {
     max_nx = std::max(max_nx, p.nx);
   }
   return n + round_up((size_t)(max_nx + 8) * (3 * kTabStride + kCartoonW) * 8, 256) + 256 /* dout */ + 256 /* nfb */ +
-         plan_bytes(ps);
+         plan_bytes(ps) + round_up(litem_count(ps) * sizeof(LItem), 256);
 }
 
 sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *stream, void *arena, size_t arena_bytes) {
@@ -950,6 +1155,8 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
   p += round_up((2 * (size_t)e.S + 2) * nl * sizeof(BL), 256);
   e.tiles_dev = (Tile *)p;
   plan_caps(ps, &e.tiles_cap, &e.tune_cap);
+  e.litems_dev = (LItem *)((char *)e.tiles_dev + round_up((e.tiles_cap + e.tune_cap) * sizeof(Tile), 256));
+  e.litems_cap = litem_count(ps);
   for (Star &st : e.stars)
     for (int l = 0; l < st.prm.n_levels; ++l) st.lv[l].nfb = e.nfb;
   upload_tables(e, max_nx);

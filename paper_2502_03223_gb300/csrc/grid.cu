@@ -32,11 +32,10 @@ __device__ __forceinline__ double sgn_z(int f) {
 
 // axis ghosts j in [-7, 0] for rows [1, nz+8]; blockIdx.z: plane (25 metric
 // fields, then the 6 primitives)
-__global__ void k_parity_x(Lev L, double *__restrict__ U) {
-  const int j = -7 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+__device__ __forceinline__ void parity_x_body(const Lev &L, double *__restrict__ U, int bx, int by, int f) {
+  const int j = -7 + (int)(bx * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(by * blockDim.y + threadIdx.y);
   if (j > 0 || k > L.nz + GH) return;
-  const int f = blockIdx.z;
   const int d = cid(L, j, k), s = cid(L, 1 - j, k);
   if (f < NMET) {
     double *u = U + (size_t)f * L.P;
@@ -48,12 +47,13 @@ __global__ void k_parity_x(Lev L, double *__restrict__ U) {
   }
 }
 
+__global__ void k_parity_x(Lev L, double *__restrict__ U) { parity_x_body(L, U, blockIdx.x, blockIdx.y, blockIdx.z); }
+
 // equator ghosts k in [-7, 0] for all columns; blockIdx.z as above
-__global__ void k_parity_z(Lev L, double *__restrict__ U) {
-  const int j = -7 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = -7 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+__device__ __forceinline__ void parity_z_body(const Lev &L, double *__restrict__ U, int bx, int by, int f) {
+  const int j = -7 + (int)(bx * blockDim.x + threadIdx.x);
+  const int k = -7 + (int)(by * blockDim.y + threadIdx.y);
   if (j > L.nx + GH || k > 0) return;
-  const int f = blockIdx.z;
   const int d = cid(L, j, k), s = cid(L, j, 1 - k);
   if (f < NMET) {
     double *u = U + (size_t)f * L.P;
@@ -64,6 +64,8 @@ __global__ void k_parity_z(Lev L, double *__restrict__ U) {
     u[d] = (q == pUZ ? -1.0 : 1.0) * u[s];
   }
 }
+
+__global__ void k_parity_z(Lev L, double *__restrict__ U) { parity_z_body(L, U, blockIdx.x, blockIdx.y, blockIdx.z); }
 
 // planar slab: zero-gradient copy into every ghost cell
 __global__ void k_outflow(Lev L, double *__restrict__ U) {
@@ -87,9 +89,9 @@ __global__ void k_outflow(Lev L, double *__restrict__ U) {
 // (blockIdx.y) that share the interpolation weights.
 constexpr int kOuterGroups = 5;
 
-__global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict__ U, double tau, int metric,
-                        int prims) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void outer_body(const Lev &L, const double *__restrict__ Un, double *__restrict__ U,
+                                           double tau, int metric, int prims, int bx, int group) {
+  int i = bx * blockDim.x + threadIdx.x;
   const int w = L.nx + GH, top = GH * w;
   int j, k;
   if (i < top) {
@@ -111,7 +113,7 @@ __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict
   const double wx[3] = {0.5 * tx * (tx - 1.0), (1.0 - tx) * (1.0 + tx), 0.5 * tx * (tx + 1.0)};
   const double wz[3] = {0.5 * tz * (tz - 1.0), (1.0 - tz) * (1.0 + tz), 0.5 * tz * (tz + 1.0)};
   const int d = cid(L, j, k), c0 = cid(L, i0, k0);
-  for (int f = blockIdx.y; metric && f < NMET; f += kOuterGroups) {
+  for (int f = group; metric && f < NMET; f += kOuterGroups) {
     const double qinf = (f == fW || f == fAL) ? 1.0 : 0.0;
     const double *u = Un + (size_t)f * P + c0;
     const double u0 = u[0] - qinf;
@@ -122,11 +124,16 @@ __global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict
       for (int a = 0; a < 3; ++a) s += wx[a] * wz[b] * (u[(b - 1) * L.px + (a - 1)] - qinf - u0);
     U[(size_t)f * P + d] = qinf + fac * (u0 + s);
   }
-  if (blockIdx.y == 0 && prims) {
+  if (group == 0 && prims) {
     const int sc = cid(L, min(j, L.nx), min(k, L.nz));
 #pragma unroll
     for (int f = 0; f < NPRIM; ++f) L.prim[(size_t)f * P + d] = L.prim[(size_t)f * P + sc];
   }
+}
+
+__global__ void k_outer(Lev L, const double *__restrict__ Un, double *__restrict__ U, double tau, int metric,
+                        int prims) {
+  outer_body(L, Un, U, tau, metric, prims, blockIdx.x, blockIdx.y);
 }
 
 __device__ __forceinline__ double minmod(double a, double b) {
@@ -155,10 +162,10 @@ __device__ __forceinline__ bool buffer_cell(const Lev &L, int lo, int i, int &j,
 
 // Buffer-zone prolongation of the metric (Sec. II.D): 8th-order Lagrange,
 // tensor product over 8x8 parent cells, one thread per (buffer cell, field).
-__global__ void k_prolong_metric(Lev L, Lev Pa, double *__restrict__ U, const double *__restrict__ Up, int lo) {
+__device__ __forceinline__ void prolong_metric_body(const Lev &L, const Lev &Pa, double *__restrict__ U,
+                                                    const double *__restrict__ Up, int lo, int blk, int f) {
   int j, k;
-  if (!buffer_cell(L, lo, blockIdx.x * blockDim.x + threadIdx.x, j, k)) return;
-  const int f = blockIdx.y;
+  if (!buffer_cell(L, lo, blk * blockDim.x + threadIdx.x, j, k)) return;
   const bool ex = (j & 1) == 0, ez = (k & 1) == 0;
   const int mx = ex ? j / 2 : (j + 1) / 2, mz = ez ? k / 2 : (k + 1) / 2;
   const int bx = ex ? mx - 3 : mx - 4, bz = ez ? mz - 3 : mz - 4;
@@ -176,11 +183,16 @@ __global__ void k_prolong_metric(Lev L, Lev Pa, double *__restrict__ U, const do
   U[(size_t)f * L.P + cid(L, j, k)] = u0 + s;
 }
 
+__global__ void k_prolong_metric(Lev L, Lev Pa, double *__restrict__ U, const double *__restrict__ Up, int lo) {
+  prolong_metric_body(L, Pa, U, Up, lo, blockIdx.x, blockIdx.y);
+}
+
 // Buffer-zone primitives by minmod-limited linear prolongation, then the
 // conserved variables from them with the prolongated metric.
-__global__ void k_prolong_hydro(Lev L, Lev Pa, DevParams p, double *__restrict__ U, int lo) {
+__device__ __forceinline__ void prolong_hydro_body(const Lev &L, const Lev &Pa, const DevParams &p,
+                                                   double *__restrict__ U, int lo, int bx) {
   int j, k;
-  if (!buffer_cell(L, lo, blockIdx.x * blockDim.x + threadIdx.x, j, k)) return;
+  if (!buffer_cell(L, lo, bx * blockDim.x + threadIdx.x, j, k)) return;
   const size_t P = L.P, PP = Pa.P;
   const bool ex = (j & 1) == 0, ez = (k & 1) == 0;
   const int mx = ex ? j / 2 : (j + 1) / 2, mz = ez ? k / 2 : (k + 1) / 2;
@@ -204,6 +216,10 @@ __global__ void k_prolong_hydro(Lev L, Lev Pa, DevParams p, double *__restrict__
   prim_to_cons(p, pr, U[(size_t)fW * P + d], g, (j - 0.5) * L.dx, q);
 #pragma unroll
   for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + d] = q[v];
+}
+
+__global__ void k_prolong_hydro(Lev L, Lev Pa, DevParams p, double *__restrict__ U, int lo) {
+  prolong_hydro_body(L, Pa, p, U, lo, blockIdx.x);
 }
 
 // det gt = 1 and tr At = 0 after every stage (Sec. II.B.1):
@@ -351,12 +367,12 @@ void launch_time_interp(const Lev &P, const double *uold, const double *pold, co
 // q as the volume-weighted average of the 2x2 children, the metric by 8th-
 // order Lagrange (nodes shifted inward so that none passes the child edge N).
 // blockIdx.z + f0: the field (metric 0..24, conserved 25..29).
-__global__ void k_restrict(Lev C, Lev Pa, int f0) {
-  const int j = 1 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+__device__ __forceinline__ void restrict_body(const Lev &C, const Lev &Pa, int f0, int blkx, int blky, int plane) {
+  const int j = 1 + (int)(blkx * blockDim.x + threadIdx.x);
+  const int k = 1 + (int)(blky * blockDim.y + threadIdx.y);
   const int nh = Pa.nx / 2;
   if (j > nh || k > nh) return;
-  const int f = f0 + (int)blockIdx.z;
+  const int f = f0 + plane;
   const size_t P = C.P, PP = Pa.P;
   const int d = cid(Pa, j, k);
   const int c00 = cid(C, 2 * j - 1, 2 * k - 1);
@@ -387,17 +403,19 @@ __global__ void k_restrict(Lev C, Lev Pa, int f0) {
   Pa.un[(size_t)f * PP + d] = u0 + s;
 }
 
+__global__ void k_restrict(Lev C, Lev Pa, int f0) { restrict_body(C, Pa, f0, blockIdx.x, blockIdx.y, blockIdx.z); }
+
 // The metric part of the restriction as two passes through shared memory: the
 // x-interpolation of every child row a tile of parent cells needs (each row
 // serves four parent rows), then the z-interpolation of those row values;
 // the same 8 x 8 weights as k_restrict, applied as separable sums.  Block:
 // RX x RZ parent cells of one field (blockIdx.z).
 constexpr int RX = 32, RZ = 8, RROWS = 2 * RZ + 6;
-__global__ void __launch_bounds__(RX * RZ) k_restrict_metric(Lev C, Lev Pa) {
+__device__ __forceinline__ void restrict_metric_body(const Lev &C, const Lev &Pa, int bx, int by, int f) {
   __shared__ double row[RROWS][RX];
   const int nh = Pa.nx / 2, N = C.nx;
-  const int j0 = 1 + (int)blockIdx.x * RX, k0 = 1 + (int)blockIdx.y * RZ;
-  const double *u = C.un + (size_t)blockIdx.z * C.P;
+  const int j0 = 1 + bx * RX, k0 = 1 + by * RZ;
+  const double *u = C.un + (size_t)f * C.P;
   // pass 1: child rows rs .. rs + RROWS - 1 interpolated in x at each parent
   // column; rs = 2 k0 - 4, or N - 7 when the tile holds only the last two rows
   const int rs = min(2 * k0 - 4, N - 7);
@@ -427,13 +445,17 @@ __global__ void __launch_bounds__(RX * RZ) k_restrict_metric(Lev C, Lev Pa) {
   double s = 0.0;
 #pragma unroll
   for (int b = 0; b < 8; ++b) s += wz[b] * row[r0 + b][threadIdx.x];
-  Pa.un[(size_t)blockIdx.z * Pa.P + cid(Pa, j, k)] = s;
+  Pa.un[(size_t)f * Pa.P + cid(Pa, j, k)] = s;
+}
+
+__global__ void __launch_bounds__(RX * RZ) k_restrict_metric(Lev C, Lev Pa) {
+  restrict_metric_body(C, Pa, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // Reflux (Sec. II.D): parent cells next to the child's outer faces get the
 // sum of the fine fluxes (RK-weighted) instead of the coarse flux.
-__global__ void k_reflux(Lev C, Lev Pa, double dt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void reflux_body(const Lev &C, const Lev &Pa, double dt, int bx) {
+  const int i = bx * blockDim.x + threadIdx.x;
   const int nh = Pa.nx / 2;
   if (i >= 2 * nh) return;
   const bool xface = i < nh;
@@ -448,6 +470,8 @@ __global__ void k_reflux(Lev C, Lev Pa, double dt) {
     Pa.un[(size_t)(fQD + v) * Pa.P + d] += dt * (fine - coarse) / vol;
   }
 }
+
+__global__ void k_reflux(Lev C, Lev Pa, double dt) { reflux_body(C, Pa, dt, blockIdx.x); }
 
 // ---------------------------------------------------------------- diagnostics
 
@@ -652,6 +676,82 @@ __global__ void k_diag_final(const double *__restrict__ partials, int n, double 
   if (t == 0)
 #pragma unroll
     for (int q = 0; q < DIAG_Q; ++q) out[q] = acc[q];
+}
+
+// ---------------------------------------------------------------- level-list kernels
+//
+// The same bodies over the items of a level list (all levels of one depth of
+// a batch's stars, say): one launch instead of one per level.  The grid is
+// sized for the largest item; blocks beyond an item's extent do nothing.
+constexpr int kParityPlanes = NMET + NPRIM;
+
+__global__ void kl_parity_x(const LItem *__restrict__ items) {
+  const LItem &it = items[blockIdx.z / kParityPlanes];
+  parity_x_body(it.L, it.B, blockIdx.x, blockIdx.y, blockIdx.z % kParityPlanes);
+}
+__global__ void kl_parity_z(const LItem *__restrict__ items) {
+  const LItem &it = items[blockIdx.z / kParityPlanes];
+  parity_z_body(it.L, it.B, blockIdx.x, blockIdx.y, blockIdx.z % kParityPlanes);
+}
+__global__ void kl_outer(const LItem *__restrict__ items, double tau, int metric, int prims) {
+  const LItem &it = items[blockIdx.z];
+  outer_body(it.L, it.A, it.B, tau, metric, prims, blockIdx.x, blockIdx.y);
+}
+__global__ void kl_prolong_metric(const LItem *__restrict__ items, int full) {
+  const LItem &it = items[blockIdx.z];
+  prolong_metric_body(it.L, it.Pa, it.B, it.A, full ? it.L.nx + 1 : it.L.nx + 5, blockIdx.x, blockIdx.y);
+}
+__global__ void kl_prolong_hydro(const LItem *__restrict__ items, int full) {
+  const LItem &it = items[blockIdx.z];
+  prolong_hydro_body(it.L, it.Pa, it.P, it.B, full ? it.L.nx + 1 : it.L.nx + 5, blockIdx.x);
+}
+__global__ void __launch_bounds__(RX * RZ) kl_restrict_metric(const LItem *__restrict__ items) {
+  const LItem &it = items[blockIdx.z / NMET];
+  restrict_metric_body(it.L, it.Pa, blockIdx.x, blockIdx.y, blockIdx.z % NMET);
+}
+__global__ void kl_restrict(const LItem *__restrict__ items) {
+  const LItem &it = items[blockIdx.z / NCONS];
+  restrict_body(it.L, it.Pa, NMET, blockIdx.x, blockIdx.y, blockIdx.z % NCONS);
+}
+__global__ void kl_reflux(const LItem *__restrict__ items, double dt) {
+  const LItem &it = items[blockIdx.z];
+  reflux_body(it.L, it.Pa, dt, blockIdx.x);
+}
+
+void launch_l_parity_x(const LItem *items, int n, int max_nx, cudaStream_t s) {
+  if (n <= 0) return;
+  kl_parity_x<<<dim3(1, (max_nx + GH + 15) / 16, n * kParityPlanes), dim3(8, 16), 0, s>>>(items);
+}
+
+void launch_l_parity_z(const LItem *items, int n, int max_nx, cudaStream_t s) {
+  if (n <= 0) return;
+  kl_parity_z<<<dim3((max_nx + 2 * GH + 31) / 32, 1, n * kParityPlanes), dim3(32, 8), 0, s>>>(items);
+}
+
+void launch_l_outer(const LItem *items, int n, int max_nx, double tau, int metric, int prims, cudaStream_t s) {
+  if (n <= 0) return;
+  const int cells = GH * (max_nx + GH) + GH * max_nx;
+  kl_outer<<<dim3((cells + 127) / 128, kOuterGroups, n), 128, 0, s>>>(items, tau, metric, prims);
+}
+
+void launch_l_prolong(const LItem *items, int n, int max_nx, int full, cudaStream_t s) {
+  if (n <= 0) return;
+  const int lo = full ? max_nx + 1 : max_nx + 5, w = max_nx + GH;
+  const int cells = ((max_nx + GH) - lo + 1) * w + (w - lo + 1) * (lo - 1);
+  kl_prolong_metric<<<dim3((cells + 127) / 128, NMET, n), 128, 0, s>>>(items, full);
+  kl_prolong_hydro<<<dim3((cells + 127) / 128, 1, n), 128, 0, s>>>(items, full);
+}
+
+void launch_l_restrict(const LItem *items, int n, int max_nx, cudaStream_t s) {
+  if (n <= 0) return;
+  const int nh = max_nx / 2;
+  kl_restrict_metric<<<dim3((nh + RX - 1) / RX, (nh + RZ - 1) / RZ, n * NMET), dim3(RX, RZ), 0, s>>>(items);
+  kl_restrict<<<dim3((nh + 31) / 32, (nh + 3) / 4, n * NCONS), dim3(32, 4), 0, s>>>(items);
+}
+
+void launch_l_reflux(const LItem *items, int n, int max_nx, double dt, cudaStream_t s) {
+  if (n <= 0) return;
+  kl_reflux<<<dim3((max_nx + 127) / 128, 1, n), 128, 0, s>>>(items, dt);
 }
 
 // ---------------------------------------------------------------- host launchers

@@ -473,9 +473,10 @@ __global__ void k_prim2cons_all(Lev L, DevParams p, double *__restrict__ U) {
 }
 
 // primitive recovery on [j0, j1] x [k0, k1] of state U
-__global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0, int j1, int k0, int k1, int skip_corner) {
-  const int j = j0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-  const int k = k0 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
+__device__ __forceinline__ void c2p_region_body(const Lev &L, const DevParams &p, double *__restrict__ U, int j0, int j1,
+                                                int k0, int k1, int skip_corner, int bx, int by) {
+  const int j = j0 + (int)(bx * blockDim.x + threadIdx.x);
+  const int k = k0 + (int)(by * blockDim.y + threadIdx.y);
   if (j > j1 || k > k1 || (skip_corner && j == j1 && k == k1)) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -490,6 +491,25 @@ __global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0,
 #pragma unroll
     for (int v = 0; v < NCONS; ++v) U[(size_t)(fQD + v) * P + id] = q[v];
   L.status[id] = st;
+}
+
+__global__ void k_c2p_region(Lev L, DevParams p, double *__restrict__ U, int j0, int j1, int k0, int k1, int skip_corner) {
+  c2p_region_body(L, p, U, j0, j1, k0, k1, skip_corner, blockIdx.x, blockIdx.y);
+}
+
+// primitive recovery on the parent cells a restriction and reflux changed,
+// [1, N/2 + 1]^2 without the corner, of every item of a level list
+__global__ void kl_c2p_restricted(const LItem *__restrict__ items) {
+  const LItem &it = items[blockIdx.z];
+  const int nh = it.Pa.nx / 2;
+  c2p_region_body(it.Pa, it.P, it.Pa.un, 1, nh + 1, 1, nh + 1, 1, blockIdx.x, blockIdx.y);
+}
+
+void launch_l_c2p_restricted(const LItem *items, int n, int max_nx, cudaStream_t s) {
+  if (n <= 0) return;
+  const int nh = max_nx / 2;                  // the largest parent's N/2
+  dim3 b(32, 4), g((nh + 1 + 31) / 32, (nh + 1 + 3) / 4, n);
+  kl_c2p_restricted<<<g, b, 0, s>>>(items);
 }
 
 // ---------------------------------------------------------------- batched persistent kernels

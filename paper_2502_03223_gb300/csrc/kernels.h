@@ -56,6 +56,24 @@ __device__ __forceinline__ void for_tiles(const Batch &b, F &&f) {
 static_assert(sizeof(BL) % sizeof(int) == 0, "BL is copied as ints");
 
 enum BKind { B_FLUX_X = 0, B_FLUX_Z, B_HYDRO, B_CARTOON, B_DERIVS, B_POINT, B_RK, B_NKIND };
+
+// ---- level lists: one launch of a per-level operation (ghost fill,
+// prolongation, restriction, reflux, recovery) over several levels, e.g. the
+// same depth of every star of a batch; item i is handled by the blocks of
+// grid slice blockIdx.z / (the operation's planes) == i
+struct LItem {
+  Lev L, Pa;                // the level and its parent (restriction: the child and the parent)
+  DevParams P;              // the star's parameters
+  const double *A;          // input state: the parent's stage state (prolongation), U^n (outer boundary)
+  double *B;                // output state: the level's stage state (ghost fill), its U^n (restriction)
+};
+void launch_l_parity_x(const LItem *items, int n, int max_nx, cudaStream_t s);
+void launch_l_parity_z(const LItem *items, int n, int max_nx, cudaStream_t s);        // after the x parity
+void launch_l_outer(const LItem *items, int n, int max_nx, double tau, int metric, int prims, cudaStream_t s);
+void launch_l_prolong(const LItem *items, int n, int max_nx, int full, cudaStream_t s); // metric, then hydro
+void launch_l_restrict(const LItem *items, int n, int max_nx, cudaStream_t s);        // metric, then conserved
+void launch_l_reflux(const LItem *items, int n, int max_nx, double dt, cudaStream_t s);
+void launch_l_c2p_restricted(const LItem *items, int n, int max_nx, cudaStream_t s);
 void launch_b_flux_x(const Batch &b, const DevParams &p, cudaStream_t s);
 void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s);
 void launch_b_hydro_div(const Batch &b, const DevParams &p, cudaStream_t s);
