@@ -338,9 +338,13 @@ namespace sacra {
 // pr: rho, u_x, u_y, u_z, P, eps; q: psi^6 (D, S_x, S_y or x S_y, S_z, E)
 __device__ inline void prim_to_cons(const DevParams &p, const double pr[NPRIM], double W, const Sym3 &gt, double x,
                                     double q[NCONS]) {
-  const Sym3 gi = s3inv(gt, (double *)nullptr);
   const double u[3] = {pr[pUX], pr[pUY], pr[pUZ]};
-  const double w = sqrt(1.0 + W * W * s3quad(gi, u, u));
+  // matter at rest (the atmosphere): w = 1 exactly, no inverse metric needed
+  double w = 1.0;
+  if (u[0] != 0.0 || u[1] != 0.0 || u[2] != 0.0) {
+    const Sym3 gi = s3inv(gt, (double *)nullptr);
+    w = sqrt(1.0 + W * W * s3quad(gi, u, u));
+  }
   const double rho = pr[pRHO], P = pr[pP];
   const double rhw = rho * (1.0 + pr[pEPS] + P / rho) * w;
   const double psi6 = 1.0 / (W * W * W);
@@ -722,15 +726,23 @@ __device__ inline int face_flux(const DevParams &p, int dir, const T pl[5], cons
   const T tL0 = W * Bh * (mi.xx * uL[0] + mi.xy * uL[1] + mi.xz * uL[2]);
   const T tL1 = W * Dh * (m.zz * uL[1] - m.yz * uL[2]);
   const T tL2 = W * Ch * uL[2];
-  const T tR0 = W * Bh * (mi.xx * uR[0] + mi.xy * uR[1] + mi.xz * uR[2]);
-  const T tR1 = W * Dh * (m.zz * uR[1] - m.yz * uR[2]);
-  const T tR2 = W * Ch * uR[2];
+  // equal states on both sides (uniform matter, the atmosphere): the Riemann
+  // fan is the state itself for any solver, so the flux is f - v_int q
+  const bool same = pl[0] == pr[0] && pl[1] == pr[1] && pl[2] == pr[2] && pl[3] == pr[3] && pl[4] == pr[4];
   SRState<T> L, R;
   sr_state(p, pl[0], kDelta ? pl[4] + pref : pl[4], pl[4], tL0, tL1, tL2, L);
-  sr_state(p, pr[0], kDelta ? pr[4] + pref : pr[4], pr[4], tR0, tR1, tR2, R);
   T qL[5], fL[5], qR[5], fR[5];
   sr_qf(L, qL, fL);
-  sr_qf(R, qR, fR);
+  if (same) {
+    R = L;
+    for (int n = 0; n < 5; ++n) { qR[n] = qL[n]; fR[n] = fL[n]; }
+  } else {
+    const T tR0 = W * Bh * (mi.xx * uR[0] + mi.xy * uR[1] + mi.xz * uR[2]);
+    const T tR1 = W * Dh * (m.zz * uR[1] - m.yz * uR[2]);
+    const T tR2 = W * Ch * uR[2];
+    sr_state(p, pr[0], kDelta ? pr[4] + pref : pr[4], pr[4], tR0, tR1, tR2, R);
+    sr_qf(R, qR, fR);
+  }
   const T lamL = fmin(L.lm, R.lm);
   const T lamR = fmax(L.lp, R.lp);
   const T sgxx = W * (mi.xx * Bh);           // W sqrt(gt^xx)
@@ -738,7 +750,9 @@ __device__ inline int face_flux(const DevParams &p, int dir, const T pl[5], cons
 
   T F[5];
   int fb = 0;
-  if (p.solver == SACRA_HLLC) {
+  if (same) {
+    for (int n = 0; n < 5; ++n) F[n] = fL[n] - vint * qL[n];
+  } else if (p.solver == SACRA_HLLC) {
     if (lamL >= vint) {
       for (int n = 0; n < 5; ++n) F[n] = fL[n] - vint * qL[n];
     } else if (lamR <= vint) {
@@ -799,7 +813,7 @@ __device__ inline int face_flux(const DevParams &p, int dir, const T pl[5], cons
       fb = bad ? 1 : 0;
     }
   }
-  if (p.solver != SACRA_HLLC || fb) {
+  if (!same && (p.solver != SACRA_HLLC || fb)) {
     const T cmax = fmax(fabs(lamL - vint), fabs(lamR - vint));
     for (int n = 0; n < 5; ++n)
       F[n] = T(0.5) * ((fL[n] - vint * qL[n]) + (fR[n] - vint * qR[n])) - T(0.5) * cmax * (qR[n] - qL[n]);
