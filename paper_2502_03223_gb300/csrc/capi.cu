@@ -696,7 +696,11 @@ void enqueue_group_stage(Engine &e, int g, int s, double dt, bool reset_parent) 
         cudaMemsetAsync(L.freg + 2 * reg, 0, reg * sizeof(double), e.stream);
       }
     }
-  for (int kind = 0; kind < B_NKIND; ++kind) {
+  // the hydro sources read the first derivatives the derivative pass has
+  // formed, so they follow it
+  static const int kOrder[B_NKIND] = {B_FLUX_X, B_FLUX_Z, B_CARTOON, B_DERIVS, B_HYDRO, B_POINT, B_RK};
+  for (int ko = 0; ko < B_NKIND; ++ko) {
+    const int kind = kOrder[ko];
     // the diagnostics of the state at the start of the step read the
     // derivative scratch and the Ricci scalar the stage has just formed,
     // before the stage update overwrites the primitives

@@ -49,5 +49,34 @@ __device__ __forceinline__ double unit(double c, int E) {
 // |x| rounded down to a bound usable in overflow checks (x ^ sign: |x| or |x| - 1)
 __device__ __forceinline__ long long mag(long long x) { return x ^ (x >> 63); }
 
+// x / 2^k rounded towards minus infinity, for any k >= 0
+__device__ __forceinline__ long long shr(long long x, int k) { return k < 63 ? (x >> k) : (x >> 63); }
+
+// The 6th-order central first-difference numerator 45 (u_1 - u_-1) - 9 (u_2 -
+// u_-2) + (u_3 - u_-3) of the six values u[n s], n = +-1..+-3, exactly on the
+// grid 2^(E - kGrid) of their largest exponent field (E >= 1); E = -1 when a
+// value is not finite.
+__device__ __forceinline__ void diff6(const double *u, int s, long long &num, int &E) {
+  long long b[6];
+#pragma unroll
+  for (int n = 0; n < 3; ++n) {
+    b[2 * n] = bits(u[(n + 1) * s]);
+    b[2 * n + 1] = bits(u[-(n + 1) * s]);
+  }
+  int e = 1;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) e = max(e, expo(b[n]));
+  if (e == 2047) {
+    num = 0;
+    E = -1;
+    return;
+  }
+  long long v[6];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) v[n] = fix(b[n], e);
+  num = 45 * (v[0] - v[1]) - 9 * (v[2] - v[3]) + (v[4] - v[5]);
+  E = e;
+}
+
 }  // namespace fx
 }  // namespace sacra

@@ -3,6 +3,7 @@
 // per-cell flux divergence with cylindrical areas/volumes and the geometric and
 // gravitational sources, primitive recovery, initial conserved variables.
 #include "kernels.h"
+#include "z4c.cuh"
 
 namespace sacra {
 
@@ -348,8 +349,13 @@ __device__ __forceinline__ T cd1(const double *u, int s, T idx) {
 //          + (W^2/2) alpha v_a v_b d_k gt^ab + (alpha/W) v_i v^i d_k W]
 //        (+ alpha W^-3 (S_y vbar^y + P)/x for k = x, cylindrical),
 //   s_E  = W^-3 (alpha K^ij S_ij - rho h w^2 v^i d_i alpha), s_D = s_Sphi = 0.
+// DS: the level's derivative scratch of the same stage (the derivative pass
+// has run), whose first derivatives of alpha, W, beta^i and gt_ij replace the
+// six-point differences here in the FP64 form; nullptr: the differences are
+// formed here.
 template <typename T>
-__device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax, int j, int k) {
+__device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax,
+                                               int kmax, int j, int k, const void *DS = nullptr) {
   if (j > jmax || k > kmax) return;
   const size_t P = L.P;
   const int id = cid(L, j, k);
@@ -394,22 +400,29 @@ __device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p,
   // gt^ac v_c, used in v_a v_b d gt^ab = -(gt^ac v_c)(gt^bd v_d) d gt_cd
   T gv[3];
   s3vec(gi, vd, gv);
+  // FP64 sources with an FP64 derivative scratch take its first derivatives;
+  // the FP32 sources keep their own differences (the arithmetic of the mixed form)
+  const bool use_ds = DS != nullptr && sizeof(T) == 8 && !(p.mixed & SACRA_MIXED_Z4C);
+  // d_x (e = 0) or d_z (e = 1) of metric field f
+  auto d1 = [&](int f, int e) -> T {
+    if (use_ds) return reinterpret_cast<const double *>(DS)[(size_t)(DS_D1 + 3 * d1_of(f) + (e == 0 ? 0 : 2)) * P + id];
+    return cd1<T>(U + (size_t)f * P + id, st[e], i60[e]);
+  };
   T src[2], dal[2];
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
-    const int s = st[e];
-    dal[e] = cd1<T>(U + (size_t)fAL * P + id, s, i60[e]);
-    const T dW = cd1<T>(U + (size_t)fW * P + id, s, i60[e]);
+    dal[e] = d1(fAL, e);
+    const T dW = d1(fW, e);
     T vdb = T(0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) vdb += vd[i] * cd1<T>(U + (size_t)(fBX + i) * P + id, s, i60[e]);
+    for (int i = 0; i < 3; ++i) vdb += vd[i] * d1(fBX + i, e);
     Sym3T<T> dg;
-    dg.xx = cd1<T>(U + (size_t)fHXX * P + id, s, i60[e]);
-    dg.xy = cd1<T>(U + (size_t)fHXY * P + id, s, i60[e]);
-    dg.xz = cd1<T>(U + (size_t)fHXZ * P + id, s, i60[e]);
-    dg.yy = cd1<T>(U + (size_t)fHYY * P + id, s, i60[e]);
-    dg.yz = cd1<T>(U + (size_t)fHYZ * P + id, s, i60[e]);
-    dg.zz = cd1<T>(U + (size_t)fHZZ * P + id, s, i60[e]);
+    dg.xx = d1(fHXX, e);
+    dg.xy = d1(fHXY, e);
+    dg.xz = d1(fHXZ, e);
+    dg.yy = d1(fHYY, e);
+    dg.yz = d1(fHYZ, e);
+    dg.zz = d1(fHZZ, e);
     const T vvdgi = -s3quad(dg, gv, gv);
     const T dalW3 = iW3 * dal[e] - T(3) * al * iW3 * iW * dW;
     src[e] = Pp * dalW3 - iW3 * rhw2 * (dal[e] - vdb + T(0.5) * W * W * al * vvdgi + al * iW * vv * dW);
@@ -554,7 +567,8 @@ __global__ void __launch_bounds__(256, 2) kb_flux_z_st(Batch b, DevParams p) {
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_hydro_rhs(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
-    hydro_rhs_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+    hydro_rhs_cell<T>(q.L, q.P, q.U, q.jmax, q.kmax, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y,
+                      q.P.evolve ? q.DS : nullptr);
   });
 }
 

@@ -257,11 +257,6 @@ __global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__rest
 // AK advection + KO of all 25 fields.
 __constant__ int kD1Fields[16] = {fW, fHXX, fHXY, fHXZ, fHYY, fHYZ, fHZZ, fKH, fGX, fGY, fGZ, fTH, fAL, fBX, fBY, fBZ};
 __constant__ int kD2Fields[11] = {fW, fHXX, fHXY, fHXZ, fHYY, fHYZ, fHZZ, fAL, fBX, fBY, fBZ};
-// DS_RS: the Ricci scalar of the pointwise pass, written when the diagnostics
-// of the step's starting state are formed in the same stage.  The plane index
-// counts FP64 planes in both forms: in the FP32 form it lies past the FP32
-// planes of the same allocation (DS_N FP64 planes).
-constexpr int DS_D1 = 0, DS_D2 = 48, DS_AK = 114, DS_RS = 139, DS_N = 140;
 
 __device__ __forceinline__ bool y_zero(int f) {
   return f == fW || f == fKH || f == fTH || f == fAL || f == fGZ || f == fBZ || f == fBBZ || f == fHZZ || f == fAZZ;
@@ -305,12 +300,6 @@ __device__ __forceinline__ T fdko(const double *u, int s) {
 // FP32; the cartoon planes it reads are FP32 as well.
 constexpr int DTX = 32, DTZ = 8, DHX = DTX + 8, DHZ = DTZ + 8;
 
-__host__ __device__ constexpr int d1_of(int f) {
-  return f <= fHZZ ? f : (f == fKH ? 7 : (f >= fGX && f <= fGZ ? 8 + f - fGX : (f == fTH ? 11 : (f == fAL ? 12 : (f >= fBX && f <= fBZ ? 13 + f - fBX : -1)))));
-}
-__host__ __device__ constexpr int d2_of(int f) {
-  return f <= fHZZ ? f : (f == fAL ? 7 : (f >= fBX && f <= fBZ ? 8 + f - fBX : -1));
-}
 // calls fn(std::integral_constant<int, F>) for F = F0 .. NMET - 1 (compile-time field loop)
 template <int F0>
 struct FieldLoop {
@@ -469,19 +458,21 @@ __device__ __forceinline__ double zdiff_num(const double *c, int sz) {
 template <typename T>
 __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
                                                 double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k,
-                                                double *sdz = nullptr, int j0 = 0) {
+                                                long long *sdn = nullptr, int *sde = nullptr, int j0 = 0) {
   static_assert(sizeof(T) == 8, "the FP32 form is z4c_derivs_f32_tile");
-  // XCH (sdz given): the mixed derivative d_xz is the x-difference of the
-  // z-difference numerators of the neighbouring columns, which the block
-  // exchanges through shared memory (row of blockDim.x + 6 columns per thread
-  // row: each thread its own column, the three threads at either end of a
-  // row one halo column each); every thread of the block runs the field loop
-  // (it has barriers)
-  const bool xch = sdz != nullptr;
+  // XCH (sdn, sde given): the mixed derivative d_xz is the x-difference of the
+  // z-difference numerators of the neighbouring columns, exact integers on
+  // each column's own grid (numerator, exponent), which the block exchanges
+  // through shared memory (row of blockDim.x + 6 columns per thread row: each
+  // thread its own column, the three threads at either end of a row one halo
+  // column each); every thread of the block runs the field loop (it has
+  // barriers)
+  const bool xch = sdn != nullptr;
   const bool active = j <= jmax && k <= kmax;
   if (!xch && !active) return;
   const int bw = (int)blockDim.x + 6, tx = (int)threadIdx.x;
-  double *srow = xch ? sdz + (size_t)threadIdx.y * bw : nullptr;
+  long long *rown = xch ? sdn + (size_t)threadIdx.y * bw : nullptr;
+  int *rowe = xch ? sde + (size_t)threadIdx.y * bw : nullptr;
   const size_t P = L.P;
   const int id = cid(L, j, k);
   const int sz = L.px;
@@ -503,7 +494,8 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
     const int a1 = kD1Of[f], a2 = kD2Of[f];
     const bool yz = y_zero(f);
     const double *u = U + (size_t)f * P + id;
-    double cown = 0.0;                 // z-difference numerator of this thread's column
+    long long cn = 0;                  // z-difference numerator of this thread's column ...
+    int ce = 1;                        // ... on the grid 2^(ce - kGrid); -1: not finite
     if (active) {
       long long X[9], Z[9];
 #pragma unroll
@@ -514,14 +506,16 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
       int E = 0;
 #pragma unroll
       for (int n = 0; n < 9; ++n) E = max(E, max(fx::expo(X[n]), fx::expo(Z[n])));
-      bool fast = E >= 128 && E < 2047, zero = false;
+      bool fast = E < 2047, zero = false;
       long long d1xn = 0, d1zn = 0, d2xn = 0, d2zn = 0, kxn = 0, kzn = 0, lxn = 0, lzn = 0;
       if (E == 0) {                                   // zeros (or subnormals: FP64 form)
         long long o = 0;
 #pragma unroll
         for (int n = 0; n < 9; ++n) o |= (X[n] | Z[n]) & ~(1ll << 63);
         zero = o == 0;
-      } else if (fast) {
+        fast = false;
+      }
+      if (fast) {
 #pragma unroll
         for (int n = 0; n < 9; ++n) {
           X[n] = fx::fix(X[n], E);
@@ -537,6 +531,8 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
         // on the values) is checked on its pair sums
         d1xn = 45 * ox1 - 9 * ox2 + ox3;
         d1zn = 45 * oz1 - 9 * oz2 + oz3;
+        cn = d1zn;
+        ce = E;
         if (a2 >= 0) {
           // the sums wrap (unsigned) where the check fails; the FP64 form then replaces them
           typedef unsigned long long u64;
@@ -568,7 +564,6 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
           if (a1 >= 0) {
             DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (double)d1xn * fx::unit(i60x, E);
             DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (double)d1zn * fx::unit(i60z, E);
-            cown = (double)d1zn * fx::unit(1.0, E);
           }
           if (a2 >= 0) {
             DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = (double)d2xn * fx::unit(i180x, E);
@@ -600,8 +595,8 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
         if (a1 >= 0) {
           DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (45.0 * (Dx[5] - Dx[3]) - 9.0 * (Dx[6] - Dx[2]) + (Dx[7] - Dx[1])) * i60x;
           DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (45.0 * (Dz[5] - Dz[3]) - 9.0 * (Dz[6] - Dz[2]) + (Dz[7] - Dz[1])) * i60z;
-          cown = zdiff_num(u, sz);
         }
+        if (a2 >= 0 && xch && !zero) fx::diff6(u, sz, cn, ce);
         if (a2 >= 0) {
           DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = (270.0 * (Dx[5] + Dx[3]) - 27.0 * (Dx[6] + Dx[2]) + 2.0 * (Dx[7] + Dx[1])) * i180x;
           DS[(size_t)(DS_D2 + 6 * a2 + 5) * P + id] = (270.0 * (Dz[5] + Dz[3]) - 27.0 * (Dz[6] + Dz[2]) + 2.0 * (Dz[7] + Dz[1])) * i180z;
@@ -625,31 +620,65 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
       }
       DS[(size_t)(DS_AK + f) * P + id] = adv;
     } else if (xch && a2 >= 0 && own_col) {
-      cown = zdiff_num(u, sz);          // a column right of the region that cells of the region use
+      fx::diff6(u, sz, cn, ce);         // a column right of the region that cells of the region use
     }
     if (a2 >= 0) {
       double dxz = 0.0;
+      bool fp64 = !xch;
       if (xch) {
         __syncthreads();                                 // the previous field's row is read
-        srow[tx + 3] = own_col ? cown : 0.0;
+        rown[tx + 3] = own_col ? cn : 0;
+        rowe[tx + 3] = own_col ? ce : 1;
         if (tx < 3 || tx >= (int)blockDim.x - 3) {
           const int e = tx < 3 ? tx : tx + 6;            // halo slot: columns j0 - 3 .. j0 - 1, j0 + bx .. + 2
           const int jc = j0 - 3 + e;
-          srow[e] = (k <= kmax && jc <= jmax + 3) ? zdiff_num(U + (size_t)f * P + cid(L, jc, k), sz) : 0.0;
+          long long hn = 0;
+          int he = 1;
+          if (k <= kmax && jc <= jmax + 3) fx::diff6(U + (size_t)f * P + cid(L, jc, k), sz, hn, he);
+          rown[e] = hn;
+          rowe[e] = he;
         }
         __syncthreads();
         if (active) {
-          const double *r = srow + tx + 3;                 // r[n]: z-difference numerator at column j + n
-          dxz = 45.0 * (r[1] - r[-1]) - 9.0 * (r[2] - r[-2]) + (r[3] - r[-3]);
+          // the six neighbouring numerators on one grid, 54 bits below the
+          // largest of them (the weighted sum then stays below 2^62): exact for
+          // numerators within 2^54 of the largest, combined exactly
+          const long long *rn = rown + tx + 3;
+          const int *re = rowe + tx + 3;
+          int top = -100000;
+          bool fin = true;
+#pragma unroll
+          for (int n = -3; n <= 3; ++n)
+            if (n != 0) {
+              fin = fin && re[n] >= 0;
+              if (rn[n] != 0) top = max(top, re[n] + 64 - __clzll(fx::mag(rn[n])));
+            }
+          if (!fin) {
+            fp64 = true;
+          } else if (top > -100000) {
+            const int G = top - 54;
+            long long v[7];
+#pragma unroll
+            for (int n = -3; n <= 3; ++n)
+              if (n != 0) {
+                const int sh = re[n] - G;
+                v[n + 3] = sh >= 0 ? (long long)((unsigned long long)rn[n] << sh) : fx::shr(rn[n], -sh);
+              }
+            const long long c = 45 * (v[4] - v[2]) - 9 * (v[5] - v[1]) + (v[6] - v[0]);
+            dxz = (double)c * fx::unit(ixz, G);
+          }
         }
-      } else if (active) {
+      }
+      if (active && fp64) {
+        dxz = 0.0;
 #pragma unroll
         for (int n = 1; n <= 3; ++n) {
           const double w = n == 1 ? 45.0 : (n == 2 ? -9.0 : 1.0);
           dxz += w * (zdiff_num(u + n, sz) - zdiff_num(u - n, sz));
         }
+        dxz *= ixz;
       }
-      if (active) DS[(size_t)(DS_D2 + 6 * a2 + 2) * P + id] = dxz * ixz;
+      if (active) DS[(size_t)(DS_D2 + 6 * a2 + 2) * P + id] = dxz;
     }
   }
   if (!active) return;
@@ -674,11 +703,12 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
 template <typename T>
 __global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const double *__restrict__ U,
                                                      double *__restrict__ DS, int jmax, int kmax, int cyl) {
-  __shared__ double sdz[(32 + 6) * 4];   // the launch shape is 32 x 4
+  __shared__ long long sdn[(32 + 6) * 4];   // the launch shape is 32 x 4
+  __shared__ int sde[(32 + 6) * 4];
   const int j0 = blockIdx.x * blockDim.x + 1;
   const bool xch = blockDim.x == 32 && blockDim.y == 4;
   z4c_derivs_cell<T>(L, p, U, DS, jmax, kmax, cyl, j0 + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
-                     xch ? sdz : nullptr, j0);
+                     xch ? sdn : nullptr, xch ? sde : nullptr, j0);
 }
 
 __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,
@@ -824,12 +854,13 @@ __global__ void __launch_bounds__(128, 3) kb_cartoon_f32(Batch b, const double *
 
 constexpr int kDxzRow = 304;   // (blockDim.x + 6) * blockDim.y for every tuned shape up to 256 threads
 __global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
-  __shared__ double sdz[kDxzRow];
+  __shared__ long long sdn[kDxzRow];
+  __shared__ int sde[kDxzRow];
   const int cyl = p.geometry == SACRA_CYLINDRICAL;
   const bool xch = ((int)blockDim.x + 6) * (int)blockDim.y <= kDxzRow;
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     z4c_derivs_cell<double>(q.L, q.P, q.U, reinterpret_cast<double *>(q.DS), q.jmax, q.kmax, cyl, tl.j0 + threadIdx.x,
-                            tl.k0 + threadIdx.y, xch ? sdz : nullptr, tl.j0);
+                            tl.k0 + threadIdx.y, xch ? sdn : nullptr, xch ? sde : nullptr, tl.j0);
   });
 }
 

@@ -8,6 +8,23 @@
 
 namespace sacra {
 
+// Derivative scratch of a level (planes of stride P): DS_D1 + 3 a + k the
+// first derivative d_k (x, y, z) of field slot a = d1_of(f) (16 fields),
+// DS_D2 + 6 a + q the second derivatives (pair order xx, xy, xz, yy, yz, zz)
+// of slot a = d2_of(f) (11 fields), DS_AK + f advection plus Kreiss-Oliger of
+// all 25 fields.  DS_RS: the Ricci scalar of the pointwise pass, written when
+// the diagnostics of the step's starting state are formed in the same stage;
+// the plane index counts FP64 planes in both forms (in the FP32 form it lies
+// past the FP32 planes of the same allocation of DS_N FP64 planes).
+constexpr int DS_D1 = 0, DS_D2 = 48, DS_AK = 114, DS_RS = 139, DS_N = 140;
+
+__host__ __device__ constexpr int d1_of(int f) {
+  return f <= fHZZ ? f : (f == fKH ? 7 : (f >= fGX && f <= fGZ ? 8 + f - fGX : (f == fTH ? 11 : (f == fAL ? 12 : (f >= fBX && f <= fBZ ? 13 + f - fBX : -1)))));
+}
+__host__ __device__ constexpr int d2_of(int f) {
+  return f <= fHZZ ? f : (f == fAL ? 7 : (f >= fBX && f <= fBZ ? 8 + f - fBX : -1));
+}
+
 // symmetric-pair index of (i, j)
 __device__ __forceinline__ int sp(int i, int j) {
   return (i == j) ? (i == 0 ? 0 : (i == 1 ? 3 : 5)) : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 4));
