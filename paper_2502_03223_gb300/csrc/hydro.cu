@@ -131,20 +131,13 @@ __device__ __forceinline__ void ppm_tile_states(const double *sm, int t, int lin
   }
 }
 
-// The FP32 face interpolation as an increment over the cell value u[0],
-// from exact differences (integer splits, no FP64 instruction).
-__device__ __forceinline__ float face6_delta(const double *u, int s, F2 &c) {
-  c = split_f64(u[0]);
-  return (3.0f * f32_diff(split_f64(u[-2 * s]), c) - 25.0f * f32_diff(split_f64(u[-s]), c)
-          + 150.0f * f32_diff(split_f64(u[s]), c) - 25.0f * f32_diff(split_f64(u[2 * s]), c)
-          + 3.0f * f32_diff(split_f64(u[3 * s]), c)) * (1.0f / 256.0f);
-}
-
 // The same face in FP32 (mixed precision), arranged so that rounding scales
 // with what varies across the face, not with rho or P:
 //  * the pressure is reconstructed as the offset P - P_j (PPM commutes with a
 //    constant shift) from exact differences, and the HLLC solver carries it
 //    as that offset (face_flux with pref = P_j);
+//  * the metric at the face is the cell value plus an FP32 increment formed
+//    from exact differences (integer splits, no FP64 instruction);
 //  * the normal momentum flux then lacks g_f P_j, g = alpha W^-3 at the face;
 //    it is split as g_j P_j (cell j, FP64: the large part, which cancels
 //    between the faces of a cell in FP64) plus (g_f - g_j) P_j in FP32 from
@@ -152,60 +145,132 @@ __device__ __forceinline__ float face6_delta(const double *u, int s, F2 &c) {
 //      g_f / g_j - 1 = [x - 3y - 3y^2 - y^3] / (1 + y)^3,
 //      x = dalpha / alpha_j, y = dW / W_j.
 // The only FP64 instructions are the 5 of g_j P_j and the final addition.
-template <int DIR>
-__device__ inline void flux_at_f32(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
-                                   double out[NCONS], int *fb) {
-  const size_t P = L.P;
-  const int s = DIR == 0 ? 1 : L.px;
-  const int id = cid(L, j, k);
-  const int pf[4] = {pRHO, pUX, pUY, pUZ};
-  float pl[5], pr[5];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const double *a = L.prim + (size_t)pf[v] * P + id;
-    const float c[6] = {f32_of(a[-2 * s]), f32_of(a[-s]), f32_of(a[0]), f32_of(a[s]), f32_of(a[2 * s]), f32_of(a[3 * s])};
-    ppm_pair(c, pl[v], pr[v]);
+//
+// The FP32 form hands a face to the FP64 solver where FP32 rounding could
+// change a discrete branch: a stencil with a strong density or pressure
+// contrast (a stellar surface, the atmosphere: reconstructed values of order
+// eps_32 * max decide the positivity fallback there, and the contact pressure
+// of a near-vacuum Riemann problem is of that order too), and every face where
+// the FP32 HLLC fails.  Elsewhere the branches have wide margins.
+constexpr float kMixedContrast = 1e-3f;
+
+// The FP32 inputs of a face come from a source with two views of cell j + n,
+// n = -2..3 along the face normal: pair(q, n), the split (hi, lo) of slot q
+// (0 rho, 1 P, 2 alpha, 3 W, 4-6 beta^i, 7-12 h_ij), and single(v, n), u_i
+// rounded to FP32 (v = 0, 1, 2).  Both sources give the same values.
+constexpr int kF32Pair = 13, kF32Single = 3, kF32Slots = 2 * kF32Pair + kF32Single;
+__device__ __forceinline__ int f32_pair_field(int q) {
+  return q == 0 ? -1 - pRHO : (q == 1 ? -1 - pP : (q == 2 ? fAL : (q == 3 ? fW : (q < 7 ? fBX + q - 4 : fHXX + q - 7))));
+}
+
+// per-face loads from the level's arrays
+struct F32Global {
+  const double *prim, *U;
+  size_t P;
+  int id, s;
+  __device__ __forceinline__ F2 pair(int q, int n) const {
+    const int f = f32_pair_field(q);
+    return split_f64(f < 0 ? prim[(size_t)(-1 - f) * P + id + n * s] : U[(size_t)f * P + id + n * s]);
   }
-  const double *aP = L.prim + (size_t)pP * P + id;
-  const double Pj = aP[0];
-  const F2 Ps = split_f64(Pj);
+  __device__ __forceinline__ float single(int v, int n) const { return f32_of(prim[(size_t)(pUX + v) * P + id + n * s]); }
+};
+
+// the staged tile (f32_tile): slot-major, then line, then cell along the normal
+struct F32Staged {
+  const float *sm;
+  int nli, nc, line, c0;     // c0: the tile index of cell j
+  __device__ __forceinline__ F2 pair(int q, int n) const {
+    const float *a = sm + (size_t)((2 * q) * nli + line) * nc + c0 + n;
+    return F2{a[0], a[(size_t)nli * nc]};
+  }
+  __device__ __forceinline__ float single(int v, int n) const {
+    return sm[(size_t)((2 * kF32Pair + v) * nli + line) * nc + c0 + n];
+  }
+};
+
+// face interpolation (3,-25,150,150,-25,3)/256 of slot q as an increment over
+// the cell value, from exact differences; c: the cell's split
+template <class Src>
+__device__ __forceinline__ float face6_delta(const Src &src, int q, F2 &c) {
+  c = src.pair(q, 0);
+  return (3.0f * f32_diff(src.pair(q, -2), c) - 25.0f * f32_diff(src.pair(q, -1), c)
+          + 150.0f * f32_diff(src.pair(q, 1), c) - 25.0f * f32_diff(src.pair(q, 2), c)
+          + 3.0f * f32_diff(src.pair(q, 3), c)) * (1.0f / 256.0f);
+}
+
+// The FP32 flux of face (j, k) from src; false where the face goes to the
+// FP64 solver (a contrast in the stencil, or a failed FP32 HLLC: *fb set)
+template <int DIR, class Src>
+__device__ inline bool flux_f32(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                const Src &src, double out[NCONS], int *fb) {
+  float rmin = src.pair(0, -2).hi, rmax = rmin, qmin = src.pair(1, -2).hi, qmax = qmin;
+#pragma unroll
+  for (int n = -1; n <= 3; ++n) {
+    const float rv = src.pair(0, n).hi, qv = src.pair(1, n).hi;
+    rmin = fminf(rmin, rv); rmax = fmaxf(rmax, rv);
+    qmin = fminf(qmin, qv); qmax = fmaxf(qmax, qv);
+  }
+  if (!(rmin > kMixedContrast * rmax && qmin > kMixedContrast * qmax)) return false;
+  float pl[5], pr[5];
+  {
+    float c[6];
+#pragma unroll
+    for (int n = -2; n <= 3; ++n) {
+      const F2 r = src.pair(0, n);
+      c[n + 2] = r.hi + r.lo;
+    }
+    ppm_pair(c, pl[0], pr[0]);
+  }
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    float c[6];
+#pragma unroll
+    for (int n = -2; n <= 3; ++n) c[n + 2] = src.single(v, n);
+    ppm_pair(c, pl[v + 1], pr[v + 1]);
+  }
+  const F2 Ps = src.pair(1, 0);
   const float pref = Ps.hi + Ps.lo;
   {
-    const float c[6] = {f32_diff(split_f64(aP[-2 * s]), Ps), f32_diff(split_f64(aP[-s]), Ps), 0.0f,
-                        f32_diff(split_f64(aP[s]), Ps), f32_diff(split_f64(aP[2 * s]), Ps), f32_diff(split_f64(aP[3 * s]), Ps)};
+    const float c[6] = {f32_diff(src.pair(1, -2), Ps), f32_diff(src.pair(1, -1), Ps), 0.0f,
+                        f32_diff(src.pair(1, 1), Ps), f32_diff(src.pair(1, 2), Ps), f32_diff(src.pair(1, 3), Ps)};
     ppm_pair(c, pl[4], pr[4]);
     if (!(pl[0] > 0.0f) || !(pl[4] + pref > 0.0f)) {
+      const F2 r = src.pair(0, 0);
+      pl[0] = r.hi + r.lo;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) pl[v] = f32_of(L.prim[(size_t)pf[v] * P + id]);
+      for (int v = 0; v < 3; ++v) pl[v + 1] = src.single(v, 0);
       pl[4] = 0.0f;
     }
     if (!(pr[0] > 0.0f) || !(pr[4] + pref > 0.0f)) {
+      const F2 r = src.pair(0, 1);
+      pr[0] = r.hi + r.lo;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) pr[v] = f32_of(L.prim[(size_t)pf[v] * P + id + s]);
+      for (int v = 0; v < 3; ++v) pr[v + 1] = src.single(v, 1);
       pr[4] = c[3];
     }
   }
   F2 ca, cw, cb;
-  const float da = face6_delta(U + (size_t)fAL * P + id, s, ca);
-  const float dW = face6_delta(U + (size_t)fW * P + id, s, cw);
+  const float da = face6_delta(src, 2, ca);
+  const float dW = face6_delta(src, 3, cw);
   const float aj = ca.hi + ca.lo, Wj = cw.hi + cw.lo;
   const float alpha = aj + da, W = Wj + dW;
   float beta[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const float d = face6_delta(U + (size_t)(fBX + i) * P + id, s, cb);
+    const float d = face6_delta(src, 4 + i, cb);
     beta[i] = (cb.hi + cb.lo) + d;
   }
   Sym3T<float> g;
   float gv[6];
 #pragma unroll
   for (int a = 0; a < 6; ++a) {
-    const float d = face6_delta(U + (size_t)(fHXX + a) * P + id, s, cb);
+    const float d = face6_delta(src, 7 + a, cb);
     gv[a] = (cb.hi + cb.lo) + d;
   }
   g.xx = 1.0f + gv[0]; g.xy = gv[1]; g.xz = gv[2]; g.yy = 1.0f + gv[3]; g.yz = gv[4]; g.zz = 1.0f + gv[5];
   float o[5];
   *fb = face_flux<float>(p, DIR, pl, pr, alpha, beta, W, g, o, pref);
+  if (*fb) return false;
   // (g_f - g_j) P_j in FP32
   const float x = da / aj, y = dW / Wj, y1 = 1.0f + y;
   const float rel = (x - y * (3.0f + y * (3.0f + y))) / (y1 * y1 * y1);
@@ -215,39 +280,76 @@ __device__ inline void flux_at_f32(const Lev &L, const DevParams &p, const doubl
 #pragma unroll
   for (int v = 0; v < NCONS; ++v) out[v] = f64_of(o[v]);
   // g_j P_j in FP64
-  const double aj64 = U[(size_t)fAL * P + id], Wj64 = U[(size_t)fW * P + id];
+  const size_t P = L.P;
+  const int id = cid(L, j, k);
+  const double aj64 = U[(size_t)fAL * P + id], Wj64 = U[(size_t)fW * P + id], Pj = L.prim[(size_t)pP * P + id];
   out[n] += aj64 * Pj / (Wj64 * Wj64 * Wj64);
+  return true;
 }
 
-// The flux of one face in arithmetic T.  The FP32 form hands a face to the
-// FP64 solver where FP32 rounding could change a discrete branch: a stencil
-// with a strong density or pressure contrast (a stellar surface, the
-// atmosphere: reconstructed values of order eps_32 * max decide the
-// positivity fallback there, and the contact pressure of a near-vacuum
-// Riemann problem is of that order too), and every face where the FP32 HLLC
-// fails.  Elsewhere the branches have wide margins.
-constexpr float kMixedContrast = 1e-3f;
-
-template <typename T, int DIR>
-__device__ inline void flux_face(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
-                                 double out[NCONS], int *fb) {
-  if constexpr (sizeof(T) == 4) {
-    const int s = DIR == 0 ? 1 : L.px;
-    const double *r = L.prim + (size_t)pRHO * L.P + cid(L, j, k);
-    const double *q = L.prim + (size_t)pP * L.P + cid(L, j, k);
-    float rmin = split_f64(r[-2 * s]).hi, rmax = rmin, qmin = split_f64(q[-2 * s]).hi, qmax = qmin;
-#pragma unroll
-    for (int n = -1; n <= 3; ++n) {
-      const float rv = split_f64(r[n * s]).hi, qv = split_f64(q[n * s]).hi;
-      rmin = fminf(rmin, rv); rmax = fmaxf(rmax, rv);
-      qmin = fminf(qmin, qv); qmax = fmaxf(qmax, qv);
-    }
-    if (rmin > kMixedContrast * rmax && qmin > kMixedContrast * qmax) {
-      flux_at_f32<DIR>(L, p, U, j, k, out, fb);
-      if (!*fb) return;
-    }
-  }
+// the FP64 solver for the faces the FP32 form hands over (few): out of line,
+// so that its registers do not weigh on the FP32 path
+template <int DIR>
+__device__ __noinline__ void flux_at_f64_call(const Lev &L, const DevParams &p, const double *__restrict__ U, int j,
+                                              int k, double out[NCONS], int *fb) {
   flux_at_f64<DIR>(L, p, U, j, k, out, fb);
+}
+
+// The flux of one face in arithmetic T (FP32: from src, else the FP64 solver).
+template <typename T, int DIR, class Src>
+__device__ inline void flux_face(const Lev &L, const DevParams &p, const double *__restrict__ U, int j, int k,
+                                 const Src &src, double out[NCONS], int *fb) {
+  if constexpr (sizeof(T) == 4) {
+    if (flux_f32<DIR>(L, p, U, j, k, src, out, fb)) return;
+    flux_at_f64_call<DIR>(L, p, U, j, k, out, fb);
+  } else {
+    flux_at_f64<DIR>(L, p, U, j, k, out, fb);
+  }
+}
+
+// The FP32 inputs of a tile's faces staged through shared memory: every cell
+// of the tile's lines that a face of the region uses (cells a0-2 .. a0+nal+2
+// along the normal) split once, instead of once per face that reads it (six).
+// Layout and views as F32Staged; kF32Slots * nli * (nal + 5) floats.
+__host__ __device__ constexpr int f32_tile_floats(int nal, int nli) { return kF32Slots * nli * (nal + 5); }
+
+template <int DIR>
+__device__ __forceinline__ void f32_tile(const Lev &L, const double *__restrict__ U, int j0, int k0, int jmax,
+                                         int kmax, float *sm) {
+  const int nal = DIR == 0 ? (int)blockDim.x : (int)blockDim.y, nli = DIR == 0 ? (int)blockDim.y : (int)blockDim.x;
+  const int nth = (int)(blockDim.x * blockDim.y), tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+  const int nc = nal + 5;
+  const int a0 = DIR == 0 ? j0 : k0, l0 = DIR == 0 ? k0 : j0;
+  const int amax = DIR == 0 ? jmax : kmax, lmax = DIR == 0 ? kmax : jmax;
+  const int per = nli * nc;
+  // one cell per thread and pass, its sixteen loads issued together; cells
+  // contiguous in memory go to neighbouring threads (along x for x-faces,
+  // across the lines (columns j) for z-faces)
+  for (int cell = tid; cell < per; cell += nth) {
+    const int c = DIR == 0 ? cell % nc : cell / nli, line = DIR == 0 ? cell / nc : cell % nli;
+    const int along = a0 - 2 + c;
+    if (l0 + line > lmax || along > amax + 3) continue;
+    const int j = DIR == 0 ? along : l0 + line, k = DIR == 0 ? l0 + line : along;
+    const int id = cid(L, j, k);
+    float *o = sm + (size_t)line * nc + c;
+    double u[kF32Pair + kF32Single];
+#pragma unroll
+    for (int q = 0; q < kF32Pair; ++q) {
+      const int f = f32_pair_field(q);
+      u[q] = f < 0 ? L.prim[(size_t)(-1 - f) * L.P + id] : U[(size_t)f * L.P + id];
+    }
+#pragma unroll
+    for (int v = 0; v < kF32Single; ++v) u[kF32Pair + v] = L.prim[(size_t)(pUX + v) * L.P + id];
+#pragma unroll
+    for (int q = 0; q < kF32Pair; ++q) {
+      const F2 v = split_f64(u[q]);
+      o[(size_t)(2 * q) * per] = v.hi;
+      o[(size_t)(2 * q + 1) * per] = v.lo;
+    }
+#pragma unroll
+    for (int v = 0; v < kF32Single; ++v) o[(size_t)(2 * kF32Pair + v) * per] = f32_of(u[kF32Pair + v]);
+  }
+  __syncthreads();
 }
 
 // x-faces j+1/2 for j in [0, jmax], rows [1, kmax].  Stores area-weighted
@@ -256,7 +358,7 @@ __device__ inline void flux_face(const Lev &L, const DevParams &p, const double 
 template <typename T>
 __device__ __forceinline__ void flux_x_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent, int j, int k, double wbp,
-                                                 const double *stage_sm = nullptr) {
+                                                 const double *stage_sm = nullptr, const float *stage32 = nullptr) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
@@ -264,8 +366,13 @@ __device__ __forceinline__ void flux_x_cell(const Lev &L, const DevParams &p, co
     double pl[5], pr[5];
     ppm_tile_states<0>(stage_sm, threadIdx.x, threadIdx.y, pl, pr);
     flux_states_f64<0>(L, p, U, j, k, pl, pr, f, &fb);
+  } else if (stage32) {
+    const int nal = 0 == 0 ? (int)blockDim.x : (int)blockDim.y, nli = 0 == 0 ? (int)blockDim.y : (int)blockDim.x;
+    const F32Staged src{stage32, nli, nal + 5, (int)threadIdx.y, (int)threadIdx.x + 2};
+    flux_face<float, 0>(L, p, U, j, k, src, f, &fb);
   } else {
-    flux_face<T, 0>(L, p, U, j, k, f, &fb);
+    const F32Global src{L.prim, U, L.P, cid(L, j, k), 1};
+    flux_face<T, 0>(L, p, U, j, k, src, f, &fb);
   }
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
   const double xf = j * L.dx;
@@ -294,7 +401,7 @@ __global__ void __launch_bounds__(128) k_flux_x(Lev L, DevParams p, const double
 template <typename T>
 __device__ __forceinline__ void flux_z_cell(const Lev &L, const DevParams &p, const double *__restrict__ U, int jmax, int kmax,
                                                  double wb, int has_child, int has_parent, int j, int k, double wbp,
-                                                 const double *stage_sm = nullptr) {
+                                                 const double *stage_sm = nullptr, const float *stage32 = nullptr) {
   if (j > jmax || k > kmax) return;
   double f[NCONS];
   int fb;
@@ -302,8 +409,13 @@ __device__ __forceinline__ void flux_z_cell(const Lev &L, const DevParams &p, co
     double pl[5], pr[5];
     ppm_tile_states<1>(stage_sm, threadIdx.y, threadIdx.x, pl, pr);
     flux_states_f64<1>(L, p, U, j, k, pl, pr, f, &fb);
+  } else if (stage32) {
+    const int nal = 1 == 0 ? (int)blockDim.x : (int)blockDim.y, nli = 1 == 0 ? (int)blockDim.y : (int)blockDim.x;
+    const F32Staged src{stage32, nli, nal + 5, (int)threadIdx.x, (int)threadIdx.y + 2};
+    flux_face<float, 1>(L, p, U, j, k, src, f, &fb);
   } else {
-    flux_face<T, 1>(L, p, U, j, k, f, &fb);
+    const F32Global src{L.prim, U, L.P, cid(L, j, k), L.px};
+    flux_face<T, 1>(L, p, U, j, k, src, f, &fb);
   }
   const bool cyl = p.geometry == SACRA_CYLINDRICAL;
   // equatorial mirror plane: D, S_x, S_phi, E are even in z, their z-fluxes vanish there
@@ -564,6 +676,26 @@ __global__ void __launch_bounds__(256, 2) kb_flux_z_st(Batch b, DevParams p) {
   });
 }
 
+// FP32 faces with their inputs staged through shared memory (dynamic buffer
+// of f32_tile_floats(...) floats)
+__global__ void __launch_bounds__(256, 2) kb_flux_x_st32(Batch b, DevParams p) {
+  extern __shared__ float f32_sm[];
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    f32_tile<0>(q.L, q.U, tl.j0, tl.k0, q.jmax, q.kmax, f32_sm);
+    flux_x_cell<float>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x,
+                       tl.k0 + threadIdx.y, q.wbp, nullptr, f32_sm);
+  });
+}
+
+__global__ void __launch_bounds__(256, 2) kb_flux_z_st32(Batch b, DevParams p) {
+  extern __shared__ float f32_sm[];
+  for_tiles(b, [&](const BL &q, const Tile &tl) {
+    f32_tile<1>(q.L, q.U, tl.j0, tl.k0, q.jmax, q.kmax, f32_sm);
+    flux_z_cell<float>(q.L, q.P, q.U, q.jmax, q.kmax, q.wb, q.has_child, q.has_parent, tl.j0 + threadIdx.x,
+                       tl.k0 + threadIdx.y, q.wbp, nullptr, f32_sm);
+  });
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_hydro_rhs(Batch b, DevParams p) {
   for_tiles(b, [&](const BL &q, const Tile &tl) {
@@ -573,24 +705,34 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 0) kb_hydro_rhs(Batc
 }
 
 // The FP64 faces always stage their PPM (one kernel per direction, so every
-// tile shape gives the same values); the buffer of every candidate shape
-// stays within the 48 KB a launch may take without opting in, and a shape
-// beyond it would keep the per-face form.
+// tile shape gives the same values), the FP32 faces their split inputs (the
+// staged and per-face forms give the same values); a shape whose buffer would
+// pass the 48 KB a launch may take without opting in keeps the per-face form.
 constexpr size_t kPpmSmemMax = 48 * 1024;
 
 void launch_b_flux_x(const Batch &b, const DevParams &p, cudaStream_t s) {
   if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_FLUX) {
+    const size_t sm = f32_tile_floats(b.block.x, b.block.y) * sizeof(float);
+    if (sm <= kPpmSmemMax) kb_flux_x_st32<<<b.grid, b.block, sm, s>>>(b, p);
+    else kb_flux_x<float><<<b.grid, b.block, 0, s>>>(b, p);
+    return;
+  }
   const size_t sm = ppm_tile_doubles(b.block.x, b.block.y) * sizeof(double);
-  if (p.mixed & SACRA_MIXED_FLUX) kb_flux_x<float><<<b.grid, b.block, 0, s>>>(b, p);
-  else if (sm <= kPpmSmemMax) kb_flux_x_st<<<b.grid, b.block, sm, s>>>(b, p);
+  if (sm <= kPpmSmemMax) kb_flux_x_st<<<b.grid, b.block, sm, s>>>(b, p);
   else kb_flux_x<double><<<b.grid, b.block, 0, s>>>(b, p);
 }
 
 void launch_b_flux_z(const Batch &b, const DevParams &p, cudaStream_t s) {
   if (b.ntiles <= 0) return;
+  if (p.mixed & SACRA_MIXED_FLUX) {
+    const size_t sm = f32_tile_floats(b.block.y, b.block.x) * sizeof(float);
+    if (sm <= kPpmSmemMax) kb_flux_z_st32<<<b.grid, b.block, sm, s>>>(b, p);
+    else kb_flux_z<float><<<b.grid, b.block, 0, s>>>(b, p);
+    return;
+  }
   const size_t sm = ppm_tile_doubles(b.block.y, b.block.x) * sizeof(double);
-  if (p.mixed & SACRA_MIXED_FLUX) kb_flux_z<float><<<b.grid, b.block, 0, s>>>(b, p);
-  else if (sm <= kPpmSmemMax) kb_flux_z_st<<<b.grid, b.block, sm, s>>>(b, p);
+  if (sm <= kPpmSmemMax) kb_flux_z_st<<<b.grid, b.block, sm, s>>>(b, p);
   else kb_flux_z<double><<<b.grid, b.block, 0, s>>>(b, p);
 }
 

@@ -129,3 +129,40 @@ def test_mixed_uniform_state_exact():
     for f in range(30):
         a = gpu.read(0, S.STATE_STEP, f)[G:G + cfg.nz, G:G + cfg.nx]
         assert np.array_equal(a, before[f][G:G + cfg.nz, G:G + cfg.nx]), f
+
+
+def test_staged_fp32_faces_equal_the_per_face_form():
+    """The FP32 face fluxes of a stage (inputs split once per cell of a tile
+    and staged through shared memory) equal, bit for bit, the per-face form
+    that splits every input of every face again (the allocation-free entry
+    point runs that form): the same FP32 arithmetic on the same values.  A
+    moving bump gives faces with velocity; the stellar surface gives faces
+    that go to the FP64 solver."""
+    import torch
+    cfg, tov = W.tov_config("staged32", rho_c=1.28e-3, n_levels=1, N=64, dx_fine=0.5, rk=0)
+    cfg = dataclasses.replace(cfg, precision=S.MIXED_FLUX | S.MIXED_SOURCES)
+    d = W.tov_level_data(cfg, tov, 0)
+    X, Z = W.cell_centres(cfg, 0)
+    bump = np.exp(-((X - 4.0) ** 2 + (Z - 3.0) ** 2) / 4.0)
+    d[26] = 0.1 * bump * X / (np.abs(X) + 1.0)
+    d[28] = 0.05 * bump * Z / (np.abs(Z) + 1.0)
+    sim = S.Sacra(cfg)
+    sim.set_initial_data(0, S.PRIM_METRIC, d)
+    sim.fill(0, cfg.dt)
+    P = sim.px * sim.pz
+    state = np.stack([sim.read(0, S.STATE_STEP, f) for f in range(30)]).reshape(30 * P)
+    prims = np.stack([sim.read(0, S.PRIMS, f) for f in range(6)]).reshape(6 * P)
+    sim.rk_stage(0, cfg.dt)
+    ref = np.stack([sim.read(0, S.RHS, 25 + v) for v in range(5)])
+    dev = torch.device("cuda")
+    out = torch.full((5 * P,), float("nan"), dtype=torch.float64, device=dev)
+    rc = S.hydro_rhs_noalloc(cfg, 0, torch.from_numpy(state).to(dev).data_ptr(),
+                             torch.from_numpy(prims).to(dev).data_ptr(), out.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(5, sim.pz, sim.px)
+    for v in range(5):
+        a = got[v][G:G + cfg.nz, G:G + cfg.nx]
+        b = ref[v][G:G + cfg.nz, G:G + cfg.nx]
+        assert np.array_equal(a, b), (v, float(np.max(np.abs(a - b))))
