@@ -54,13 +54,14 @@ UNIT = "cell-updates/s"
 # rotation and plane differences folded into one 9-point sum per output (591
 # per cell of the plane patch).  Pointwise kernels (no stencil redundancy):
 # the FP64 operations their formulation executes per unit, from ncu's
-# instruction counters (dfma x 2 + dmul + dadd), the stage update at the
-# migration star's recovery iteration counts.  Units: a cell of the update
-# region; a face for the flux kernels; a cell of the plane patch for the
-# cartoon kernel.
+# instruction counters (dfma x 2 + dmul + dadd) on stage 0 of the migration
+# star's second step: they include what the data decide (faces between equal
+# states take the state's own flux, matter at rest skips its Lorentz factor,
+# the recovery's iteration counts).  Units: a cell of the update region; a face
+# for the flux kernels; a cell of the plane patch for the cartoon kernel.
 METHOD_FLOPS = {
-    "k_z4c_derivs": 2139.0, "k_cartoon": 591.0, "k_z4c_point": 2001.0, "k_flux_x": 756.0,
-    "k_flux_z": 784.0, "k_hydro_rhs": 563.0, "k_rk_update": 463.0,
+    "k_z4c_derivs": 2139.0, "k_cartoon": 591.0, "k_z4c_point": 2001.0, "k_flux_x": 508.0,
+    "k_flux_z": 536.0, "k_hydro_rhs": 391.0, "k_rk_update": 396.0,
 }
 NOMINAL_FP64_TFLOPS = 1.25
 
@@ -330,10 +331,35 @@ def timed_region(sim, nsteps, dt, dist, with_diag):
     return ev0.elapsed_time(ev1), sim.launch_count - n0, diag, clocks
 
 
+def snapshot(sim, cfg):
+    """The state of every level (host copies, the layout set_initial_data RAW takes)."""
+    out = []
+    for l in range(cfg.n_levels):
+        a = np.empty(30 * sim.px * sim.pz, dtype=np.float64)
+        sim.read_level(l, a)
+        out.append(a)
+    return out
+
+
+def restore(sim, snap, dt, warm=2):
+    """Back to a snapshot (primitives recovered from it), then `warm` graph steps."""
+    from paper_2502_03223_gb300 import sacra2d as S
+    for l, a in enumerate(snap):
+        sim.set_initial_data(l, S.RAW, a)
+    for _ in range(warm):
+        sim.step(dt, 1, use_graph=True)
+    sim.sync()
+
+
 def bench_context(cfg, datas, args, dist, ws, repeats, repeat_steps, steps=None, tune=True):
     """Build a context of cfg, warm it up, autotune it (outside the timed
     regions), then time `steps` steps (the line's region) and `repeats` more
-    regions of `repeat_steps` steps each.  Returns (sim, result dict)."""
+    regions of `repeat_steps` steps each.  The star evolves (the migration
+    star sheds matter into the atmosphere, which moves work between kernels),
+    so every repeat starts from the state the line's region started from (a
+    snapshot, restored outside the timed region): the median is over the same
+    stretch of evolution.  Returns (sim, result dict); result["_snap"] holds
+    the snapshot when repeats > 0."""
     from paper_2502_03223_gb300 import sacra2d as S
     steps = args.steps if steps is None else steps
     sim = S.Sacra(cfg)
@@ -350,6 +376,9 @@ def bench_context(cfg, datas, args, dist, ws, repeats, repeat_steps, steps=None,
     sim.sync()
     diag0 = sim.constraints() if lockstep else None
     cps = cell_updates_per_step(cfg)
+    snap = snapshot(sim, cfg) if repeats > 0 else None
+    if snap is not None:
+        restore(sim, snap, dt)     # the line's region starts from the snapshot too
     ms, launches, diag_in, clocks = timed_region(sim, steps, dt, dist, lockstep)
     ms = max_over_ranks(dist, ms)
     res = {"value": ws * cps * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
@@ -358,15 +387,18 @@ def bench_context(cfg, datas, args, dist, ws, repeats, repeat_steps, steps=None,
     if repeats > 0:
         vals, rclk = [], []
         for _ in range(repeats):
+            restore(sim, snap, dt)
             rms, _, _, rc = timed_region(sim, repeat_steps, dt, dist, lockstep)
             rms = max_over_ranks(dist, rms)
             vals.append(ws * cps * repeat_steps / (rms * 1e-3))
             rclk.append(rc.get("sm_mhz"))
-        res["repeats"] = {"n": repeats, "steps_each": repeat_steps, "median_value": float(np.median(vals)),
+        res["repeats"] = {"n": repeats, "steps_each": repeat_steps, "from": "the line's starting state (restored)",
+                          "median_value": float(np.median(vals)),
                           "values": vals, "median_ms_per_step": ws * cps / float(np.median(vals)) * 1e3,
                           "sm_mhz": rclk}
     res["_diag_in"] = diag_in
     res["_diag0"] = diag0
+    res["_snap"] = snap
     return sim, res
 
 
@@ -618,7 +650,10 @@ def run_native(args, dist, rank, ws, local):
            "steps": e2e_steps, "what": "per step: all levels' state host->device (pinned), one step with its "
                                        "diagnostics read back, all levels' evolved state device->host (pinned)"}
 
-    # ---- per-kernel device time (eager launches bracketed by CUDA events)
+    # ---- per-kernel device time (eager launches bracketed by CUDA events), from
+    # the timed regions' starting state
+    if r64.get("_snap") is not None:
+        restore(sim, r64["_snap"], cfg.dt)
     sim.profile(True)
     prof_steps = max(2, min(args.steps, 5))
     for _ in range(prof_steps):
@@ -662,6 +697,8 @@ def run_native(args, dist, rank, ws, local):
 
     # ---- the same per-kernel breakdown of the mixed-precision step
     if msim is not None:
+        if rmx.get("_snap") is not None:
+            restore(msim, rmx["_snap"], cfg.dt)
         msim.profile(True)
         for _ in range(prof_steps):
             msim.step_constraints(cfg.dt, 1, use_graph=False)
