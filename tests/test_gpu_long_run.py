@@ -12,7 +12,7 @@ import pytest
 from paper_2502_03223_gb300 import sacra2d as S
 from paper_2502_03223_gb300 import workloads as W
 
-from gpu_common import G, both
+from gpu_common import G, STATE_GROUPS, both, group_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -58,17 +58,19 @@ def test_rho_l1_after_100_steps_every_level(kind, rk):
         b = orc.read(l, 2, 0)[G:G + cfg.nz, G:G + cfg.nx]
         errs.append(float(np.abs(a - b).sum() / np.abs(b).sum()))
     # the metric after 100 steps, for the record: the largest difference per
-    # field relative to the field's own largest magnitude on the level
-    met = 0.0
+    # field relative to the largest magnitude of its physical group on the
+    # level (the y-components of a star without rotation are rounding noise on
+    # both sides, so their own maximum is no scale)
+    met, where = 0.0, None
     for l in range(cfg.n_levels):
+        B = [orc.read(l, 0, f)[G:G + cfg.nz, G:G + cfg.nx] for f in range(30)]
         for f in range(25):
-            b = orc.read(l, 0, f)[G:G + cfg.nz, G:G + cfg.nx]
             a = gpu.read(l, S.STATE_STEP, f)[G:G + cfg.nz, G:G + cfg.nx]
-            s = float(np.max(np.abs(b)))
-            if s > 0:
-                met = max(met, float(np.max(np.abs(a - b))) / s)
-    print("%s %s: rho L1 per level %s; worst metric field difference %.2e of its scale"
-          % (kind, "RK4" if rk == 0 else "SSP-RK3", " ".join("%.2e" % e for e in errs), met))
+            s = group_scale(B, STATE_GROUPS, f)
+            if s > 0 and float(np.max(np.abs(a - B[f]))) / s > met:
+                met, where = float(np.max(np.abs(a - B[f]))) / s, (l, f)
+    print("%s %s: rho L1 per level %s; worst metric difference %.2e of its group scale (level, field %s)"
+          % (kind, "RK4" if rk == 0 else "SSP-RK3", " ".join("%.2e" % e for e in errs), met, where))
     assert max(errs) <= 1e-9, errs
     gpu.close()
     orc.close()
