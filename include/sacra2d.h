@@ -254,6 +254,16 @@ sacra_status sacra_hydro_rhs_noalloc(const sacra_params *p, int level, const dou
    update); SACRA_ERR_ARG past the last kind. */
 sacra_status sacra_tune(sacra_ctx *c, int reps);
 sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *tile_y, int *blocks_per_sm);
+/* Pins kind `kind`'s launch configuration instead of tuning it: the tile
+   shape tile_x x tile_y, one of the autotuner's candidates (32x4, 64x2, 16x8,
+   128x1 for every kind; 32x8 and 64x4 also for kinds 0, 1, 2 and 4, whose
+   kernels take 256 threads; the FP32 derivative pass of the mixed form
+   accepts only its fixed shape), and the persistent grid size blocks_per_sm,
+   one of 1, 2, 3, 4, 6, 8, 12.  A step's results do not depend on these
+   choices.  Drops the context's captured CUDA graphs (the next graph step
+   captures anew).  Errors: SACRA_ERR_ARG for a kind, shape or grid size
+   outside those lists. */
+sacra_status sacra_set_tuning(sacra_ctx *c, int kind, int tile_x, int tile_y, int blocks_per_sm);
 
 /* ---- Learned seed of the primitive recovery (no counterpart in the paper).
    A 9 -> 64 -> 64 -> 1 tanh network (BF16 weights, FP32 arithmetic) predicts
@@ -325,6 +335,7 @@ sacra_status sacra_batch_read_state(sacra_batch *b, int star, int level, int whi
 sacra_status sacra_batch_constraints(sacra_batch *b, int star, sacra_diag *out);
 sacra_status sacra_batch_tune(sacra_batch *b, int reps);
 sacra_status sacra_batch_get_tuning(const sacra_batch *b, int kind, int *tile_x, int *tile_y, int *blocks_per_sm);
+sacra_status sacra_batch_set_tuning(sacra_batch *b, int kind, int tile_x, int tile_y, int blocks_per_sm);
 sacra_status sacra_batch_sync(sacra_batch *b);
 long long sacra_batch_launch_count(const sacra_batch *b);
 sacra_status sacra_batch_profile(sacra_batch *b, int enable);

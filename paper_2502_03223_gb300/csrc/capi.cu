@@ -1394,6 +1394,28 @@ sacra_status get_tuning(const Engine &e, int kind, int *tile_x, int *tile_y, int
   return SACRA_OK;
 }
 
+// pins one kind's launch configuration to a candidate of the autotuner
+sacra_status set_tuning(Engine &e, int kind, int tile_x, int tile_y, int blocks_per_sm) {
+  if (kind < 0 || kind >= B_NKIND) return SACRA_ERR_ARG;
+  bool shape_ok = false, m_ok = false;
+  if (fixed_shape(e, kind)) {
+    const Shape f = kind_shape(e, kind);
+    shape_ok = f.x == tile_x && f.y == tile_y;
+  } else if (max_threads(kind) >= 256) {
+    for (const Shape &sh : kShapes256) shape_ok = shape_ok || (sh.x == tile_x && sh.y == tile_y);
+  } else {
+    for (const Shape &sh : kShapes128) shape_ok = shape_ok || (sh.x == tile_x && sh.y == tile_y);
+  }
+  for (int m : kBlocksPerSm) m_ok = m_ok || m == blocks_per_sm;
+  if (!shape_ok || !m_ok) return SACRA_ERR_ARG;
+  drop_graphs(e);
+  if (!fixed_shape(e, kind)) e.cfg[kind].shape = Shape{tile_x, tile_y};
+  e.cfg[kind].blocks_per_sm = blocks_per_sm;
+  const sacra_status st = upload_plan(e);
+  if (st != SACRA_OK) return st;
+  return cuda_check(e, "set_tuning");
+}
+
 sacra_status set_profile(Engine &e, int enable) {
   e.prof = enable != 0;
   e.recs.clear();
@@ -1565,6 +1587,10 @@ sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *ti
   return c ? get_tuning(c->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
 }
 
+sacra_status sacra_set_tuning(sacra_ctx *c, int kind, int tile_x, int tile_y, int blocks_per_sm) {
+  return c ? set_tuning(c->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
+}
+
 size_t sacra_mlp_bytes(void) { return sizeof(MlpNet); }
 
 sacra_status sacra_mlp_collect(sacra_ctx *c, float *dev_tuples, long long capacity, long long *n) {
@@ -1653,6 +1679,10 @@ sacra_status sacra_batch_tune(sacra_batch *b, int reps) { return b ? tune(b->e, 
 
 sacra_status sacra_batch_get_tuning(const sacra_batch *b, int kind, int *tile_x, int *tile_y, int *blocks_per_sm) {
   return b ? get_tuning(b->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
+}
+
+sacra_status sacra_batch_set_tuning(sacra_batch *b, int kind, int tile_x, int tile_y, int blocks_per_sm) {
+  return b ? set_tuning(b->e, kind, tile_x, tile_y, blocks_per_sm) : SACRA_ERR_ARG;
 }
 
 sacra_status sacra_batch_sync(sacra_batch *b) { return b ? sync(b->e) : SACRA_ERR_ARG; }

@@ -161,13 +161,58 @@ __device__ __forceinline__ void deltas_ten(float c1, float sn, const float u[5],
   d[4] = sn * u[2] + c1 * u[4] + (sn * s[2] + c * s[4]);
 }
 
-__device__ __forceinline__ void cartoon_f32_cell(const Lev &L, const double *__restrict__ U, const double *__restrict__ tab,
-                                                     int tab_stride, int j, int k) {
+// The nine x-neighbours u(x_{jj-4+n}, z_k), n = 0..8, of a cell's stencil as
+// FP32 splits: read and split per cell (Cartoon32Global) or from a tile's
+// row staged in shared memory (Cartoon32Staged); both give the same values.
+struct Cartoon32Global {
+  const double *U;
+  size_t P;
+  int c0;                  // cid(jj - 4, k)
+  __device__ __forceinline__ F2 at(int a, int n) const { return split_f64(U[(size_t)kCartoonFields[a] * P + c0 + n]); }
+};
+struct Cartoon32Staged {
+  const float *sm;         // [2 a (+1 for lo)][row][column], columns from the tile's base column
+  int per, nc, row, c0;    // per = rows * nc; c0: the column of jj - 4
+  __device__ __forceinline__ F2 at(int a, int n) const {
+    const float *h = sm + (size_t)(2 * a) * per + (size_t)row * nc + c0 + n;
+    return F2{h[0], h[per]};
+  }
+};
+
+// the tile's stencil columns, base = (smallest jj of the tile) - 4 .. base + bx + 7
+__host__ __device__ constexpr int cartoon32_tile_floats(int bx, int by) { return 2 * 20 * by * (bx + 8); }
+__device__ __forceinline__ int cartoon32_base(int j0) { return (j0 >= 1 ? j0 : 1) - 4; }
+
+__device__ __forceinline__ void cartoon32_tile(const Lev &L, const double *__restrict__ U, int j0, int k0, float *sm) {
+  const int bx = (int)blockDim.x, by = (int)blockDim.y, nc = bx + 8, per = by * nc;
+  const int nth = bx * by, tid = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+  const int base = cartoon32_base(j0);
+  const size_t P = L.P;
+  for (int e = tid; e < per; e += nth) {              // one stencil point per thread and pass, its 20 fields together
+    const int c = e % nc, row = e / nc;
+    const int j = base + c, k = k0 + row;
+    if (j > L.nx + GH || k > L.nz + 7) continue;      // past every stencil of the region's cells
+    const int id = cid(L, j, k);
+    double u[20];
+#pragma unroll
+    for (int a = 0; a < 20; ++a) u[a] = U[(size_t)kCartoonFields[a] * P + id];
+#pragma unroll
+    for (int a = 0; a < 20; ++a) {
+      const F2 v = split_f64(u[a]);
+      sm[(size_t)(2 * a) * per + e] = v.hi;
+      sm[(size_t)(2 * a + 1) * per + e] = v.lo;
+    }
+  }
+  __syncthreads();
+}
+
+template <class Src>
+__device__ __forceinline__ void cartoon_f32_cell(const Lev &L, const Src &src, const double *__restrict__ tab,
+                                                 int tab_stride, int j, int k) {
   if (j > L.nx + 4 || k > L.nz + 7) return;
   const bool flip = j <= 0;
   const int jj = flip ? 1 - j : j;
   const size_t P = L.P;
-  const int c0 = cid(L, jj, k);
   float w[3][9], cm1[3], sn[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
@@ -181,12 +226,11 @@ __device__ __forceinline__ void cartoon_f32_cell(const Lev &L, const double *__r
   float u0[20], sv[3][20];
 #pragma unroll
   for (int a = 0; a < 20; ++a) {
-    const double *u = U + (size_t)kCartoonFields[a] * P + c0 - 4;
-    const F2 c = split_f64(u[4]);
+    const F2 c = src.at(a, 4);
     u0[a] = c.hi + c.lo;
     float dn[9];
 #pragma unroll
-    for (int n = 0; n < 9; ++n) dn[n] = n == 4 ? 0.0f : f32_diff(split_f64(u[n]), c);
+    for (int n = 0; n < 9; ++n) dn[n] = n == 4 ? 0.0f : f32_diff(src.at(a, n), c);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       float acc = 0.0f;
@@ -247,7 +291,10 @@ __device__ __forceinline__ void cartoon_f32_cell(const Lev &L, const double *__r
 
 __global__ void __launch_bounds__(128) k_cartoon_f32(Lev L, const double *__restrict__ U, const double *__restrict__ tab,
                                                      int tab_stride) {
-  cartoon_f32_cell(L, U, tab, tab_stride, blockIdx.x * blockDim.x + threadIdx.x - 2, blockIdx.y * blockDim.y + threadIdx.y - 2);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x - 2, k = blockIdx.y * blockDim.y + threadIdx.y - 2;
+  if (j > L.nx + 4 || k > L.nz + 7) return;
+  const Cartoon32Global src{U, L.P, cid(L, j <= 0 ? 1 - j : j, k) - 4};
+  cartoon_f32_cell(L, src, tab, tab_stride, j, k);
 }
 
 // ---------------------------------------------------------------- derivative pass
@@ -846,9 +893,16 @@ __global__ void __launch_bounds__(128) kb_cartoon_f64(Batch b, const double *__r
   });
 }
 
+// FP32 cartoon planes, every tile's stencil rows split once into shared
+// memory (dynamic buffer of cartoon32_tile_floats(...) floats)
 __global__ void __launch_bounds__(128, 3) kb_cartoon_f32(Batch b, const double *__restrict__ tab, int tab_stride) {
+  extern __shared__ float c32_sm[];
   for_tiles(b, [&](const BL &q, const Tile &tl) {
-    cartoon_f32_cell(q.L, q.U, tab, tab_stride, tl.j0 + threadIdx.x, tl.k0 + threadIdx.y);
+    cartoon32_tile(q.L, q.U, tl.j0, tl.k0, c32_sm);
+    const int j = tl.j0 + threadIdx.x, jj = j <= 0 ? 1 - j : j;
+    const int nc = (int)blockDim.x + 8;
+    const Cartoon32Staged src{c32_sm, (int)blockDim.y * nc, nc, (int)threadIdx.y, jj - 4 - cartoon32_base(tl.j0)};
+    cartoon_f32_cell(q.L, src, tab, tab_stride, j, tl.k0 + threadIdx.y);
   });
 }
 
@@ -876,7 +930,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 0) kb_z4c_point(Batc
 void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int tab_stride, const double *tabw,
                       cudaStream_t s) {
   if (b.ntiles <= 0) return;
-  if (p.mixed & SACRA_MIXED_Z4C) kb_cartoon_f32<<<b.grid, b.block, 0, s>>>(b, tab, tab_stride);
+  if (p.mixed & SACRA_MIXED_Z4C)
+    kb_cartoon_f32<<<b.grid, b.block, cartoon32_tile_floats(b.block.x, b.block.y) * sizeof(float), s>>>(b, tab, tab_stride);
   else kb_cartoon_f64<<<b.grid, b.block, 0, s>>>(b, tabw);
 }
 

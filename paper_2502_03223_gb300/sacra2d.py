@@ -27,10 +27,10 @@ STATE_STEP, STATE_STAGE, PRIMS, RHS, STATUS = 0, 1, 2, 3, 4
 EXPORTS = ["sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
            "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_read_level",
            "sacra_constraints", "sacra_sync", "sacra_launch_count", "sacra_profile", "sacra_profile_get", "sacra_hydro_rhs_noalloc", "sacra_tune",
-           "sacra_get_tuning", "sacra_destroy", "sacra_last_error",
+           "sacra_get_tuning", "sacra_set_tuning", "sacra_destroy", "sacra_last_error",
            "sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
            "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
-           "sacra_batch_sync", "sacra_batch_launch_count", "sacra_batch_profile", "sacra_batch_profile_get",
+           "sacra_batch_set_tuning", "sacra_batch_sync", "sacra_batch_launch_count", "sacra_batch_profile", "sacra_batch_profile_get",
            "sacra_batch_destroy", "sacra_batch_last_error", "sacra_mlp_bytes", "sacra_mlp_collect",
            "sacra_mlp_train", "sacra_mlp_grad", "sacra_set_mlp", "sacra_c2p_counting", "sacra_c2p_counts",
            "sacra_batch_set_mlp", "sacra_batch_mlp_collect"]
@@ -95,6 +95,8 @@ def load(path: str = LIB_PATH):
     L.sacra_tune.restype = C.c_int
     L.sacra_get_tuning.argtypes = [vp, C.c_int, ip, ip, ip]
     L.sacra_get_tuning.restype = C.c_int
+    L.sacra_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+    L.sacra_set_tuning.restype = C.c_int
     L.sacra_destroy.argtypes = [vp]
     L.sacra_last_error.argtypes = [vp]
     L.sacra_last_error.restype = C.c_char_p
@@ -108,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.sacra_batch_constraints.argtypes = [vp, C.c_int, C.POINTER(SacraDiag)]
     L.sacra_batch_tune.argtypes = [vp, C.c_int]
     L.sacra_batch_get_tuning.argtypes = [vp, C.c_int, ip, ip, ip]
+    L.sacra_batch_set_tuning.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
     L.sacra_batch_sync.argtypes = [vp]
     L.sacra_batch_launch_count.argtypes = [vp]
     L.sacra_batch_launch_count.restype = C.c_longlong
@@ -133,7 +136,7 @@ def load(path: str = LIB_PATH):
         getattr(L, name).restype = C.c_int
     for name in ("sacra_batch_arena_bytes", "sacra_init_batch", "sacra_batch_set_initial_data", "sacra_batch_step",
                  "sacra_batch_read_state", "sacra_batch_constraints", "sacra_batch_tune", "sacra_batch_get_tuning",
-                 "sacra_batch_sync", "sacra_batch_profile", "sacra_batch_profile_get"):
+                 "sacra_batch_set_tuning", "sacra_batch_sync", "sacra_batch_profile", "sacra_batch_profile_get"):
         getattr(L, name).restype = C.c_int
     for name in ("sacra_arena_bytes", "sacra_init_grid", "sacra_set_initial_data", "sacra_regrid_ghosts",
                  "sacra_rk_stage", "sacra_step", "sacra_step_constraints", "sacra_read_state", "sacra_read_level",
@@ -329,6 +332,11 @@ class Sacra:
             out[name] = (x.value, y.value, m.value)
         return out
 
+    def set_tuning(self, kind, tile_x, tile_y, blocks_per_sm):
+        """Pin one kernel kind's tile shape and persistent grid size (kind: index or name)."""
+        k = KIND_NAMES.index(kind) if isinstance(kind, str) else int(kind)
+        self._chk(self._L.sacra_set_tuning(self._c, k, tile_x, tile_y, blocks_per_sm), "set_tuning")
+
 
 def mlp_train(tuples, steps=2000, batch_blocks=32, lr=3e-3, seed=1, record_loss=False, stream=None, kmin=0.0):
     """Train the recovery seed on the GPU.  tuples: a CUDA float32 tensor of
@@ -475,6 +483,11 @@ class SacraBatch:
             self._chk(self._L.sacra_batch_get_tuning(self._b, k, C.byref(x), C.byref(y), C.byref(m)), "get_tuning")
             out[name] = (x.value, y.value, m.value)
         return out
+
+    def set_tuning(self, kind, tile_x, tile_y, blocks_per_sm):
+        """Pin one kernel kind's tile shape and persistent grid size (kind: index or name)."""
+        k = KIND_NAMES.index(kind) if isinstance(kind, str) else int(kind)
+        self._chk(self._L.sacra_batch_set_tuning(self._b, k, tile_x, tile_y, blocks_per_sm), "batch_set_tuning")
 
     def profile(self, enable=True):
         self._chk(self._L.sacra_batch_profile(self._b, 1 if enable else 0), "batch_profile")
