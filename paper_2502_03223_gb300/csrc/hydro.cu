@@ -512,12 +512,14 @@ __device__ __forceinline__ void hydro_rhs_cell(const Lev &L, const DevParams &p,
   // gt^ac v_c, used in v_a v_b d gt^ab = -(gt^ac v_c)(gt^bd v_d) d gt_cd
   T gv[3];
   s3vec(gi, vd, gv);
-  // FP64 sources with an FP64 derivative scratch take its first derivatives;
-  // the FP32 sources keep their own differences (the arithmetic of the mixed form)
-  const bool use_ds = DS != nullptr && sizeof(T) == 8 && !(p.mixed & SACRA_MIXED_Z4C);
+  // The sources take the first derivatives the stage's derivative pass has
+  // written when that pass ran in the same arithmetic (FP64 sources with the
+  // FP64 pass; FP32 sources with the FP32 pass, whose stencil sums of exact
+  // differences are the ones cd1 forms), else form their own
+  const bool use_ds = DS != nullptr && (sizeof(T) == 8) == !(p.mixed & SACRA_MIXED_Z4C);
   // d_x (e = 0) or d_z (e = 1) of metric field f
   auto d1 = [&](int f, int e) -> T {
-    if (use_ds) return reinterpret_cast<const double *>(DS)[(size_t)(DS_D1 + 3 * d1_of(f) + (e == 0 ? 0 : 2)) * P + id];
+    if (use_ds) return reinterpret_cast<const T *>(DS)[(size_t)(DS_D1 + 3 * d1_of(f) + (e == 0 ? 0 : 2)) * P + id];
     return cd1<T>(U + (size_t)f * P + id, st[e], i60[e]);
   };
   T src[2], dal[2];

@@ -83,6 +83,38 @@ def test_tuning_keeps_the_state_and_picks_valid_shapes():
             assert _same(a.read(l, S.STATE_STEP, f), b.read(l, S.STATE_STEP, f)), (l, f)
 
 
+def test_pinned_shapes_give_the_same_state_mixed():
+    """Launch shapes change no value, in the mixed form too, where they also
+    decide which FP32 face kernel runs: z-faces on 64 x 4 tiles would need a
+    65 KB staging buffer and take the per-face form; the others stage their
+    FP32 inputs in shared memory."""
+    cfg, tov = W.tov_config("pin", rho_c=1.28e-3, n_levels=2, N=48, dx_fine=0.5, rk=1)
+    cfg = dataclasses.replace(cfg, precision=7)
+    datas = [W.tov_level_data(cfg, tov, l) for l in range(2)]
+    runs = []
+    for pins in ({}, {"flux_x": (64, 4, 3), "flux_z": (64, 4, 3), "cartoon": (128, 1, 2), "hydro_rhs": (16, 8, 6),
+                      "z4c_point": (64, 2, 4), "rk_update": (128, 1, 1)}):
+        sim = S.Sacra(cfg)
+        for l, d in enumerate(datas):
+            sim.set_initial_data(l, S.PRIM_METRIC, d)
+        for kind, (tx, ty, m) in pins.items():
+            sim.set_tuning(kind, tx, ty, m)
+            assert sim.tuning()[kind] == (tx, ty, m)
+        sim.step(cfg.dt, 3, use_graph=True)
+        runs.append(sim)
+    for l in range(2):
+        for f in range(30):
+            assert _same(runs[0].read(l, S.STATE_STEP, f), runs[1].read(l, S.STATE_STEP, f)), (l, f)
+        for f in range(6):
+            assert _same(runs[0].read(l, S.PRIMS, f), runs[1].read(l, S.PRIMS, f)), (l, f)
+    with pytest.raises(S.SacraError):
+        runs[0].set_tuning("rk_update", 32, 8, 4)       # 256 threads: beyond the kernel's launch bounds
+    with pytest.raises(S.SacraError):
+        runs[0].set_tuning("flux_x", 32, 4, 5)          # not a candidate grid size
+    for r in runs:
+        r.close()
+
+
 def test_batch_tuning_then_graph_steps_match_untuned():
     stars = _stars(7)
     dt = min(c.dt for c, _ in stars)
