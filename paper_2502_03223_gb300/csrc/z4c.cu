@@ -367,9 +367,13 @@ __host__ __device__ constexpr bool y_zero_c(int f) {
 }
 
 // one block = one tile of DTX x DTZ cells with origin (j0, k0)
+// The field loop is double-buffered: the loads of field f + 1 are issued
+// before field f's stencils run from the other buffer, and one barrier per
+// field separates a buffer's last reads from its next writes.
+constexpr int kStagePer = (DHX * DHZ + DTX * DTZ - 1) / (DTX * DTZ);   // staged points per thread and field
 __device__ __forceinline__ void z4c_derivs_f32_tile(const Lev &L, const DevParams &p, const double *__restrict__ U,
                                                     float *__restrict__ DS, int jmax, int kmax, int cyl, int j0, int k0,
-                                                    float2 (*tile)[DHX]) {
+                                                    float2 (*tiles)[DHZ][DHX]) {
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * DTX + tx;
   const int j = j0 + tx, k = k0 + tz;
   const bool live = j <= jmax && k <= kmax;
@@ -388,17 +392,38 @@ __device__ __forceinline__ void z4c_derivs_f32_tile(const Lev &L, const DevParam
 #pragma unroll
   for (int q = 0; q < 7; ++q) ev[q] = ed[q] = 0.0f;
 
+  // the tile points this thread stages (the same for every field): their
+  // offsets in a field's plane, -1 past the tile or the padded level
+  int soff[kStagePer];
+#pragma unroll
+  for (int r = 0; r < kStagePer; ++r) {
+    const int e = tid + r * DTX * DTZ;
+    const int gj = j0 - 4 + e % DHX, gk = k0 - 4 + e / DHX;
+    soff[r] = (e < DHX * DHZ && gj <= jlim && gk <= klim) ? cid(L, gj, gk) : -1;
+  }
+  double pre[kStagePer];
+  auto fetch = [&](int f) {
+#pragma unroll
+    for (int r = 0; r < kStagePer; ++r) pre[r] = soff[r] >= 0 ? U[(size_t)f * P + soff[r]] : 0.0;
+  };
+  auto stage = [&](float2 (*t)[DHX]) {
+#pragma unroll
+    for (int r = 0; r < kStagePer; ++r) {
+      const int e = tid + r * DTX * DTZ;
+      if (e < DHX * DHZ) {
+        const F2 v = soff[r] >= 0 ? split_f64(pre[r]) : F2{0.0f, 0.0f};
+        t[e / DHX][e % DHX] = make_float2(v.hi, v.lo);
+      }
+    }
+  };
+  fetch(0);
+  stage(tiles[0]);
+  __syncthreads();
+
   FieldLoop<0>::run([&](auto fc) {
     constexpr int f = decltype(fc)::value;
-    const double *Uf = U + (size_t)f * P;
-    for (int e = tid; e < DHX * DHZ; e += DTX * DTZ) {
-      const int ex = e % DHX, ez = e / DHX;
-      const int gj = j0 - 4 + ex, gk = k0 - 4 + ez;
-      F2 v = {0.0f, 0.0f};
-      if (gj <= jlim && gk <= klim) v = split_f64(Uf[cid(L, gj, gk)]);
-      tile[ez][ex] = make_float2(v.hi, v.lo);
-    }
-    __syncthreads();
+    float2 (*tile)[DHX] = tiles[f & 1];
+    if constexpr (f + 1 < NMET) fetch(f + 1);
     if (live) {
       const int cx = tx + 4, cz = tz + 4;
       const float2 c = tile[cz][cx];
@@ -465,6 +490,7 @@ __device__ __forceinline__ void z4c_derivs_f32_tile(const Lev &L, const DevParam
         ed[eq] = d1x;
       }
     }
+    if constexpr (f + 1 < NMET) stage(tiles[(f + 1) & 1]);
     __syncthreads();
   });
   if (live && edge) {
@@ -760,15 +786,15 @@ __global__ void __launch_bounds__(128) k_z4c_derivs(Lev L, DevParams p, const do
 
 __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParams p, const double *__restrict__ U,
                                                               float *__restrict__ DS, int jmax, int kmax, int cyl) {
-  __shared__ float2 tile[DHZ][DHX];
-  z4c_derivs_f32_tile(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * DTX + 1, blockIdx.y * DTZ + 1, tile);
+  __shared__ float2 tiles[2][DHZ][DHX];
+  z4c_derivs_f32_tile(L, p, U, DS, jmax, kmax, cyl, blockIdx.x * DTX + 1, blockIdx.y * DTZ + 1, tiles);
 }
 
 __global__ void __launch_bounds__(DTX * DTZ, 4) kb_z4c_derivs_f32(Batch b, DevParams p) {
-  __shared__ float2 tile[DHZ][DHX];
+  __shared__ float2 tiles[2][DHZ][DHX];
   const int cyl = p.geometry == SACRA_CYLINDRICAL;
   for_tiles(b, [&](const BL &q, const Tile &tl) {
-    z4c_derivs_f32_tile(q.L, q.P, q.U, reinterpret_cast<float *>(q.DS), q.jmax, q.kmax, cyl, tl.j0, tl.k0, tile);
+    z4c_derivs_f32_tile(q.L, q.P, q.U, reinterpret_cast<float *>(q.DS), q.jmax, q.kmax, cyl, tl.j0, tl.k0, tiles);
   });
 }
 
