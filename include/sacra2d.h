@@ -256,9 +256,10 @@ sacra_status sacra_tune(sacra_ctx *c, int reps);
 sacra_status sacra_get_tuning(const sacra_ctx *c, int kind, int *tile_x, int *tile_y, int *blocks_per_sm);
 /* Pins kind `kind`'s launch configuration instead of tuning it: the tile
    shape tile_x x tile_y, one of the autotuner's candidates (32x4, 64x2, 16x8,
-   128x1 for every kind; 32x8 and 64x4 also for kinds 0, 1, 2 and 4, whose
-   kernels take 256 threads; the FP32 derivative pass of the mixed form
-   accepts only its fixed shape), and the persistent grid size blocks_per_sm,
+   128x1 for kinds 0-3, 5 and 6; 32x8 and 64x4 also for kinds 0-2, whose
+   kernels take 256 threads; kind 4, the derivative pass, accepts only its
+   fixed shape: 16x8 in FP64, 32x8 in the mixed form), and the persistent
+   grid size blocks_per_sm,
    one of 1, 2, 3, 4, 6, 8, 12.  A step's results do not depend on these
    choices.  Drops the context's captured CUDA graphs (the next graph step
    captures anew).  Errors: SACRA_ERR_ARG for a kind, shape or grid size

@@ -312,11 +312,11 @@ bool kind_used(const Engine &e, int kind) {
   return true;
 }
 
-bool fixed_shape(const Engine &e, int kind) { return kind == B_DERIVS && (e.dp.mixed & SACRA_MIXED_Z4C); }
+bool fixed_shape(const Engine &, int kind) { return kind == B_DERIVS; }
 
 Shape kind_shape(const Engine &e, int kind) {
   if (fixed_shape(e, kind)) {
-    const dim3 b = z4c_derivs_f32_block();
+    const dim3 b = (e.dp.mixed & SACRA_MIXED_Z4C) ? z4c_derivs_f32_block() : z4c_derivs_f64_block();
     return {(int)b.x, (int)b.y};
   }
   return e.cfg[kind].shape;

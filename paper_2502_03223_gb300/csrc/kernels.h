@@ -89,8 +89,9 @@ void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s);
 // value widened) into the FP64 scratch plane z4c_ricci_plane()
 void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s, int store_rs = 0);
 void launch_b_rk_update(const Batch &b, const DevParams &p, int stage, double dt, cudaStream_t s);
-// the FP32 derivative pass has a fixed tile shape
+// the derivative passes have fixed tile shapes (their shared-memory staging)
 dim3 z4c_derivs_f32_block();
+dim3 z4c_derivs_f64_block();
 
 void launch_flux_x(const Lev &L, const DevParams &p, const double *U, int jmax, int kmax, double wb, int has_child,
                    int has_parent, cudaStream_t s);

@@ -528,10 +528,20 @@ __device__ __forceinline__ double zdiff_num(const double *c, int sz) {
   return 45.0 * (c[sz] - c[-sz]) - 9.0 * (c[2 * sz] - c[-2 * sz]) + (c[3 * sz] - c[-3 * sz]);
 }
 
+// Staged form (tb given; block FDX x FDZ, tile origin j0, k0): each field's
+// tile with a 4-cell halo is held in shared memory as the values' bit
+// patterns, double-buffered: the loads of field f + 1 are issued before field
+// f's stencils run from the other buffer, and one barrier per field closes
+// it.  The stencils read the same values as from global memory.
+constexpr int FDX = 16, FDZ = 8, FHX = FDX + 8, FHZ = FDZ + 8;
+constexpr int kF64Per = FHX * FHZ / (FDX * FDZ);      // staged points per thread and field
+static_assert(FHX * FHZ == kF64Per * FDX * FDZ, "the halo tile splits evenly over the block");
+
 template <typename T>
 __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p, const double *__restrict__ U,
                                                 double *__restrict__ DS, int jmax, int kmax, int cyl, int j, int k,
-                                                long long *sdn = nullptr, int *sde = nullptr, int j0 = 0) {
+                                                long long *sdn = nullptr, int *sde = nullptr, int j0 = 0,
+                                                long long (*tb)[FHZ][FHX] = nullptr, int k0 = 0) {
   static_assert(sizeof(T) == 8, "the FP32 form is z4c_derivs_f32_tile");
   // XCH (sdn, sde given): the mixed derivative d_xz is the x-difference of the
   // z-difference numerators of the neighbouring columns, exact integers on
@@ -562,19 +572,58 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
   const double ko = p.ko, ikx = L.idx, ikz = L.idz;
   const double kfx = ko * ikx, kfz = ko * ikz;
   const bool same_d = ikx == ikz;
+  // staged form: this thread's points of the halo tile (offset in a field's
+  // plane, -1 past the padded level) and the loads in flight
+  const int tid = (int)(threadIdx.y * blockDim.x + threadIdx.x), tz = (int)threadIdx.y;
+  int soff[kF64Per];
+  long long pre[kF64Per];
+  if (tb) {
+#pragma unroll
+    for (int r = 0; r < kF64Per; ++r) {
+      const int e = tid + r * FDX * FDZ;
+      const int gj = j0 - 4 + e % FHX, gk = k0 - 4 + e / FHX;
+      soff[r] = (gj <= L.nx + GH && gk <= L.nz + GH) ? cid(L, gj, gk) : -1;
+    }
+  }
+  auto fetch = [&](int f) {
+#pragma unroll
+    for (int r = 0; r < kF64Per; ++r) pre[r] = soff[r] >= 0 ? fx::bits(U[(size_t)f * P + soff[r]]) : 0ll;
+  };
+  auto stage = [&](long long (*t)[FHX]) {
+#pragma unroll
+    for (int r = 0; r < kF64Per; ++r) {
+      const int e = tid + r * FDX * FDZ;
+      t[e / FHX][e % FHX] = pre[r];
+    }
+  };
+  if (tb) {
+    fetch(0);
+    stage(tb[0]);
+    __syncthreads();
+  }
 #pragma unroll 1
   for (int f = 0; f < NMET; ++f) {
     const int a1 = kD1Of[f], a2 = kD2Of[f];
     const bool yz = y_zero(f);
     const double *u = U + (size_t)f * P + id;
+    long long (*tile)[FHX] = tb ? tb[f & 1] : nullptr;
+    if (tb && f + 1 < NMET) fetch(f + 1);
     long long cn = 0;                  // z-difference numerator of this thread's column ...
     int ce = 1;                        // ... on the grid 2^(ce - kGrid); -1: not finite
     if (active) {
       long long X[9], Z[9];
+      if (tile) {
 #pragma unroll
-      for (int n = 0; n < 9; ++n) {
-        X[n] = fx::bits(u[n - 4]);
-        Z[n] = n == 4 ? X[4] : fx::bits(u[(n - 4) * sz]);
+        for (int n = 0; n < 9; ++n) {
+          X[n] = tile[tz + 4][tx + n];
+          Z[n] = n == 4 ? X[4] : tile[tz + n][tx + 4];
+        }
+      } else {
+#pragma unroll
+        for (int n = 0; n < 9; ++n) {
+          X[n] = fx::bits(u[n - 4]);
+          Z[n] = n == 4 ? X[4] : fx::bits(u[(n - 4) * sz]);
+        }
       }
       int E = 0;
 #pragma unroll
@@ -604,8 +653,10 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
         // on the values) is checked on its pair sums
         d1xn = 45 * ox1 - 9 * ox2 + ox3;
         d1zn = 45 * oz1 - 9 * oz2 + oz3;
-        cn = d1zn;
-        ce = E;
+        if (!tile) {
+          cn = d1zn;
+          ce = E;
+        }
         if (a2 >= 0) {
           // the sums wrap (unsigned) where the check fails; the FP64 form then replaces them
           typedef unsigned long long u64;
@@ -669,7 +720,7 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
           DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (45.0 * (Dx[5] - Dx[3]) - 9.0 * (Dx[6] - Dx[2]) + (Dx[7] - Dx[1])) * i60x;
           DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (45.0 * (Dz[5] - Dz[3]) - 9.0 * (Dz[6] - Dz[2]) + (Dz[7] - Dz[1])) * i60z;
         }
-        if (a2 >= 0 && xch && !zero) fx::diff6(u, sz, cn, ce);
+        if (a2 >= 0 && xch && !zero && !tile) fx::diff6(u, sz, cn, ce);
         if (a2 >= 0) {
           DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = (270.0 * (Dx[5] + Dx[3]) - 27.0 * (Dx[6] + Dx[2]) + 2.0 * (Dx[7] + Dx[1])) * i180x;
           DS[(size_t)(DS_D2 + 6 * a2 + 5) * P + id] = (270.0 * (Dz[5] + Dz[3]) - 27.0 * (Dz[6] + Dz[2]) + 2.0 * (Dz[7] + Dz[1])) * i180z;
@@ -692,14 +743,20 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
         o[4 * P] = dyz;
       }
       DS[(size_t)(DS_AK + f) * P + id] = adv;
-    } else if (xch && a2 >= 0 && own_col) {
-      fx::diff6(u, sz, cn, ce);         // a column right of the region that cells of the region use
+    }
+    if (xch && a2 >= 0 && own_col) {
+      // staged: every column's numerator from its own six z-values on their own
+      // grid (the halo columns' form), so d_xz does not depend on where the
+      // tile edges fall; per-cell form: a column right of the region that
+      // cells of the region use
+      if (tile) fx::diff6_bits(&tile[tz + 4][tx + 4], FHX, cn, ce);
+      else if (!active) fx::diff6(u, sz, cn, ce);
     }
     if (a2 >= 0) {
       double dxz = 0.0;
       bool fp64 = !xch;
       if (xch) {
-        __syncthreads();                                 // the previous field's row is read
+        if (!tb) __syncthreads();                        // the previous field's row is read (staged: the field's closing barrier)
         rown[tx + 3] = own_col ? cn : 0;
         rowe[tx + 3] = own_col ? ce : 1;
         if (tx < 3 || tx >= (int)blockDim.x - 3) {
@@ -707,7 +764,10 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
           const int jc = j0 - 3 + e;
           long long hn = 0;
           int he = 1;
-          if (k <= kmax && jc <= jmax + 3) fx::diff6(U + (size_t)f * P + cid(L, jc, k), sz, hn, he);
+          if (k <= kmax && jc <= jmax + 3) {
+            if (tile) fx::diff6_bits(&tile[tz + 4][jc - j0 + 4], FHX, hn, he);
+            else fx::diff6(U + (size_t)f * P + cid(L, jc, k), sz, hn, he);
+          }
           rown[e] = hn;
           rowe[e] = he;
         }
@@ -752,6 +812,10 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
         dxz *= ixz;
       }
       if (active) DS[(size_t)(DS_D2 + 6 * a2 + 2) * P + id] = dxz;
+    }
+    if (tb) {
+      if (f + 1 < NMET) stage(tb[(f + 1) & 1]);
+      __syncthreads();
     }
   }
   if (!active) return;
@@ -932,15 +996,16 @@ __global__ void __launch_bounds__(128, 3) kb_cartoon_f32(Batch b, const double *
   });
 }
 
-constexpr int kDxzRow = 304;   // (blockDim.x + 6) * blockDim.y for every tuned shape up to 256 threads
-__global__ void __launch_bounds__(256) kb_z4c_derivs(Batch b, DevParams p) {
+// the FP64 derivative pass on FDX x FDZ tiles, staged and double-buffered
+constexpr int kDxzRow = (FDX + 6) * FDZ;
+__global__ void __launch_bounds__(FDX * FDZ, 4) kb_z4c_derivs(Batch b, DevParams p) {
   __shared__ long long sdn[kDxzRow];
   __shared__ int sde[kDxzRow];
+  __shared__ long long tb[2][FHZ][FHX];
   const int cyl = p.geometry == SACRA_CYLINDRICAL;
-  const bool xch = ((int)blockDim.x + 6) * (int)blockDim.y <= kDxzRow;
   for_tiles(b, [&](const BL &q, const Tile &tl) {
     z4c_derivs_cell<double>(q.L, q.P, q.U, reinterpret_cast<double *>(q.DS), q.jmax, q.kmax, cyl, tl.j0 + threadIdx.x,
-                            tl.k0 + threadIdx.y, xch ? sdn : nullptr, xch ? sde : nullptr, tl.j0);
+                            tl.k0 + threadIdx.y, sdn, sde, tl.j0, tb, tl.k0);
   });
 }
 
@@ -964,7 +1029,7 @@ void launch_b_cartoon(const Batch &b, const DevParams &p, const double *tab, int
 void launch_b_z4c_derivs(const Batch &b, const DevParams &p, cudaStream_t s) {
   if (b.ntiles <= 0) return;
   if (p.mixed & SACRA_MIXED_Z4C) kb_z4c_derivs_f32<<<b.grid, dim3(DTX, DTZ), 0, s>>>(b, p);
-  else kb_z4c_derivs<<<b.grid, b.block, 0, s>>>(b, p);
+  else kb_z4c_derivs<<<b.grid, dim3(FDX, FDZ), 0, s>>>(b, p);
 }
 
 void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s, int store_rs) {
@@ -974,6 +1039,7 @@ void launch_b_z4c_point(const Batch &b, const DevParams &p, cudaStream_t s, int 
 }
 
 dim3 z4c_derivs_f32_block() { return dim3(DTX, DTZ); }
+dim3 z4c_derivs_f64_block() { return dim3(FDX, FDZ); }
 
 int z4c_scratch_planes() { return DS_N; }
 int z4c_ricci_plane() { return DS_RS; }
