@@ -56,8 +56,7 @@ __device__ __forceinline__ long long shr(long long x, int k) { return k < 63 ? (
 // u_-2) + (u_3 - u_-3) of the six values u[n s], n = +-1..+-3, exactly on the
 // grid 2^(E - kGrid) of their largest exponent field (E >= 1); E = -1 when a
 // value is not finite.  diff6_of takes the bit patterns of u_1, u_-1, u_2,
-// u_-2, u_3, u_-3; diff6 reads them from u[n s], diff6_bits from the patterns
-// c[n s].
+// u_-2, u_3, u_-3; diff6_bits reads them from the patterns c[n s].
 __device__ __forceinline__ void diff6_of(const long long b[6], long long &num, int &E) {
   int e = 1;
 #pragma unroll
@@ -74,15 +73,6 @@ __device__ __forceinline__ void diff6_of(const long long b[6], long long &num, i
   E = e;
 }
 
-__device__ __forceinline__ void diff6(const double *u, int s, long long &num, int &E) {
-  long long b[6];
-#pragma unroll
-  for (int n = 0; n < 3; ++n) {
-    b[2 * n] = bits(u[(n + 1) * s]);
-    b[2 * n + 1] = bits(u[-(n + 1) * s]);
-  }
-  diff6_of(b, num, E);
-}
 __device__ __forceinline__ void diff6_bits(const long long *c, int s, long long &num, int &E) {
   long long b[6];
 #pragma unroll

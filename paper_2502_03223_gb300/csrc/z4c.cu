@@ -543,14 +543,15 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
                                                 long long *sdn = nullptr, int *sde = nullptr, int j0 = 0,
                                                 long long (*tb)[FHZ][FHX] = nullptr, int k0 = 0) {
   static_assert(sizeof(T) == 8, "the FP32 form is z4c_derivs_f32_tile");
-  // XCH (sdn, sde given): the mixed derivative d_xz is the x-difference of the
-  // z-difference numerators of the neighbouring columns, exact integers on
-  // each column's own grid (numerator, exponent), which the block exchanges
-  // through shared memory (row of blockDim.x + 6 columns per thread row: each
-  // thread its own column, the three threads at either end of a row one halo
-  // column each); every thread of the block runs the field loop (it has
-  // barriers)
-  const bool xch = sdn != nullptr;
+  // Staged form (tb, sdn, sde given): the mixed derivative d_xz is the
+  // x-difference of the z-difference numerators of the neighbouring columns,
+  // exact integers on each column's own grid (numerator, exponent), which the
+  // block exchanges through shared memory (row of blockDim.x + 6 columns per
+  // thread row: each thread its own column, the three threads at either end of
+  // a row one halo column each); every thread of the block runs the field loop
+  // (it has barriers).  Per-cell form (none given): d_xz in FP64 from the
+  // column differences.
+  const bool xch = tb != nullptr;
   const bool active = j <= jmax && k <= kmax;
   if (!xch && !active) return;
   const int bw = (int)blockDim.x + 6, tx = (int)threadIdx.x;
@@ -653,10 +654,6 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
         // on the values) is checked on its pair sums
         d1xn = 45 * ox1 - 9 * ox2 + ox3;
         d1zn = 45 * oz1 - 9 * oz2 + oz3;
-        if (!tile) {
-          cn = d1zn;
-          ce = E;
-        }
         if (a2 >= 0) {
           // the sums wrap (unsigned) where the check fails; the FP64 form then replaces them
           typedef unsigned long long u64;
@@ -720,7 +717,6 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
           DS[(size_t)(DS_D1 + 3 * a1 + 0) * P + id] = (45.0 * (Dx[5] - Dx[3]) - 9.0 * (Dx[6] - Dx[2]) + (Dx[7] - Dx[1])) * i60x;
           DS[(size_t)(DS_D1 + 3 * a1 + 2) * P + id] = (45.0 * (Dz[5] - Dz[3]) - 9.0 * (Dz[6] - Dz[2]) + (Dz[7] - Dz[1])) * i60z;
         }
-        if (a2 >= 0 && xch && !zero && !tile) fx::diff6(u, sz, cn, ce);
         if (a2 >= 0) {
           DS[(size_t)(DS_D2 + 6 * a2 + 0) * P + id] = (270.0 * (Dx[5] + Dx[3]) - 27.0 * (Dx[6] + Dx[2]) + 2.0 * (Dx[7] + Dx[1])) * i180x;
           DS[(size_t)(DS_D2 + 6 * a2 + 5) * P + id] = (270.0 * (Dz[5] + Dz[3]) - 27.0 * (Dz[6] + Dz[2]) + 2.0 * (Dz[7] + Dz[1])) * i180z;
@@ -745,18 +741,17 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
       DS[(size_t)(DS_AK + f) * P + id] = adv;
     }
     if (xch && a2 >= 0 && own_col) {
-      // staged: every column's numerator from its own six z-values on their own
-      // grid (the halo columns' form), so d_xz does not depend on where the
-      // tile edges fall; per-cell form: a column right of the region that
-      // cells of the region use
-      if (tile) fx::diff6_bits(&tile[tz + 4][tx + 4], FHX, cn, ce);
-      else if (!active) fx::diff6(u, sz, cn, ce);
+      // every column's numerator from its own six z-values on their own grid
+      // (the halo columns' form), so d_xz does not depend on where the tile
+      // edges fall; this includes the columns right of the region that cells
+      // of the region use
+      fx::diff6_bits(&tile[tz + 4][tx + 4], FHX, cn, ce);
     }
     if (a2 >= 0) {
       double dxz = 0.0;
       bool fp64 = !xch;
       if (xch) {
-        if (!tb) __syncthreads();                        // the previous field's row is read (staged: the field's closing barrier)
+        // (the previous field's row reads end before the field's closing barrier)
         rown[tx + 3] = own_col ? cn : 0;
         rowe[tx + 3] = own_col ? ce : 1;
         if (tx < 3 || tx >= (int)blockDim.x - 3) {
@@ -764,10 +759,7 @@ __device__ __forceinline__ void z4c_derivs_cell(const Lev &L, const DevParams &p
           const int jc = j0 - 3 + e;
           long long hn = 0;
           int he = 1;
-          if (k <= kmax && jc <= jmax + 3) {
-            if (tile) fx::diff6_bits(&tile[tz + 4][jc - j0 + 4], FHX, hn, he);
-            else fx::diff6(U + (size_t)f * P + cid(L, jc, k), sz, hn, he);
-          }
+          if (k <= kmax && jc <= jmax + 3) fx::diff6_bits(&tile[tz + 4][jc - j0 + 4], FHX, hn, he);
           rown[e] = hn;
           rowe[e] = he;
         }
