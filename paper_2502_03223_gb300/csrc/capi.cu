@@ -205,6 +205,12 @@ struct Engine {
   DevParams dp;
   int S = 4;                      // stages per step
   cudaStream_t stream = nullptr;
+  // uploads of a level's state (set_initial_data, RAW): the host-to-device
+  // copy runs in row chunks on its own stream, each chunk's recovery on the
+  // context's stream as soon as that chunk has arrived
+  static constexpr int kUpChunks = 8;
+  cudaStream_t up_stream = nullptr;
+  cudaEvent_t up_start = nullptr, up_chunk[kUpChunks] = {};
   char *arena = nullptr;
   bool own_arena = false;
   double *tab = nullptr, *tabw = nullptr, *dout = nullptr;
@@ -1100,6 +1106,16 @@ size_t engine_bytes(const std::vector<sacra_params> &ps) {
 
 sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *stream, void *arena, size_t arena_bytes) {
   e.stream = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&e.up_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&e.up_start, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return SACRA_ERR_CUDA;
+  }
+  for (cudaEvent_t &ev : e.up_chunk)
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return SACRA_ERR_CUDA;
+    }
   const size_t need = engine_bytes(ps);
   if (arena) {
     if (arena_bytes < need || ((uintptr_t)arena & 255)) return SACRA_ERR_OOM;
@@ -1172,8 +1188,13 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
 
 void engine_free(Engine &e) {
   cudaStreamSynchronize(e.stream);
+  if (e.up_stream) cudaStreamSynchronize(e.up_stream);
   drop_graphs(e);
   for (cudaEvent_t x : e.pool) cudaEventDestroy(x);
+  if (e.up_start) cudaEventDestroy(e.up_start);
+  for (cudaEvent_t x : e.up_chunk)
+    if (x) cudaEventDestroy(x);
+  if (e.up_stream) cudaStreamDestroy(e.up_stream);
   if (e.own_arena && e.arena) cudaFree(e.arena);
 }
 
@@ -1192,13 +1213,34 @@ sacra_status set_initial_data(Engine &e, int star, int level, int kind, const do
     cudaMemcpy2DAsync(L.prim, L.P * 8, host + (size_t)NMET * np, np * 8, np * 8, 5, cudaMemcpyHostToDevice, e.stream);
     run(e, K_PRIM2CONS, (long long)np, [&] { launch_prim2cons_all(L, st.dp, L.un, e.stream); });
   } else if (kind == SACRA_RAW) {
-    cudaMemcpy2DAsync(L.un, L.P * 8, host, np * 8, np * 8, NST, cudaMemcpyHostToDevice, e.stream);
-    run(e, K_C2P, (long long)np, [&] { launch_c2p_region(L, st.dp, L.un, 1 - GH, L.nx + GH, 1 - GH, L.nz + GH, e.stream); });
+    // rows [1 - GH, nz + GH] in kUpChunks chunks: the copy of chunk c + 1 (upload
+    // stream, after everything enqueued on the context's stream so far)
+    // overlaps the recovery of chunk c (context stream, after chunk c arrived)
+    cudaEventRecord(e.up_start, e.stream);
+    cudaStreamWaitEvent(e.up_stream, e.up_start, 0);
+    const int nrow = L.pz;
+    for (int c = 0; c < Engine::kUpChunks; ++c) {
+      const int r0 = nrow * c / Engine::kUpChunks, r1 = nrow * (c + 1) / Engine::kUpChunks;
+      if (r1 <= r0) continue;
+      const size_t off = (size_t)r0 * L.px;
+      cudaMemcpy2DAsync(L.un + off, L.P * 8, host + off, np * 8, (size_t)(r1 - r0) * L.px * 8, NST,
+                        cudaMemcpyHostToDevice, e.up_stream);
+      cudaEventRecord(e.up_chunk[c], e.up_stream);
+      cudaStreamWaitEvent(e.stream, e.up_chunk[c], 0);
+      // padded row r is k = r - GH + 1
+      run(e, K_C2P, (long long)(r1 - r0) * L.px, [&] {
+        launch_c2p_region(L, st.dp, L.un, 1 - GH, L.nx + GH, r0 - GH + 1, r1 - GH, e.stream);
+      });
+    }
   } else {
     return fail(e, SACRA_ERR_ARG, "unknown kind");
   }
   cudaMemcpyAsync(L.us, L.un, (size_t)NST * L.P * 8, cudaMemcpyDeviceToDevice, e.stream);
-  if (cudaStreamSynchronize(e.stream) != cudaSuccess) return cuda_check(e, "set_initial_data");
+  // the host buffer may be reused once it has been copied: wait for the copies
+  // (RAW: the last chunk; the recovery goes on on the context's stream)
+  const cudaError_t werr =
+      kind == SACRA_RAW ? cudaStreamSynchronize(e.up_stream) : cudaStreamSynchronize(e.stream);
+  if (werr != cudaSuccess) return cuda_check(e, "set_initial_data");
   st.have_data[level] = true;
   for (int l = 0; l < st.prm.n_levels; ++l) st.have_old[l] = false;   // no earlier time slice of the new data
   return cuda_check(e, "set_initial_data");
