@@ -146,7 +146,14 @@ sacra_status sacra_init_grid(const sacra_params *p, void *cuda_stream, void *are
    (rho, u_x, u_y, u_z, P); eps follows from the EOS and the conserved
    variables from Eq. cons_var, on every cell including the padding.
    kind SACRA_RAW: n_fields = 30 padded state planes (metric + conserved);
-   the primitives are recovered.  host_planes: n_fields * pz * px doubles. */
+   the primitives are recovered on every cell (which may reset a cell to the
+   atmosphere or the cold curve and rewrite its conserved variables, as any
+   recovery does).  The RAW copy runs in row chunks on a stream of the
+   context's own, each chunk's recovery on the context's stream once the chunk
+   has arrived; the call returns when the host buffer has been copied, and the
+   recovery is ordered before every later call's work on the context.
+   host_planes: n_fields * pz * px doubles (pinned memory lets the copy run at
+   the link's rate). */
 sacra_status sacra_set_initial_data(sacra_ctx *c, int level, int kind, const double *host_planes, int n_fields);
 
 /* Ghost and buffer fill (what = SACRA_FILL) for RK stage `stage` of a step of
