@@ -637,18 +637,26 @@ def run_native(args, dist, rank, ws, local):
     d2h = sum(a.nbytes for a in host_out) + ctypes.sizeof(S.SacraDiag)
     sim.sync()
     barrier(dist)
+    phase = [0.0, 0.0, 0.0]        # host time in the uploads, the step, the readback
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         for l in range(cfg.n_levels):
             sim.set_initial_data(l, S.RAW, host_in[l])
+        tb = time.perf_counter()
         sim.step_constraints(cfg.dt, 1, use_graph=True)
+        tc = time.perf_counter()
         for l in range(cfg.n_levels):
             sim.read_level(l, host_out[l])
+        td = time.perf_counter()
+        phase[0] += tb - ta; phase[1] += tc - tb; phase[2] += td - tc
     el = time.perf_counter() - t0
     el = max_over_ranks(dist, el)
     e2e = {"value": ws * cps * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "steps": e2e_steps, "what": "per step: all levels' state host->device (pinned), one step with its "
-                                       "diagnostics read back, all levels' evolved state device->host (pinned)"}
+                                       "diagnostics read back, all levels' evolved state device->host (pinned)",
+           "ms_per_step": {"upload": phase[0] / e2e_steps * 1e3, "step": phase[1] / e2e_steps * 1e3,
+                           "readback": phase[2] / e2e_steps * 1e3}}
 
     # ---- per-kernel device time (eager launches bracketed by CUDA events), from
     # the timed regions' starting state
