@@ -215,6 +215,7 @@ struct Engine {
   bool own_arena = false;
   double *tab = nullptr, *tabw = nullptr, *dout = nullptr;
   unsigned long long *nfb = nullptr;
+  int *tctr = nullptr;            // the tile counter of the batched launches (zeroed before each)
   int sms = 1;
   // plan of the batched launches
   std::vector<std::pair<int, int>> slots;   // (star, level)
@@ -576,10 +577,12 @@ Batch batch_of(const Engine &e, int g, int s, int kind) {
   b.block = dim3(sh.x, sh.y);
   const long long nb = (long long)e.sms * e.cfg[kind].blocks_per_sm;
   b.grid = (int)std::max(1LL, std::min<long long>(nb, b.ntiles));
+  b.ctr = e.tctr;
   return b;
 }
 
 void launch_kind(Engine &e, int kind, const Batch &b, int s, double dt) {
+  cudaMemsetAsync(b.ctr, 0, sizeof(int), e.stream);   // launches on the one stream: one counter serves all
   switch (kind) {
     case B_FLUX_X: launch_b_flux_x(b, e.dp, e.stream); break;
     case B_FLUX_Z: launch_b_flux_z(b, e.dp, e.stream); break;
@@ -945,6 +948,7 @@ sacra_status tune(Engine &e, int reps) {
     bt.ntiles = (int)t.size();
     bt.block = dim3(sh.x, sh.y);
     bt.grid = (int)std::max(1LL, std::min<long long>((long long)e.sms * m, bt.ntiles));
+    bt.ctr = e.tctr;
     launch_kind(e, kind, bt, 0, 0.0);   // warm-up
     cudaEventRecord(a, e.stream);
     for (int r = 0; r < reps; ++r) launch_kind(e, kind, bt, 0, 0.0);
@@ -1101,6 +1105,7 @@ size_t engine_bytes(const std::vector<sacra_params> &ps) {
     max_nx = std::max(max_nx, p.nx);
   }
   return n + round_up((size_t)(max_nx + 8) * (3 * kTabStride + kCartoonW) * 8, 256) + 256 /* dout */ + 256 /* nfb */ +
+         256 /* tile counter */ +
          plan_bytes(ps) + round_up(litem_count(ps) * sizeof(LItem), 256);
 }
 
@@ -1169,6 +1174,8 @@ sacra_status engine_init(Engine &e, const std::vector<sacra_params> &ps, void *s
   e.dout = (double *)p;
   p += 256;
   e.nfb = (unsigned long long *)p;
+  p += 256;
+  e.tctr = (int *)p;
   p += 256;
   const size_t nl = e.slots.size();
   e.bl_dev = (BL *)p;

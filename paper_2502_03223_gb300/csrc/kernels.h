@@ -35,22 +35,45 @@ struct Batch {
   int ntiles;
   int grid;                 // persistent blocks
   dim3 block;               // tile shape = block shape
+  int *ctr;                 // tiles handed out past the first gridDim.x (zero at the launch)
 };
-// Grid-stride walk over the tiles of a batched launch: the block copies the
-// tile's level view into shared memory (so that every thread reads the level
-// and its parameters from there) and calls f(view, tile) with all threads.
-template <class F>
+// Walk over the tiles of a batched launch.  DYN: block b starts with tile b,
+// then takes the next tile not yet handed out from the launch's counter, so
+// that a block on cheap tiles (atmosphere) takes more of them than one on
+// costly tiles (matter under recovery); otherwise a grid stride (the kernels
+// whose tiles cost the same, where the counter only adds register pressure).
+// The block copies the tile's level view into shared memory (so that every
+// thread reads the level and its parameters from there) and calls f(view,
+// tile) with all threads.  Tiles are independent, so which block handles a
+// tile changes no value.
+template <bool DYN = true, class F>
 __device__ __forceinline__ void for_tiles(const Batch &b, F &&f) {
   __shared__ BL sb;
   const int nth = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
-    const Tile tl = b.tiles[t];
-    const int *src = reinterpret_cast<const int *>(b.bl + tl.bl);
-    int *dst = reinterpret_cast<int *>(&sb);
-    for (int i = tid; i < (int)(sizeof(BL) / sizeof(int)); i += nth) dst[i] = src[i];
-    __syncthreads();
-    f(sb, tl);
-    __syncthreads();
+  if constexpr (DYN) {
+    __shared__ int next;
+    int t = blockIdx.x;
+    while (t < b.ntiles) {
+      const Tile tl = b.tiles[t];
+      const int *src = reinterpret_cast<const int *>(b.bl + tl.bl);
+      int *dst = reinterpret_cast<int *>(&sb);
+      for (int i = tid; i < (int)(sizeof(BL) / sizeof(int)); i += nth) dst[i] = src[i];
+      __syncthreads();
+      f(sb, tl);
+      if (tid == 0) next = (int)gridDim.x + atomicAdd(b.ctr, 1);
+      __syncthreads();
+      t = next;
+    }
+  } else {
+    for (int t = blockIdx.x; t < b.ntiles; t += gridDim.x) {
+      const Tile tl = b.tiles[t];
+      const int *src = reinterpret_cast<const int *>(b.bl + tl.bl);
+      int *dst = reinterpret_cast<int *>(&sb);
+      for (int i = tid; i < (int)(sizeof(BL) / sizeof(int)); i += nth) dst[i] = src[i];
+      __syncthreads();
+      f(sb, tl);
+      __syncthreads();
+    }
   }
 }
 static_assert(sizeof(BL) % sizeof(int) == 0, "BL is copied as ints");

@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(DTX * DTZ, 3) k_z4c_derivs_f32(Lev L, DevParam
 __global__ void __launch_bounds__(DTX * DTZ, 4) kb_z4c_derivs_f32(Batch b, DevParams p) {
   __shared__ float2 tiles[2][DHZ][DHX];
   const int cyl = p.geometry == SACRA_CYLINDRICAL;
-  for_tiles(b, [&](const BL &q, const Tile &tl) {
+  for_tiles<false>(b, [&](const BL &q, const Tile &tl) {
     z4c_derivs_f32_tile(q.L, q.P, q.U, reinterpret_cast<float *>(q.DS), q.jmax, q.kmax, cyl, tl.j0, tl.k0, tiles);
   });
 }
@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(FDX * FDZ, 4) kb_z4c_derivs(Batch b, DevParams
 
 template <typename T>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 0) kb_z4c_point(Batch b, DevParams p, int store_rs) {
-  for_tiles(b, [&](const BL &q, const Tile &tl) {
+  for_tiles<false>(b, [&](const BL &q, const Tile &tl) {
     double *rs = store_rs ? reinterpret_cast<double *>(q.DS) + (size_t)DS_RS * q.L.P : nullptr;
     z4c_point_cell<T>(q.L, q.P, q.U, reinterpret_cast<const T *>(q.DS), q.jmax, q.kmax, tl.j0 + threadIdx.x,
                       tl.k0 + threadIdx.y, rs);
