@@ -2,17 +2,39 @@
 // per-face PPM reconstruction + metric interpolation + tetrad HLLC/TVDLF flux,
 // per-cell flux divergence with cylindrical areas/volumes and the geometric and
 // gravitational sources, primitive recovery, initial conserved variables.
+#include "fixed.cuh"
 #include "kernels.h"
 #include "z4c.cuh"
 
 namespace sacra {
 
 // 6-point (6th-order) interpolation of a metric field to the face between
-// u[0] and u[s], in difference form about u[0]: (3,-25,150,150,-25,3)/256.
-__device__ __forceinline__ double face6(const double *u, int s) {
+// u[0] and u[s]: (3,-25,150,150,-25,3)/256.  FP64 form: difference form about
+// u[0] (exact on constants).
+__device__ __forceinline__ double face6_fp64(const double *u, int s) {
   const double u0 = u[0];
   return u0 + (3.0 * (u[-2 * s] - u0) - 25.0 * (u[-s] - u0) + 150.0 * (u[s] - u0) - 25.0 * (u[2 * s] - u0)
                + 3.0 * (u[3 * s] - u0)) * (1.0 / 256.0);
+}
+// The same interpolant as an exact integer sum: the six values on the
+// fixed-point grid of their largest exponent (fixed.cuh; one guard bit, |v| <
+// 2^54, so the weighted sum, weight sum 356, stays below 2^63), one
+// conversion and an exact power-of-two scale: the interpolant rounded once,
+// in two FP64 operations instead of twelve.  Non-finite values and values
+// near the bottom of the normal range take the FP64 form.
+__device__ __forceinline__ double face6(const double *u, int s) {
+  long long b[6];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) b[n] = fx::bits(u[(n - 2) * s]);
+  int E = 0;
+#pragma unroll
+  for (int n = 0; n < 6; ++n) E = max(E, fx::expo(b[n]));
+  if (E < 64 || E == 2047) return face6_fp64(u, s);
+  long long v[6];
+#pragma unroll
+  for (int n = 0; n < 6; ++n) v[n] = fx::fix(b[n], E);
+  const long long S = 3 * (v[0] + v[5]) - 25 * (v[1] + v[4]) + 150 * (v[2] + v[3]);
+  return (double)S * fx::unit(1.0 / 256.0, E);
 }
 
 // Face j+1/2 (dir 0, stride 1) or k+1/2 (dir 1, stride px) of cell (j, k):
