@@ -511,7 +511,9 @@ __device__ __forceinline__ void diag_block_reduce(double acc[DIAG_Q], double (*s
 
 // S: storage type of the derivative scratch and the cartoon planes (FP32 in
 // the mixed-precision Z4c form); the constraint algebra is FP64 either way.
-template <typename S>
+// RSK: the Ricci scalar comes from RS (formed by the pointwise pass of the
+// same stage); otherwise the kernel forms the Ricci tensor itself.
+template <typename S, bool RSK>
 __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__restrict__ DS,
                                                  const double *__restrict__ RS, int covered, int evolve,
                                                  double *__restrict__ partials) {
@@ -542,45 +544,42 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__
         // DS holds the derivative scratch of the Z4c pass for this level
         constexpr int D1 = 0, D2 = 48;
         Z4cIn<double> z;
-        z.W = U[(size_t)fW * P + id]; z.al = U[(size_t)fAL * P + id];
+        // the fields the constraints take (lapse, shift, Gt^i and B^i enter
+        // neither); every loop below is unrolled so that all indices are
+        // compile-time constants and the arrays stay in registers
+        z.W = U[(size_t)fW * P + id];
         z.Kh = U[(size_t)fKH * P + id]; z.Th = U[(size_t)fTH * P + id];
-        // every loop below is unrolled so that all indices are compile-time
-        // constants and the arrays stay in registers
 #pragma unroll
         for (int a = 0; a < 6; ++a) { z.h[a] = U[(size_t)(fHXX + a) * P + id]; z.A[a] = U[(size_t)(fAXX + a) * P + id]; }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          z.Gt[c] = U[(size_t)(fGX + c) * P + id]; z.beta[c] = U[(size_t)(fBX + c) * P + id];
-          z.B[c] = U[(size_t)(fBBX + c) * P + id];
-        }
+        // the first derivatives the constraints take: W, gt_ij, Khat, Theta
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           z.dW[c] = DS[(size_t)(D1 + c) * P + id];
 #pragma unroll
           for (int a = 0; a < 6; ++a) z.dh[a][c] = DS[(size_t)(D1 + 3 * (1 + a) + c) * P + id];
           z.dKh[c] = DS[(size_t)(D1 + 21 + c) * P + id];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) z.dGt[a][c] = DS[(size_t)(D1 + 3 * (8 + a) + c) * P + id];
           z.dTh[c] = DS[(size_t)(D1 + 33 + c) * P + id];
-          z.dal[c] = DS[(size_t)(D1 + 36 + c) * P + id];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) z.db[a][c] = DS[(size_t)(D1 + 3 * (13 + a) + c) * P + id];
         }
         Geo<double> G;
-        geo_fill(z, G);
-        if (RS) {
-          // the pointwise pass of the same stage has formed the Ricci scalar
+        if constexpr (RSK) {
+          // the pointwise pass of the same stage has formed the Ricci scalar:
+          // only the metric and its inverse are needed here
+          G.g.xx = 1.0 + z.h[0]; G.g.xy = z.h[1]; G.g.xz = z.h[2];
+          G.g.yy = 1.0 + z.h[3]; G.g.yz = z.h[4]; G.g.zz = 1.0 + z.h[5];
+          G.gi = s3inv(G.g, (double *)nullptr);
           G.Rs = RS[id];
         } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) z.dGt[a][c] = DS[(size_t)(D1 + 3 * (8 + a) + c) * P + id];
 #pragma unroll
           for (int q = 0; q < 6; ++q) {
             z.ddW[q] = DS[(size_t)(D2 + q) * P + id];
 #pragma unroll
             for (int a = 0; a < 6; ++a) z.ddh[a][q] = DS[(size_t)(D2 + 6 * (1 + a) + q) * P + id];
-            z.ddal[q] = DS[(size_t)(D2 + 42 + q) * P + id];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) z.ddb[a][q] = DS[(size_t)(D2 + 6 * (8 + a) + q) * P + id];
           }
+          geo_fill(z, G);
           geo_ricci(z, G);
         }
         double pr[NPRIM];
@@ -615,21 +614,28 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__
           dA[a][2] = (45.0 * (u[L.px] - u[-L.px]) - 9.0 * (u[2 * L.px] - u[-2 * L.px]) + (u[3 * L.px] - u[-3 * L.px])) * i60z;
           dA[a][1] = (cyl && a != 5) ? (double)reinterpret_cast<const S *>(L.dy)[(size_t)(fAXX + a) * P + id] : 0.0;
         }
-        // v^k = d_j gt^jk = -gt^ja gt^kb d_j gt_ab (summed over j)
-        double v[3];
+        // v^k = d_j gt^jk = -gt^ja gt^kb d_j gt_ab = -gt^kb w_b, w_b = gt^ja d_j gt_ab
+        double wv[3];
 #pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {
+        for (int b = 0; b < 3; ++b) {
           double t = 0.0;
 #pragma unroll
           for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const double ga = gim[jj][a];
-#pragma unroll
-              for (int b = 0; b < 3; ++b) t -= ga * gim[kk][b] * z.dh[sp(a, b)][jj];
-            }
-          v[kk] = t;
+            for (int a = 0; a < 3; ++a) t += gim[jj][a] * z.dh[sp(a, b)][jj];
+          wv[b] = t;
         }
+        double v[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) v[kk] = -(gim[kk][0] * wv[0] + gim[kk][1] * wv[1] + gim[kk][2] * wv[2]);
+        // Gt^l_ji At^j_l = Gt_{m,ji} At^jm = (1/2) At^jm d_i gt_jm: of the three
+        // derivative terms of Gt_{m,ji} the two with d_j and d_m cancel against
+        // the symmetric At^jm
+        double Au[6];      // At^jm
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+          for (int m = jj; m < 3; ++m) Au[sp(jj, m)] = Am[jj][0] * gim[0][m] + Am[jj][1] * gim[1][m] + Am[jj][2] * gim[2][m];
         const double i3W = 3.0 / z.W;
         double M[3];
 #pragma unroll
@@ -641,10 +647,8 @@ __global__ void __launch_bounds__(DIAG_T) k_diag(Lev L, DevParams p, const S *__
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) s += gim[jj][kk] * dA[sp(kk, ii)][jj];
           }
-#pragma unroll
-          for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
-            for (int l = 0; l < 3; ++l) s -= G.G2[l][sp(jj, ii)] * Am[jj][l];
+          s -= 0.5 * (Au[0] * z.dh[0][ii] + Au[3] * z.dh[3][ii] + Au[5] * z.dh[5][ii]
+                      + 2.0 * (Au[1] * z.dh[1][ii] + Au[2] * z.dh[2][ii] + Au[4] * z.dh[4][ii]));
 #pragma unroll
           for (int l = 0; l < 3; ++l) s -= i3W * Am[l][ii] * z.dW[l];
           s -= (2.0 / 3.0) * (z.dKh[ii] + 2.0 * z.dTh[ii]) + 8.0 * PI * Si[ii];
@@ -809,11 +813,15 @@ int diag_blocks(const Lev &L) { return (L.nx * L.nz + DIAG_T - 1) / DIAG_T; }
 
 void launch_diag(const Lev &L, const DevParams &p, const double *DS, int covered, int evolve, double *partials, int slot,
                  cudaStream_t s, const double *RS) {
-  if (p.mixed & SACRA_MIXED_Z4C)
-    k_diag<float><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, reinterpret_cast<const float *>(DS), RS, covered, evolve,
-                                                    partials + (size_t)slot * DIAG_Q);
-  else
-    k_diag<double><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, RS, covered, evolve, partials + (size_t)slot * DIAG_Q);
+  double *out = partials + (size_t)slot * DIAG_Q;
+  const float *DSf = reinterpret_cast<const float *>(DS);
+  if (p.mixed & SACRA_MIXED_Z4C) {
+    if (RS) k_diag<float, true><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DSf, RS, covered, evolve, out);
+    else k_diag<float, false><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DSf, RS, covered, evolve, out);
+  } else {
+    if (RS) k_diag<double, true><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, RS, covered, evolve, out);
+    else k_diag<double, false><<<diag_blocks(L), DIAG_T, 0, s>>>(L, p, DS, RS, covered, evolve, out);
+  }
 }
 
 void launch_diag_final(const double *partials, int n, double *out, cudaStream_t s) {
