@@ -62,8 +62,8 @@ def build_opcount(force: bool = False) -> str:
 
 
 def opcount(cfg, level_data) -> dict:
-    """Algorithmic FLOPs of one RK stage, per face or cell and per phase,
-    counted on the oracle's plain restatement (see opcount.cpp)."""
+    """Floating-point operations of one RK stage, per face or cell and per
+    phase, counted on the oracle's plain restatement (see opcount.cpp)."""
     import json
     import tempfile
     exe = build_opcount()

@@ -4,8 +4,9 @@
 // by a scalar that counts floating-point operations (add/sub, mul, div, sqrt
 // and transcendental calls each count 1; comparisons and fabs count 0).  A
 // small TOV hierarchy is set up and one RK stage is taken phase by phase, so
-// that the count of each phase per cell (or face) is the algorithmic FLOP
-// count of the plain restatement of the method.  Output: one JSON object.
+// that the count of each phase per cell (or face) is the operation count of
+// the plain restatement of the method (its loops as written, zero-weight taps
+// included).  Output: one JSON object.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
