@@ -183,6 +183,57 @@ __device__ __forceinline__ void prolong_metric_body(const Lev &L, const Lev &Pa,
   U[(size_t)f * L.P + cid(L, j, k)] = u0 + s;
 }
 
+// Pairs of buffer cells (j, k), (j, k + 1) with k odd: lo is odd and N even
+// on refined levels, so the rows of both parts of the strip pair up.
+__device__ __forceinline__ bool buffer_pair(const Lev &L, int lo, int i, int &j, int &k) {
+  const int w = L.nx + GH;
+  const int prow = ((L.nz + GH) - lo + 1) / 2;   // row pairs (lo, lo+1) .. (N+7, N+8)
+  const int top = prow * w;
+  if (i < top) {
+    j = 1 + i % w;
+    k = lo + 2 * (i / w);
+    return true;
+  }
+  i -= top;
+  const int cols = w - lo + 1;
+  if (i >= cols * ((lo - 1) / 2)) return false;
+  j = lo + i % cols;
+  k = 1 + 2 * (i / cols);
+  return true;
+}
+
+// The metric prolongation of a pair of buffer cells one above the other: the
+// two children share their parent cell (same u0) and seven of their eight
+// parent rows, so the x-interpolations of the nine rows are formed once.
+// Each child's sums are those of prolong_metric_body, in the same order.
+__device__ __forceinline__ void prolong_metric_pair_body(const Lev &L, const Lev &Pa, double *__restrict__ U,
+                                                         const double *__restrict__ Up, int lo, int blk, int f) {
+  int j, k;
+  if (!buffer_pair(L, lo, blk * blockDim.x + threadIdx.x, j, k)) return;
+  const bool ex = (j & 1) == 0;
+  const int mx = ex ? j / 2 : (j + 1) / 2, mz = (k + 1) / 2;   // k odd: both children in parent row mz
+  const int bx = ex ? mx - 3 : mx - 4, bz = mz - 4;
+  const double *u = Up + (size_t)f * Pa.P;
+  const double u0 = u[cid(Pa, mx, mz)];
+  const int pb = cid(Pa, bx, bz);
+  double r[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) {
+    double q = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) q += (ex ? cW.prol[a] : cW.prol[7 - a]) * (u[pb + t * Pa.px + a] - u0);
+    r[t] = q;
+  }
+  double so = 0.0, se = 0.0;   // child k (odd: rows bz..bz+7), child k+1 (even: rows bz+1..bz+8)
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    so += cW.prol[7 - b] * r[b];
+    se += cW.prol[b] * r[b + 1];
+  }
+  U[(size_t)f * L.P + cid(L, j, k)] = u0 + so;
+  U[(size_t)f * L.P + cid(L, j, k + 1)] = u0 + se;
+}
+
 __global__ void k_prolong_metric(Lev L, Lev Pa, double *__restrict__ U, const double *__restrict__ Up, int lo) {
   prolong_metric_body(L, Pa, U, Up, lo, blockIdx.x, blockIdx.y);
 }
@@ -703,7 +754,7 @@ __global__ void kl_outer(const LItem *__restrict__ items, double tau, int metric
 }
 __global__ void kl_prolong_metric(const LItem *__restrict__ items, int full) {
   const LItem &it = items[blockIdx.z];
-  prolong_metric_body(it.L, it.Pa, it.B, it.A, full ? it.L.nx + 1 : it.L.nx + 5, blockIdx.x, blockIdx.y);
+  prolong_metric_pair_body(it.L, it.Pa, it.B, it.A, full ? it.L.nx + 1 : it.L.nx + 5, blockIdx.x, blockIdx.y);
 }
 __global__ void kl_prolong_hydro(const LItem *__restrict__ items, int full) {
   const LItem &it = items[blockIdx.z];
@@ -742,7 +793,7 @@ void launch_l_prolong(const LItem *items, int n, int max_nx, int full, cudaStrea
   if (n <= 0) return;
   const int lo = full ? max_nx + 1 : max_nx + 5, w = max_nx + GH;
   const int cells = ((max_nx + GH) - lo + 1) * w + (w - lo + 1) * (lo - 1);
-  kl_prolong_metric<<<dim3((cells + 127) / 128, NMET, n), 128, 0, s>>>(items, full);
+  kl_prolong_metric<<<dim3((cells / 2 + 127) / 128, NMET, n), 128, 0, s>>>(items, full);
   kl_prolong_hydro<<<dim3((cells + 127) / 128, 1, n), 128, 0, s>>>(items, full);
 }
 
